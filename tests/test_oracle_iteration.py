@@ -1,0 +1,151 @@
+"""Pins of the oracle's Algorithm 1 / 1' / 2 (Eqs. 18-20, 29-31) against what
+the paper and the mathematics fix: the first iterate is filtered
+backprojection followed by the TV prox (Sec. 2.2, Sec. 3), the beta = 0 limit
+is the weighted least-squares solution (closed form), the few-view limit
+with an injective A is x_true, the limit does not depend on D or tau (the
+Theorem of Sec. 2.2) and equals an independent Chambolle-Pock run on
+K = [A; grad], and the dual fixed point is mu* = W(Ax* - b) (Eq. 20)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+
+def explicit_A(N, V, B):
+    A = np.zeros((V * B, N * N))
+    for j in range(N * N):
+        e = np.zeros(N * N)
+        e[j] = 1.0
+        A[:, j] = O.project(e.reshape(N, N), V, B).ravel()
+    return A
+
+
+def lowdose_problem(N=8, V=16, B=13, seed=1, noise=0.01):
+    rng = np.random.default_rng(seed)
+    xt = 0.5 + 0.5 * rng.uniform(size=(N, N))
+    b = O.project(xt, V, B) + noise * rng.standard_normal((V, B))
+    w = rng.uniform(0.5, 2.0, (V, B))
+    return xt, b, w
+
+
+def test_first_iterate_is_fbp_then_tv():
+    # x^0 = mu^0 = 0: x^1 = prox_{tau g}(sigma tau A^T D b).
+    N, V, B = 16, 20, 23
+    xt = synth.ellipse_phantom(N, 3, 0)
+    b = O.project(xt, V, B)
+    tau, sigma, beta, ntv = 0.05, 0.8, 0.02, 7
+    for mode in (0, 1):
+        w = np.full((V, B), 2.0) if mode == 0 else None
+        taps = O.ramp_taps(mode, V, B, tau, 0.5 if mode == 0 else 0.0)
+        st, _ = O.pdtv(b, w, taps, mode, beta, tau, sigma, ntv, 1, N)
+        z = sigma * tau * O.backproject(O.filt(b, taps), N)
+        lam = tau * beta if mode == 0 else tau
+        x1, _, _ = O.tv_prox(z, lam, ntv)
+        np.testing.assert_allclose(st.x, x1, rtol=0, atol=1e-13)
+
+
+def test_beta_zero_limit_is_weighted_least_squares():
+    # Algorithm 1' converges to argmin_{x>=0} 1/2||Ax-b||_W^2; with a
+    # positive unconstrained solution that is (A^T W A)^-1 A^T W b.
+    N, V, B = 8, 16, 13
+    xt, b, w = lowdose_problem(N, V, B)
+    A = explicit_A(N, V, B)
+    xw = np.linalg.solve(A.T @ (w.ravel()[:, None] * A), A.T @ (w.ravel() * b.ravel()))
+    assert xw.min() > 0
+    kappa = float(np.mean(1 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    sigma, _, _ = O.step_sizes(0, N, V, B, taps, w, tau)
+    st, _ = O.pdtv(b, w, taps, 0, 0.0, tau, sigma, 10, 20000, N)
+    assert np.linalg.norm(st.x.ravel() - xw) / np.linalg.norm(xw) < 1e-10
+    # dual fixed point of Eq. 20: mu* = W (A x* - b)
+    r = w * (O.project(st.x, V, B) - b)
+    assert np.linalg.norm(st.mu - r) / np.linalg.norm(r) < 1e-8
+
+
+def test_fewview_injective_limit_is_truth():
+    # I > J and A injective: Ax = b, x >= 0 has the single point x_true.
+    N, V, B = 8, 16, 13
+    xt, _, _ = lowdose_problem(N, V, B)
+    b = O.project(xt, V, B)
+    tau = 0.01
+    taps = O.ramp_taps(1, V, B, tau)
+    sigma, _, _ = O.step_sizes(1, N, V, B, taps, None, tau)
+    st, tr = O.pdtv(b, None, taps, 1, 0.0, tau, sigma, 10, 3000, N, trace=True)
+    assert np.linalg.norm(st.x - xt) / np.linalg.norm(xt) < 1e-8
+    assert tr[-1] < 1e-7 and tr[-1] < tr[0]
+
+
+def test_tv_limit_matches_chambolle_pock_and_plain_iteration():
+    # Theorem (Sec. 2.2): the saddle point gives the minimiser of Eq. 1 for
+    # any non-singular D.  Three routes: ramp-preconditioned Algorithm 1,
+    # unpreconditioned (D = I) Algorithm 1, and Chambolle-Pock on K = [A; grad].
+    N, V, B = 16, 24, 23
+    rng = np.random.default_rng(5)
+    xt = synth.ellipse_phantom(N, 4, 3)
+    b = O.project(xt, V, B) + 0.3 * rng.standard_normal((V, B))
+    w = rng.uniform(0.5, 2.0, (V, B))
+    beta = 0.5
+    kappa = float(np.mean(1 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    sigma, _, _ = O.step_sizes(0, N, V, B, taps, w, tau)
+    st, tr = O.pdtv(b, w, taps, 0, beta, tau, sigma, 50, 1500, N, trace=True)
+    xa = st.x
+    # plain iteration, same problem
+    tau1 = 0.01
+    sig1, _, _ = O.step_sizes(0, N, V, B, np.ones(1), w, tau1)
+    st1, _ = O.pdtv(b, w, np.ones(1), 0, beta, tau1, sig1, 50, 4000, N)
+    assert np.linalg.norm(st1.x - xa) / np.linalg.norm(xa) < 1e-10
+    # Chambolle-Pock on [A; grad]
+    L = np.sqrt(O.power_norm(0, N, V, B, iters=300) + 8.0)
+    xr = O.cp_reference(b, w, 0, beta, 0.99 / (0.2 * L), 0.99 * 0.2 / L, 60000, N)
+    assert np.linalg.norm(xr - xa) / np.linalg.norm(xa) < 2e-5
+    fa, fr = O.cost(xa, b, w, beta), O.cost(xr, b, w, beta)
+    assert fa <= fr + 1e-9 * abs(fr)
+    assert tr[-1] == pytest.approx(fa, rel=1e-12)
+
+
+def test_limit_independent_of_tau():
+    N, V, B = 12, 18, 17
+    rng = np.random.default_rng(2)
+    xt = synth.ellipse_phantom(N, 3, 1)
+    b = O.project(xt, V, B) + 0.2 * rng.standard_normal((V, B))
+    w = rng.uniform(0.5, 2.0, (V, B))
+    beta = 0.3
+    kappa = float(np.mean(1 / w))
+    xs = []
+    for f in (0.25, 1.0, 4.0):
+        tau = f * O.default_tau(0, V, kappa)
+        taps = O.ramp_taps(0, V, B, tau, kappa)
+        sigma, _, _ = O.step_sizes(0, N, V, B, taps, w, tau)
+        st, _ = O.pdtv(b, w, taps, 0, beta, tau, sigma, 50, 3000, N)
+        xs.append(st.x)
+    for x in xs[1:]:
+        assert np.linalg.norm(x - xs[0]) / np.linalg.norm(xs[0]) < 1e-6
+
+
+def test_resume_is_bit_exact():
+    N, V, B = 10, 12, 15
+    xt, b, w = lowdose_problem(N, V, B, seed=4)
+    taps = O.ramp_taps(0, V, B, 0.05, 0.7)
+    st, _ = O.pdtv(b, w, taps, 0, 0.1, 0.05, 0.5, 5, 7, N)
+    sa, _ = O.pdtv(b, w, taps, 0, 0.1, 0.05, 0.5, 5, 3, N)
+    sa, _ = O.pdtv(b, w, taps, 0, 0.1, 0.05, 0.5, 5, 4, N, state=sa)
+    np.testing.assert_array_equal(sa.x, st.x)
+    np.testing.assert_array_equal(sa.mu, st.mu)
+
+
+def test_power_norm_matches_matrix_norm():
+    N, V, B = 8, 10, 13
+    A = explicit_A(N, V, B)
+    taps = O.ramp_taps(0, V, B, 0.1, 0.3)
+    D = np.array([[taps[B - 1 + (i - j)] for j in range(B)] for i in range(B)])
+    DD = np.kron(np.eye(V), D)
+    M = A.T @ DD @ A
+    assert O.power_norm(0, N, V, B, taps=taps, iters=500) == pytest.approx(np.linalg.norm(M, 2), rel=1e-6)
+    w = np.random.default_rng(0).uniform(0.5, 2.0, V * B)
+    Mw = np.diag(w ** -0.5) @ DD @ np.diag(w ** -0.5)
+    got = O.power_norm(1, N, V, B, taps=taps, w=w.reshape(V, B), iters=2000)
+    assert got == pytest.approx(np.linalg.norm(Mw, 2), rel=1e-6)
