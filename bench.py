@@ -1,0 +1,364 @@
+"""Benchmark: ramp-preconditioned PD-TV iterations/sec on the low-dose
+workload at scale (512 x 512 image of 20 random ellipses, 720 parallel views
+over 180 degrees, 736 bins, transmission Poisson I0 = 5e3 with statistical
+weights, beta = 0.005, 30 iterations of Algorithm 1 per solve).
+
+One step = one ct_pdtv_solve call: setup (kappa, tau, taps, power-method
+step sizes) and 30 iterations, all on the GPU.  value = iterations/sec over
+all ranks (each rank solves its own slice: independent replicas, weak
+scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference implementation
+of this project) on the same workload and metric, one PD iteration per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORK = dict(name="lowdose_512x512_v720_b736", n=512, views=720, bins=736, ellipses=20,
+            i0=5e3, beta=0.005, iters=30, tv_iters=10, power_iters=20)
+METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
+UNIT = "iterations/s"
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def phantom(seed):
+    return synth.ellipse_phantom(WORK["n"], WORK["ellipses"], seed) * (2.0 / WORK["n"])
+
+
+# ----------------------------------------------------------------------
+# clocks sampled while the timed region runs
+# ----------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        cmd = ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+               "--format=csv,noheader,nounits"]
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(cmd, capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------
+# algorithmic work of the dominant kernel (backprojection A^T)
+# ----------------------------------------------------------------------
+def joseph_nnz(n, v_count, b_count):
+    """Non-zeros of the Joseph system matrix (count of (ray, pixel) weights
+    that are non-zero), from the geometry definition in include/ctpd.h."""
+    h, hb = 0.5 * (n - 1), 0.5 * (b_count - 1)
+    steps = np.arange(n) - h
+    d = np.arange(b_count) - hb
+    nnz = 0
+    for v in range(v_count):
+        t = v * math.pi / v_count
+        c, s = math.cos(t), math.sin(t)
+        rows = (4 * v <= v_count) or (4 * v >= 3 * v_count)
+        a, m = (1 / c, -s / c) if rows else (1 / s, -c / s)
+        u = h + d[:, None] * a + steps[None, :] * m
+        i0 = np.floor(u)
+        f = u - i0
+        nnz += int((((i0 >= 0) & (i0 < n)) & (f < 1)).sum() + (((i0 + 1 >= 0) & (i0 + 1 < n)) & (f > 0)).sum())
+    return nnz
+
+
+# ----------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------
+def oracle_inputs(seed=0):
+    import oracle as O
+    x = phantom(seed)
+    b, w = synth.poisson_data(O.project(x, WORK["views"], WORK["bins"]), WORK["i0"], seed + 100)
+    kappa = float(np.mean(1.0 / w))
+    tau = O.default_tau(0, WORK["views"], kappa)
+    taps = O.ramp_taps(0, WORK["views"], WORK["bins"], tau, kappa)
+    return b, w, tau, taps
+
+
+def oracle_iterations(b, w, tau, taps, k, state=None):
+    import oracle as O
+    return O.pdtv(b, w, taps, 0, WORK["beta"], tau, 0.5, WORK["tv_iters"], k, WORK["n"], state=state)[0]
+
+
+def cpu_baseline(iters=2):
+    b, w, tau, taps = oracle_inputs()
+    t0 = time.perf_counter()
+    oracle_iterations(b, w, tau, taps, iters)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} iterations of Algorithm 1 at 512^2/720 views/736 bins, "
+                      f"FP64 C oracle, single thread, setup excluded ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    b, w, tau, taps = oracle_inputs()
+    st = None
+    for _ in range(args.warmup):
+        st = oracle_iterations(b, w, tau, taps, 1, st)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = oracle_iterations(b, w, tau, taps, 1, st)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORK["name"], "n": WORK["n"], "views": WORK["views"],
+                       "bins": WORK["bins"], "beta": WORK["beta"], "i0": WORK["i0"],
+                       "iters_per_step": 1, "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one Algorithm-1 iteration per step, FP64 C oracle, "
+                                       "single thread, setup excluded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1609_06041_gb300.build as pb
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        pb.build()
+    if world > 1:
+        dist.barrier()
+    pb.build()
+    import paper_1609_06041_gb300 as P
+
+    N, V, B = WORK["n"], WORK["views"], WORK["bins"]
+    g = P.Geometry(N, V, B)
+    # synthetic slice for this rank: phantom -> A (on the GPU) -> Poisson data
+    xt = torch.from_numpy(phantom(rank).astype(np.float32)).cuda()
+    p = P.ct_project(g, xt).cpu().numpy()
+    b_np, w_np = synth.poisson_data(p, WORK["i0"], rank + 100)
+    b = torch.from_numpy(b_np.astype(np.float32)).cuda()
+    w = torch.from_numpy(w_np.astype(np.float32)).cuda()
+    prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=WORK["iters"], tv_iters=WORK["tv_iters"],
+                       precond=1, power_iters=WORK["power_iters"], beta=WORK["beta"])
+    ws = P.workspace_for(g, prm)
+    x = torch.empty(N, N, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        P.ct_pdtv_solve(g, b, w, prm, x_out=x, workspace=ws, report=False)
+
+    for _ in range(max(args.warmup, 3)):
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, L2 flushed between them (untimed) ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = P.ct_kernel_launches()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            solve()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = P.ct_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    t_ms = sum(a.elapsed_time(c) for a, c in ev)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    iters_total = WORK["iters"] * args.steps * world
+    value = iters_total / (t_ms / 1e3)
+
+    # ---- breakdown: setup vs iterations (resume runs iterations only) ----
+    _, rep = P.ct_pdtv_solve(g, b, w, prm, x_out=x, workspace=ws, report=True)
+    prm_r = P.PDTVParams(**{**prm.__dict__, "resume": 1})
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    flush.fill_(1.0)
+    e0.record(stream)
+    for _ in range(reps):
+        P.ct_pdtv_solve(g, b, w, prm_r, x_out=x, workspace=ws, report=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / reps
+    step_ms = t_ms / args.steps
+
+    # ---- dominant kernel: A^T on this workload, CUDA events, same stream ----
+    mub = torch.randn(V, B, device="cuda")
+    img = torch.empty(N, N, device="cuda")
+    for _ in range(3):
+        P.ct_backproject(g, mub, img)
+    nrep = 50
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(nrep):
+        P.ct_backproject(g, mub, img)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    at_ms = k0.elapsed_time(k1) / nrep
+    fw0, fw1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fw0.record(stream)
+    for _ in range(nrep):
+        P.ct_project(g, img, mub)
+    fw1.record(stream)
+    torch.cuda.synchronize()
+    a_ms = fw0.elapsed_time(fw1) / nrep
+    nnz = joseph_nnz(N, V, B)
+    flops = 2.0 * nnz
+    achieved = flops / (at_ms / 1e3) / 1e12
+
+    # ---- end to end through the public API with host buffers ----
+    b_h = torch.from_numpy(b_np.astype(np.float32)).pin_memory()
+    w_h = torch.from_numpy(w_np.astype(np.float32)).pin_memory()
+    x_h = torch.empty(N, N).pin_memory()
+    b_d, w_d = torch.empty_like(b), torch.empty_like(w)
+
+    def e2e_step():
+        b_d.copy_(b_h, non_blocking=True)
+        w_d.copy_(w_h, non_blocking=True)
+        P.ct_pdtv_solve(g, b_d, w_d, prm, x_out=x, workspace=ws, report=False)
+        x_h.copy_(x, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ee[i][0].record(stream)
+        e2e_step()
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(c) for a, c in ee)
+    e2e_value = WORK["iters"] * args.steps * world / (e2e_ms / 1e3)
+
+    clocks = sampler.summary()
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORK["name"], "n": N, "views": V, "bins": B,
+                       "beta": WORK["beta"], "i0": WORK["i0"], "iters_per_step": WORK["iters"],
+                       "tv_iters": WORK["tv_iters"], "power_iters": WORK["power_iters"],
+                       "l2": "flushed between steps (512 MB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "breakdown_ms": {"solve": step_ms, "iterations_only": loop_ms,
+                             "setup": step_ms - loop_ms, "per_iteration": loop_ms / WORK["iters"],
+                             "A_launch": a_ms, "AT_launch": at_ms},
+            "loop_iterations_per_s": WORK["iters"] / (loop_ms / 1e3) * world,
+            "report": {k: rep[k] for k in ("tau", "sigma", "kappa", "norm_ADA", "norm_WDW")},
+            "roofline": {"kernel": "k_backproject (A^T)", "bound": "alu", "achieved": achieved,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": None, "algorithmic_flops": flops, "nnz": nnz,
+                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * V * B * 4, "d2h_bytes_per_step": N * N * 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * ctpd.h -- C ABI of libctpd.so: ramp-filter-preconditioned first-order
+ * primal-dual TV reconstruction for 2-D parallel-beam CT on one GB300 GPU
+ * (Kudo, Yamazaki, Nemoto, Takaki, arXiv 1609.06041).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Geometry (Sec. 2.1: "standard parallel-beam geometry", uniform samples of
+ * p(r, theta)).  Unit pixels and unit detector bins.
+ *   image     x[r*N + c], float32, row-major; pixel (r, c) has centre
+ *             (c - (N-1)/2, r - (N-1)/2).
+ *   sinogram  s[v*B + d], float32, view-major; bin d of view v is the line
+ *             x cos(t_v) + y sin(t_v) = d - (B-1)/2.
+ *   angles    t_v = v*pi/V by default (V views over 180 degrees, m = V in
+ *             Eq. 24 and Eq. 32).
+ *   batches   `batch` images / sinograms stored back to back; batch = 0 is
+ *             a no-op, 0 <= batch <= 65535.
+ * A (the system matrix of Eq. 1) is Joseph's ray-driven interpolation: a
+ * view with |cos t| >= |sin t| (default angles: 4v <= V or 4v >= 3V) steps
+ * along image rows, interpolating each row linearly at the ray's column and
+ * weighting by 1/|cos t|; other views step along columns with 1/|sin t|.
+ * ct_backproject applies exactly the transpose of the same weights.
+ *
+ * Memory.  Every float pointer argument is a DEVICE pointer owned by the
+ * caller (for example torch tensor storage), contiguous, 16-byte aligned;
+ * the library never frees it.  Host pointers are marked "host".  A
+ * geometry handle owns a few KB of device memory (per-view constants) on
+ * the device that was current at creation; use it on that device only.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Calls enqueue work and return without synchronising,
+ * except where stated.  Inputs must stay valid until the work completes.
+ *
+ * Errors.  Every entry point returns a ct_status and never aborts or
+ * throws.  CT_ERR_ARG: a bad size, NULL pointer, or unsupported option (no
+ * work enqueued).  CT_ERR_CUDA / CT_ERR_OOM: a CUDA call failed (the
+ * stream may hold partial work).  ct_last_error() gives a message for the
+ * calling thread.
+ */
+#ifndef CTPD_H
+#define CTPD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_ARG = 1,
+    CT_ERR_CUDA = 2,
+    CT_ERR_OOM = 3,
+    CT_ERR_TIMEOUT = 4,
+    CT_ERR_NONFINITE = 5
+} ct_status;
+
+enum { CT_LOWDOSE = 0, CT_FEWVIEW = 1 };
+
+typedef struct ct_geometry ct_geometry;
+
+/* Library version, e.g. "ctpd 0.1 sm_103a". */
+const char *ct_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ct_last_error(void);
+
+/* Kernels enqueued by this library so far (all threads), for launch
+ * accounting; never decreases. */
+unsigned long long ct_kernel_launches(void);
+
+/*
+ * Create a 2-D parallel-beam geometry (Sec. 2.1): N x N image, V views,
+ * B bins.  angles (host, V doubles, radians) may be NULL for t_v = v*pi/V.
+ * 1 <= N, V, B <= 8192.  On success *out receives a handle; destroy it with
+ * ct_geometry_destroy.  Allocates and fills a small device table on the
+ * current device (synchronous).
+ */
+ct_status ct_geometry_create(int n, int n_views, int n_bins,
+                             const double *angles, ct_geometry **out);
+void ct_geometry_destroy(ct_geometry *geom);
+
+/*
+ * Forward projection sino = A img (A of Eq. 1; Joseph interpolation).
+ * img: batch x N x N, sino: batch x V x B (overwritten).
+ */
+ct_status ct_project(const ct_geometry *geom, const float *img, float *sino,
+                     int batch, void *stream);
+
+/*
+ * Backprojection img = A^T sino (the A^T of Eq. 19), a pixel-driven gather
+ * that recomputes A's interpolation weights bit for bit; deterministic and
+ * free of atomics.  sino: batch x V x B, img: batch x N x N (overwritten).
+ */
+ct_status ct_backproject(const ct_geometry *geom, const float *sino, float *img,
+                         int batch, void *stream);
+
+/*
+ * Taps of the preconditioner D = F^-1 H F applied along the detector axis
+ * of every view: mode CT_LOWDOSE the smoothed ramp H = |w|/(2 m tau +
+ * kappa |w|) (Eq. 24), mode CT_FEWVIEW the ramp H = |w|/(2 m tau) (Eq. 32),
+ * m = V.  The discrete filter is the linear convolution over the detector
+ * with t[k] = (1/P) sum_j H(w_j) cos(2 pi j k / P), |k| <= B-1, on the
+ * period P = 2^ceil(log2(2B)), w_j = 2 pi min(j, P-j)/P.  taps (device,
+ * 2B-1 floats) receives t[-(B-1)] .. t[B-1] (centre at index B-1).
+ * tau > 0, kappa >= 0 (kappa ignored for CT_FEWVIEW).
+ */
+ct_status ct_ramp_taps(const ct_geometry *geom, int mode, double tau, double kappa,
+                       float *taps, void *stream);
+
+/*
+ * Per-view linear convolution out[v][d] = sum_e taps[half-1 + d - e] in[v][e]
+ * (the D of Eqs. 18-20 and 29-31), zero beyond the detector edges.
+ * taps: device, 2*half_len-1 floats centred at half_len-1, 1 <= half_len <= B.
+ * in, out: batch x V x B; in == out is not allowed.
+ */
+ct_status ct_ramp_filter(const ct_geometry *geom, const float *taps, int half_len,
+                         const float *in, float *out, int batch, void *stream);
+
+/* Parameters of ct_pdtv_solve (zero-initialise, then set what you need). */
+typedef struct {
+    int mode;         /* CT_LOWDOSE: Algorithm 1 (beta > 0) / 1' (beta = 0);
+                         CT_FEWVIEW: Algorithm 2 (beta ignored, Sec. 3)      */
+    int iters;        /* outer iterations to run (>= 0)                       */
+    int tv_iters;     /* inner projected-gradient steps of the TV prox (Eq. 17),
+                         0 -> 10; warm-started across outer iterations       */
+    int precond;      /* 1: ramp preconditioner D (Eq. 24 / Eq. 32);
+                         0: D = I (the unpreconditioned iteration)           */
+    int power_iters;  /* power-method iterations for sigma (0 -> 20)         */
+    int resume;       /* 1: continue from the state held in `workspace`       */
+    double beta;      /* TV weight of Eq. 1 (low-dose)                         */
+    double tau;       /* primal step; <= 0: low-dose pi*kappa/(2m) with
+                         kappa = mean(1/w) (Eq. 24), few-view 0.01            */
+    double sigma;     /* dual step; <= 0: rho * the bound of the Alg. 1 / Alg. 2
+                         box from power-method operator norms                 */
+    double rho;       /* safety factor for the automatic sigma (0 -> 0.95)    */
+} ct_pdtv_params;
+
+/* Scalars of a solve, copied to the host at the end when requested. */
+typedef struct {
+    double tau, sigma, kappa, lambda;  /* lambda = tau*beta (Alg. 1), tau (Alg. 2) */
+    double norm_ADA;   /* ||A^T D A|| = ||D^1/2 A A^T D^T/2||                    */
+    double norm_WDW;   /* ||W^-1/2 D W^-1/2|| = ||D^1/2 W^-1 D^T/2|| (low-dose)   */
+    int k;             /* iterations done in total (including resumed ones)      */
+} ct_pdtv_report;
+
+/* Device workspace (bytes) a solve with these parameters needs. */
+size_t ct_pdtv_workspace_bytes(const ct_geometry *geom, const ct_pdtv_params *params);
+
+/*
+ * Ramp-preconditioned primal-dual TV reconstruction: Algorithm 1 / 1'
+ * (low-dose, min_{x>=0} beta TV(x) + 1/2 ||Ax - b||_W^2, Eq. 1) or
+ * Algorithm 2 (few-view, min TV(x) s.t. Ax = b, x >= 0, Eq. 25), iteration
+ * for iteration as boxed in the paper:
+ *   Step 1  mu_bar = -sigma D b (k = 0), else 2 mu^k - mu^{k-1}
+ *           [- sigma D W^-1 (mu^k - mu^{k-1}) for Algorithm 1]
+ *   Step 2  x^{k+1} = prox_{tau g}(x^k - tau A^T mu_bar)
+ *   Step 3  mu^{k+1} = mu^k + sigma D (A x^{k+1} - b [- W^-1 mu^k])
+ * b: V x B line integrals.  w: V x B statistical weights W = diag(w), w > 0
+ * (CT_LOWDOSE; NULL for CT_FEWVIEW).  x_out: N x N, receives x^K (with
+ * params->resume it must hold the x of the resumed state).
+ * workspace: device memory of ct_pdtv_workspace_bytes(); it holds the whole
+ * iteration state (mu, mu_bar, TV dual field, scalars), so a later call
+ * with resume = 1 continues exactly.  workspace == NULL: the library
+ * allocates it stream-ordered and frees it at the end (no resume).
+ * report (host, may be NULL): filled after the stream has been synchronised
+ * (the only synchronising path of this call).
+ * The call enqueues only device work (no host round trip), so it can be
+ * captured into a CUDA graph when workspace and report are non-NULL / NULL.
+ */
+ct_status ct_pdtv_solve(const ct_geometry *geom, const float *b, const float *w,
+                        const ct_pdtv_params *params, float *x_out,
+                        void *workspace, ct_pdtv_report *report, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTPD_H */

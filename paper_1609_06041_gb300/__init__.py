@@ -1,0 +1,25 @@
+"""GB300-native ramp-preconditioned primal-dual TV reconstruction for CT
+(Kudo, Yamazaki, Nemoto, Takaki, arXiv 1609.06041).
+
+The compute path is libctpd.so (hand-written CUDA for sm_103a) behind the
+C ABI of include/ctpd.h; ``ctpd`` is its thin Python binding.
+"""
+from .ctpd import (  # noqa: F401
+    CT_FEWVIEW,
+    CT_LOWDOSE,
+    CTError,
+    Geometry,
+    PDTVParams,
+    ct_backproject,
+    ct_geometry_create,
+    ct_geometry_destroy,
+    ct_kernel_launches,
+    ct_last_error,
+    ct_pdtv_solve,
+    ct_pdtv_workspace_bytes,
+    ct_project,
+    ct_ramp_filter,
+    ct_ramp_taps,
+    ct_version,
+    workspace_for,
+)

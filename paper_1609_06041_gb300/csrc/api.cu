@@ -1,0 +1,347 @@
+// api.cu -- host side of the C ABI declared in include/ctpd.h: argument
+// checks, geometry tables, workspace layout and the solve loop of
+// Algorithm 1 / 1' / 2 (arXiv 1609.06041, Secs. 2.3 and 3.1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ctpd_internal.cuh"
+
+using namespace ctpd;
+
+std::atomic<unsigned long long> ctpd::g_launches{0};
+
+struct ct_geometry : public Geometry {};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ct_status fail(ct_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ct_status cuda_check(const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return CT_OK;
+    snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout of one solve (offsets in bytes, 256-aligned).
+struct Layout {
+    size_t scal, partials, taps, winv, mu, mubar, r, z, xT, p0, p1, total;
+};
+
+Layout layout(const Geometry *g)
+{
+    Layout L;
+    const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
+    size_t o = 0;
+    L.scal = o;     o += align256(sizeof(double) * S_COUNT);
+    L.partials = o; o += align256(sizeof(double) * dot_partials_doubles());
+    L.taps = o;     o += align256(sizeof(float) * (2 * (size_t)g->n_bins - 1));
+    L.winv = o;     o += align256(sizeof(float) * I);
+    L.mu = o;       o += align256(sizeof(float) * I);
+    L.mubar = o;    o += align256(sizeof(float) * I);
+    L.r = o;        o += align256(sizeof(float) * I);
+    L.z = o;        o += align256(sizeof(float) * J);
+    L.xT = o;       o += align256(sizeof(float) * J);
+    L.p0 = o;       o += align256(sizeof(float) * 2 * J);
+    L.p1 = o;       o += align256(sizeof(float) * 2 * J);
+    L.total = o;
+    return L;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *ct_version(void) { return "ctpd 0.1 sm_103a"; }
+
+const char *ct_last_error(void) { return g_err; }
+
+unsigned long long ct_kernel_launches(void) { return g_launches.load(); }
+
+ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angles,
+                             ct_geometry **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(CT_ERR_ARG, "ct_geometry_create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 8192 || n_views < 1 || n_views > 8192 || n_bins < 1 || n_bins > 8192)
+        return fail(CT_ERR_ARG, "ct_geometry_create: sizes must be in [1, 8192]");
+    ct_geometry *g = new (std::nothrow) ct_geometry();
+    if (!g) return fail(CT_ERR_OOM, "ct_geometry_create: out of host memory");
+    g->n = n;
+    g->n_views = n_views;
+    g->n_bins = n_bins;
+    g->n_fft = 1;
+    while (g->n_fft < 2 * n_bins) g->n_fft <<= 1;
+    cudaGetDevice(&g->device);
+    g->h_angles = new double[n_views];
+    ViewP *hv = new ViewP[n_views];
+    for (int v = 0; v < n_views; ++v) {
+        double t = angles ? angles[v] : (double)v * M_PI / (double)n_views;
+        double c = cos(t), s = sin(t);
+        if (angles && !isfinite(t)) {
+            delete[] hv;
+            ct_geometry_destroy(g);
+            return fail(CT_ERR_ARG, "ct_geometry_create: angle %d is not finite", v);
+        }
+        g->h_angles[v] = t;
+        int rows = angles ? (fabs(c) >= fabs(s)) : ((4 * v <= n_views) || (4 * v >= 3 * n_views));
+        ViewP &P = hv[v];
+        memset(&P, 0, sizeof(P));
+        P.rows = rows;
+        if (rows) {
+            P.a = (float)(1.0 / c);
+            P.m = (float)(-s / c);
+            P.scale = (float)(1.0 / fabs(c));
+            P.inv_a = (float)c;
+        } else {
+            P.a = (float)(1.0 / s);
+            P.m = (float)(-c / s);
+            P.scale = (float)(1.0 / fabs(s));
+            P.inv_a = (float)s;
+        }
+    }
+    cudaError_t e = cudaMalloc(&g->d_views, sizeof(ViewP) * n_views);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_views, hv, sizeof(ViewP) * n_views, cudaMemcpyHostToDevice);
+    delete[] hv;
+    if (e != cudaSuccess) {
+        snprintf(g_err, sizeof(g_err), "ct_geometry_create: %s", cudaGetErrorString(e));
+        ct_geometry_destroy(g);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
+    }
+    kernel_attrs_filter();
+    kernel_attrs_tv();
+    ct_status st = cuda_check("ct_geometry_create");
+    if (st != CT_OK) {
+        ct_geometry_destroy(g);
+        return st;
+    }
+    *out = g;
+    return CT_OK;
+}
+
+void ct_geometry_destroy(ct_geometry *g)
+{
+    if (!g) return;
+    if (g->d_views) cudaFree(g->d_views);
+    delete[] g->h_angles;
+    delete g;
+}
+
+ct_status ct_project(const ct_geometry *g, const float *img, float *sino, int batch, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || batch < 0 || batch > 65535) return fail(CT_ERR_ARG, "ct_project: bad argument");
+    if (batch == 0) return CT_OK;
+    if (!img || !sino) return fail(CT_ERR_ARG, "ct_project: NULL pointer");
+    if (!aligned16(img) || !aligned16(sino)) return fail(CT_ERR_ARG, "ct_project: pointers must be 16-byte aligned");
+    launch_project(g, img, nullptr, sino, 0, nullptr, nullptr, nullptr, batch, S(stream));
+    return cuda_check("ct_project");
+}
+
+ct_status ct_backproject(const ct_geometry *g, const float *sino, float *img, int batch, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || batch < 0 || batch > 65535) return fail(CT_ERR_ARG, "ct_backproject: bad argument");
+    if (batch == 0) return CT_OK;
+    if (!img || !sino) return fail(CT_ERR_ARG, "ct_backproject: NULL pointer");
+    if (!aligned16(img) || !aligned16(sino)) return fail(CT_ERR_ARG, "ct_backproject: pointers must be 16-byte aligned");
+    launch_backproject(g, sino, img, 0, nullptr, nullptr, batch, S(stream));
+    return cuda_check("ct_backproject");
+}
+
+ct_status ct_ramp_taps(const ct_geometry *g, int mode, double tau, double kappa, float *taps, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || !taps || (mode != CT_LOWDOSE && mode != CT_FEWVIEW) || !(tau > 0.0) ||
+        (mode == CT_LOWDOSE && !(kappa >= 0.0)))
+        return fail(CT_ERR_ARG, "ct_ramp_taps: bad argument");
+    launch_taps(g, mode, nullptr, tau, kappa, taps, S(stream));
+    return cuda_check("ct_ramp_taps");
+}
+
+ct_status ct_ramp_filter(const ct_geometry *g, const float *taps, int half_len, const float *in,
+                         float *out, int batch, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || half_len < 1 || half_len > g->n_bins || batch < 0 || batch > 65535)
+        return fail(CT_ERR_ARG, "ct_ramp_filter: bad argument");
+    if (batch == 0) return CT_OK;
+    if (!taps || !in || !out || in == out) return fail(CT_ERR_ARG, "ct_ramp_filter: bad pointer");
+    launch_filter(g, taps, half_len, in, out, nullptr, nullptr, 0, nullptr, batch, S(stream));
+    return cuda_check("ct_ramp_filter");
+}
+
+size_t ct_pdtv_workspace_bytes(const ct_geometry *g, const ct_pdtv_params *p)
+{
+    (void)p;
+    if (!g) return 0;
+    return layout(g).total;
+}
+
+ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
+                        const ct_pdtv_params *prm, float *x_out, void *workspace,
+                        ct_pdtv_report *report, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || !b || !prm || !x_out) return fail(CT_ERR_ARG, "ct_pdtv_solve: NULL argument");
+    const int mode = prm->mode;
+    if (mode != CT_LOWDOSE && mode != CT_FEWVIEW) return fail(CT_ERR_ARG, "ct_pdtv_solve: unknown mode");
+    if (mode == CT_LOWDOSE && !w) return fail(CT_ERR_ARG, "ct_pdtv_solve: low-dose needs weights w");
+    if (prm->iters < 0 || prm->tv_iters < 0 || prm->power_iters < 0)
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: negative iteration count");
+    if (mode == CT_LOWDOSE && !(prm->beta >= 0.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: beta must be >= 0");
+    if (prm->resume && !workspace) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
+    if (!aligned16(b) || !aligned16(x_out) || (w && !aligned16(w)) || (workspace && !aligned16(workspace)))
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: pointers must be 16-byte aligned");
+    const double rho = prm->rho > 0.0 ? prm->rho : 0.95;
+    if (!(rho < 1.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: rho must be in (0, 1)");
+    const int ntv = prm->tv_iters > 0 ? prm->tv_iters : 10;
+    const int npow = prm->power_iters > 0 ? prm->power_iters : 20;
+    cudaStream_t st = S(stream);
+    const Layout L = layout(g);
+    const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
+
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    if (!ws) {
+        cudaError_t e = cudaMallocAsync((void **)&ws, L.total, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CT_ERR_OOM, "ct_pdtv_solve: workspace allocation failed");
+        }
+        owned = true;
+    }
+    double *scal = (double *)(ws + L.scal);
+    double *partials = (double *)(ws + L.partials);
+    float *taps = (float *)(ws + L.taps);
+    float *winv = (float *)(ws + L.winv);
+    float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
+    float *z = (float *)(ws + L.z), *xT = (float *)(ws + L.xT);
+    float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};
+    const int half = prm->precond ? g->n_bins : 1;
+    const int lowdose = mode == CT_LOWDOSE;
+
+    long long k0 = 0;
+    if (prm->resume) {
+        double kd = 0.0;
+        cudaMemcpyAsync(&kd, scal + S_K, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        k0 = (long long)kd;
+    } else {
+        // ---- setup (Alg. 1 / Alg. 2 boxes): kappa, tau, D, sigma ----
+        cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
+        if (lowdose) {
+            launch_recip(w, winv, I, st);
+            launch_dot(winv, nullptr, I, scal, S_RED0, partials, st);
+            launch_scalars(scal, SC_KAPPA_FROM_SUM, (double)I, 0, 0, 0, st);
+        }
+        launch_scalars(scal, SC_TAU, prm->tau, (double)g->n_views, 0, mode, st);
+        if (prm->precond) launch_taps(g, mode, scal, 0.0, 0.0, taps, st);
+        else launch_fill(taps, 1.0f, 1, st);
+        if (!(prm->sigma > 0.0)) {
+            // ||A^T D A|| by the power method from the all-ones image
+            float *v = z, *u = xT;
+            launch_fill(v, 1.0f, J, st);
+            for (int it = 0; it < npow; ++it) {
+                launch_dot(v, v, J, scal, S_RED0, partials, st);
+                launch_normalize(v, v, J, scal, S_RED0, st);
+                launch_project(g, v, nullptr, r, 0, nullptr, nullptr, nullptr, 1, st);
+                launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
+                launch_backproject(g, mubar, u, 0, nullptr, nullptr, 1, st);
+                launch_dot(v, u, J, scal, S_RED0, partials, st);
+                launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NADA, st);
+                std::swap(v, u);
+            }
+            if (lowdose) {
+                // ||W^-1/2 D W^-1/2|| from the all-ones sinogram
+                float *sv = mu, *su = r, *sw = mubar;
+                launch_sqrt(winv, sw, I, st);
+                launch_fill(sv, 1.0f, I, st);
+                for (int it = 0; it < npow; ++it) {
+                    launch_dot(sv, sv, I, scal, S_RED0, partials, st);
+                    launch_normalize(sv, sv, I, scal, S_RED0, st);
+                    launch_filter(g, taps, half, sv, su, sw, sw, 0, nullptr, 1, st);
+                    launch_dot(sv, su, I, scal, S_RED0, partials, st);
+                    launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NWDW, st);
+                    std::swap(sv, su);
+                }
+            }
+        }
+        launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);
+        launch_scalars(scal, SC_LAMBDA, lowdose ? prm->beta : 0.0, 0, 0, mode, st);
+        // ---- x^0 = mu^0 = 0, p = 0; Step 1 at k = 0: mu_bar = -sigma D b ----
+        launch_fill(x_out, 0.0f, J, st);
+        launch_fill(xT, 0.0f, J, st);
+        launch_fill(pbuf[0], 0.0f, 2 * J, st);
+        launch_fill(pbuf[1], 0.0f, 2 * J, st);
+        launch_fill(mu, 0.0f, I, st);
+        launch_filter(g, taps, half, b, mubar, nullptr, nullptr, 1, scal, 1, st);
+    }
+    ct_status cs = cuda_check("ct_pdtv_solve setup");
+    if (cs != CT_OK) {
+        if (owned) cudaFreeAsync(ws, st);
+        return cs;
+    }
+
+    // ---- the iteration: Steps 2 and 3, with the next Step 1 fused ----
+    const int chunk = tv_max_steps();
+    const int chunks = ntv == 0 ? 1 : (ntv + chunk - 1) / chunk;
+    int cur = (int)((k0 * chunks) & 1);
+    for (int k = 0; k < prm->iters; ++k) {
+        // Step 2: z = x^k - tau A^T mu_bar ; x^{k+1} = prox_{tau g}(z)
+        launch_backproject(g, mubar, z, 1, x_out, scal, 1, st);
+        int left = ntv;
+        do {
+            int steps = std::min(left, chunk);
+            left -= steps;
+            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, xT, g->n, steps, left == 0, scal, st);
+            cur ^= 1;
+        } while (left > 0);
+        // Step 3 residual r = A x^{k+1} - b [- W^-1 mu^k]
+        launch_project(g, x_out, xT, r, lowdose ? 1 : 2, b, winv, mu, 1, st);
+        // Step 3 dual update and Step 1 of the next iteration
+        launch_dual_update(g, taps, half, r, mu, mubar, winv, lowdose, scal, st);
+    }
+    launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
+    cs = cuda_check("ct_pdtv_solve");
+    if (report && cs == CT_OK) {
+        double h[S_COUNT];
+        cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) cs = fail(CT_ERR_CUDA, "ct_pdtv_solve: %s", cudaGetErrorString(e));
+        report->tau = h[S_TAU];
+        report->sigma = h[S_SIGMA];
+        report->kappa = h[S_KAPPA];
+        report->lambda = h[S_LAMBDA];
+        report->norm_ADA = h[S_NADA];
+        report->norm_WDW = h[S_NWDW];
+        report->k = (int)h[S_K];
+    }
+    if (owned) cudaFreeAsync(ws, st);
+    return cs;
+}
+
+}  // extern "C"

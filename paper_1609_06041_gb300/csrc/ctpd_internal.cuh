@@ -1,0 +1,120 @@
+// ctpd_internal.cuh -- shared definitions of the CUDA path (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/ctpd.h"
+
+namespace ctpd {
+
+// Per-view constants of Joseph's projector, rounded once to float on the
+// host from double-precision trig.  With h = (N-1)/2, hb = (B-1)/2, a view
+// that steps along image rows crosses row r of ray d at the column
+//     u(d, r) = h + (d - hb) * a + (r - h) * m,   a = 1/cos t, m = -sin t/cos t,
+// and a column-stepping view crosses column c at the row
+//     u(d, c) = h + (d - hb) * a + (c - h) * m,   a = 1/sin t, m = -cos t/sin t.
+// Each step contributes the linear interpolation of the row (column) at u,
+// and the ray sum is scaled by 1/|cos t| (1/|sin t|).
+struct ViewP {
+    float a;       // d coefficient
+    float m;       // step coefficient
+    float scale;   // path length per step, |a|
+    float inv_a;   // 1/a (cos t or sin t), for the pixel->ray inverse map
+    int rows;      // 1: steps along rows; 0: along columns
+    int pad0, pad1, pad2;
+};
+
+struct Geometry {
+    int n, n_views, n_bins, device;
+    int n_fft;            // P = 2^ceil(log2(2B))
+    ViewP *d_views;       // device, n_views entries
+    double *h_angles;     // host copy
+};
+
+// The ray/step intersection coordinate.  Written with explicit round-to-
+// nearest intrinsics so that the forward projector and the backprojector,
+// which both call this function, compute bit-identical u (and hence
+// bit-identical interpolation weights): A^T is exactly the transpose of A.
+__device__ __forceinline__ float joseph_u(float dp, float a, float sp, float m, float h)
+{
+    return __fadd_rn(__fmaf_rn(dp, a, __fmul_rn(sp, m)), h);
+}
+
+// floor(u) and the fractional part; the left pixel gets weight 1-f, the
+// right pixel weight f.
+__device__ __forceinline__ void joseph_split(float u, int &i0, float &f)
+{
+    float fl = floorf(u);
+    i0 = (int)fl;
+    f = __fsub_rn(u, fl);
+}
+
+// Device scalar block at the start of a solve workspace (doubles).
+enum {
+    S_KAPPA = 0, S_TAU, S_SIGMA, S_LAMBDA, S_INV8LAM, S_NADA, S_NWDW, S_K,
+    S_RED0 = 16,   // reduction results
+    S_COUNT = 64
+};
+
+// Number of kernels this library has enqueued (all threads), for callers
+// that account for launches.
+extern std::atomic<unsigned long long> g_launches;
+inline void counted(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- kernels (defined in the k_*.cu files) ----
+// Forward projection; `mode`: 0 plain out = A x; 1 low-dose residual
+// out = A x - b - winv*mu; 2 few-view residual out = A x - b.
+void launch_project(const Geometry *g, const float *x, const float *xT, float *out,
+                    int mode, const float *b, const float *winv, const float *mu,
+                    int batch, cudaStream_t st);
+// Backprojection; mode 0: out = A^T y; mode 1: out = xin - tau*A^T y with
+// tau = (float)scal[S_TAU].
+void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
+                        const float *xin, const double *scal, int batch, cudaStream_t st);
+void launch_transpose(const float *x, float *xT, int n, int batch, cudaStream_t st);
+
+// Filter: out = post .* (D (pre .* in)) * (scal ? -sigma : 1); pre/post
+// may be NULL.  mode 0 plain, 1 "-sigma D in" (start of the iteration).
+void launch_filter(const Geometry *g, const float *taps, int half, const float *in,
+                   float *out, const float *pre, const float *post, int mode,
+                   const double *scal, int batch, cudaStream_t st);
+// Fused Step 3 + next Step 1 for one iteration, per view:
+//   mu' = mu + sigma D r;  mu_bar = 2 mu' - mu [- sigma D (winv .* (mu' - mu))].
+void launch_dual_update(const Geometry *g, const float *taps, int half, const float *r,
+                        float *mu, float *mu_bar, const float *winv, int lowdose,
+                        const double *scal, cudaStream_t st);
+void launch_taps(const Geometry *g, int mode, const double *scal, double tau, double kappa,
+                 float *taps, cudaStream_t st);
+
+// TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
+// dual field p = (px, py)), temporal blocking in shared memory.
+// Runs `steps` dual steps reading p_in and writing p_out; when final != 0
+// also writes x = max(0, z + lam div p) and its transpose xT.
+void launch_tv(const float *z, const float *p_in, float *p_out, float *x, float *xT,
+               int n, int steps, int final, const double *scal, cudaStream_t st);
+int tv_max_steps();
+
+// Small helpers
+void launch_fill(float *p, float v, size_t n, cudaStream_t st);
+void launch_recip(const float *w, float *winv, size_t n, cudaStream_t st);
+void launch_sqrt(const float *a, float *out, size_t n, cudaStream_t st);
+void launch_scale_by(const float *in, const float *s, int sqrt_s, float *out, size_t n, cudaStream_t st);
+// scal[slot] = sum(a .* b) (b may be NULL: sum(a)), deterministic two-pass.
+void launch_dot(const float *a, const float *b, size_t n, double *scal, int slot,
+                double *partials, cudaStream_t st);
+// out = in / sqrt(scal[slot])
+void launch_normalize(const float *in, float *out, size_t n, const double *scal, int slot,
+                      cudaStream_t st);
+// scalar program: set tau/sigma/lambda from norms and parameters
+void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0,
+                    cudaStream_t st);
+enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET };
+
+size_t dot_partials_doubles();
+void kernel_attrs_filter();
+void kernel_attrs_tv();
+
+}  // namespace ctpd

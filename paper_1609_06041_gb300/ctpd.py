@@ -1,0 +1,247 @@
+"""Thin Python binding of libctpd.so (include/ctpd.h), one function per C
+entry point with the same name.  Arguments are torch CUDA tensors; this
+module only checks shapes and passes raw device pointers and the current
+CUDA stream.  All arithmetic runs in the library's CUDA kernels; there is no
+CPU or PyTorch fallback: a missing library raises at import time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctpd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA extension first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+CT_OK, CT_ERR_ARG, CT_ERR_CUDA, CT_ERR_OOM, CT_ERR_TIMEOUT, CT_ERR_NONFINITE = range(6)
+CT_LOWDOSE, CT_FEWVIEW = 0, 1
+
+
+class ct_pdtv_params(ctypes.Structure):
+    _fields_ = [("mode", _i), ("iters", _i), ("tv_iters", _i), ("precond", _i),
+                ("power_iters", _i), ("resume", _i), ("beta", _d), ("tau", _d),
+                ("sigma", _d), ("rho", _d)]
+
+
+class ct_pdtv_report(ctypes.Structure):
+    _fields_ = [("tau", _d), ("sigma", _d), ("kappa", _d), ("lambda_", _d),
+                ("norm_ADA", _d), ("norm_WDW", _d), ("k", _i)]
+
+    def as_dict(self):
+        return {"tau": self.tau, "sigma": self.sigma, "kappa": self.kappa,
+                "lambda": self.lambda_, "norm_ADA": self.norm_ADA,
+                "norm_WDW": self.norm_WDW, "k": self.k}
+
+
+EXPORTS = {
+    "ct_version": ([], ctypes.c_char_p),
+    "ct_last_error": ([], ctypes.c_char_p),
+    "ct_kernel_launches": ([], ctypes.c_ulonglong),
+    "ct_geometry_create": ([_i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
+    "ct_geometry_destroy": ([_vp], None),
+    "ct_project": ([_vp, _vp, _vp, _i, _vp], _i),
+    "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
+    "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
+    "ct_ramp_filter": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
+    "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
+    "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
+                       ctypes.POINTER(ct_pdtv_report), _vp], _i),
+}
+for _name, (_args, _res) in EXPORTS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+class CTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status != CT_OK:
+        raise CTError(status, _lib.ct_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, name, shape_tail=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected (..., {shape_tail})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _batch(t, ndim_tail):
+    b = 1
+    for s in t.shape[:-ndim_tail]:
+        b *= s
+    return b
+
+
+def ct_version() -> str:
+    return _lib.ct_version().decode()
+
+
+def ct_last_error() -> str:
+    return _lib.ct_last_error().decode()
+
+
+def ct_kernel_launches() -> int:
+    return int(_lib.ct_kernel_launches())
+
+
+class Geometry:
+    """2-D parallel-beam geometry handle (ct_geometry_create / _destroy)."""
+
+    def __init__(self, n: int, n_views: int, n_bins: int, angles=None):
+        self.n, self.n_views, self.n_bins = int(n), int(n_views), int(n_bins)
+        self._h = ctypes.c_void_p()
+        arr = None
+        if angles is not None:
+            import numpy as np
+            a = np.ascontiguousarray(angles, dtype=np.float64)
+            if a.shape != (self.n_views,):
+                raise ValueError("angles must have n_views entries")
+            arr = a
+        self._angles = arr
+        ptr = None if arr is None else arr.ctypes.data_as(ctypes.c_void_p)
+        _check(_lib.ct_geometry_create(self.n, self.n_views, self.n_bins, ptr, ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.ct_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ct_geometry_create(n, n_views, n_bins, angles=None) -> Geometry:
+    return Geometry(n, n_views, n_bins, angles)
+
+
+def ct_geometry_destroy(g: Geometry) -> None:
+    g.close()
+
+
+def ct_project(g: Geometry, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """sino = A img (batched over leading dims)."""
+    pi = _dev(img, "img", (g.n, g.n))
+    if out is None:
+        out = torch.empty(*img.shape[:-2], g.n_views, g.n_bins, device=img.device, dtype=torch.float32)
+    po = _dev(out, "out", (g.n_views, g.n_bins))
+    _check(_lib.ct_project(g.handle, pi, po, _batch(img, 2), _stream()))
+    return out
+
+
+def ct_backproject(g: Geometry, sino: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """img = A^T sino (batched over leading dims)."""
+    ps = _dev(sino, "sino", (g.n_views, g.n_bins))
+    if out is None:
+        out = torch.empty(*sino.shape[:-2], g.n, g.n, device=sino.device, dtype=torch.float32)
+    po = _dev(out, "out", (g.n, g.n))
+    _check(_lib.ct_backproject(g.handle, ps, po, _batch(sino, 2), _stream()))
+    return out
+
+
+def ct_ramp_taps(g: Geometry, mode: int, tau: float, kappa: float = 0.0, out=None) -> torch.Tensor:
+    """Taps of D (Eq. 24 / Eq. 32), 2B-1 values centred at B-1."""
+    if out is None:
+        out = torch.empty(2 * g.n_bins - 1, device="cuda", dtype=torch.float32)
+    _check(_lib.ct_ramp_taps(g.handle, int(mode), float(tau), float(kappa), _dev(out, "taps"), _stream()))
+    return out
+
+
+def ct_ramp_filter(g: Geometry, taps: torch.Tensor, sino: torch.Tensor, out=None) -> torch.Tensor:
+    """Per-view linear convolution with centred taps (the D of Eqs. 18-20)."""
+    if taps.numel() % 2 != 1:
+        raise ValueError("taps must have an odd length 2*half-1")
+    half = (taps.numel() + 1) // 2
+    pt = _dev(taps, "taps")
+    ps = _dev(sino, "sino", (g.n_views, g.n_bins))
+    if out is None:
+        out = torch.empty_like(sino)
+    po = _dev(out, "out", (g.n_views, g.n_bins))
+    _check(_lib.ct_ramp_filter(g.handle, pt, half, ps, po, _batch(sino, 2), _stream()))
+    return out
+
+
+@dataclass
+class PDTVParams:
+    mode: int = CT_LOWDOSE
+    iters: int = 20
+    tv_iters: int = 10
+    precond: int = 1
+    power_iters: int = 20
+    resume: int = 0
+    beta: float = 0.0
+    tau: float = 0.0
+    sigma: float = 0.0
+    rho: float = 0.95
+
+    def to_c(self):
+        return ct_pdtv_params(int(self.mode), int(self.iters), int(self.tv_iters), int(self.precond),
+                              int(self.power_iters), int(self.resume), float(self.beta),
+                              float(self.tau), float(self.sigma), float(self.rho))
+
+
+def ct_pdtv_workspace_bytes(g: Geometry, params: PDTVParams) -> int:
+    p = params.to_c()
+    return int(_lib.ct_pdtv_workspace_bytes(g.handle, ctypes.byref(p)))
+
+
+def ct_pdtv_solve(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, params: PDTVParams,
+                  x_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                  report: bool = True):
+    """Algorithm 1 / 1' / 2.  Returns (x, report dict or None).
+    `workspace` (uint8 CUDA tensor of ct_pdtv_workspace_bytes) holds the
+    iteration state for params.resume."""
+    pb = _dev(b, "b", (g.n_views, g.n_bins))
+    pw = None if w is None else _dev(w, "w", (g.n_views, g.n_bins))
+    if x_out is None:
+        x_out = torch.empty(g.n, g.n, device=b.device, dtype=torch.float32)
+    px = _dev(x_out, "x_out", (g.n, g.n))
+    pws = None
+    if workspace is not None:
+        if not workspace.is_cuda or workspace.numel() * workspace.element_size() < ct_pdtv_workspace_bytes(g, params):
+            raise ValueError("workspace too small")
+        pws = ctypes.c_void_p(workspace.data_ptr())
+    p = params.to_c()
+    rep = ct_pdtv_report() if report else None
+    _check(_lib.ct_pdtv_solve(g.handle, pb, pw, ctypes.byref(p), px, pws,
+                              ctypes.byref(rep) if rep is not None else None, _stream()))
+    return x_out, (rep.as_dict() if rep is not None else None)
+
+
+def workspace_for(g: Geometry, params: PDTVParams, device="cuda") -> torch.Tensor:
+    n = ct_pdtv_workspace_bytes(g, params)
+    return torch.empty(n, dtype=torch.uint8, device=device)

@@ -1,0 +1,147 @@
+"""GPU parity of the whole iteration (Algorithm 1 / 1' / 2) against the FP64
+oracle run with the same tau, sigma, n_tv and taps: relative L2 <= 1e-3 on
+the image after the stated iterations (and on the dual variable)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_util import need_gpu, rel_l2, to_gpu, to_np, f32
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+
+
+def lowdose_case(N, V, B, seed, n_ell=10, i0=1e4):
+    x = synth.ellipse_phantom(N, n_ell, seed) * (2.0 / N)
+    b, w = synth.poisson_data(O.project(x, V, B), i0, seed + 100)
+    return x, f32(b), f32(w)
+
+
+def run_both(P, N, V, B, b, w, mode, beta, iters, ntv, tau, sigma, precond=1, kappa=None):
+    g = P.Geometry(N, V, B)
+    if precond:
+        kap = float(np.mean(1.0 / w)) if mode == 0 else 0.0
+        taps = O.ramp_taps(mode, V, B, tau, kap)
+    else:
+        taps = np.ones(1)
+    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=ntv, precond=precond, beta=beta,
+                       tau=tau, sigma=sigma)
+    ws = P.workspace_for(g, prm)
+    xg, rep = P.ct_pdtv_solve(g, to_gpu(b), None if w is None else to_gpu(w), prm, workspace=ws)
+    st, _ = O.pdtv(b, w, taps, mode, beta, tau, sigma, ntv, iters, N)
+    return to_np(xg), st, rep, ws, g
+
+
+def test_lowdose_64_parity():
+    # 64^2, 90 views, 95 bins, Poisson I0 = 1e4, beta = 0.01, 20 iterations.
+    P = need_gpu()
+    N, V, B = 64, 90, 95
+    x, b, w = lowdose_case(N, V, B, 0)
+    kappa = float(np.mean(1.0 / w))
+    tau = O.default_tau(0, V, kappa)
+    xg, st, rep, _, _ = run_both(P, N, V, B, b, w, 0, 0.01, 20, 10, tau, 0.5)
+    assert rel_l2(xg, st.x) <= TOL
+    assert rep["k"] == 20 and rep["tau"] == pytest.approx(tau) and rep["sigma"] == pytest.approx(0.5)
+    assert rep["kappa"] == pytest.approx(kappa, rel=1e-5)
+
+
+def test_lowdose_beta_zero_parity():
+    # Algorithm 1': the prox reduces to max(0, .)
+    P = need_gpu()
+    N, V, B = 48, 60, 70
+    x, b, w = lowdose_case(N, V, B, 3)
+    tau = O.default_tau(0, V, float(np.mean(1.0 / w)))
+    xg, st, _, _, _ = run_both(P, N, V, B, b, w, 0, 0.0, 15, 10, tau, 0.6)
+    assert rel_l2(xg, st.x) <= TOL
+
+
+def test_fewview_parity():
+    # noiseless few-view data, Algorithm 2
+    P = need_gpu()
+    N, V, B = 96, 16, 137
+    x = f32(synth.ellipse_phantom(N, 8, 4))
+    b = f32(O.project(x, V, B))
+    xg, st, rep, _, _ = run_both(P, N, V, B, b, None, 1, 0.0, 25, 10, 0.01, 0.9)
+    assert rel_l2(xg, st.x) <= TOL
+
+
+def test_plain_iteration_parity():
+    # D = I: the unpreconditioned iteration on the same problem
+    P = need_gpu()
+    N, V, B = 40, 30, 57
+    x = f32(synth.ellipse_phantom(N, 6, 9))
+    b = f32(O.project(x, V, B))
+    xg, st, _, _, _ = run_both(P, N, V, B, b, None, 1, 0.0, 30, 10, 0.01, 0.5, precond=0)
+    assert rel_l2(xg, st.x) <= TOL
+
+
+def test_many_tv_steps_chunked():
+    # n_tv larger than one launch's temporal-blocking depth
+    P = need_gpu()
+    N, V, B = 70, 40, 101
+    x, b, w = lowdose_case(N, V, B, 5)
+    tau = O.default_tau(0, V, float(np.mean(1.0 / w)))
+    xg, st, _, _, _ = run_both(P, N, V, B, b, w, 0, 0.05, 6, 53, tau, 0.5)
+    assert rel_l2(xg, st.x) <= TOL
+
+
+def test_resume_matches_single_run():
+    P = need_gpu()
+    N, V, B = 64, 90, 95
+    x, b, w = lowdose_case(N, V, B, 1)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=0, iters=12, beta=0.01, sigma=0.5)
+    ws = P.workspace_for(g, prm)
+    x_all, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm, workspace=ws)
+    prm5 = P.PDTVParams(mode=0, iters=5, beta=0.01, sigma=0.5)
+    ws2 = P.workspace_for(g, prm5)
+    xr, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm5, workspace=ws2)
+    prm7 = P.PDTVParams(mode=0, iters=7, beta=0.01, sigma=0.5, resume=1)
+    xr, rep = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm7, x_out=xr, workspace=ws2)
+    assert rep["k"] == 12
+    assert np.array_equal(to_np(x_all), to_np(xr))
+
+
+def test_auto_step_sizes_match_oracle():
+    # sigma from the power method (Alg. 1 box) on the GPU vs the oracle's
+    P = need_gpu()
+    N, V, B = 64, 90, 95
+    x, b, w = lowdose_case(N, V, B, 2)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=0, iters=1, beta=0.01, power_iters=40)
+    _, rep = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    kappa = float(np.mean(1.0 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    sigma, nada, nwdw = O.step_sizes(0, N, V, B, taps, w, tau, iters=40)
+    assert rep["norm_ADA"] == pytest.approx(nada, rel=1e-4)
+    assert rep["norm_WDW"] == pytest.approx(nwdw, rel=1e-4)
+    assert rep["sigma"] == pytest.approx(sigma, rel=1e-4)
+
+
+def test_solve_converges_on_gpu():
+    # long run: the few-view residual falls and the image approaches x_true
+    P = need_gpu()
+    N, V, B = 64, 32, 95
+    x = f32(synth.ellipse_phantom(N, 6, 11))
+    b = f32(O.project(x, V, B))
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=1, iters=300)
+    xg, rep = P.ct_pdtv_solve(g, to_gpu(b), None, prm)
+    xg = to_np(xg)
+    res = np.linalg.norm(O.project(xg, V, B) - b) / np.linalg.norm(b)
+    assert res < 1e-2
+    assert rel_l2(xg, x) < 0.2
+
+
+def test_full_size_two_iterations():
+    # 512^2, 720 views, 736 bins, I0 = 5e3, beta = 0.005: two iterations
+    # against the oracle (the oracle needs a few seconds per iteration).
+    P = need_gpu()
+    N, V, B = 512, 720, 736
+    x, b, w = lowdose_case(N, V, B, 0, n_ell=20, i0=5e3)
+    tau = O.default_tau(0, V, float(np.mean(1.0 / w)))
+    xg, st, _, _, _ = run_both(P, N, V, B, b, w, 0, 0.005, 2, 10, tau, 0.5)
+    assert rel_l2(xg, st.x) <= TOL
