@@ -8,8 +8,8 @@ torch = pytest.importorskip("torch")
 def need_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import paper_1609_06041_gb300.build as b
-    b.build()
+    from conftest import build_library
+    build_library()
     import paper_1609_06041_gb300 as P
     return P
 

@@ -21,8 +21,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib_path():
-    import paper_1609_06041_gb300.build as b
-    return b.build()
+    from conftest import build_library
+    return build_library()
 
 
 def test_library_exports_every_declared_symbol(lib_path):
