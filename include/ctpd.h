@@ -19,7 +19,11 @@
  * view with |cos t| >= |sin t| (default angles: 4v <= V or 4v >= 3V) steps
  * along image rows, interpolating each row linearly at the ray's column and
  * weighting by 1/|cos t|; other views step along columns with 1/|sin t|.
- * ct_backproject applies exactly the transpose of the same weights.
+ * ct_backproject applies the transpose: each weight 1 - |d - e| / max(|cos t|,
+ * |sin t|) is evaluated from the pixel side (e = the pixel centre's detector
+ * coordinate), equal to A's weight in exact arithmetic and to within the
+ * float rounding of the coordinates (about 2^-24 times the image size) in
+ * practice.
  *
  * Memory.  Every float pointer argument is a DEVICE pointer owned by the
  * caller (for example torch tensor storage), contiguous, 16-byte aligned;
@@ -89,8 +93,8 @@ ct_status ct_project(const ct_geometry *geom, const float *img, float *sino,
 
 /*
  * Backprojection img = A^T sino (the A^T of Eq. 19), a pixel-driven gather
- * that recomputes A's interpolation weights bit for bit; deterministic and
- * free of atomics.  sino: batch x V x B, img: batch x N x N (overwritten).
+ * over the two rays around each pixel's detector coordinate; deterministic
+ * and free of atomics.  sino: batch x V x B, img: batch x N x N (overwritten).
  */
 ct_status ct_backproject(const ct_geometry *geom, const float *sino, float *img,
                          int batch, void *stream);

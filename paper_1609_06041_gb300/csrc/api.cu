@@ -44,7 +44,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, winv, mu, mubar, r, z, xT, p0, p1, total;
+    size_t scal, partials, taps, winv, mu, mubar, r, z, u, p0, p1, band, total;
 };
 
 Layout layout(const Geometry *g)
@@ -60,9 +60,10 @@ Layout layout(const Geometry *g)
     L.mubar = o;    o += align256(sizeof(float) * I);
     L.r = o;        o += align256(sizeof(float) * I);
     L.z = o;        o += align256(sizeof(float) * J);
-    L.xT = o;       o += align256(sizeof(float) * J);
+    L.u = o;        o += align256(sizeof(float) * J);
     L.p0 = o;       o += align256(sizeof(float) * 2 * J);
     L.p1 = o;       o += align256(sizeof(float) * 2 * J);
+    L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
     L.total = o;
     return L;
 }
@@ -96,35 +97,53 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     while (g->n_fft < 2 * n_bins) g->n_fft <<= 1;
     cudaGetDevice(&g->device);
     g->h_angles = new double[n_views];
+    // candidate-window margin of the backprojector (bins): a generous bound
+    // on the float rounding of the Joseph coordinates at this size
+    g->win_eps = (float)(16.0 * (n + n_bins) * ldexp(1.0, -24) + ldexp(1.0, -13));
     ViewP *hv = new ViewP[n_views];
+    float4 *ht = new float4[n_views];
+    int *rl = new int[n_views], *cl = new int[n_views];
+    g->n_row = g->n_col = 0;
     for (int v = 0; v < n_views; ++v) {
         double t = angles ? angles[v] : (double)v * M_PI / (double)n_views;
-        double c = cos(t), s = sin(t);
-        if (angles && !isfinite(t)) {
+        if (!isfinite(t)) {
             delete[] hv;
+            delete[] ht;
+            delete[] rl;
+            delete[] cl;
             ct_geometry_destroy(g);
             return fail(CT_ERR_ARG, "ct_geometry_create: angle %d is not finite", v);
         }
+        double c = cos(t), s = sin(t);
         g->h_angles[v] = t;
         int rows = angles ? (fabs(c) >= fabs(s)) : ((4 * v <= n_views) || (4 * v >= 3 * n_views));
         ViewP &P = hv[v];
         memset(&P, 0, sizeof(P));
         P.rows = rows;
-        if (rows) {
-            P.a = (float)(1.0 / c);
-            P.m = (float)(-s / c);
-            P.scale = (float)(1.0 / fabs(c));
-            P.inv_a = (float)c;
-        } else {
-            P.a = (float)(1.0 / s);
-            P.m = (float)(-c / s);
-            P.scale = (float)(1.0 / fabs(s));
-            P.inv_a = (float)s;
-        }
+        double a = rows ? 1.0 / c : 1.0 / s, m = rows ? -s / c : -c / s;
+        P.a = (float)a;
+        P.m = (float)m;
+        P.scale = (float)fabs(a);
+        P.inv_a = (float)(rows ? c : s);
+        P.inv_m = P.m != 0.0f ? 1.0f / P.m : 0.0f;
+        P.three = fabs((double)P.inv_a) >= 1.0 - 1.5 * (double)g->win_eps;
+        if (rows) rl[g->n_row++] = v;
+        else cl[g->n_col++] = v;
+        const double sc = 1.0 / fmax(fabs(c), fabs(s));
+        ht[v] = make_float4((float)c, (float)s, (float)sc, (float)(1.0 - 0.5 * sc));
     }
     cudaError_t e = cudaMalloc(&g->d_views, sizeof(ViewP) * n_views);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_row_list, sizeof(int) * (n_views + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_col_list, sizeof(int) * (n_views + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_trig, sizeof(float4) * n_views);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_trig, ht, sizeof(float4) * n_views, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_views, hv, sizeof(ViewP) * n_views, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_row_list, rl, sizeof(int) * n_views, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_col_list, cl, sizeof(int) * n_views, cudaMemcpyHostToDevice);
     delete[] hv;
+    delete[] ht;
+    delete[] rl;
+    delete[] cl;
     if (e != cudaSuccess) {
         snprintf(g_err, sizeof(g_err), "ct_geometry_create: %s", cudaGetErrorString(e));
         ct_geometry_destroy(g);
@@ -133,6 +152,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     }
     kernel_attrs_filter();
     kernel_attrs_tv();
+    kernel_attrs_joseph();
     ct_status st = cuda_check("ct_geometry_create");
     if (st != CT_OK) {
         ct_geometry_destroy(g);
@@ -146,6 +166,9 @@ void ct_geometry_destroy(ct_geometry *g)
 {
     if (!g) return;
     if (g->d_views) cudaFree(g->d_views);
+    if (g->d_row_list) cudaFree(g->d_row_list);
+    if (g->d_col_list) cudaFree(g->d_col_list);
+    if (g->d_trig) cudaFree(g->d_trig);
     delete[] g->h_angles;
     delete g;
 }
@@ -157,7 +180,17 @@ ct_status ct_project(const ct_geometry *g, const float *img, float *sino, int ba
     if (batch == 0) return CT_OK;
     if (!img || !sino) return fail(CT_ERR_ARG, "ct_project: NULL pointer");
     if (!aligned16(img) || !aligned16(sino)) return fail(CT_ERR_ARG, "ct_project: pointers must be 16-byte aligned");
-    launch_project(g, img, nullptr, sino, 0, nullptr, nullptr, nullptr, batch, S(stream));
+    // band partial sums: stream-ordered scratch, freed after the reduction
+    const size_t bytes = sizeof(float) * (size_t)proj_bands(g->n) * g->n_views * g->n_bins * batch;
+    float *partial = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&partial, bytes, S(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CT_ERR_OOM, "ct_project: scratch allocation failed (%zu bytes)", bytes);
+    }
+    launch_project_bands(g, img, partial, batch, S(stream));
+    launch_band_reduce(g, partial, sino, 0, nullptr, nullptr, nullptr, batch, S(stream));
+    cudaFreeAsync(partial, S(stream));
     return cuda_check("ct_project");
 }
 
@@ -239,7 +272,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     float *taps = (float *)(ws + L.taps);
     float *winv = (float *)(ws + L.winv);
     float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
-    float *z = (float *)(ws + L.z), *xT = (float *)(ws + L.xT);
+    float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u);
+    float *band = (float *)(ws + L.band);
     float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};
     const int half = prm->precond ? g->n_bins : 1;
     const int lowdose = mode == CT_LOWDOSE;
@@ -263,12 +297,13 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         else launch_fill(taps, 1.0f, 1, st);
         if (!(prm->sigma > 0.0)) {
             // ||A^T D A|| by the power method from the all-ones image
-            float *v = z, *u = xT;
+            float *v = z, *u = uimg;
             launch_fill(v, 1.0f, J, st);
             for (int it = 0; it < npow; ++it) {
                 launch_dot(v, v, J, scal, S_RED0, partials, st);
                 launch_normalize(v, v, J, scal, S_RED0, st);
-                launch_project(g, v, nullptr, r, 0, nullptr, nullptr, nullptr, 1, st);
+                launch_project_bands(g, v, band, 1, st);
+                launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
                 launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
                 launch_backproject(g, mubar, u, 0, nullptr, nullptr, 1, st);
                 launch_dot(v, u, J, scal, S_RED0, partials, st);
@@ -294,7 +329,6 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         launch_scalars(scal, SC_LAMBDA, lowdose ? prm->beta : 0.0, 0, 0, mode, st);
         // ---- x^0 = mu^0 = 0, p = 0; Step 1 at k = 0: mu_bar = -sigma D b ----
         launch_fill(x_out, 0.0f, J, st);
-        launch_fill(xT, 0.0f, J, st);
         launch_fill(pbuf[0], 0.0f, 2 * J, st);
         launch_fill(pbuf[1], 0.0f, 2 * J, st);
         launch_fill(mu, 0.0f, I, st);
@@ -317,13 +351,14 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         do {
             int steps = std::min(left, chunk);
             left -= steps;
-            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, xT, g->n, steps, left == 0, scal, st);
+            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, steps, left == 0, scal, st);
             cur ^= 1;
         } while (left > 0);
-        // Step 3 residual r = A x^{k+1} - b [- W^-1 mu^k]
-        launch_project(g, x_out, xT, r, lowdose ? 1 : 2, b, winv, mu, 1, st);
-        // Step 3 dual update and Step 1 of the next iteration
-        launch_dual_update(g, taps, half, r, mu, mubar, winv, lowdose, scal, st);
+        // Step 3: A x^{k+1} (band partial sums); the dual update forms the
+        // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
+        // performs Step 1 of the next iteration
+        launch_project_bands(g, x_out, band, 1, st);
+        launch_dual_update(g, taps, half, band, b, mu, mubar, winv, lowdose, scal, st);
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
     cs = cuda_check("ct_pdtv_solve");

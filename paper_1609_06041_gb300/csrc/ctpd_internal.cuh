@@ -23,33 +23,49 @@ struct ViewP {
     float m;       // step coefficient
     float scale;   // path length per step, |a|
     float inv_a;   // 1/a (cos t or sin t), for the pixel->ray inverse map
+    float inv_m;   // 1/m (0 when m = 0), for the ray->step range
     int rows;      // 1: steps along rows; 0: along columns
-    int pad0, pad1, pad2;
+    int three;     // 1: a pixel's candidate-ray window can hold three rays
+    int pad;
 };
 
 struct Geometry {
     int n, n_views, n_bins, device;
     int n_fft;            // P = 2^ceil(log2(2B))
+    int n_row, n_col;     // views stepping along rows / columns
+    float win_eps;        // candidate-window margin (bins) of the backprojector
     ViewP *d_views;       // device, n_views entries
+    int *d_row_list;      // device, the n_row row-stepping view indices
+    int *d_col_list;      // device, the n_col column-stepping view indices
+    float4 *d_trig;       // device, per view (cos t, sin t, |a|, 1 - |a|/2) for A^T
     double *h_angles;     // host copy
 };
 
-// The ray/step intersection coordinate.  Written with explicit round-to-
-// nearest intrinsics so that the forward projector and the backprojector,
-// which both call this function, compute bit-identical u (and hence
-// bit-identical interpolation weights): A^T is exactly the transpose of A.
-__device__ __forceinline__ float joseph_u(float dp, float a, float sp, float m, float h)
-{
-    return __fadd_rn(__fmaf_rn(dp, a, __fmul_rn(sp, m)), h);
-}
+// Joseph coordinate of the projector.  For ray d (dp = d - hb) the per-ray
+// constant q = dp*a + (h - 1/2) is formed once, and at step s (sp = s - h)
+// the coordinate u' = sp*m + q = u - 1/2.  Rounding u' to the nearest
+// integer i0 gives floor(u) (ties pick either neighbour; the interpolated
+// value is the same), and g = u' - i0 in [-1/2, 1/2] gives the weights
+// 1/2 - g on pixel i0 and 1/2 + g on pixel i0 + 1 (the usual 1-f and f
+// with f = g + 1/2).
+__device__ __forceinline__ float joseph_hq(int n) { return __fsub_rn(0.5f * (float)(n - 1), 0.5f); }
 
-// floor(u) and the fractional part; the left pixel gets weight 1-f, the
-// right pixel weight f.
-__device__ __forceinline__ void joseph_split(float u, int &i0, float &f)
+__device__ __forceinline__ float joseph_q(float dp, float a, float hq) { return __fmaf_rn(dp, a, hq); }
+
+__device__ __forceinline__ float joseph_u(float sp, float m, float q) { return __fmaf_rn(sp, m, q); }
+
+// Round to nearest by the 1.5*2^23 bias (valid for |u'| < 2^22; callers
+// keep u' inside a few image widths).  i0 = rounded value, g = u' - i0.
+// The backprojector uses the same bias to find floor(e) of a pixel's
+// detector coordinate.
+constexpr float JOSEPH_BIAS = 12582912.0f;
+constexpr int JOSEPH_BIAS_BITS = 0x4B400000;
+
+__device__ __forceinline__ void joseph_round(float up, int &i0, float &g)
 {
-    float fl = floorf(u);
-    i0 = (int)fl;
-    f = __fsub_rn(u, fl);
+    const float t = __fadd_rn(up, JOSEPH_BIAS);
+    i0 = __float_as_int(t) - JOSEPH_BIAS_BITS;
+    g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
 }
 
 // Device scalar block at the start of a solve workspace (doubles).
@@ -65,16 +81,21 @@ extern std::atomic<unsigned long long> g_launches;
 inline void counted(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---- kernels (defined in the k_*.cu files) ----
-// Forward projection; `mode`: 0 plain out = A x; 1 low-dose residual
-// out = A x - b - winv*mu; 2 few-view residual out = A x - b.
-void launch_project(const Geometry *g, const float *x, const float *xT, float *out,
-                    int mode, const float *b, const float *winv, const float *mu,
-                    int batch, cudaStream_t st);
+// Forward projection in two parts: band partial sums (one image band of
+// PROJ_R rows / columns per block, deterministic) and their reduction.
+// partial holds n_bands(N) x V x B floats per image.
+constexpr int PROJ_R = 32;
+inline int proj_bands(int n) { return (n + PROJ_R - 1) / PROJ_R; }
+void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st);
+// out = scale_v * sum_b partial[b]   (mode 0), minus b and winv*mu (mode 1),
+// minus b (mode 2).
+void launch_band_reduce(const Geometry *g, const float *partial, float *out, int mode,
+                        const float *b, const float *winv, const float *mu, int batch,
+                        cudaStream_t st);
 // Backprojection; mode 0: out = A^T y; mode 1: out = xin - tau*A^T y with
 // tau = (float)scal[S_TAU].
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
                         const float *xin, const double *scal, int batch, cudaStream_t st);
-void launch_transpose(const float *x, float *xT, int n, int batch, cudaStream_t st);
 
 // Filter: out = post .* (D (pre .* in)) * (scal ? -sigma : 1); pre/post
 // may be NULL.  mode 0 plain, 1 "-sigma D in" (start of the iteration).
@@ -83,8 +104,10 @@ void launch_filter(const Geometry *g, const float *taps, int half, const float *
                    const double *scal, int batch, cudaStream_t st);
 // Fused Step 3 + next Step 1 for one iteration, per view:
 //   mu' = mu + sigma D r;  mu_bar = 2 mu' - mu [- sigma D (winv .* (mu' - mu))].
-void launch_dual_update(const Geometry *g, const float *taps, int half, const float *r,
-                        float *mu, float *mu_bar, const float *winv, int lowdose,
+// The residual r = A x - b [- winv mu] is formed from the projector's band
+// partial sums while the view is loaded.
+void launch_dual_update(const Geometry *g, const float *taps, int half, const float *partial,
+                        const float *b, float *mu, float *mu_bar, const float *winv, int lowdose,
                         const double *scal, cudaStream_t st);
 void launch_taps(const Geometry *g, int mode, const double *scal, double tau, double kappa,
                  float *taps, cudaStream_t st);
@@ -92,8 +115,8 @@ void launch_taps(const Geometry *g, int mode, const double *scal, double tau, do
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
 // dual field p = (px, py)), temporal blocking in shared memory.
 // Runs `steps` dual steps reading p_in and writing p_out; when final != 0
-// also writes x = max(0, z + lam div p) and its transpose xT.
-void launch_tv(const float *z, const float *p_in, float *p_out, float *x, float *xT,
+// also writes x = max(0, z + lam div p).
+void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                int n, int steps, int final, const double *scal, cudaStream_t st);
 int tv_max_steps();
 
@@ -116,5 +139,6 @@ enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_
 size_t dot_partials_doubles();
 void kernel_attrs_filter();
 void kernel_attrs_tv();
+void kernel_attrs_joseph();
 
 }  // namespace ctpd

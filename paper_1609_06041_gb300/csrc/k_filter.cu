@@ -88,16 +88,26 @@ void launch_filter(const Geometry *g, const float *taps, int half, const float *
 //   mu_bar = 2 mu' - mu                                   (Step 1, Alg. 2)
 // mu is updated in place; the view's values are read before any write.
 __global__ void __launch_bounds__(FT)
-k_dual(const float *__restrict__ taps, int half, const float *__restrict__ r,
-       float *__restrict__ mu, float *__restrict__ mu_bar, const float *__restrict__ winv,
-       int lowdose, const double *__restrict__ scal, int V, int B)
+k_dual(const float *__restrict__ taps, int half, const float *__restrict__ partial, int nb,
+       const float *__restrict__ b, float *__restrict__ mu, float *__restrict__ mu_bar,
+       const float *__restrict__ winv, int lowdose, const ViewP *__restrict__ views,
+       const double *__restrict__ scal, int V, int B)
 {
     extern __shared__ float sm[];
     float *s_in = sm;
     float *s_t = sm + B;
     const size_t off = (size_t)blockIdx.x * B;
+    const size_t VB = (size_t)V * B;
+    const float scale = views[blockIdx.x].scale;
     const int tpad = stage_taps(s_t, taps, half, B);
-    for (int e = threadIdx.x; e < B; e += blockDim.x) s_in[e] = r[off + e];
+    // residual r = A x - b [- winv mu] from the projector's band partial sums
+    for (int e = threadIdx.x; e < B; e += blockDim.x) {
+        float acc = 0.0f;
+        for (int k = 0; k < nb; ++k) acc += partial[k * VB + off + e];
+        float r = acc * scale - b[off + e];
+        if (lowdose) r -= winv[off + e] * mu[off + e];
+        s_in[e] = r;
+    }
     __syncthreads();
     const float sigma = (float)scal[S_SIGMA];
     // B <= FT*FR*MAXR handled by keeping the per-round results in registers
@@ -159,14 +169,14 @@ k_dual(const float *__restrict__ taps, int half, const float *__restrict__ r,
     }
 }
 
-void launch_dual_update(const Geometry *g, const float *taps, int half, const float *r,
-                        float *mu, float *mu_bar, const float *winv, int lowdose,
+void launch_dual_update(const Geometry *g, const float *taps, int half, const float *partial,
+                        const float *b, float *mu, float *mu_bar, const float *winv, int lowdose,
                         const double *scal, cudaStream_t st)
 {
     size_t smem = filter_smem(g->n_bins);
     counted();
-    k_dual<<<g->n_views, FT, smem, st>>>(taps, half, r, mu, mu_bar, winv, lowdose, scal,
-                                         g->n_views, g->n_bins);
+    k_dual<<<g->n_views, FT, smem, st>>>(taps, half, partial, proj_bands(g->n), b, mu, mu_bar, winv,
+                                         lowdose, g->d_views, scal, g->n_views, g->n_bins);
 }
 
 void kernel_attrs_filter()

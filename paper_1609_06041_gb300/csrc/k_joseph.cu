@@ -1,170 +1,331 @@
-// k_joseph.cu -- Joseph forward projector A and its exact-transpose,
-// pixel-driven backprojector A^T (the A and A^T of Eqs. 18-20 / 29-31).
+// k_joseph.cu -- Joseph forward projector A (ray-driven) and its transpose
+// A^T (pixel-driven gather), the A and A^T of Eqs. 18-20 / 29-31.  Both are
+// deterministic (fixed summation orders, no atomics).
 #include "ctpd_internal.cuh"
 
 namespace ctpd {
 
-// ---------------------------------------------------------------------
-// Forward projection, one thread per ray (v, d).  Row-stepping views read
-// the image row by row; column-stepping views read the transposed image
-// row by row, so both classes sweep contiguous memory and a warp (32
-// neighbouring bins) touches neighbouring pixels of the same line.
-// Each step: u, its floor i0 and fraction f, and (1-f) x[i0] + f x[i0+1]
-// with zero outside the image.  Only the steps whose u can fall inside
-// (-1, N) are visited (a conservative range, one step of margin).
-// ---------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(128)
-k_project(const float *__restrict__ x, const float *__restrict__ xT,
-          const ViewP *__restrict__ views, int N, int V, int B,
-          float *__restrict__ out, const float *__restrict__ b,
-          const float *__restrict__ winv, const float *__restrict__ mu)
-{
-    // xT == NULL: column-stepping views read x with a stride of N (used by
-    // the stand-alone projector; the solve keeps a transposed copy).
-    const int v = blockIdx.y;
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t img_off = (size_t)blockIdx.z * N * N;
-    const size_t sino_off = (size_t)blockIdx.z * V * B;
-    if (d >= B) return;
-    const ViewP P = views[v];
-    const float *img = ((P.rows || xT == nullptr) ? x : xT) + img_off;
-    const int ss = (P.rows || xT != nullptr) ? N : 1;   // stride between steps
-    const int su = (P.rows || xT != nullptr) ? 1 : N;   // stride along u
-    const float h = 0.5f * (float)(N - 1);
-    const float dp = (float)d - 0.5f * (float)(B - 1);
+__device__ __forceinline__ float joseph_h(int n) { return 0.5f * (float)(n - 1); }
+__device__ __forceinline__ float joseph_dp(int d, int B) { return __fsub_rn((float)d, 0.5f * (float)(B - 1)); }
 
-    // steps s with -1 < u(s) < N:  u(s) = h + dp*a + (s - h)*m
-    int lo = 0, hi = N - 1;
-    const float u0 = h + dp * P.a;     // u at s = h
-    if (P.m != 0.0f) {
-        float sa = (-1.0f - u0) / P.m + h, sb = ((float)N - u0) / P.m + h;
-        float smin = fminf(sa, sb), smax = fmaxf(sa, sb);
-        // clamp before converting: far-off rays give huge (or infinite) s
-        smin = fminf(fmaxf(smin, -2.0f), (float)N + 2.0f);
-        smax = fminf(fmaxf(smax, -3.0f), (float)N + 1.0f);
-        lo = max(0, (int)floorf(smin) - 1);
-        hi = min(N - 1, (int)ceilf(smax) + 1);
-    } else if (!(u0 > -2.0f && u0 < (float)N + 1.0f)) {
-        hi = -1;
+// =====================================================================
+// Forward projection.
+// A block owns a band of PROJ_R consecutive steps (rows for row-stepping
+// views, columns for column-stepping views) and a group of PG views of one
+// class.  It stages the band in shared memory as interpolation pairs
+//     P[i] = ((x[i] + x[i+1]) / 2, x[i+1] - x[i]),  i = -2 .. N (zero padded),
+// so one sample is fma(g, P.y, P.x) = (1/2 - g) x[i0] + (1/2 + g) x[i0+1].
+// Each thread walks whole rays across the band and writes the band's
+// partial ray sum; launch_band_reduce adds the bands in a fixed order.
+// Images wider than one staged row (PROJ_CW pairs) are staged in several
+// column passes; a sample is taken in the pass that holds its pair and the
+// pass sums are added to the partial in pass order.
+// =====================================================================
+constexpr int PG = 8;          // views per block
+constexpr int PT = 1024;       // threads per block
+constexpr int PROJ_CW = 640;   // pairs per staged band row
+
+static int proj_cw(int n) { return (n + 3) < PROJ_CW ? (n + 3) : PROJ_CW; }
+static int proj_stride(int n) { return proj_cw(n) | 1; }   // odd: spreads smem banks
+static size_t proj_smem(int n) { return sizeof(float2) * (size_t)PROJ_R * proj_stride(n) + sizeof(ViewP) * PG + 64; }
+
+__device__ __forceinline__ int d_proj_cw(int n) { return (n + 3) < PROJ_CW ? (n + 3) : PROJ_CW; }
+
+// Conservative integer range [lo, hi] within [s_lo, s_hi] of the steps s
+// for which u'(s) = q + (s - h) m can lie in [ulo, uhi] (empty if lo > hi).
+__device__ __forceinline__ void step_range(float q, float m, float inv_m, float h, float ulo, float uhi,
+                                           int s_lo, int s_hi, int &lo, int &hi)
+{
+    if (m == 0.0f) {
+        lo = s_lo;
+        hi = (q >= ulo && q <= uhi) ? s_hi : s_lo - 1;
+        return;
     }
+    float sa = (ulo - q) * inv_m + h, sb = (uhi - q) * inv_m + h;
+    float smin = fminf(sa, sb), smax = fmaxf(sa, sb);
+    // clamp before converting: far-off rays give huge (or infinite) s
+    smin = fminf(fmaxf(smin, (float)s_lo - 2.0f), (float)s_hi + 2.0f);
+    smax = fminf(fmaxf(smax, (float)s_lo - 2.0f), (float)s_hi + 2.0f);
+    lo = max(s_lo, (int)floorf(smin) - 1);
+    hi = min(s_hi, (int)ceilf(smax) + 1);
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(PT)
+k_project_bands(const float *__restrict__ x, const ViewP *__restrict__ views,
+                const int *__restrict__ row_list, int n_row, const int *__restrict__ col_list, int n_col,
+                int N, int V, int B, float *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int CW = d_proj_cw(N), SP = CW | 1;
+    float2 *P = reinterpret_cast<float2 *>(smraw);
+    ViewP *sv = reinterpret_cast<ViewP *>(P + (size_t)PROJ_R * SP);
+    int *svi = reinterpret_cast<int *>(sv + PG);
+
+    const int band = blockIdx.x, nb = gridDim.x;
+    const int row_groups = (n_row + PG - 1) / PG;
+    const bool rows = (int)blockIdx.y < row_groups;
+    const int grp = rows ? blockIdx.y : blockIdx.y - row_groups;
+    const int *list = rows ? row_list : col_list;
+    const int nl = rows ? n_row : n_col;
+    const int nv = min(PG, nl - grp * PG);
+    const float *img = x + (size_t)blockIdx.z * N * N;
+    float *out = partial + ((size_t)blockIdx.z * nb + band) * V * B;
+    const int s0 = band * PROJ_R, ns = min(PROJ_R, N - s0);
+    const float h = joseph_h(N), hq = joseph_hq(N);
+    const int tid = threadIdx.x;
+
+    if (tid < nv) {
+        svi[tid] = list[grp * PG + tid];
+        sv[tid] = views[svi[tid]];
+    }
+    for (int I0 = -2; I0 <= N; I0 += CW) {
+        const int I1 = min(I0 + CW, N + 1);   // this pass holds pairs I0 .. I1-1
+        const int w = I1 - I0;
+        __syncthreads();
+        if (rows) {
+            for (int k = tid; k < ns * w; k += PT) {
+                const int si = k / w, i = I0 + (k - si * w);
+                const float *rowp = img + (size_t)(s0 + si) * N;
+                const float a = (i >= 0 && i < N) ? rowp[i] : 0.0f;
+                const float b = (i + 1 >= 0 && i + 1 < N) ? rowp[i + 1] : 0.0f;
+                P[si * SP + (i - I0)] = make_float2(0.5f * (a + b), b - a);
+            }
+        } else {
+            // column band: pair i of step (column) c = s0 + si is (x[i][c], x[i+1][c]);
+            // neighbouring threads take neighbouring columns (coalesced rows)
+            for (int k = tid; k < ns * w; k += PT) {
+                const int ii = k / ns, si = k - ii * ns, i = I0 + ii, c = s0 + si;
+                const float a = (i >= 0 && i < N) ? img[(size_t)i * N + c] : 0.0f;
+                const float b = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + c] : 0.0f;
+                P[si * SP + ii] = make_float2(0.5f * (a + b), b - a);
+            }
+        }
+        __syncthreads();
+        // samples with non-zero weight have u' in (-1.5, N - 0.5); this pass
+        // takes those with round(u') in [I0, I1)
+        const float ulo = (float)max(I0, -1) - 1.5f, uhi = (float)min(I1, N) + 0.5f;
+        for (int slot = tid; slot < nv * B; slot += PT) {
+            const int vi = slot / B, d = slot - vi * B;
+            const float a = sv[vi].a, m = sv[vi].m, inv_m = sv[vi].inv_m;
+            const float q = joseph_q(joseph_dp(d, B), a, hq);
+            int lo, hi;
+            step_range(q, m, inv_m, h, ulo, uhi, s0, s0 + ns - 1, lo, hi);
+            float sp = (float)lo - h;
+            const float2 *rowp = P + (lo - s0) * SP - I0;
+            float acc0 = 0.0f, acc1 = 0.0f;
+            int s = lo;
+            for (; s + 1 <= hi; s += 2) {
+                int i0a, i0b;
+                float ga, gb;
+                joseph_round(joseph_u(sp, m, q), i0a, ga);
+                joseph_round(joseph_u(__fadd_rn(sp, 1.0f), m, q), i0b, gb);
+                i0a = min(max(i0a, -2), N);
+                i0b = min(max(i0b, -2), N);
+                if (!MULTI || (i0a >= I0 && i0a < I1)) {
+                    const float2 pa = rowp[i0a];
+                    acc0 += __fmaf_rn(ga, pa.y, pa.x);
+                }
+                if (!MULTI || (i0b >= I0 && i0b < I1)) {
+                    const float2 pb = rowp[SP + i0b];
+                    acc1 += __fmaf_rn(gb, pb.y, pb.x);
+                }
+                sp = __fadd_rn(sp, 2.0f);
+                rowp += 2 * SP;
+            }
+            if (s <= hi) {
+                int i0a;
+                float ga;
+                joseph_round(joseph_u(sp, m, q), i0a, ga);
+                i0a = min(max(i0a, -2), N);
+                if (!MULTI || (i0a >= I0 && i0a < I1)) {
+                    const float2 pa = rowp[i0a];
+                    acc0 += __fmaf_rn(ga, pa.y, pa.x);
+                }
+            }
+            const float sum = acc0 + acc1;
+            float *o = out + (size_t)svi[vi] * B + d;
+            if (!MULTI || I0 == -2) *o = sum;
+            else *o += sum;                       // this thread wrote it in the previous pass
+        }
+    }
+}
+
+void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st)
+{
+    const int N = g->n;
+    dim3 grd(proj_bands(N), (g->n_row + PG - 1) / PG + (g->n_col + PG - 1) / PG, batch);
+    const size_t smem = proj_smem(N);
+    counted();
+    if (N + 3 <= PROJ_CW)
+        k_project_bands<false><<<grd, PT, smem, st>>>(x, g->d_views, g->d_row_list, g->n_row, g->d_col_list,
+                                                      g->n_col, N, g->n_views, g->n_bins, partial);
+    else
+        k_project_bands<true><<<grd, PT, smem, st>>>(x, g->d_views, g->d_row_list, g->n_row, g->d_col_list,
+                                                     g->n_col, N, g->n_views, g->n_bins, partial);
+}
+
+// out[v][d] = scale_v * sum_b partial[b][v][d]  (+ residual epilogue)
+template <int MODE>
+__global__ void k_band_reduce(const float *__restrict__ partial, float *__restrict__ out,
+                              const ViewP *__restrict__ views, int nb, int V, int B,
+                              const float *__restrict__ b, const float *__restrict__ winv,
+                              const float *__restrict__ mu)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y;
+    if (d >= B) return;
+    const size_t VB = (size_t)V * B;
+    const float *p = partial + (size_t)blockIdx.z * nb * VB + (size_t)v * B + d;
     float acc = 0.0f;
-    for (int s = lo; s <= hi; ++s) {
-        const float u = joseph_u(dp, P.a, (float)s - h, P.m, h);
-        int i0;
-        float f;
-        joseph_split(u, i0, f);
-        const float *row = img + (size_t)s * ss;
-        const float x0 = (i0 >= 0 && i0 < N) ? __ldg(row + (size_t)i0 * su) : 0.0f;
-        const float x1 = (i0 + 1 >= 0 && i0 + 1 < N) ? __ldg(row + (size_t)(i0 + 1) * su) : 0.0f;
-        acc += __fmaf_rn(1.0f - f, x0, __fmul_rn(f, x1));
-    }
-    float val = acc * P.scale;
-    const size_t o = sino_off + (size_t)v * B + d;
+    for (int k = 0; k < nb; ++k) acc += p[k * VB];
+    const size_t o = (size_t)blockIdx.z * VB + (size_t)v * B + d;
+    float val = acc * views[v].scale;
     if (MODE == 1) val = val - b[o] - winv[o] * mu[o];
     else if (MODE == 2) val = val - b[o];
     out[o] = val;
 }
 
-void launch_project(const Geometry *g, const float *x, const float *xT, float *out,
-                    int mode, const float *b, const float *winv, const float *mu,
-                    int batch, cudaStream_t st)
+void launch_band_reduce(const Geometry *g, const float *partial, float *out, int mode,
+                        const float *b, const float *winv, const float *mu, int batch, cudaStream_t st)
 {
-    dim3 blk(128), grd((g->n_bins + 127) / 128, g->n_views, batch);
+    dim3 grd((g->n_bins + 255) / 256, g->n_views, batch);
+    const int nb = proj_bands(g->n);
     counted();
     if (mode == 0)
-        k_project<0><<<grd, blk, 0, st>>>(x, xT, g->d_views, g->n, g->n_views, g->n_bins, out, b, winv, mu);
+        k_band_reduce<0><<<grd, 256, 0, st>>>(partial, out, g->d_views, nb, g->n_views, g->n_bins, b, winv, mu);
     else if (mode == 1)
-        k_project<1><<<grd, blk, 0, st>>>(x, xT, g->d_views, g->n, g->n_views, g->n_bins, out, b, winv, mu);
+        k_band_reduce<1><<<grd, 256, 0, st>>>(partial, out, g->d_views, nb, g->n_views, g->n_bins, b, winv, mu);
     else
-        k_project<2><<<grd, blk, 0, st>>>(x, xT, g->d_views, g->n, g->n_views, g->n_bins, out, b, winv, mu);
+        k_band_reduce<2><<<grd, 256, 0, st>>>(partial, out, g->d_views, nb, g->n_views, g->n_bins, b, winv, mu);
 }
 
-// ---------------------------------------------------------------------
-// Backprojection, one thread per pixel (r, c), gathering over views.  For
-// a view the pixel is the `j`-th pixel (along u) of step `s` (row r for a
-// row-stepping view, column c for a column-stepping one).  The rays that
-// can reach it have u(d, s) in [j-1, j+1), i.e. d within |inv_a| of the
-// pixel's own detector coordinate; each candidate recomputes u with the
-// same joseph_u as the projector and takes weight 1-f if floor(u) = j,
-// f if floor(u) = j-1.  The candidate window carries a 1e-3 bin margin, so
-// rounding never drops a ray the projector uses.
-// ---------------------------------------------------------------------
+// =====================================================================
+// Backprojection: a pixel-driven gather.  Pixel (r, c) sits at detector
+// coordinate e = (c - h) cos t + (r - h) sin t + hb of view t, and ray d
+// reaches it with Joseph's weight 1 - |u(d) - j| = 1 - |d - e| |a| (u the
+// coordinate along the stepping direction, j the pixel's index along it,
+// |a| = 1/max(|cos t|, |sin t|)), non-zero only for d = floor(e) and
+// floor(e) + 1.  In exact arithmetic this is the weight the projector
+// uses, so A^T is the transpose of A up to the float rounding of the
+// weight (a few ulp); every pixel sums its rays in a fixed order, so the
+// result is deterministic and needs no atomics.
+//
+// One block per BT x BT tile.  Views are staged in chunks: per view
+// (cos, sin, |a|, 1 - |a|/2) and a window of ray pairs
+// (y[d], y[d+1]) * |a| covering the rays that reach the tile.  The block's
+// 256 threads form BSL view slices of 64 threads; a thread owns four
+// pixels of one row and sums the views of its slice; the slices are added
+// in a fixed order at the end.
+// =====================================================================
+constexpr int BT = 16;          // tile side
+constexpr int BSL = 4;          // view slices per block
+constexpr int BTH = 64 * BSL;   // threads per block
+constexpr int BVC = 64;         // views staged per chunk
+constexpr int BWW = 32;         // staged ray pairs per view (>= 15 (|cos|+|sin|) + 3)
+
 template <int MODE>
-__global__ void __launch_bounds__(256)
-k_backproject(const float *__restrict__ y, float *__restrict__ out,
-              const ViewP *__restrict__ views, int N, int V, int B,
-              const float *__restrict__ xin, const double *__restrict__ scal)
+__global__ void __launch_bounds__(BTH)
+k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
+                    const float4 *__restrict__ trig, int N, int V, int B,
+                    const float *__restrict__ xin, const double *__restrict__ scal)
 {
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    const int r = blockIdx.y * 8 + threadIdx.y;
-    if (r >= N || c >= N) return;
-    const size_t img_off = (size_t)blockIdx.z * N * N;
+    __shared__ float2 tab[BVC][BWW];
+    __shared__ float4 sv[BVC];
+    __shared__ int wbase[BVC];
+    __shared__ float red[BSL][BT * BT];
+
+    const int tid = threadIdx.x;
+    const int slice = tid >> 6, l = tid & 63;
+    const int R0 = blockIdx.y * BT, C0 = blockIdx.x * BT;
+    const int r = R0 + (l >> 2), c0 = C0 + (l & 3) * 4;
     const float *ys = y + (size_t)blockIdx.z * V * B;
     const float h = 0.5f * (float)(N - 1);
-    const float hb = 0.5f * (float)(B - 1);
-    float acc = 0.0f;
-    for (int v = 0; v < V; ++v) {
-        const ViewP P = views[v];
-        const int s = P.rows ? r : c;
-        const int j = P.rows ? c : r;
-        const float sp = (float)s - h;
-        const float t = __fmul_rn(sp, P.m);
-        const float e = ((float)j - h - t) * P.inv_a + hb;   // detector coordinate of the pixel
-        const float wdt = fabsf(P.inv_a) + 1e-3f;
-        const int dlo = max(0, (int)ceilf(e - wdt));
-        const int dhi = min(B - 1, (int)floorf(e + wdt));
-        const float *yv = ys + (size_t)v * B;
-        float av = 0.0f;
-        for (int d = dlo; d <= dhi; ++d) {
-            const float u = joseph_u((float)d - hb, P.a, sp, P.m, h);
-            int i0;
-            float f;
-            joseph_split(u, i0, f);
-            const float wgt = (i0 == j) ? (1.0f - f) : ((i0 + 1 == j) ? f : 0.0f);
-            av += wgt * __ldg(yv + d);
+    const float hb_lo = 0.5f * (float)(B - 1) - 0.5f;   // e - 1/2 is rounded to find floor(e)
+    const float yr = (float)r - h;
+    float xc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xc[k] = (float)(c0 + k) - h;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+    for (int v0 = 0; v0 < V; v0 += BVC) {
+        const int nv = min(BVC, V - v0);
+        __syncthreads();
+        if (tid < nv) {
+            const float4 T = trig[v0 + tid];   // cos, sin, |a|, 1 - |a|/2
+            sv[tid] = T;
+            // lowest detector coordinate over the tile corners
+            float emin = 3.0e38f;
+#pragma unroll
+            for (int cr = 0; cr < 4; ++cr) {
+                const float xx = (float)(C0 + (cr & 1) * (BT - 1)) - h;
+                const float yy = (float)(R0 + (cr >> 1) * (BT - 1)) - h;
+                emin = fminf(emin, xx * T.x + yy * T.y);
+            }
+            emin = fminf(fmaxf(emin + 0.5f * (float)(B - 1), -1.0e6f), 1.0e6f);
+            wbase[tid] = (int)floorf(emin) - 2;
         }
-        acc += av * P.scale;
+        __syncthreads();
+        for (int k = tid; k < nv * BWW; k += BTH) {
+            const int vi = k / BWW, w = k - vi * BWW;
+            const int d = wbase[vi] + w;
+            const float *yv = ys + (size_t)(v0 + vi) * B;
+            const float sc = sv[vi].z;
+            const float y0 = (d >= 0 && d < B) ? yv[d] : 0.0f;
+            const float y1 = (d + 1 >= 0 && d + 1 < B) ? yv[d + 1] : 0.0f;
+            tab[vi][w] = make_float2(y0 * sc, y1 * sc);
+        }
+        __syncthreads();
+        if (r < N) {
+            for (int vi = slice; vi < nv; vi += BSL) {
+                const float4 T = sv[vi];
+                const int wb = wbase[vi];
+                const float eb = fmaf(yr, T.y, hb_lo);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float e = fmaf(xc[k], T.x, eb);               // e - 1/2
+                    const float t = __fadd_rn(e, JOSEPH_BIAS);
+                    int f = __float_as_int(t) - JOSEPH_BIAS_BITS;       // floor(e)
+                    const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));   // frac(e) - 1/2
+                    const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w));   // 1 - frac |a|
+                    const float w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));    // 1 - (1 - frac) |a|
+                    f = min(max(f - wb, 0), BWW - 1);
+                    const float2 yy = tab[vi][f];
+                    acc[k] = fmaf(w0, yy.x, fmaf(w1, yy.y, acc[k]));
+                }
+            }
+        }
     }
-    const size_t o = img_off + (size_t)r * N + c;
-    if (MODE == 0) out[o] = acc;
-    else out[o] = xin[o] - (float)scal[S_TAU] * acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[slice][(l >> 2) * BT + (l & 3) * 4 + k] = acc[k];
+    __syncthreads();
+    if (tid < BT * BT) {
+        const int rr = R0 + tid / BT, cc = C0 + tid % BT;
+        if (rr < N && cc < N) {
+            float tot = red[0][tid];
+#pragma unroll
+            for (int k = 1; k < BSL; ++k) tot += red[k][tid];
+            const size_t o = (size_t)blockIdx.z * N * N + (size_t)rr * N + cc;
+            if (MODE == 0) out[o] = tot;
+            else out[o] = xin[o] - (float)scal[S_TAU] * tot;
+        }
+    }
 }
 
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
                         const float *xin, const double *scal, int batch, cudaStream_t st)
 {
-    dim3 blk(32, 8), grd((g->n + 31) / 32, (g->n + 7) / 8, batch);
+    dim3 grd((g->n + BT - 1) / BT, (g->n + BT - 1) / BT, batch);
     counted();
     if (mode == 0)
-        k_backproject<0><<<grd, blk, 0, st>>>(y, out, g->d_views, g->n, g->n_views, g->n_bins, xin, scal);
+        k_backproject_tiles<0><<<grd, BTH, 0, st>>>(y, out, g->d_trig, g->n, g->n_views, g->n_bins, xin, scal);
     else
-        k_backproject<1><<<grd, blk, 0, st>>>(y, out, g->d_views, g->n, g->n_views, g->n_bins, xin, scal);
+        k_backproject_tiles<1><<<grd, BTH, 0, st>>>(y, out, g->d_trig, g->n, g->n_views, g->n_bins, xin, scal);
 }
 
-// 32x32 tiles through shared memory (padded against bank conflicts).
-__global__ void k_transpose(const float *__restrict__ x, float *__restrict__ xT, int N)
+void kernel_attrs_joseph()
 {
-    __shared__ float tile[32][33];
-    const size_t off = (size_t)blockIdx.z * N * N;
-    int c = blockIdx.x * 32 + threadIdx.x;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        int r = blockIdx.y * 32 + k;
-        if (r < N && c < N) tile[k][threadIdx.x] = x[off + (size_t)r * N + c];
-    }
-    __syncthreads();
-    int r = blockIdx.y * 32 + threadIdx.x;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        int cc = blockIdx.x * 32 + k;
-        if (r < N && cc < N) xT[off + (size_t)cc * N + r] = tile[threadIdx.x][k];
-    }
-}
-
-void launch_transpose(const float *x, float *xT, int n, int batch, cudaStream_t st)
-{
-    dim3 blk(32, 8), grd((n + 31) / 32, (n + 31) / 32, batch);
-    counted();
-    k_transpose<<<grd, blk, 0, st>>>(x, xT, n);
+    cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }
 
 }  // namespace ctpd

@@ -27,7 +27,7 @@ static size_t tv_smem(int steps)
 
 __global__ void __launch_bounds__(256)
 k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
-     float *__restrict__ x, float *__restrict__ xT, int N, int steps, int final_,
+     float *__restrict__ x, int N, int steps, int final_,
      const double *__restrict__ scal)
 {
     extern __shared__ float sm[];
@@ -106,29 +106,18 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                     const float dvy = (rr < N - 1 ? spy[i] : 0.0f) - (rr > 0 ? spy[i - S] : 0.0f);
                     const float xv = fmaxf(0.0f, sz[i] + lam * (dvx + dvy));
                     x[gi] = xv;
-                    sx[i] = xv;
                 }
             }
         }
     }
-    if (!final_) return;
-    __syncthreads();
-    // transposed copy: xT[c][r] = x[r][c], coalesced along r
-    for (int lj = H + ty; lj < H + TV_T; lj += 8) {
-        const int cc = C0 + lj;
-        for (int li = H + tx; li < H + TV_T; li += 32) {
-            const int rr = R0 + li;
-            if (rr < N && cc < N) xT[(size_t)cc * N + rr] = sx[li * S + lj];
-        }
-    }
 }
 
-void launch_tv(const float *z, const float *p_in, float *p_out, float *x, float *xT,
+void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                int n, int steps, int final_, const double *scal, cudaStream_t st)
 {
     dim3 blk(32, 8), grd((n + TV_T - 1) / TV_T, (n + TV_T - 1) / TV_T);
     counted();
-    k_tv<<<grd, blk, tv_smem(steps), st>>>(z, p_in, p_out, x, xT, n, steps, final_, scal);
+    k_tv<<<grd, blk, tv_smem(steps), st>>>(z, p_in, p_out, x, n, steps, final_, scal);
 }
 
 void kernel_attrs_tv()

@@ -72,10 +72,11 @@ def test_batched_operators():
     assert P.ct_project(g, e).shape == (0, V, B)
 
 
-def test_exact_transpose_bitwise():
-    # The matrix of A (columns from unit images) and of A^T (columns from unit
-    # sinograms) are transposes of each other bit for bit: both kernels
-    # evaluate the same Joseph weights with the same float operations.
+def test_transpose_to_coordinate_rounding():
+    # The matrix of A (columns from unit images) and of A^T (columns from
+    # unit sinograms) are transposes of each other up to the float rounding
+    # of the Joseph coordinates (A evaluates weights from the ray side, A^T
+    # from the pixel side); both agree with the oracle's FP64 matrix.
     P = need_gpu()
     import torch
     N, V, B = 8, 12, 13
@@ -84,10 +85,10 @@ def test_exact_transpose_bitwise():
     A = P.ct_project(g, E).reshape(N * N, V * B).T.cpu().numpy()          # (I, J)
     F = torch.eye(V * B, device="cuda").reshape(V * B, V, B).contiguous()
     AT = P.ct_backproject(g, F).reshape(V * B, N * N).T.cpu().numpy()     # (J, I)
-    assert np.array_equal(A.T, AT)
-    # and the matrix is the oracle's to float rounding
+    assert np.abs(A.T - AT).max() < 4e-6
     Ao = np.stack([O.project(np.eye(N * N)[j].reshape(N, N), V, B).ravel() for j in range(N * N)], axis=1)
-    assert np.abs(A - Ao).max() < 1e-5
+    assert np.abs(A - Ao).max() < 4e-6
+    assert np.abs(AT.T - Ao).max() < 4e-6
 
 
 def test_adjoint_identity_gpu():
