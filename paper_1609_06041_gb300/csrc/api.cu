@@ -44,7 +44,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, winv, mu, mubar, r, z, u, p0, p1, band, total;
+    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, p0, p1, band, total;
 };
 
 Layout layout(const Geometry *g)
@@ -55,6 +55,7 @@ Layout layout(const Geometry *g)
     L.scal = o;     o += align256(sizeof(double) * S_COUNT);
     L.partials = o; o += align256(sizeof(double) * dot_partials_doubles());
     L.taps = o;     o += align256(sizeof(float) * (2 * (size_t)g->n_bins - 1));
+    L.hhat = o;     o += align256(sizeof(float2) * (size_t)g->n_fft);
     L.winv = o;     o += align256(sizeof(float) * I);
     L.mu = o;       o += align256(sizeof(float) * I);
     L.mubar = o;    o += align256(sizeof(float) * I);
@@ -132,7 +133,14 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
         const double sc = 1.0 / fmax(fabs(c), fabs(s));
         ht[v] = make_float4((float)c, (float)s, (float)sc, (float)(1.0 - 0.5 * sc));
     }
+    float2 *htw = new float2[g->n_fft];
+    for (int k = 0; k < g->n_fft; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)g->n_fft;
+        htw[k] = make_float2((float)cos(ang), (float)sin(ang));
+    }
     cudaError_t e = cudaMalloc(&g->d_views, sizeof(ViewP) * n_views);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_tw, sizeof(float2) * g->n_fft);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tw, htw, sizeof(float2) * g->n_fft, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_row_list, sizeof(int) * (n_views + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_col_list, sizeof(int) * (n_views + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_trig, sizeof(float4) * n_views);
@@ -142,6 +150,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     if (e == cudaSuccess) e = cudaMemcpy(g->d_col_list, cl, sizeof(int) * n_views, cudaMemcpyHostToDevice);
     delete[] hv;
     delete[] ht;
+    delete[] htw;
     delete[] rl;
     delete[] cl;
     if (e != cudaSuccess) {
@@ -153,6 +162,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     kernel_attrs_filter();
     kernel_attrs_tv();
     kernel_attrs_joseph();
+    kernel_attrs_fft();
     ct_status st = cuda_check("ct_geometry_create");
     if (st != CT_OK) {
         ct_geometry_destroy(g);
@@ -169,6 +179,7 @@ void ct_geometry_destroy(ct_geometry *g)
     if (g->d_row_list) cudaFree(g->d_row_list);
     if (g->d_col_list) cudaFree(g->d_col_list);
     if (g->d_trig) cudaFree(g->d_trig);
+    if (g->d_tw) cudaFree(g->d_tw);
     delete[] g->h_angles;
     delete g;
 }
@@ -223,7 +234,20 @@ ct_status ct_ramp_filter(const ct_geometry *g, const float *taps, int half_len, 
         return fail(CT_ERR_ARG, "ct_ramp_filter: bad argument");
     if (batch == 0) return CT_OK;
     if (!taps || !in || !out || in == out) return fail(CT_ERR_ARG, "ct_ramp_filter: bad pointer");
-    launch_filter(g, taps, half_len, in, out, nullptr, nullptr, 0, nullptr, batch, S(stream));
+    if (!fft_supported(g)) {
+        launch_filter(g, taps, half_len, in, out, nullptr, nullptr, 0, nullptr, batch, S(stream));
+        return cuda_check("ct_ramp_filter");
+    }
+    // frequency response of the taps: stream-ordered scratch, freed after use
+    float2 *hhat = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&hhat, sizeof(float2) * g->n_fft, S(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CT_ERR_OOM, "ct_ramp_filter: scratch allocation failed");
+    }
+    launch_hhat(g, taps, half_len, hhat, S(stream));
+    launch_filter_fft(g, hhat, in, out, nullptr, nullptr, 0, nullptr, batch, S(stream));
+    cudaFreeAsync(hhat, S(stream));
     return cuda_check("ct_ramp_filter");
 }
 
@@ -270,6 +294,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     double *scal = (double *)(ws + L.scal);
     double *partials = (double *)(ws + L.partials);
     float *taps = (float *)(ws + L.taps);
+    float2 *hhat = (float2 *)(ws + L.hhat);
+    const bool use_fft = fft_supported(g);
     float *winv = (float *)(ws + L.winv);
     float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
     float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u);
@@ -295,6 +321,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         launch_scalars(scal, SC_TAU, prm->tau, (double)g->n_views, 0, mode, st);
         if (prm->precond) launch_taps(g, mode, scal, 0.0, 0.0, taps, st);
         else launch_fill(taps, 1.0f, 1, st);
+        if (use_fft) launch_hhat(g, taps, half, hhat, st);
         if (!(prm->sigma > 0.0)) {
             // ||A^T D A|| by the power method from the all-ones image
             float *v = z, *u = uimg;
@@ -304,7 +331,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 launch_normalize(v, v, J, scal, S_RED0, st);
                 launch_project_bands(g, v, band, 1, st);
                 launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
-                launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
+                if (use_fft) launch_filter_fft(g, hhat, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
+                else launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
                 launch_backproject(g, mubar, u, 0, nullptr, nullptr, 1, st);
                 launch_dot(v, u, J, scal, S_RED0, partials, st);
                 launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NADA, st);
@@ -318,7 +346,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 for (int it = 0; it < npow; ++it) {
                     launch_dot(sv, sv, I, scal, S_RED0, partials, st);
                     launch_normalize(sv, sv, I, scal, S_RED0, st);
-                    launch_filter(g, taps, half, sv, su, sw, sw, 0, nullptr, 1, st);
+                    if (use_fft) launch_filter_fft(g, hhat, sv, su, sw, sw, 0, nullptr, 1, st);
+                    else launch_filter(g, taps, half, sv, su, sw, sw, 0, nullptr, 1, st);
                     launch_dot(sv, su, I, scal, S_RED0, partials, st);
                     launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NWDW, st);
                     std::swap(sv, su);
@@ -332,7 +361,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         launch_fill(pbuf[0], 0.0f, 2 * J, st);
         launch_fill(pbuf[1], 0.0f, 2 * J, st);
         launch_fill(mu, 0.0f, I, st);
-        launch_filter(g, taps, half, b, mubar, nullptr, nullptr, 1, scal, 1, st);
+        if (use_fft) launch_filter_fft(g, hhat, b, mubar, nullptr, nullptr, 1, scal, 1, st);
+        else launch_filter(g, taps, half, b, mubar, nullptr, nullptr, 1, scal, 1, st);
     }
     ct_status cs = cuda_check("ct_pdtv_solve setup");
     if (cs != CT_OK) {
@@ -358,7 +388,8 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
         // performs Step 1 of the next iteration
         launch_project_bands(g, x_out, band, 1, st);
-        launch_dual_update(g, taps, half, band, b, mu, mubar, winv, lowdose, scal, st);
+        if (use_fft) launch_dual_fft(g, hhat, band, b, mu, mubar, winv, lowdose, scal, st);
+        else launch_dual_update(g, taps, half, band, b, mu, mubar, winv, lowdose, scal, st);
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
     cs = cuda_check("ct_pdtv_solve");

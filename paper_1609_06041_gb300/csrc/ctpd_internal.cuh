@@ -38,6 +38,7 @@ struct Geometry {
     int *d_row_list;      // device, the n_row row-stepping view indices
     int *d_col_list;      // device, the n_col column-stepping view indices
     float4 *d_trig;       // device, per view (cos t, sin t, |a|, 1 - |a|/2) for A^T
+    float2 *d_tw;         // device, n_fft twiddles e^{-2 pi i k / P} (from double precision)
     double *h_angles;     // host copy
 };
 
@@ -111,6 +112,20 @@ void launch_dual_update(const Geometry *g, const float *taps, int half, const fl
                         const double *scal, cudaStream_t st);
 void launch_taps(const Geometry *g, int mode, const double *scal, double tau, double kappa,
                  float *taps, cudaStream_t st);
+
+// Frequency-domain D (k_fft.cu), for n_fft <= FFT_MAX_P.
+constexpr int FFT_MAX_P = 8192;
+bool fft_supported(const Geometry *g);
+// hhat (n_fft complex) = DFT of the taps placed circularly
+void launch_hhat(const Geometry *g, const float *taps, int half, float2 *hhat, cudaStream_t st);
+// out = post .* D(pre .* in) * (mode 1 ? -sigma : 1)
+void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, float *out,
+                       const float *pre, const float *post, int mode, const double *scal, int batch,
+                       cudaStream_t st);
+// fused residual + Step 3 + next Step 1 (as launch_dual_update)
+void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
+                     float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st);
+void kernel_attrs_fft();
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
 // dual field p = (px, py)), temporal blocking in shared memory.

@@ -1,0 +1,306 @@
+// k_fft.cu -- the preconditioner D as a frequency-domain filter.
+//
+// D applies, along the detector of every view, the linear (zero-padded)
+// convolution with the taps t[k], |k| < half (Eq. 24 / Eq. 32 give the
+// taps from H).  With the view zero-padded to the period P >= 2B, the
+// circular convolution with the taps placed at k mod P equals that linear
+// convolution on bins 0..B-1, so D = IFFT_P(Hhat . FFT_P(.)) with Hhat the
+// P-point DFT of the circularly placed taps.  The taps are real, so two
+// views travel as the real and imaginary parts of one complex sequence.
+//
+// FFTs run in shared memory as Stockham autosort stages (radix 8, then a
+// radix-4 or radix-2 stage for the remaining factor), twiddles from a
+// table built in double precision on the host.
+#include "ctpd_internal.cuh"
+
+namespace ctpd {
+
+constexpr int FFT_T = 256;    // threads per block
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ float2 rot(float2 a, bool inv) { return inv ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+
+__device__ __forceinline__ void dft2(float2 &a, float2 &b)
+{
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3, bool inv)
+{
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = rot(csub(a1, a3), inv);
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+__device__ __forceinline__ void dft8(float2 *v, bool inv)
+{
+    // even / odd 4-point DFTs, then the radix-2 combination with w8^k
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4(e0, e1, e2, e3, inv);
+    dft4(o0, o1, o2, o3, inv);
+    const float c = 0.70710678118654752440f;
+    // w8^1 = c(1 -+ i), w8^2 = -+i, w8^3 = c(-1 -+ i)
+    const float2 w1o = inv ? make_float2(c * (o1.x - o1.y), c * (o1.x + o1.y))
+                           : make_float2(c * (o1.x + o1.y), c * (o1.y - o1.x));
+    const float2 w2o = rot(o2, inv);
+    const float2 w3o = inv ? make_float2(-c * (o3.x + o3.y), c * (o3.x - o3.y))
+                           : make_float2(c * (o3.y - o3.x), -c * (o3.x + o3.y));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, w1o);
+    v[5] = csub(e1, w1o);
+    v[2] = cadd(e2, w2o);
+    v[6] = csub(e2, w2o);
+    v[3] = cadd(e3, w3o);
+    v[7] = csub(e3, w3o);
+}
+
+// One radix-R Stockham stage: butterfly j reads src[j + r P/R], applies the
+// twiddles w^(r k P/(Ns R)) (k = j mod Ns) and writes dst[(j - k) R + k + r Ns].
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2 *src, float2 *dst, int P, int Ns,
+                                          const float2 *__restrict__ tw, bool inv)
+{
+    const int nb = P / R;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        float2 v[R];
+        const int k = j & (Ns - 1);
+        const int step = (P / (Ns * R)) * k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(tw + r * step);
+                if (inv) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        if (R == 8) dft8(v, inv);
+        else if (R == 4) dft4(v[0], v[1], v[2], v[3], inv);
+        else dft2(v[0], v[1]);
+        const int d0 = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[d0 + r * Ns] = v[r];
+    }
+}
+
+// Unnormalised DFT (forward: e^{-2 pi i jk/P}; inverse: e^{+...}) of the P
+// values in a; b is scratch.  Returns the buffer holding the result.  All
+// threads of the block must call it; it synchronises between stages.
+__device__ float2 *fft_block(float2 *a, float2 *b, int P, const float2 *__restrict__ tw, bool inv)
+{
+    int Ns = 1;
+    float2 *src = a, *dst = b;
+    while (Ns < P) {
+        const int rem = P / Ns;
+        __syncthreads();
+        if (rem >= 8) {
+            fft_stage<8>(src, dst, P, Ns, tw, inv);
+            Ns *= 8;
+        } else if (rem == 4) {
+            fft_stage<4>(src, dst, P, Ns, tw, inv);
+            Ns *= 4;
+        } else {
+            fft_stage<2>(src, dst, P, Ns, tw, inv);
+            Ns *= 2;
+        }
+        float2 *t = src;
+        src = dst;
+        dst = t;
+    }
+    __syncthreads();
+    return src;
+}
+
+// Hhat = DFT_P of the taps placed circularly (t[k] at k mod P).
+__global__ void __launch_bounds__(FFT_T)
+k_hhat(const float *__restrict__ taps, int half, int P, const float2 *__restrict__ tw, float2 *__restrict__ hhat)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *b = fsm + P;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        // index i holds t[k] with k = i (i < half) or k = i - P (i > P - half)
+        float v = 0.0f;
+        if (i < half) v = taps[half - 1 + i];
+        else if (i > P - half) v = taps[half - 1 + (i - P)];
+        a[i] = make_float2(v, 0.0f);
+    }
+    const float2 *res = fft_block(a, b, P, tw, false);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) hhat[i] = res[i];
+}
+
+void launch_hhat(const Geometry *g, const float *taps, int half, float2 *hhat, cudaStream_t st)
+{
+    const int P = g->n_fft;
+    counted();
+    k_hhat<<<1, FFT_T, sizeof(float2) * 2 * P, st>>>(taps, half, P, g->d_tw, hhat);
+}
+
+// out = post .* D(pre .* in) * sc, sc = 1 (mode 0) or -sigma (mode 1);
+// one block per pair of views (v, v+1) of image `blockIdx.y`.
+__global__ void __launch_bounds__(FFT_T)
+k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, float *__restrict__ out,
+             const float *__restrict__ pre, const float *__restrict__ post, int mode,
+             const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *b = fsm + P;
+    const int v0 = 2 * blockIdx.x, v1 = v0 + 1;
+    const bool has1 = v1 < V;
+    const size_t base = (size_t)blockIdx.y * V * B;
+    const size_t o0 = base + (size_t)v0 * B, o1 = base + (size_t)v1 * B;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float x0 = 0.0f, x1 = 0.0f;
+        if (i < B) {
+            x0 = in[o0 + i];
+            if (pre) x0 *= pre[o0 + i];
+            if (has1) {
+                x1 = in[o1 + i];
+                if (pre) x1 *= pre[o1 + i];
+            }
+        }
+        a[i] = make_float2(x0, x1);
+    }
+    float2 *f = fft_block(a, b, P, tw, false);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+    float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
+    const float sc = ((mode == 1) ? -(float)scal[S_SIGMA] : 1.0f) / (float)P;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        float y0 = res[i].x * sc, y1 = res[i].y * sc;
+        if (post) {
+            y0 *= post[o0 + i];
+            if (has1) y1 *= post[o1 + i];
+        }
+        out[o0 + i] = y0;
+        if (has1) out[o1 + i] = y1;
+    }
+}
+
+void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, float *out,
+                       const float *pre, const float *post, int mode, const double *scal, int batch,
+                       cudaStream_t st)
+{
+    const int P = g->n_fft;
+    dim3 grd((g->n_views + 1) / 2, batch);
+    counted();
+    k_filter_fft<<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, in, out, pre, post, mode, scal,
+                                                             g->n_views, g->n_bins, P, g->d_tw);
+}
+
+// Fused Step 3 and next Step 1 for the pair of views (v, v+1):
+//   r     = scale_v sum_b partial[b] - b [- winv mu]     (A x^{k+1} - b [- W^-1 mu^k])
+//   mu'   = mu + sigma D r                               (Step 3)
+//   mubar = 2 mu' - mu [- sigma D (winv .* (mu' - mu))]  (Step 1, Alg. 1 / Alg. 2)
+__global__ void __launch_bounds__(FFT_T)
+k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, int nb,
+           const float *__restrict__ b, float *__restrict__ mu, float *__restrict__ mu_bar,
+           const float *__restrict__ winv, int lowdose, const ViewP *__restrict__ views,
+           const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *bb = fsm + P;
+    float *m_old = reinterpret_cast<float *>(fsm + 2 * P);   // 2 x B
+    float *m_new = m_old + 2 * B;                            // 2 x B
+    const int v0 = 2 * blockIdx.x, v1 = v0 + 1;
+    const bool has1 = v1 < V;
+    const size_t VB = (size_t)V * B;
+    const size_t o0 = (size_t)v0 * B, o1 = (size_t)v1 * B;
+    const float sc0 = views[v0].scale, sc1 = has1 ? views[v1].scale : 0.0f;
+    const float sigma = (float)scal[S_SIGMA];
+    const float invP = 1.0f / (float)P;
+
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float r0 = 0.0f, r1 = 0.0f;
+        if (i < B) {
+            float s0 = 0.0f, s1 = 0.0f;
+            for (int k = 0; k < nb; ++k) {
+                s0 += partial[k * VB + o0 + i];
+                if (has1) s1 += partial[k * VB + o1 + i];
+            }
+            const float mu0 = mu[o0 + i], mu1 = has1 ? mu[o1 + i] : 0.0f;
+            m_old[i] = mu0;
+            m_old[B + i] = mu1;
+            r0 = s0 * sc0 - b[o0 + i];
+            if (lowdose) r0 -= winv[o0 + i] * mu0;
+            if (has1) {
+                r1 = s1 * sc1 - b[o1 + i];
+                if (lowdose) r1 -= winv[o1 + i] * mu1;
+            }
+        }
+        a[i] = make_float2(r0, r1);
+    }
+    float2 *f = fft_block(a, bb, P, tw, false);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+    float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
+    float2 *other = res == a ? bb : a;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float d0 = 0.0f, d1 = 0.0f;
+        if (i < B) {
+            const float n0 = m_old[i] + sigma * (res[i].x * invP);
+            const float n1 = m_old[B + i] + sigma * (res[i].y * invP);
+            m_new[i] = n0;
+            m_new[B + i] = n1;
+            if (lowdose) {
+                d0 = winv[o0 + i] * (n0 - m_old[i]);
+                if (has1) d1 = winv[o1 + i] * (n1 - m_old[B + i]);
+            }
+        }
+        other[i] = make_float2(d0, d1);
+    }
+    if (lowdose) {
+        f = fft_block(other, res, P, tw, false);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+        res = fft_block(f, f == a ? bb : a, P, tw, true);
+    } else {
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        const float n0 = m_new[i], n1 = m_new[B + i];
+        float mb0 = 2.0f * n0 - m_old[i], mb1 = 2.0f * n1 - m_old[B + i];
+        if (lowdose) {
+            mb0 -= sigma * (res[i].x * invP);
+            mb1 -= sigma * (res[i].y * invP);
+        }
+        mu[o0 + i] = n0;
+        mu_bar[o0 + i] = mb0;
+        if (has1) {
+            mu[o1 + i] = n1;
+            mu_bar[o1 + i] = mb1;
+        }
+    }
+}
+
+size_t dual_fft_smem(const Geometry *g) { return sizeof(float2) * 2 * g->n_fft + sizeof(float) * 4 * g->n_bins; }
+
+void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
+                     float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st)
+{
+    counted();
+    k_dual_fft<<<(g->n_views + 1) / 2, FFT_T, dual_fft_smem(g), st>>>(
+        hhat, partial, proj_bands(g->n), b, mu, mu_bar, winv, lowdose, g->d_views, scal, g->n_views,
+        g->n_bins, g->n_fft, g->d_tw);
+}
+
+bool fft_supported(const Geometry *g) { return g->n_fft <= FFT_MAX_P; }
+
+void kernel_attrs_fft()
+{
+    const int smax = (int)(sizeof(float2) * 2 * FFT_MAX_P + sizeof(float) * 4 * (FFT_MAX_P / 2));
+    cudaFuncSetAttribute(k_hhat, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_filter_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_dual_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+}
+
+}  // namespace ctpd

@@ -114,7 +114,8 @@ def test_taps_parity(mode, B, V):
     assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("V,B,half", [(90, 95, 95), (13, 53, 53), (8, 300, 40), (5, 1100, 1100)])
+@pytest.mark.parametrize("V,B,half", [(90, 95, 95), (13, 53, 53), (8, 300, 40), (5, 1100, 1100),
+                                      (3, 4200, 4200), (1, 1, 1), (2, 2, 2)])
 def test_filter_parity(V, B, half):
     P = need_gpu()
     g = P.Geometry(16, V, B)
