@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORK = dict(name="lowdose_512x512_v720_b736", n=512, views=720, bins=736, ellipses=20,
-            i0=5e3, beta=0.005, iters=30, tv_iters=10, power_iters=20)
+            i0=5e3, beta=0.005, iters=30, tv_iters=10, norm_iters=16)
 METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
@@ -208,7 +208,7 @@ def run_ours(args):
     b = torch.from_numpy(b_np.astype(np.float32)).cuda()
     w = torch.from_numpy(w_np.astype(np.float32)).cuda()
     prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=WORK["iters"], tv_iters=WORK["tv_iters"],
-                       precond=1, power_iters=WORK["power_iters"], beta=WORK["beta"])
+                       precond=1, norm_iters=WORK["norm_iters"], beta=WORK["beta"])
     ws = P.workspace_for(g, prm)
     x = torch.empty(N, N, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
@@ -322,7 +322,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORK["name"], "n": N, "views": V, "bins": B,
                        "beta": WORK["beta"], "i0": WORK["i0"], "iters_per_step": WORK["iters"],
-                       "tv_iters": WORK["tv_iters"], "power_iters": WORK["power_iters"],
+                       "tv_iters": WORK["tv_iters"], "norm_iters": WORK["norm_iters"],
                        "l2": "flushed between steps (512 MB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "breakdown_ms": {"solve": step_ms, "iterations_only": loop_ms,
@@ -362,7 +362,7 @@ def run_ncu_case(args):
     b = torch.from_numpy(b_np.astype(np.float32)).cuda()
     w = torch.from_numpy(w_np.astype(np.float32)).cuda()
     prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=3, tv_iters=WORK["tv_iters"], precond=1,
-                       power_iters=2, beta=WORK["beta"])
+                       norm_iters=2, beta=WORK["beta"])
     x, rep = P.ct_pdtv_solve(g, b, w, prm)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": "solve", "report": rep}))

@@ -130,13 +130,14 @@ typedef struct {
                          0 -> 10; warm-started across outer iterations       */
     int precond;      /* 1: ramp preconditioner D (Eq. 24 / Eq. 32);
                          0: D = I (the unpreconditioned iteration)           */
-    int power_iters;  /* power-method iterations for sigma (0 -> 20)         */
+    int norm_iters;   /* Lanczos steps for the operator norms of the automatic
+                         sigma (0 -> 16, at most 64)                          */
     int resume;       /* 1: continue from the state held in `workspace`       */
     double beta;      /* TV weight of Eq. 1 (low-dose)                         */
     double tau;       /* primal step; <= 0: low-dose pi*kappa/(2m) with
                          kappa = mean(1/w) (Eq. 24), few-view 0.01            */
     double sigma;     /* dual step; <= 0: rho * the bound of the Alg. 1 / Alg. 2
-                         box from power-method operator norms                 */
+                         box from Lanczos estimates of the operator norms     */
     double rho;       /* safety factor for the automatic sigma (0 -> 0.95)    */
 } ct_pdtv_params;
 

@@ -44,7 +44,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, p0, p1, band, total;
+    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, total;
 };
 
 Layout layout(const Geometry *g)
@@ -62,6 +62,7 @@ Layout layout(const Geometry *g)
     L.r = o;        o += align256(sizeof(float) * I);
     L.z = o;        o += align256(sizeof(float) * J);
     L.u = o;        o += align256(sizeof(float) * J);
+    L.w3 = o;       o += align256(sizeof(float) * J);
     L.p0 = o;       o += align256(sizeof(float) * 2 * J);
     L.p1 = o;       o += align256(sizeof(float) * 2 * J);
     L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
@@ -70,6 +71,36 @@ Layout layout(const Geometry *g)
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// Largest eigenvalue of the symmetric positive semi-definite operator `op`
+// (n-vectors) by k Lanczos steps from the all-ones vector, into scal[slot]:
+//   w = op(q_j) - beta_{j-1} q_{j-1};  alpha_j = <w, q_j>;  w -= alpha_j q_j;
+//   beta_j = |w|;  q_{j+1} = w / beta_j,
+// then the largest eigenvalue of the tridiagonal (alpha, beta) (bisection,
+// double precision).  q, qp, w are n-vector buffers; the whole recurrence
+// stays on the device.
+template <class Op>
+void lanczos_norm(Op op, float *q, float *qp, float *w, size_t n, int k, double *scal, double *partials,
+                  int slot, cudaStream_t st)
+{
+    launch_fill(q, 1.0f, n, st);
+    launch_dot(q, q, n, scal, S_RED0, partials, st);
+    launch_normalize(q, q, n, scal, S_RED0, st);
+    for (int j = 0; j < k; ++j) {
+        op(q, w);
+        if (j > 0) launch_axpy_neg(w, qp, n, scal, S_LZ + 2 * j - 1, st);
+        launch_dot(w, q, n, scal, S_LZ + 2 * j, partials, st);
+        launch_axpy_neg(w, q, n, scal, S_LZ + 2 * j, st);
+        launch_dot(w, w, n, scal, S_RED0, partials, st);
+        launch_scalars(scal, SC_NORM_SQRT, (double)S_RED0, 0, 0, S_LZ + 2 * j + 1, st);
+        launch_normalize(w, w, n, scal, S_RED0, st);
+        float *t = qp;
+        qp = q;
+        q = w;
+        w = t;
+    }
+    launch_scalars(scal, SC_LANCZOS_MAX, (double)k, 0, 0, slot, st);
+}
 
 }  // namespace
 
@@ -267,7 +298,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const int mode = prm->mode;
     if (mode != CT_LOWDOSE && mode != CT_FEWVIEW) return fail(CT_ERR_ARG, "ct_pdtv_solve: unknown mode");
     if (mode == CT_LOWDOSE && !w) return fail(CT_ERR_ARG, "ct_pdtv_solve: low-dose needs weights w");
-    if (prm->iters < 0 || prm->tv_iters < 0 || prm->power_iters < 0)
+    if (prm->iters < 0 || prm->tv_iters < 0 || prm->norm_iters < 0)
         return fail(CT_ERR_ARG, "ct_pdtv_solve: negative iteration count");
     if (mode == CT_LOWDOSE && !(prm->beta >= 0.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: beta must be >= 0");
     if (prm->resume && !workspace) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
@@ -276,7 +307,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const double rho = prm->rho > 0.0 ? prm->rho : 0.95;
     if (!(rho < 1.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: rho must be in (0, 1)");
     const int ntv = prm->tv_iters > 0 ? prm->tv_iters : 10;
-    const int npow = prm->power_iters > 0 ? prm->power_iters : 20;
+    const int nlz = std::min(prm->norm_iters > 0 ? prm->norm_iters : 16, (int)LANCZOS_MAX);
     cudaStream_t st = S(stream);
     const Layout L = layout(g);
     const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
@@ -298,7 +329,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const bool use_fft = fft_supported(g);
     float *winv = (float *)(ws + L.winv);
     float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
-    float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u);
+    float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u), *w3img = (float *)(ws + L.w3);
     float *band = (float *)(ws + L.band);
     float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};
     const int half = prm->precond ? g->n_bins : 1;
@@ -323,35 +354,24 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         else launch_fill(taps, 1.0f, 1, st);
         if (use_fft) launch_hhat(g, taps, half, hhat, st);
         if (!(prm->sigma > 0.0)) {
-            // ||A^T D A|| by the power method from the all-ones image
-            float *v = z, *u = uimg;
-            launch_fill(v, 1.0f, J, st);
-            for (int it = 0; it < npow; ++it) {
-                launch_dot(v, v, J, scal, S_RED0, partials, st);
-                launch_normalize(v, v, J, scal, S_RED0, st);
+            // ||A^T D A|| by Lanczos on the image side
+            auto op_ada = [&](const float *v, float *out) {
                 launch_project_bands(g, v, band, 1, st);
                 launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
                 if (use_fft) launch_filter_fft(g, hhat, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
                 else launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
-                launch_backproject(g, mubar, u, 0, nullptr, nullptr, 1, st);
-                launch_dot(v, u, J, scal, S_RED0, partials, st);
-                launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NADA, st);
-                std::swap(v, u);
-            }
+                launch_backproject(g, mubar, out, 0, nullptr, nullptr, 1, st);
+            };
+            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, partials, S_NADA, st);
             if (lowdose) {
-                // ||W^-1/2 D W^-1/2|| from the all-ones sinogram
-                float *sv = mu, *su = r, *sw = mubar;
+                // ||W^-1/2 D W^-1/2|| by Lanczos on the sinogram side
+                float *sw = mubar;
                 launch_sqrt(winv, sw, I, st);
-                launch_fill(sv, 1.0f, I, st);
-                for (int it = 0; it < npow; ++it) {
-                    launch_dot(sv, sv, I, scal, S_RED0, partials, st);
-                    launch_normalize(sv, sv, I, scal, S_RED0, st);
-                    if (use_fft) launch_filter_fft(g, hhat, sv, su, sw, sw, 0, nullptr, 1, st);
-                    else launch_filter(g, taps, half, sv, su, sw, sw, 0, nullptr, 1, st);
-                    launch_dot(sv, su, I, scal, S_RED0, partials, st);
-                    launch_scalars(scal, SC_NORM_FROM_DOT, 0, 0, 0, S_NWDW, st);
-                    std::swap(sv, su);
-                }
+                auto op_wdw = [&](const float *v, float *out) {
+                    if (use_fft) launch_filter_fft(g, hhat, v, out, sw, sw, 0, nullptr, 1, st);
+                    else launch_filter(g, taps, half, v, out, sw, sw, 0, nullptr, 1, st);
+                };
+                lanczos_norm(op_wdw, mu, r, band, I, nlz, scal, partials, S_NWDW, st);
             }
         }
         launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);

@@ -73,8 +73,10 @@ __device__ __forceinline__ void joseph_round(float up, int &i0, float &g)
 enum {
     S_KAPPA = 0, S_TAU, S_SIGMA, S_LAMBDA, S_INV8LAM, S_NADA, S_NWDW, S_K,
     S_RED0 = 16,   // reduction results
-    S_COUNT = 64
+    S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1
+    S_COUNT = 32 + 2 * 64
 };
+constexpr int LANCZOS_MAX = 64;
 
 // Number of kernels this library has enqueued (all threads), for callers
 // that account for launches.
@@ -149,7 +151,10 @@ void launch_normalize(const float *in, float *out, size_t n, const double *scal,
 // scalar program: set tau/sigma/lambda from norms and parameters
 void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0,
                     cudaStream_t st);
-enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET };
+enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET, SC_COPY,
+       SC_LANCZOS_MAX, SC_NORM_SQRT };
+// w -= scal[slot] * q
+void launch_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot, cudaStream_t st);
 
 size_t dot_partials_doubles();
 void kernel_attrs_filter();

@@ -152,7 +152,53 @@ __global__ void k_scalars(double *s, int op, double a0, double a1, double a2, in
     case SC_SET:
         s[i0] = a0;
         break;
+    case SC_COPY:                       // s[i0] = s[(int)a0]
+        s[i0] = s[(int)a0];
+        break;
+    case SC_NORM_SQRT:                  // s[i0] = sqrt(s[(int)a0])
+        s[i0] = sqrt(s[(int)a0]);
+        break;
+    case SC_LANCZOS_MAX: {              // s[i0] = largest eigenvalue of the Lanczos
+        // tridiagonal T_k (k = a0): diagonal s[S_LZ + 2j], off-diagonal
+        // s[S_LZ + 2j + 1], by bisection on the Sturm count of T - x I.
+        const int k = (int)a0;
+        double lo = 0.0, hi = 0.0;
+        for (int j = 0; j < k; ++j) {   // Gershgorin bounds
+            const double al = s[S_LZ + 2 * j];
+            const double rad = (j > 0 ? fabs(s[S_LZ + 2 * j - 1]) : 0.0) + (j + 1 < k ? fabs(s[S_LZ + 2 * j + 1]) : 0.0);
+            lo = j == 0 ? al - rad : fmin(lo, al - rad);
+            hi = j == 0 ? al + rad : fmax(hi, al + rad);
+        }
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(fabs(hi), 1e-300); ++it) {
+            const double x = 0.5 * (lo + hi);
+            int below = 0;              // eigenvalues < x
+            double d = 1.0;
+            for (int j = 0; j < k; ++j) {
+                const double b = j > 0 ? s[S_LZ + 2 * j - 1] : 0.0;
+                d = (s[S_LZ + 2 * j] - x) - (j > 0 ? b * b / d : 0.0);
+                if (d == 0.0) d = -1e-300;
+                if (d < 0.0) ++below;
+            }
+            if (below == k) hi = x;     // all eigenvalues below x
+            else lo = x;
+        }
+        s[i0] = hi;
+        break;
     }
+    }
+}
+
+__global__ void k_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot)
+{
+    const float c = (float)scal[slot];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        w[i] = fmaf(-c, q[i], w[i]);
+}
+
+void launch_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot, cudaStream_t st)
+{
+    counted();
+    k_axpy_neg<<<grid_for(n, 256), 256, 0, st>>>(w, q, n, scal, slot);
 }
 
 void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0, cudaStream_t st)

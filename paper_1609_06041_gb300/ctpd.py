@@ -32,7 +32,7 @@ CT_LOWDOSE, CT_FEWVIEW = 0, 1
 
 class ct_pdtv_params(ctypes.Structure):
     _fields_ = [("mode", _i), ("iters", _i), ("tv_iters", _i), ("precond", _i),
-                ("power_iters", _i), ("resume", _i), ("beta", _d), ("tau", _d),
+                ("norm_iters", _i), ("resume", _i), ("beta", _d), ("tau", _d),
                 ("sigma", _d), ("rho", _d)]
 
 
@@ -201,7 +201,7 @@ class PDTVParams:
     iters: int = 20
     tv_iters: int = 10
     precond: int = 1
-    power_iters: int = 20
+    norm_iters: int = 20
     resume: int = 0
     beta: float = 0.0
     tau: float = 0.0
@@ -210,7 +210,7 @@ class PDTVParams:
 
     def to_c(self):
         return ct_pdtv_params(int(self.mode), int(self.iters), int(self.tv_iters), int(self.precond),
-                              int(self.power_iters), int(self.resume), float(self.beta),
+                              int(self.norm_iters), int(self.resume), float(self.beta),
                               float(self.tau), float(self.sigma), float(self.rho))
 
 
