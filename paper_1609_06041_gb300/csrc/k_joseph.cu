@@ -21,7 +21,7 @@ __device__ __forceinline__ float joseph_dp(int d, int B) { return __fsub_rn((flo
 // column passes; a sample is taken in the pass that holds its pair and the
 // pass sums are added to the partial in pass order.
 // =====================================================================
-constexpr int PG = 8;          // views per block
+constexpr int PG = 16;         // views per block
 constexpr int PT = 1024;       // threads per block
 constexpr int PROJ_CW = 640;   // pairs per staged band row
 
@@ -111,39 +111,59 @@ k_project_bands(const float *__restrict__ x, const ViewP *__restrict__ views,
             const float q = joseph_q(joseph_dp(d, B), a, hq);
             int lo, hi;
             step_range(q, m, inv_m, h, ulo, uhi, s0, s0 + ns - 1, lo, hi);
-            float sp = (float)lo - h;
-            const float2 *rowp = P + (lo - s0) * SP - I0;
-            float acc0 = 0.0f, acc1 = 0.0f;
-            int s = lo;
-            for (; s + 1 <= hi; s += 2) {
-                int i0a, i0b;
-                float ga, gb;
-                joseph_round(joseph_u(sp, m, q), i0a, ga);
-                joseph_round(joseph_u(__fadd_rn(sp, 1.0f), m, q), i0b, gb);
-                i0a = min(max(i0a, -2), N);
-                i0b = min(max(i0b, -2), N);
-                if (!MULTI || (i0a >= I0 && i0a < I1)) {
-                    const float2 pa = rowp[i0a];
-                    acc0 += __fmaf_rn(ga, pa.y, pa.x);
+            const float sp = (float)lo - h;
+            int ridx = (lo - s0) * SP;                 // pair array offset of step lo
+            float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+            if (!MULTI) {
+                // steps lo, lo+1, ... as u'(s) = sp_k m + q with sp_k = (s - h) exact;
+                // the pair index i0 + 2 is clamped to [0, N + 2] (both ends are zero pairs)
+                const unsigned top = (unsigned)(N + 2);
+                float spk = sp;
+                int s = lo;
+                for (; s + 3 <= hi; s += 4) {
+                    float2 pr[4];
+                    float gg[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float up = joseph_u(__fadd_rn(spk, (float)u), m, q);
+                        const float t = __fadd_rn(up, JOSEPH_BIAS);
+                        const unsigned ip = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
+                        gg[u] = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
+                        pr[u] = P[ridx + u * SP + (int)ip];
+                    }
+                    acc0 += __fmaf_rn(gg[0], pr[0].y, pr[0].x);
+                    acc1 += __fmaf_rn(gg[1], pr[1].y, pr[1].x);
+                    acc2 += __fmaf_rn(gg[2], pr[2].y, pr[2].x);
+                    acc3 += __fmaf_rn(gg[3], pr[3].y, pr[3].x);
+                    spk = __fadd_rn(spk, 4.0f);
+                    ridx += 4 * SP;
                 }
-                if (!MULTI || (i0b >= I0 && i0b < I1)) {
-                    const float2 pb = rowp[SP + i0b];
-                    acc1 += __fmaf_rn(gb, pb.y, pb.x);
+                for (; s <= hi; ++s) {
+                    const float up = joseph_u(spk, m, q);
+                    const float t = __fadd_rn(up, JOSEPH_BIAS);
+                    const unsigned ip = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
+                    const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
+                    const float2 p = P[ridx + (int)ip];
+                    acc0 += __fmaf_rn(g, p.y, p.x);
+                    spk = __fadd_rn(spk, 1.0f);
+                    ridx += SP;
                 }
-                sp = __fadd_rn(sp, 2.0f);
-                rowp += 2 * SP;
+            } else {
+                float spk = sp;
+                for (int s = lo; s <= hi; ++s) {
+                    int i0;
+                    float g;
+                    joseph_round(joseph_u(spk, m, q), i0, g);
+                    i0 = min(max(i0, -2), N);
+                    if (i0 >= I0 && i0 < I1) {
+                        const float2 p = P[ridx + (i0 - I0)];
+                        acc0 += __fmaf_rn(g, p.y, p.x);
+                    }
+                    spk = __fadd_rn(spk, 1.0f);
+                    ridx += SP;
+                }
             }
-            if (s <= hi) {
-                int i0a;
-                float ga;
-                joseph_round(joseph_u(sp, m, q), i0a, ga);
-                i0a = min(max(i0a, -2), N);
-                if (!MULTI || (i0a >= I0 && i0a < I1)) {
-                    const float2 pa = rowp[i0a];
-                    acc0 += __fmaf_rn(ga, pa.y, pa.x);
-                }
-            }
-            const float sum = acc0 + acc1;
+            const float sum = (acc0 + acc1) + (acc2 + acc3);
             float *o = out + (size_t)svi[vi] * B + d;
             if (!MULTI || I0 == -2) *o = sum;
             else *o += sum;                       // this thread wrote it in the previous pass
@@ -278,18 +298,19 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
         if (r < N) {
             for (int vi = slice; vi < nv; vi += BSL) {
                 const float4 T = sv[vi];
-                const int wb = wbase[vi];
+                const int fb = JOSEPH_BIAS_BITS + wbase[vi];
                 const float eb = fmaf(yr, T.y, hb_lo);
+                const float2 *tv = tab[vi];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float e = fmaf(xc[k], T.x, eb);               // e - 1/2
                     const float t = __fadd_rn(e, JOSEPH_BIAS);
-                    int f = __float_as_int(t) - JOSEPH_BIAS_BITS;       // floor(e)
+                    // floor(e) - wbase, kept inside the staged window
+                    const unsigned f = min((unsigned)(__float_as_int(t) - fb), (unsigned)(BWW - 1));
                     const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));   // frac(e) - 1/2
                     const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w));   // 1 - frac |a|
                     const float w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));    // 1 - (1 - frac) |a|
-                    f = min(max(f - wb, 0), BWW - 1);
-                    const float2 yy = tab[vi][f];
+                    const float2 yy = tv[f];
                     acc[k] = fmaf(w0, yy.x, fmaf(w1, yy.y, acc[k]));
                 }
             }
