@@ -121,6 +121,29 @@ ct_status ct_ramp_taps(const ct_geometry *geom, int mode, double tau, double kap
 ct_status ct_ramp_filter(const ct_geometry *geom, const float *taps, int half_len,
                          const float *in, float *out, int batch, void *stream);
 
+/*
+ * ct_ramp_filter without any device memory allocation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory while they run: for example a caller that reserves all of
+ * its memory at start-up and must not touch the allocator afterwards, or
+ * one that calls from a context where an allocation (which can block or
+ * fail under memory pressure) is not acceptable.
+ *
+ * Same arguments and result as ct_ramp_filter.  Instead of a scratch
+ * buffer from the allocator it uses one fixed device array of 8192 complex
+ * values (64 KiB) that every GPU which loads the library holds until the
+ * process exits, so it supports n_bins <= 4096 (a transform of at most
+ * 8192 points); larger geometries return CT_ERR_ARG with a message.
+ * The first call on a device looks up that array's device address (a
+ * synchronous runtime query); make that first call before any stream
+ * capture.  All calls share the array and each call overwrites all of its
+ * contents, so calls whose work may overlap on the GPU (other streams,
+ * other threads) race with each other: serialise them.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ */
+ct_status ct_ramp_filter_noalloc(const ct_geometry *geom, const float *taps, int half_len,
+                                 const float *in, float *out, int batch, void *stream);
+
 /* Parameters of ct_pdtv_solve (zero-initialise, then set what you need). */
 typedef struct {
     int mode;         /* CT_LOWDOSE: Algorithm 1 (beta > 0) / 1' (beta = 0);

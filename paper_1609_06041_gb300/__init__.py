@@ -19,6 +19,7 @@ from .ctpd import (  # noqa: F401
     ct_pdtv_workspace_bytes,
     ct_project,
     ct_ramp_filter,
+    ct_ramp_filter_noalloc,
     ct_ramp_taps,
     ct_version,
     workspace_for,

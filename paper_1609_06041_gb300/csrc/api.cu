@@ -15,8 +15,6 @@ using namespace ctpd;
 
 std::atomic<unsigned long long> ctpd::g_launches{0};
 
-struct ct_geometry : public Geometry {};
-
 namespace {
 
 thread_local char g_err[512] = "";
@@ -29,6 +27,18 @@ ct_status fail(ct_status s, const char *fmt, ...)
     va_end(ap);
     return s;
 }
+
+}  // namespace
+
+void ctpd::set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
 
 ct_status cuda_check(const char *where)
 {

@@ -42,6 +42,16 @@ struct Geometry {
     double *h_angles;     // host copy
 };
 
+// Records a printf-style message as the calling thread's last error.
+void set_error(const char *fmt, ...);
+
+}  // namespace ctpd
+
+// The opaque handle of the C ABI is the geometry itself.
+struct ct_geometry : public ctpd::Geometry {};
+
+namespace ctpd {
+
 // Joseph coordinate of the projector.  For ray d (dp = d - hb) the per-ray
 // constant q = dp*a + (h - 1/2) is formed once, and at step s (sp = s - h)
 // the coordinate u' = sp*m + q = u - 1/2.  Rounding u' to the nearest

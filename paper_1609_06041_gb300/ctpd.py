@@ -56,6 +56,7 @@ EXPORTS = {
     "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
     "ct_ramp_filter": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
+    "ct_ramp_filter_noalloc": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
                        ctypes.POINTER(ct_pdtv_report), _vp], _i),
@@ -192,6 +193,19 @@ def ct_ramp_filter(g: Geometry, taps: torch.Tensor, sino: torch.Tensor, out=None
         out = torch.empty_like(sino)
     po = _dev(out, "out", (g.n_views, g.n_bins))
     _check(_lib.ct_ramp_filter(g.handle, pt, half, ps, po, _batch(sino, 2), _stream()))
+    return out
+
+
+def ct_ramp_filter_noalloc(g: Geometry, taps: torch.Tensor, sino: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """ct_ramp_filter without device allocation: the caller passes `out`,
+    the library uses a fixed device array for its scratch (n_bins <= 4096)."""
+    if taps.numel() % 2 != 1:
+        raise ValueError("taps must have an odd length 2*half-1")
+    half = (taps.numel() + 1) // 2
+    pt = _dev(taps, "taps")
+    ps = _dev(sino, "sino", (g.n_views, g.n_bins))
+    po = _dev(out, "out", (g.n_views, g.n_bins))
+    _check(_lib.ct_ramp_filter_noalloc(g.handle, pt, half, ps, po, _batch(sino, 2), _stream()))
     return out
 
 
