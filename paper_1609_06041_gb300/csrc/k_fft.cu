@@ -224,11 +224,21 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float r0 = 0.0f, r1 = 0.0f;
         if (i < B) {
+            // band partial sums of A x, added in band order (loads issued ahead)
             float s0 = 0.0f, s1 = 0.0f;
-            for (int k = 0; k < nb; ++k) {
-                s0 += partial[k * VB + o0 + i];
-                if (has1) s1 += partial[k * VB + o1 + i];
+            const float *p0 = partial + o0 + i, *p1 = partial + (has1 ? o1 : o0) + i;
+            int k = 0;
+            for (; k + 4 <= nb; k += 4) {
+                const float a0 = p0[k * VB], a1 = p0[(k + 1) * VB], a2 = p0[(k + 2) * VB], a3 = p0[(k + 3) * VB];
+                const float c0 = p1[k * VB], c1 = p1[(k + 1) * VB], c2 = p1[(k + 2) * VB], c3 = p1[(k + 3) * VB];
+                s0 = (((s0 + a0) + a1) + a2) + a3;
+                s1 = (((s1 + c0) + c1) + c2) + c3;
             }
+            for (; k < nb; ++k) {
+                s0 += p0[k * VB];
+                s1 += p1[k * VB];
+            }
+            if (!has1) s1 = 0.0f;
             const float mu0 = mu[o0 + i], mu1 = has1 ? mu[o1 + i] : 0.0f;
             m_old[i] = mu0;
             m_old[B + i] = mu1;

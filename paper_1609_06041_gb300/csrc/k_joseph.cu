@@ -118,6 +118,8 @@ k_project_bands(const float *__restrict__ x, const ViewP *__restrict__ views,
                 // steps lo, lo+1, ... as u'(s) = sp_k m + q with sp_k = (s - h) exact;
                 // the pair index i0 + 2 is clamped to [0, N + 2] (both ends are zero pairs)
                 const unsigned top = (unsigned)(N + 2);
+                // q_u = q + u m: u'(s + u) = (s - h) m + q_u
+                const float qu1 = __fadd_rn(q, m), qu2 = __fmaf_rn(2.0f, m, q), qu3 = __fmaf_rn(3.0f, m, q);
                 float spk = sp;
                 int s = lo;
                 for (; s + 3 <= hi; s += 4) {
@@ -125,7 +127,8 @@ k_project_bands(const float *__restrict__ x, const ViewP *__restrict__ views,
                     float gg[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float up = joseph_u(__fadd_rn(spk, (float)u), m, q);
+                        const float qq = u == 0 ? q : (u == 1 ? qu1 : (u == 2 ? qu2 : qu3));
+                        const float up = joseph_u(spk, m, qq);
                         const float t = __fadd_rn(up, JOSEPH_BIAS);
                         const unsigned ip = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
                         gg[u] = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));

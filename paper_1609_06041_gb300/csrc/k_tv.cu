@@ -25,7 +25,9 @@ static size_t tv_smem(int steps)
     return sizeof(float) * 4 * (size_t)S * S;
 }
 
-__global__ void __launch_bounds__(256)
+constexpr int TV_THREADS = 512;   // 32 x 16
+
+__global__ void __launch_bounds__(TV_THREADS)
 k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
      float *__restrict__ x, int N, int steps, int final_,
      const double *__restrict__ scal)
@@ -38,9 +40,10 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     const size_t NN = (size_t)N * N;
     const float lam = (float)scal[S_LAMBDA];
     const float inv8 = (float)scal[S_INV8LAM];
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 16
+    constexpr int TY = TV_THREADS / 32;
 
-    for (int li = ty; li < S; li += 8) {
+    for (int li = ty; li < S; li += TY) {
         const int rr = R0 + li;
         for (int lj = tx; lj < S; lj += 32) {
             const int cc = C0 + lj;
@@ -58,7 +61,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     if (lam > 0.0f) {
         for (int it = 0; it < steps; ++it) {
             // x_l = max(0, z + lam div p) on rows/cols >= 1 of the region
-            for (int li = 1 + ty; li < S; li += 8) {
+            for (int li = 1 + ty; li < S; li += TY) {
                 const int rr = R0 + li;
                 for (int lj = 1 + tx; lj < S; lj += 32) {
                     const int cc = C0 + lj;
@@ -70,7 +73,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
             }
             __syncthreads();
             // p <- Pi(p + grad x / (8 lam)) on rows/cols 1 .. S-2
-            for (int li = 1 + ty; li < S - 1; li += 8) {
+            for (int li = 1 + ty; li < S - 1; li += TY) {
                 const int rr = R0 + li;
                 for (int lj = 1 + tx; lj < S - 1; lj += 32) {
                     const int cc = C0 + lj;
@@ -79,8 +82,8 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                     const float gy = (rr < N - 1) ? sx[i + S] - sx[i] : 0.0f;
                     const float qx = spx[i] + gx * inv8;
                     const float qy = spy[i] + gy * inv8;
-                    const float nrm = sqrtf(qx * qx + qy * qy);
-                    const float sc = 1.0f / fmaxf(1.0f, nrm);
+                    // divide by max(1, |q|)
+                    const float sc = fminf(1.0f, rsqrtf(fmaf(qx, qx, qy * qy)));
                     spx[i] = qx * sc;
                     spy[i] = qy * sc;
                 }
@@ -90,7 +93,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     }
 
     // write back the tile interior
-    for (int li = H + ty; li < H + TV_T; li += 8) {
+    for (int li = H + ty; li < H + TV_T; li += TY) {
         const int rr = R0 + li;
         for (int lj = H + tx; lj < H + TV_T; lj += 32) {
             const int cc = C0 + lj;
@@ -115,7 +118,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                int n, int steps, int final_, const double *scal, cudaStream_t st)
 {
-    dim3 blk(32, 8), grd((n + TV_T - 1) / TV_T, (n + TV_T - 1) / TV_T);
+    dim3 blk(32, TV_THREADS / 32), grd((n + TV_T - 1) / TV_T, (n + TV_T - 1) / TV_T);
     counted();
     k_tv<<<grd, blk, tv_smem(steps), st>>>(z, p_in, p_out, x, n, steps, final_, scal);
 }
