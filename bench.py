@@ -38,6 +38,10 @@ METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+# DRAM bytes (read + write) per launch of each operator's main kernel at this
+# workload, from the full ncu capture in profiles/kernels_lowdose_512_v720_b736.md
+# (update together with the kernels; None when no capture of the current kernel exists)
+TRAFFIC_BYTES = {"A": 1.087488e6, "AT": 3.053568e6}
 
 
 def dist_info():
@@ -285,8 +289,8 @@ def run_ours(args):
     flops = 2.0 * nnz
     # dominant operator: the slower of A (ct_project: band kernel + reduction)
     # and A^T (ct_backproject); both carry 2 nnz(A) algorithmic flops
-    dom_name, dom_ms = ("ct_backproject (A^T, k_backproject_tiles)", at_ms) if at_ms >= a_ms else \
-        ("ct_project (A, k_project_bands + k_band_reduce)", a_ms)
+    dom_name, dom_ms, dom_key = ("ct_backproject (A^T, k_backproject_tiles)", at_ms, "AT") if at_ms >= a_ms else \
+        ("ct_project (A, k_project_bands + k_band_reduce)", a_ms, "A")
     achieved = flops / (dom_ms / 1e3) / 1e12
 
     # ---- end to end through the public API with host buffers ----
@@ -336,7 +340,8 @@ def run_ours(args):
             "report": {k: rep[k] for k in ("tau", "sigma", "kappa", "norm_ADA", "norm_WDW")},
             "roofline": {"kernel": dom_name, "bound": "alu", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": None, "algorithmic_flops": flops, "nnz": nnz, "launch_ms": dom_ms,
+                         "traffic": TRAFFIC_BYTES.get(dom_key), "traffic_unit": "bytes/launch",
+                         "algorithmic_flops": flops, "nnz": nnz, "launch_ms": dom_ms,
                          "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
