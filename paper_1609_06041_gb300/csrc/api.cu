@@ -91,25 +91,24 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 // stays on the device.
 template <class Op>
 void lanczos_norm(Op op, float *q, float *qp, float *w, size_t n, int k, double *scal, double *partials,
-                  int slot, cudaStream_t st)
+                  unsigned *ticket, int slot, cudaStream_t st)
 {
     launch_fill(q, 1.0f, n, st);
     launch_dot(q, q, n, scal, S_RED0, partials, st);
     launch_normalize(q, q, n, scal, S_RED0, st);
     for (int j = 0; j < k; ++j) {
         op(q, w);
-        if (j > 0) launch_axpy_neg(w, qp, n, scal, S_LZ + 2 * j - 1, st);
-        launch_dot(w, q, n, scal, S_LZ + 2 * j, partials, st);
-        launch_axpy_neg(w, q, n, scal, S_LZ + 2 * j, st);
-        launch_dot(w, w, n, scal, S_RED0, partials, st);
-        launch_scalars(scal, SC_NORM_SQRT, (double)S_RED0, 0, 0, S_LZ + 2 * j + 1, st);
+        // w -= beta_{j-1} q_{j-1};  alpha_j = <w, q_j>
+        launch_axpy_dot(w, qp, n, scal, j > 0 ? S_LZ + 2 * j - 1 : -1, q, S_LZ + 2 * j, partials, ticket, -1, st);
+        // w -= alpha_j q_j;  |w|^2 -> S_RED0, beta_j = |w|
+        launch_axpy_dot(w, q, n, scal, S_LZ + 2 * j, nullptr, S_RED0, partials, ticket, S_LZ + 2 * j + 1, st);
         launch_normalize(w, w, n, scal, S_RED0, st);
         float *t = qp;
         qp = q;
         q = w;
         w = t;
     }
-    launch_scalars(scal, SC_LANCZOS_MAX, (double)k, 0, 0, slot, st);
+    launch_lanczos_max(scal, k, slot, st);
 }
 
 }  // namespace
@@ -334,6 +333,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     }
     double *scal = (double *)(ws + L.scal);
     double *partials = (double *)(ws + L.partials);
+    unsigned *ticket = (unsigned *)(partials + dot_partials_doubles() - 64);
     float *taps = (float *)(ws + L.taps);
     float2 *hhat = (float2 *)(ws + L.hhat);
     const bool use_fft = fft_supported(g);
@@ -354,6 +354,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     } else {
         // ---- setup (Alg. 1 / Alg. 2 boxes): kappa, tau, D, sigma ----
         cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
+        cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
         if (lowdose) {
             launch_recip(w, winv, I, st);
             launch_dot(winv, nullptr, I, scal, S_RED0, partials, st);
@@ -372,7 +373,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 else launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
                 launch_backproject(g, mubar, out, 0, nullptr, nullptr, 1, st);
             };
-            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, partials, S_NADA, st);
+            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, partials, ticket, S_NADA, st);
             if (lowdose) {
                 // ||W^-1/2 D W^-1/2|| by Lanczos on the sinogram side
                 float *sw = mubar;
@@ -381,7 +382,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                     if (use_fft) launch_filter_fft(g, hhat, v, out, sw, sw, 0, nullptr, 1, st);
                     else launch_filter(g, taps, half, v, out, sw, sw, 0, nullptr, 1, st);
                 };
-                lanczos_norm(op_wdw, mu, r, band, I, nlz, scal, partials, S_NWDW, st);
+                lanczos_norm(op_wdw, mu, r, band, I, nlz, scal, partials, ticket, S_NWDW, st);
             }
         }
         launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);

@@ -162,7 +162,14 @@ void launch_normalize(const float *in, float *out, size_t n, const double *scal,
 void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0,
                     cudaStream_t st);
 enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET, SC_COPY,
-       SC_LANCZOS_MAX, SC_NORM_SQRT };
+       SC_NORM_SQRT };
+// scal[out] = largest eigenvalue of the Lanczos tridiagonal of k steps
+void launch_lanczos_max(double *scal, int k, int out, cudaStream_t st);
+// w -= scal[cslot] q (cslot >= 0); scal[dslot] = <w, v or w>; scal[sqrt_out] =
+// sqrt of it (sqrt_out >= 0).  partials: dot_partials_doubles(); ticket: a
+// zero-initialised counter (left at zero).
+void launch_axpy_dot(float *w, const float *q, size_t n, double *scal, int cslot, const float *v, int dslot,
+                     double *partials, unsigned *ticket, int sqrt_out, cudaStream_t st);
 // w -= scal[slot] * q
 void launch_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot, cudaStream_t st);
 
