@@ -184,6 +184,61 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------
+# batched form: 64 slices of mixed size, view count and mode
+# ----------------------------------------------------------------------
+def measure_batched(P, steps=3, count=64, seed=0):
+    """slices/s of one ct_pdtv_solve_batched call (captured in a CUDA graph)
+    against the same slices solved one after another with ct_pdtv_solve."""
+    import torch
+    shapes = synth.mixed_slices(count, seed)
+    slices, geoms = [], {}
+    for n, v, nb, mode, sd in shapes:
+        g = geoms.setdefault((n, v, nb), P.Geometry(n, v, nb))
+        x = synth.ellipse_phantom(n, 10, sd) * ((2.0 / n) if mode == 0 else 1.0)
+        p = P.ct_project(g, torch.from_numpy(x.astype(np.float32)).cuda())
+        if mode == 0:
+            bb, ww = synth.poisson_data(p.cpu().numpy(), 1e4, sd)
+            b = torch.from_numpy(bb.astype(np.float32)).cuda()
+            w = torch.from_numpy(ww.astype(np.float32)).cuda()
+        else:
+            b, w = p, None
+        slices.append((g, b, w, P.PDTVParams(mode=mode, iters=30, beta=0.005)))
+    stream = torch.cuda.current_stream()
+    bs = P.BatchedSolve(slices)
+    bs.run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bs.run()
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / steps
+    # the same slices one after another through the single-slice solve
+    ws = bs.ws
+    for i, (g, b, w, prm) in enumerate(slices):
+        P.ct_pdtv_solve(g, b, w, prm, x_out=bs.x[i], workspace=ws[i], report=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for i, (g, b, w, prm) in enumerate(slices):
+            P.ct_pdtv_solve(g, b, w, prm, x_out=bs.x[i], workspace=ws[i], report=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1) / steps
+    return {"workload": f"{count} slices, N in (256,384,512), views in (32,90,360,720), "
+                        f"bins = ceil(1.44 N), low-dose if V*B > N^2 else few-view, 30 iterations",
+            "batched_slices_per_s": count / (t_batched / 1e3), "batched_ms": t_batched,
+            "single_slices_per_s": count / (t_single / 1e3), "single_ms": t_single,
+            "speedup": t_single / t_batched}
+
+
+# ----------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------
 def run_ours(args):
@@ -319,6 +374,10 @@ def run_ours(args):
     e2e_ms = sum(a.elapsed_time(c) for a, c in ee)
     e2e_value = WORK["iters"] * args.steps * world / (e2e_ms / 1e3)
 
+    forms = None
+    if not args.no_forms:
+        forms = {"batched": measure_batched(P)}
+
     clocks = sampler.summary()
     if rank == 0:
         cpu = None
@@ -348,6 +407,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": 2 * V * B * 4, "d2h_bytes_per_step": N * N * 4},
             "gpu_launches": launches,
             "clocks": clocks,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -385,6 +445,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args()

@@ -200,6 +200,29 @@ ct_status ct_pdtv_solve(const ct_geometry *geom, const float *b, const float *w,
                         const ct_pdtv_params *params, float *x_out,
                         void *workspace, ct_pdtv_report *report, void *stream);
 
+/*
+ * Many independent slices in one call (the batched form of the solve):
+ * slice i is ct_pdtv_solve(geoms[i], b[i], w[i], &params[i], x_out[i],
+ * workspaces[i]) with no report, for n slices of any mix of geometries
+ * (image sizes, view counts, bins), modes and parameters.
+ * geoms, b, w, params, x_out, workspaces (host arrays of n entries) hold
+ * per-slice handles, device pointers and parameters; w may be NULL when no
+ * slice is low-dose, and w[i] may be NULL for few-view slices.  Every
+ * workspace must be ct_pdtv_workspace_bytes(geoms[i], &params[i]) bytes;
+ * resume is not accepted here.  The slices run concurrently on a pool of
+ * streams the library creates per device on first use (keep that first
+ * call outside stream capture); the work is forked from `stream` and
+ * joined back into it, so later work on `stream` sees every x_out, and the
+ * whole call can be captured into a CUDA graph.  reports (host, n entries,
+ * may be NULL) are filled after synchronising `stream`.  Calls from
+ * several host threads at once share the pool; do not capture two of them
+ * at the same time.
+ */
+ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const float *const *b,
+                                const float *const *w, const ct_pdtv_params *params,
+                                float *const *x_out, void *const *workspaces,
+                                ct_pdtv_report *reports, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

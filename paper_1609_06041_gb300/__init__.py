@@ -7,6 +7,7 @@ C ABI of include/ctpd.h; ``ctpd`` is its thin Python binding.
 from .ctpd import (  # noqa: F401
     CT_FEWVIEW,
     CT_LOWDOSE,
+    BatchedSolve,
     CTError,
     Geometry,
     PDTVParams,
@@ -16,6 +17,7 @@ from .ctpd import (  # noqa: F401
     ct_kernel_launches,
     ct_last_error,
     ct_pdtv_solve,
+    ct_pdtv_solve_batched,
     ct_pdtv_workspace_bytes,
     ct_project,
     ct_ramp_filter,

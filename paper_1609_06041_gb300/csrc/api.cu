@@ -38,6 +38,25 @@ void ctpd::set_error(const char *fmt, ...)
     va_end(ap);
 }
 
+ct_status ctpd::read_report(const void *workspace, ct_pdtv_report *report)
+{
+    // the scalar block sits at the start of the workspace
+    double h[S_COUNT];
+    cudaError_t e = cudaMemcpy(h, workspace, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error("reading the solve report: %s", cudaGetErrorString(e));
+        return CT_ERR_CUDA;
+    }
+    report->tau = h[S_TAU];
+    report->sigma = h[S_SIGMA];
+    report->kappa = h[S_KAPPA];
+    report->lambda = h[S_LAMBDA];
+    report->norm_ADA = h[S_NADA];
+    report->norm_WDW = h[S_NWDW];
+    report->k = (int)h[S_K];
+    return CT_OK;
+}
+
 namespace {
 
 ct_status cuda_check(const char *where)
@@ -425,17 +444,9 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
     cs = cuda_check("ct_pdtv_solve");
     if (report && cs == CT_OK) {
-        double h[S_COUNT];
-        cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) cs = fail(CT_ERR_CUDA, "ct_pdtv_solve: %s", cudaGetErrorString(e));
-        report->tau = h[S_TAU];
-        report->sigma = h[S_SIGMA];
-        report->kappa = h[S_KAPPA];
-        report->lambda = h[S_LAMBDA];
-        report->norm_ADA = h[S_NADA];
-        report->norm_WDW = h[S_NWDW];
-        report->k = (int)h[S_K];
+        else cs = ctpd::read_report(ws, report);
     }
     if (owned) cudaFreeAsync(ws, st);
     return cs;

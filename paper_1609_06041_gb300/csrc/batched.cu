@@ -1,0 +1,121 @@
+// batched.cu -- ct_pdtv_solve_batched: many independent slices (their own
+// geometry, data, mode and parameters) solved in one call.
+//
+// Each slice's solve is the single-slice ct_pdtv_solve.  The call forks
+// the caller's stream onto a pool of streams (one pool per device, created
+// on first use and kept until exit) with events, enqueues slice i on pool
+// stream i mod S, and joins every pool stream back into the caller's
+// stream.  Small slices that cannot fill the GPU on their own then run
+// side by side.  The fork and join are stream-ordered event waits, so the
+// whole call can be captured into one CUDA graph.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "ctpd_internal.cuh"
+
+namespace {
+
+constexpr int POOL_STREAMS = 16;
+constexpr int MAX_DEVICES = 64;
+
+struct Pool {
+    bool ready = false;
+    cudaStream_t s[POOL_STREAMS];
+    cudaEvent_t fork;
+    cudaEvent_t join[POOL_STREAMS];
+};
+
+std::mutex g_pool_mu;
+Pool g_pools[MAX_DEVICES];
+
+ct_status pool_for_current(Pool **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        return CT_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    Pool &p = g_pools[dev];
+    if (!p.ready) {
+        cudaError_t e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+        for (int i = 0; i < POOL_STREAMS && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return CT_ERR_CUDA;
+        }
+        p.ready = true;
+    }
+    *out = &p;
+    return CT_OK;
+}
+
+}  // namespace
+
+extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const float *const *b,
+                                           const float *const *w, const ct_pdtv_params *params,
+                                           float *const *x_out, void *const *workspaces,
+                                           ct_pdtv_report *reports, void *stream)
+{
+    ctpd::set_error("%s", "");
+    if (n < 0 || (n > 0 && (!geoms || !b || !params || !x_out || !workspaces))) {
+        ctpd::set_error("ct_pdtv_solve_batched: bad argument");
+        return CT_ERR_ARG;
+    }
+    if (n == 0) return CT_OK;
+    for (int i = 0; i < n; ++i) {
+        if (!geoms[i] || !b[i] || !x_out[i] || !workspaces[i] || params[i].resume ||
+            (params[i].mode == CT_LOWDOSE && (!w || !w[i]))) {
+            ctpd::set_error("ct_pdtv_solve_batched: slice %d: missing geometry, data, output or workspace "
+                            "(or resume set)", i);
+            return CT_ERR_ARG;
+        }
+    }
+    Pool *pool = nullptr;
+    if (pool_for_current(&pool) != CT_OK) {
+        ctpd::set_error("ct_pdtv_solve_batched: cannot create the stream pool");
+        return CT_ERR_CUDA;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int used = n < POOL_STREAMS ? n : POOL_STREAMS;
+    cudaEventRecord(pool->fork, st);
+    for (int i = 0; i < used; ++i) cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
+    ct_status result = CT_OK;
+    for (int i = 0; i < n && result == CT_OK; ++i) {
+        result = ct_pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, &params[i], x_out[i], workspaces[i],
+                               nullptr, pool->s[i % POOL_STREAMS]);
+        if (result != CT_OK) {
+            char msg[400];
+            snprintf(msg, sizeof(msg), "%s", ct_last_error());
+            ctpd::set_error("ct_pdtv_solve_batched: slice %d: %s", i, msg);
+        }
+    }
+    // join: the caller's stream waits for every pool stream that was used
+    for (int i = 0; i < used; ++i) {
+        cudaEventRecord(pool->join[i], pool->s[i]);
+        cudaStreamWaitEvent(st, pool->join[i], 0);
+    }
+    if (result != CT_OK) return result;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctpd::set_error("ct_pdtv_solve_batched: %s", cudaGetErrorString(e));
+        return CT_ERR_CUDA;
+    }
+    if (reports) {
+        // scalars of each slice, read back after the caller's stream completes
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            ctpd::set_error("ct_pdtv_solve_batched: %s", cudaGetErrorString(e));
+            return CT_ERR_CUDA;
+        }
+        for (int i = 0; i < n; ++i) {
+            result = ctpd::read_report(workspaces[i], &reports[i]);
+            if (result != CT_OK) return result;
+        }
+    }
+    return CT_OK;
+}

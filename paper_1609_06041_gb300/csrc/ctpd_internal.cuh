@@ -44,6 +44,8 @@ struct Geometry {
 
 // Records a printf-style message as the calling thread's last error.
 void set_error(const char *fmt, ...);
+// Copies the scalars of a finished solve out of its workspace (synchronous).
+ct_status read_report(const void *workspace, ct_pdtv_report *report);
 
 }  // namespace ctpd
 

@@ -60,6 +60,9 @@ EXPORTS = {
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
                        ctypes.POINTER(ct_pdtv_report), _vp], _i),
+    "ct_pdtv_solve_batched": ([_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               ctypes.POINTER(ct_pdtv_params), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               ctypes.POINTER(ct_pdtv_report), _vp], _i),
 }
 for _name, (_args, _res) in EXPORTS.items():
     _fn = getattr(_lib, _name)
@@ -259,3 +262,40 @@ def ct_pdtv_solve(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, params: 
 def workspace_for(g: Geometry, params: PDTVParams, device="cuda") -> torch.Tensor:
     n = ct_pdtv_workspace_bytes(g, params)
     return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+class BatchedSolve:
+    """ct_pdtv_solve_batched over a fixed list of slices.  The slices'
+    workspaces and outputs are allocated once here, so run() enqueues only
+    device work (and can be captured in a CUDA graph)."""
+
+    def __init__(self, slices):
+        # slices: list of (Geometry, b, w or None, PDTVParams)
+        self.slices = list(slices)
+        n = len(self.slices)
+        self.x = [torch.empty(g.n, g.n, device=b.device, dtype=torch.float32) for g, b, w, p in self.slices]
+        self.ws = [workspace_for(g, p, b.device) for g, b, w, p in self.slices]
+        for g, b, w, p in self.slices:
+            _dev(b, "b", (g.n_views, g.n_bins))
+            if w is not None:
+                _dev(w, "w", (g.n_views, g.n_bins))
+        V = ctypes.c_void_p * n
+        self._g = V(*[g.handle for g, _, _, _ in self.slices])
+        self._b = V(*[b.data_ptr() for _, b, _, _ in self.slices])
+        self._w = V(*[(w.data_ptr() if w is not None else None) for _, _, w, _ in self.slices])
+        self._p = (ct_pdtv_params * n)(*[p.to_c() for _, _, _, p in self.slices])
+        self._x = V(*[t.data_ptr() for t in self.x])
+        self._ws = V(*[t.data_ptr() for t in self.ws])
+        self.n = n
+
+    def run(self, reports=False):
+        rep = (ct_pdtv_report * self.n)() if reports else None
+        _check(_lib.ct_pdtv_solve_batched(self.n, self._g, self._b, self._w, self._p, self._x, self._ws,
+                                          rep, _stream()))
+        return self.x, ([r.as_dict() for r in rep] if reports else None)
+
+
+def ct_pdtv_solve_batched(slices, reports=True):
+    """Solve a list of (Geometry, b, w or None, PDTVParams) slices in one call."""
+    bs = BatchedSolve(slices)
+    return bs.run(reports=reports)

@@ -114,6 +114,22 @@ def bins_for(n: int) -> int:
     return int(math.ceil(1.44 * n))
 
 
+def mixed_slices(count: int, seed: int, sizes=(256, 384, 512), views=(32, 90, 360, 720)):
+    """Slice shapes of a mixed batch: image side and view count drawn from
+    the given sets by default_rng(seed), bins = ceil(1.44 N), low-dose when
+    the sinogram has more samples than the image (V B > N^2), else few-view.
+    Returns a list of (n, n_views, n_bins, mode, seed_i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        v = int(rng.choice(views))
+        b = bins_for(n)
+        mode = 0 if v * b > n * n else 1
+        out.append((n, v, b, mode, seed * 1000 + i))
+    return out
+
+
 # The workloads, by what they are.  'scale' is the attenuation scale that
 # turns unit-range phantom intensities into line integrals of a few units
 # (x_phys = scale * v); few-view data are noiseless b = A v.

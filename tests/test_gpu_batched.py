@@ -1,0 +1,81 @@
+"""The batched form: many slices of mixed geometry and mode in one call
+(ct_pdtv_solve_batched).  Each slice must equal its single-slice solve bit
+for bit, match the FP64 oracle, and replay identically from a CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_util import need_gpu, rel_l2, to_gpu, to_np, f32
+
+pytestmark = pytest.mark.gpu
+
+
+def make_slices(P, shapes, iters, oracle_data=True):
+    out = []
+    for n, v, b, mode, sd in shapes:
+        g = P.Geometry(n, v, b)
+        if mode == 0:
+            x = synth.ellipse_phantom(n, 6, sd) * (2.0 / n)
+            bb, w = synth.poisson_data(O.project(x, v, b), 1e4, sd)
+            w = to_gpu(f32(w))
+        else:
+            bb = O.project(synth.ellipse_phantom(n, 6, sd), v, b)
+            w = None
+        prm = P.PDTVParams(mode=mode, iters=iters, beta=0.01)
+        out.append((g, to_gpu(f32(bb)), w, prm))
+    return out
+
+
+def test_batched_equals_single_slice_solves():
+    P = need_gpu()
+    shapes = [(48, 60, 70, 0, 1), (32, 8, 47, 1, 2), (64, 90, 95, 0, 3), (40, 12, 58, 1, 4), (48, 60, 70, 0, 5),
+              (17, 30, 25, 0, 6)]
+    slices = make_slices(P, shapes, 6)
+    xs, reps = P.ct_pdtv_solve_batched(slices)
+    for (g, b, w, prm), xb, rep in zip(slices, xs, reps):
+        x1, rep1 = P.ct_pdtv_solve(g, b, w, prm)
+        assert np.array_equal(to_np(xb), to_np(x1))
+        assert rep["sigma"] == rep1["sigma"] and rep["k"] == 6
+
+
+def test_batched_matches_oracle():
+    P = need_gpu()
+    shapes = [(32, 45, 47, 0, 11), (40, 10, 58, 1, 12), (24, 36, 35, 0, 13)]
+    slices = make_slices(P, shapes, 8)
+    xs, reps = P.ct_pdtv_solve_batched(slices)
+    for (g, b, w, prm), xb, rep, (n, v, nb, mode, sd) in zip(slices, xs, reps, shapes):
+        bh = to_np(b)
+        wh = None if w is None else to_np(w)
+        kappa = float(np.mean(1.0 / wh)) if mode == 0 else 0.0
+        taps = O.ramp_taps(mode, v, nb, rep["tau"], kappa)
+        st, _ = O.pdtv(bh, wh, taps, mode, 0.01, rep["tau"], rep["sigma"], 10, 8, n)
+        assert rel_l2(to_np(xb), st.x) <= 1e-3
+
+
+def test_batched_graph_replay():
+    P = need_gpu()
+    import torch
+    shapes = synth.mixed_slices(8, 7, sizes=(32, 48, 64), views=(16, 45, 90))
+    slices = make_slices(P, shapes, 5)
+    bs = P.BatchedSolve(slices)
+    xs, _ = bs.run()                      # eager (creates the stream pool)
+    torch.cuda.synchronize()
+    ref = [to_np(x).copy() for x in xs]
+    for x in bs.x:
+        x.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bs.run()
+    graph.replay()
+    torch.cuda.synchronize()
+    for x, r in zip(bs.x, ref):
+        assert np.array_equal(to_np(x), r)
+
+
+def test_batched_rejects_bad_slices():
+    P = need_gpu()
+    slices = make_slices(P, [(16, 20, 24, 0, 1)], 2)
+    g, b, w, prm = slices[0]
+    with pytest.raises(P.CTError):
+        P.ct_pdtv_solve_batched([(g, b, None, prm)])
