@@ -223,6 +223,37 @@ ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const fl
                                 float *const *x_out, void *const *workspaces,
                                 ct_pdtv_report *reports, void *stream);
 
+/*
+ * The differentiable form: `iters` iterations of Algorithm 1 (mode
+ * CT_LOWDOSE, lambda = tau beta) or Algorithm 2 (CT_FEWVIEW, lambda = tau)
+ * unrolled for `batch` slices of one geometry that share the taps of D (any
+ * real taps, 2*half_len-1 values centred at half_len-1, for example
+ * learned ones), tau, sigma and beta.  The steps are those of
+ * ct_pdtv_solve (Eqs. 18-20 / 29-31), with the prox of Eq. 17 taken as
+ * tv_iters whole-image projected-gradient steps warm-started from the
+ * previous iteration's dual field.
+ *
+ * ct_unrolled_forward writes x_K (batch x N x N) and keeps one checkpoint
+ * per iteration (x, mu, mubar, TV dual field) in `workspace`
+ * (ct_unrolled_workspace_bytes, device).  ct_unrolled_backward, given
+ * grad_x = dL/dx_K (batch x N x N, device) and the workspace of the forward
+ * call with the same arguments, recomputes each iteration from its
+ * checkpoint and applies the adjoint of every step in reverse order (A^T
+ * for A, A for A^T, D^T for D, the adjoints of the projected-gradient
+ * steps); it writes grad (device, 2*half_len floats): grad[0 .. 2*half_len-2]
+ * = dL/dtaps, grad[2*half_len-1] = dL/dbeta (0 for CT_FEWVIEW).  tau and
+ * sigma are constants of the unroll.  b, w: batch x V x B; w > 0, required
+ * for CT_LOWDOSE.  Needs n_bins <= 4096.  Both calls only enqueue work.
+ */
+size_t ct_unrolled_workspace_bytes(const ct_geometry *geom, int batch, int half_len, int iters, int tv_iters);
+ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b, const float *w, int batch,
+                              const float *taps, int half_len, double tau, double sigma, double beta,
+                              int mode, int iters, int tv_iters, float *x_out, void *workspace, void *stream);
+ct_status ct_unrolled_backward(const ct_geometry *geom, const float *b, const float *w, int batch,
+                               const float *taps, int half_len, double tau, double sigma, double beta,
+                               int mode, int iters, int tv_iters, const float *grad_x, float *grad,
+                               void *workspace, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

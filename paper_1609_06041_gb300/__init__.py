@@ -25,4 +25,15 @@ from .ctpd import (  # noqa: F401
     ct_ramp_taps,
     ct_version,
     workspace_for,
+    ct_unrolled_workspace_bytes,
+    ct_unrolled_forward,
+    ct_unrolled_backward,
+)
+from .autograd import (  # noqa: F401
+    Backproject,
+    Project,
+    UnrolledPDTV,
+    UnrolledReconstructor,
+    backproject,
+    project,
 )

@@ -140,6 +140,34 @@ void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, f
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
                      float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st);
 void kernel_attrs_fft();
+void launch_dual_fft_batched(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
+                             const float *mu_in, float *mu_out, float *mu_bar, const float *winv, int lowdose,
+                             const double *scal, int batch, cudaStream_t st);
+void launch_dual_bwd_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
+                         const float *winv, const float *mu, const float *mu1, const float *gm, const float *gmb,
+                         float *gmu, float *gr, float *gm1, float *r, float *v, int lowdose, const double *scal,
+                         int batch, cudaStream_t st);
+
+// Reductions of the adjoint (k_grad.cu).
+size_t tapcorr_partials(int nviews, int half);
+void launch_tapcorr_acc(const float *g, const float *s, int nviews, int B, int half, double coef,
+                        double *partial, double *acc, cudaStream_t st);
+void launch_sum_partials(const double *partials, size_t n, double *scal, int slot, double coef, cudaStream_t st);
+void launch_grad_out(const double *acc, int nl, const double *scal, int slot, double fac, float *grad,
+                     cudaStream_t st);
+// out = fac[0] * scale_v * sum_b partial[b]
+void launch_band_reduce_scaled(const Geometry *g, const float *partial, float *out, const double *fac, int batch,
+                               cudaStream_t st);
+
+// Whole-image TV steps and their adjoints (k_tv.cu), batched over images.
+size_t tv_px_blocks(int n, int batch);
+void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int batch, const double *scal,
+                    cudaStream_t st);
+void launch_tv_final(const float *z, const float *p, float *x, int n, int batch, const double *scal, cudaStream_t st);
+void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
+                         float *gp, int n, int batch, const double *scal, double *part_lam, cudaStream_t st);
+void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gq, float *gz, float *gp,
+                        int n, int batch, const double *scal, double *part_inv8, double *part_lam, cudaStream_t st);
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
 // dual field p = (px, py)), temporal blocking in shared memory.
@@ -164,7 +192,7 @@ void launch_normalize(const float *in, float *out, size_t n, const double *scal,
 void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0,
                     cudaStream_t st);
 enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET, SC_COPY,
-       SC_NORM_SQRT };
+       SC_NORM_SQRT, SC_AXPY_SLOT };
 // scal[out] = largest eigenvalue of the Lanczos tridiagonal of k steps
 void launch_lanczos_max(double *scal, int k, int out, cudaStream_t st);
 // w -= scal[cslot] q (cslot >= 0); scal[dslot] = <w, v or w>; scal[sqrt_out] =

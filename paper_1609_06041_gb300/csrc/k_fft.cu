@@ -205,10 +205,21 @@ void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, f
 //   mubar = 2 mu' - mu [- sigma D (winv .* (mu' - mu))]  (Step 1, Alg. 1 / Alg. 2)
 __global__ void __launch_bounds__(FFT_T)
 k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, int nb,
-           const float *__restrict__ b, float *__restrict__ mu, float *__restrict__ mu_bar,
-           const float *__restrict__ winv, int lowdose, const ViewP *__restrict__ views,
+           const float *b, const float *mu_in, float *mu, float *mu_bar,
+           const float *winv, int lowdose, const ViewP *__restrict__ views,
            const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
 {
+    // slice blockIdx.y of a batch; mu_in may equal mu (each block reads its
+    // two views completely before writing them)
+    {
+        const size_t so = (size_t)blockIdx.y * V * B;
+        partial += (size_t)blockIdx.y * nb * V * B;
+        b += so;
+        mu_in += so;
+        mu += so;
+        mu_bar += so;
+        if (winv) winv += so;
+    }
     extern __shared__ float2 fsm[];
     float2 *a = fsm, *bb = fsm + P;
     float *m_old = reinterpret_cast<float *>(fsm + 2 * P);   // 2 x B
@@ -239,7 +250,7 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
                 s1 += p1[k * VB];
             }
             if (!has1) s1 = 0.0f;
-            const float mu0 = mu[o0 + i], mu1 = has1 ? mu[o1 + i] : 0.0f;
+            const float mu0 = mu_in[o0 + i], mu1 = has1 ? mu_in[o1 + i] : 0.0f;
             m_old[i] = mu0;
             m_old[B + i] = mu1;
             r0 = s0 * sc0 - b[o0 + i];
@@ -297,10 +308,126 @@ size_t dual_fft_smem(const Geometry *g) { return sizeof(float2) * 2 * g->n_fft +
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
                      float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st)
 {
+    launch_dual_fft_batched(g, hhat, partial, b, mu, mu, mu_bar, winv, lowdose, scal, 1, st);
+}
+
+void launch_dual_fft_batched(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
+                             const float *mu_in, float *mu_out, float *mu_bar, const float *winv, int lowdose,
+                             const double *scal, int batch, cudaStream_t st)
+{
     counted();
-    k_dual_fft<<<(g->n_views + 1) / 2, FFT_T, dual_fft_smem(g), st>>>(
-        hhat, partial, proj_bands(g->n), b, mu, mu_bar, winv, lowdose, g->d_views, scal, g->n_views,
+    k_dual_fft<<<dim3((g->n_views + 1) / 2, batch), FFT_T, dual_fft_smem(g), st>>>(
+        hhat, partial, proj_bands(g->n), b, mu_in, mu_out, mu_bar, winv, lowdose, g->d_views, scal, g->n_views,
         g->n_bins, g->n_fft, g->d_tw);
+}
+
+// Adjoint of one dual step (Step 3 and the next Step 1) for the pair of
+// views (v, v+1) of slice blockIdx.y.  Forward (W = diag(winv), low-dose):
+//   r      = A x' - b - W mu
+//   mu'    = mu + sigma D r
+//   mubar' = 2 mu' - mu - sigma D W (mu' - mu)
+// Given gm = dL/dmu' and gmb = dL/dmubar', with D^T applied through the
+// conjugate response:
+//   h   = D^T gmb
+//   gm1 = gm + 2 gmb - sigma W h          (total dL/dmu')
+//   gr  = sigma D^T gm1                   (dL/dr)
+//   gmu = gm1 - W gr - gmb + sigma W h    (dL/dmu)
+// and writes r and v = W (mu' - mu) for the tap correlations
+// dL/dt += sigma (gm1 * r) - sigma (gmb * v).  Few-view drops every W term.
+__global__ void __launch_bounds__(FFT_T)
+k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, int nb,
+               const float *__restrict__ b, const float *__restrict__ winv, const float *__restrict__ mu,
+               const float *__restrict__ mu1, const float *__restrict__ gm, const float *__restrict__ gmb,
+               float *__restrict__ gmu_out, float *__restrict__ gr_out, float *__restrict__ gm1_out,
+               float *__restrict__ r_out, float *__restrict__ v_out, int lowdose,
+               const ViewP *__restrict__ views, const double *__restrict__ scal, int V, int B, int P,
+               const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *bb = fsm + P;
+    float *h_s = reinterpret_cast<float *>(fsm + 2 * P);   // 2 x B: D^T gmb
+    float *g1_s = h_s + 2 * B;                             // 2 x B: gm1
+    const size_t so = (size_t)blockIdx.y * V * B;
+    partial += (size_t)blockIdx.y * nb * V * B;
+    const int v0 = 2 * blockIdx.x, v1 = v0 + 1;
+    const bool has1 = v1 < V;
+    const size_t VB = (size_t)V * B;
+    const size_t o0 = so + (size_t)v0 * B, o1 = so + (size_t)(has1 ? v1 : v0) * B;
+    const float sigma = (float)scal[S_SIGMA];
+    const float invP = 1.0f / (float)P;
+
+    // h = D^T gmb
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        a[i] = i < B ? make_float2(gmb[o0 + i], has1 ? gmb[o1 + i] : 0.0f) : make_float2(0.0f, 0.0f);
+    float2 *f = fft_block(a, bb, P, tw, false);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float2 h = hhat[i];
+        f[i] = cmul(f[i], make_float2(h.x, -h.y));
+    }
+    float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
+    float2 *other = res == a ? bb : a;
+    // gm1 = gm + 2 gmb - sigma W h ; stage gm1 for D^T
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float g0 = 0.0f, g1v = 0.0f;
+        if (i < B) {
+            const float h0 = res[i].x * invP, h1 = res[i].y * invP;
+            h_s[i] = h0;
+            h_s[B + i] = h1;
+            g0 = gm[o0 + i] + 2.0f * gmb[o0 + i];
+            g1v = has1 ? gm[o1 + i] + 2.0f * gmb[o1 + i] : 0.0f;
+            if (lowdose) {
+                g0 -= sigma * winv[o0 + i] * h0;
+                if (has1) g1v -= sigma * winv[o1 + i] * h1;
+            }
+            g1_s[i] = g0;
+            g1_s[B + i] = g1v;
+        }
+        other[i] = make_float2(g0, g1v);
+    }
+    f = fft_block(other, res, P, tw, false);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float2 h = hhat[i];
+        f[i] = cmul(f[i], make_float2(h.x, -h.y));
+    }
+    res = fft_block(f, f == a ? bb : a, P, tw, true);
+    const float sc0 = views[v0].scale, sc1 = has1 ? views[v1].scale : 0.0f;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        // two views: k = 0 -> v0, k = 1 -> v1
+        for (int k = 0; k < (has1 ? 2 : 1); ++k) {
+            const size_t o = (k == 0 ? o0 : o1) + i;
+            const float gr = sigma * ((k == 0 ? res[i].x : res[i].y) * invP);
+            const float g1v = g1_s[k * B + i], hv = h_s[k * B + i];
+            float gmu = g1v - gmb[o];
+            float acc = 0.0f;
+            const float *pp = partial + (o - so);
+            for (int q = 0; q < nb; ++q) acc += pp[q * VB];
+            float r = acc * (k == 0 ? sc0 : sc1) - b[o];
+            float vv = 0.0f;
+            if (lowdose) {
+                gmu += -winv[o] * gr + sigma * winv[o] * hv;
+                r -= winv[o] * mu[o];
+                vv = winv[o] * (mu1[o] - mu[o]);
+            }
+            gmu_out[o] = gmu;
+            gr_out[o] = gr;
+            gm1_out[o] = g1v;
+            r_out[o] = r;
+            v_out[o] = vv;
+        }
+    }
+}
+
+size_t dual_bwd_smem(const Geometry *g) { return sizeof(float2) * 2 * g->n_fft + sizeof(float) * 4 * g->n_bins; }
+
+void launch_dual_bwd_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
+                         const float *winv, const float *mu, const float *mu1, const float *gm, const float *gmb,
+                         float *gmu, float *gr, float *gm1, float *r, float *v, int lowdose, const double *scal,
+                         int batch, cudaStream_t st)
+{
+    counted();
+    k_dual_bwd_fft<<<dim3((g->n_views + 1) / 2, batch), FFT_T, dual_bwd_smem(g), st>>>(
+        hhat, partial, proj_bands(g->n), b, winv, mu, mu1, gm, gmb, gmu, gr, gm1, r, v, lowdose, g->d_views,
+        scal, g->n_views, g->n_bins, g->n_fft, g->d_tw);
 }
 
 bool fft_supported(const Geometry *g) { return g->n_fft <= FFT_MAX_P; }
@@ -311,6 +438,7 @@ void kernel_attrs_fft()
     cudaFuncSetAttribute(k_hhat, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_filter_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_dual_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_dual_bwd_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
 }
 
 }  // namespace ctpd

@@ -205,6 +205,7 @@ __global__ void k_band_reduce(const float *__restrict__ partial, float *__restri
     float val = acc * views[v].scale;
     if (MODE == 1) val = val - b[o] - winv[o] * mu[o];
     else if (MODE == 2) val = val - b[o];
+    else if (MODE == 3) val *= (float)(*reinterpret_cast<const double *>(b));
     out[o] = val;
 }
 
@@ -220,6 +221,16 @@ void launch_band_reduce(const Geometry *g, const float *partial, float *out, int
         k_band_reduce<1><<<grd, 256, 0, st>>>(partial, out, g->d_views, nb, g->n_views, g->n_bins, b, winv, mu);
     else
         k_band_reduce<2><<<grd, 256, 0, st>>>(partial, out, g->d_views, nb, g->n_views, g->n_bins, b, winv, mu);
+}
+
+// out = fac * A x from the band partials (fac: one device double)
+void launch_band_reduce_scaled(const Geometry *g, const float *partial, float *out, const double *fac, int batch,
+                               cudaStream_t st)
+{
+    dim3 grd((g->n_bins + 255) / 256, g->n_views, batch);
+    counted();
+    k_band_reduce<3><<<grd, 256, 0, st>>>(partial, out, g->d_views, proj_bands(g->n), g->n_views, g->n_bins,
+                                          reinterpret_cast<const float *>(fac), nullptr, nullptr);
 }
 
 // =====================================================================

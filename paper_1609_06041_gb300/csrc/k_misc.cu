@@ -158,6 +158,9 @@ __global__ void k_scalars(double *s, int op, double a0, double a1, double a2, in
     case SC_NORM_SQRT:                  // s[i0] = sqrt(s[(int)a0])
         s[i0] = sqrt(s[(int)a0]);
         break;
+    case SC_AXPY_SLOT:                  // s[i0] += a0 * s[(int)a1]
+        s[i0] += a0 * s[(int)a1];
+        break;
     }
 }
 

@@ -1,0 +1,266 @@
+// unrolled.cu -- the differentiable form: K iterations of Algorithm 1 / 2
+// unrolled, with per-iteration checkpoints in the forward pass and the
+// hand-written adjoint of every step in the backward pass.
+//
+// Forward, for a batch of slices sharing one geometry, taps t, tau, sigma
+// and lambda (= tau beta for Algorithm 1, tau for Algorithm 2):
+//   mubar_0 = -sigma D b
+//   z_k      = x_k - tau A^T mubar_k
+//   x_{k+1}  = prox(z_k), n_tv projected-gradient steps from p_k -> p_{k+1}
+//   mu_{k+1}, mubar_{k+1} = dual step (Step 3 and the next Step 1)
+// The checkpoint of iteration k is (x_k, mu_k, mubar_k, p_k).
+// Backward, from dL/dx_K, for k = K-1 .. 0: recompute z_k and the prox
+// trajectory from the checkpoint, apply the adjoint of the dual step
+// (k_dual_bwd_fft), of A (A^T), of the prox (k_tv_*_bwd) and of A^T (A),
+// accumulating dL/dt (tap correlations) and dL/dlambda.  sigma and tau are
+// constants of the unroll (not differentiated).
+#include <algorithm>
+
+#include "ctpd_internal.cuh"
+
+using namespace ctpd;
+
+namespace {
+
+struct UL {
+    size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gq, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa, pb,
+        tcorr, tacc, total;
+    size_t ck_stride;   // floats per checkpoint
+};
+
+inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+UL layout(const Geometry *g, int S, int half, int iters, int ntv)
+{
+    UL L;
+    const size_t J = (size_t)g->n * g->n, I = (size_t)g->n_views * g->n_bins, F = sizeof(float);
+    L.ck_stride = (size_t)S * (4 * J + 2 * I);
+    size_t o = 0;
+    L.scal = o;  o += a256(sizeof(double) * S_COUNT);
+    L.scal2 = o; o += a256(sizeof(double) * S_COUNT);
+    L.hhat = o;  o += a256(sizeof(float2) * g->n_fft);
+    L.winv = o;  o += a256(F * S * I);
+    L.ck = o;    o += a256(F * L.ck_stride * (iters + 1));
+    L.z = o;     o += a256(F * S * J);
+    L.band = o;  o += a256(F * S * I * proj_bands(g->n));
+    L.gx = o;    o += a256(F * S * J);
+    L.gz = o;    o += a256(F * S * J);
+    L.gp = o;    o += a256(F * S * 2 * J);
+    L.gp2 = o;   o += a256(F * S * 2 * J);
+    L.gq = o;    o += a256(F * S * 2 * J);
+    L.gm = o;    o += a256(F * S * I);
+    L.gmb = o;   o += a256(F * S * I);
+    L.gmu = o;   o += a256(F * S * I);
+    L.gr = o;    o += a256(F * S * I);
+    L.gm1 = o;   o += a256(F * S * I);
+    L.rr = o;    o += a256(F * S * I);
+    L.vv = o;    o += a256(F * S * I);
+    L.traj = o;  o += a256(F * (size_t)(ntv + 1) * S * 2 * J);
+    L.pa = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
+    L.pb = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
+    L.tcorr = o; o += a256(sizeof(double) * tapcorr_partials(S * g->n_views, half));
+    L.tacc = o;  o += a256(sizeof(double) * (2 * (size_t)half - 1));
+    L.total = o;
+    return L;
+}
+
+struct CK {
+    float *x, *mu, *mubar, *p;
+};
+
+CK ck_at(char *ws, const UL &L, const Geometry *g, int S, int k)
+{
+    const size_t J = (size_t)g->n * g->n, I = (size_t)g->n_views * g->n_bins;
+    float *base = (float *)(ws + L.ck) + (size_t)k * L.ck_stride;
+    CK c;
+    c.x = base;
+    c.mu = c.x + S * J;
+    c.mubar = c.mu + S * I;
+    c.p = c.mubar + S * I;
+    return c;
+}
+
+enum { U_LAMACC = S_RED0 + 1, U_INV8ACC = S_RED0 + 2 };
+
+ct_status check_args(const Geometry *g, const float *b, const float *w, int batch, const float *taps, int half,
+                     double tau, double sigma, double beta, int mode, int iters, int ntv, void *ws)
+{
+    if (!g || !b || !taps || !ws || batch < 1 || batch > 65535 || half < 1 || half > g->n_bins || !(tau > 0.0) ||
+        !(sigma > 0.0) || !(beta >= 0.0) || iters < 0 || ntv < 0 || (mode != CT_LOWDOSE && mode != CT_FEWVIEW) ||
+        (mode == CT_LOWDOSE && !w)) {
+        set_error("ct_unrolled: bad argument");
+        return CT_ERR_ARG;
+    }
+    if (!fft_supported(g)) {
+        set_error("ct_unrolled: n_bins %d is above the frequency-domain filter's limit", g->n_bins);
+        return CT_ERR_ARG;
+    }
+    return CT_OK;
+}
+
+void set_scalars(double *scal, double *scal2, double tau, double sigma, double beta, int mode, cudaStream_t st)
+{
+    const double lam = mode == CT_LOWDOSE ? tau * beta : tau;
+    launch_scalars(scal, SC_SET, tau, 0, 0, S_TAU, st);
+    launch_scalars(scal, SC_SET, sigma, 0, 0, S_SIGMA, st);
+    launch_scalars(scal, SC_SET, lam, 0, 0, S_LAMBDA, st);
+    launch_scalars(scal, SC_SET, lam > 0.0 ? 1.0 / (8.0 * lam) : 0.0, 0, 0, S_INV8LAM, st);
+    launch_scalars(scal, SC_SET, -tau, 0, 0, S_RED0, st);       // factor of mubar's adjoint
+    launch_scalars(scal, SC_SET, 0.0, 0, 0, U_LAMACC, st);
+    launch_scalars(scal, SC_SET, 0.0, 0, 0, U_INV8ACC, st);
+    launch_scalars(scal2, SC_SET, -1.0, 0, 0, S_TAU, st);       // backprojection that adds
+}
+
+}  // namespace
+
+extern "C" size_t ct_unrolled_workspace_bytes(const ct_geometry *geom, int batch, int half_len, int iters,
+                                              int tv_iters)
+{
+    if (!geom || batch < 1 || half_len < 1 || iters < 0 || tv_iters < 0) return 0;
+    return layout(geom, batch, half_len, iters, tv_iters).total;
+}
+
+extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b, const float *w, int batch,
+                                         const float *taps, int half_len, double tau, double sigma, double beta,
+                                         int mode, int iters, int tv_iters, float *x_out, void *workspace,
+                                         void *stream)
+{
+    const Geometry *g = geom;
+    set_error("%s", "");
+    ct_status cs = check_args(g, b, w, batch, taps, half_len, tau, sigma, beta, mode, iters, tv_iters, workspace);
+    if (cs != CT_OK) return cs;
+    if (!x_out) {
+        set_error("ct_unrolled_forward: x_out is NULL");
+        return CT_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int S = batch, N = g->n, lowdose = mode == CT_LOWDOSE;
+    const size_t J = (size_t)N * N, I = (size_t)g->n_views * g->n_bins;
+    const UL L = layout(g, S, half_len, iters, tv_iters);
+    char *ws = static_cast<char *>(workspace);
+    double *scal = (double *)(ws + L.scal), *scal2 = (double *)(ws + L.scal2);
+    float2 *hhat = (float2 *)(ws + L.hhat);
+    float *winv = (float *)(ws + L.winv), *z = (float *)(ws + L.z), *band = (float *)(ws + L.band);
+    float *tmpa = (float *)(ws + L.gp), *tmpb = (float *)(ws + L.gp2);
+
+    cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
+    cudaMemsetAsync(scal2, 0, sizeof(double) * S_COUNT, st);
+    set_scalars(scal, scal2, tau, sigma, beta, mode, st);
+    launch_hhat(g, taps, half_len, hhat, st);
+    if (lowdose) launch_recip(w, winv, S * I, st);
+    CK c0 = ck_at(ws, L, g, S, 0);
+    cudaMemsetAsync(c0.x, 0, sizeof(float) * S * J, st);
+    cudaMemsetAsync(c0.mu, 0, sizeof(float) * S * I, st);
+    cudaMemsetAsync(c0.p, 0, sizeof(float) * S * 2 * J, st);
+    launch_filter_fft(g, hhat, b, c0.mubar, nullptr, nullptr, 1, scal, S, st);      // mubar_0 = -sigma D b
+    for (int k = 0; k < iters; ++k) {
+        CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
+        launch_backproject(g, c.mubar, z, 1, c.x, scal, S, st);                     // z = x - tau A^T mubar
+        if (tv_iters == 0) {
+            cudaMemcpyAsync(n.p, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
+        } else {
+            const float *src = c.p;
+            for (int l = 0; l < tv_iters; ++l) {
+                float *dst = (l == tv_iters - 1) ? n.p : ((l & 1) ? tmpb : tmpa);
+                launch_tv_step(z, src, dst, N, S, scal, st);
+                src = dst;
+            }
+        }
+        launch_tv_final(z, n.p, n.x, N, S, scal, st);                               // x_{k+1}
+        launch_project_bands(g, n.x, band, S, st);
+        launch_dual_fft_batched(g, hhat, band, b, c.mu, n.mu, n.mubar, winv, lowdose, scal, S, st);
+    }
+    cudaMemcpyAsync(x_out, ck_at(ws, L, g, S, iters).x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("ct_unrolled_forward: %s", cudaGetErrorString(e));
+        return CT_ERR_CUDA;
+    }
+    return CT_OK;
+}
+
+extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *b, const float *w, int batch,
+                                          const float *taps, int half_len, double tau, double sigma, double beta,
+                                          int mode, int iters, int tv_iters, const float *grad_x, float *grad,
+                                          void *workspace, void *stream)
+{
+    const Geometry *g = geom;
+    set_error("%s", "");
+    ct_status cs = check_args(g, b, w, batch, taps, half_len, tau, sigma, beta, mode, iters, tv_iters, workspace);
+    if (cs != CT_OK) return cs;
+    if (!grad_x || !grad) {
+        set_error("ct_unrolled_backward: NULL gradient pointer");
+        return CT_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int S = batch, N = g->n, V = g->n_views, lowdose = mode == CT_LOWDOSE;
+    const size_t J = (size_t)N * N, I = (size_t)V * g->n_bins;
+    const UL L = layout(g, S, half_len, iters, tv_iters);
+    char *ws = static_cast<char *>(workspace);
+    double *scal = (double *)(ws + L.scal), *scal2 = (double *)(ws + L.scal2);
+    const float2 *hhat = (const float2 *)(ws + L.hhat);
+    const float *winv = (const float *)(ws + L.winv);
+    float *z = (float *)(ws + L.z), *band = (float *)(ws + L.band);
+    float *gx = (float *)(ws + L.gx), *gz = (float *)(ws + L.gz);
+    float *gp = (float *)(ws + L.gp), *gp2 = (float *)(ws + L.gp2), *gq = (float *)(ws + L.gq);
+    float *gm = (float *)(ws + L.gm), *gmb = (float *)(ws + L.gmb), *gmu = (float *)(ws + L.gmu);
+    float *gr = (float *)(ws + L.gr), *gm1 = (float *)(ws + L.gm1), *rr = (float *)(ws + L.rr),
+          *vv = (float *)(ws + L.vv);
+    float *traj = (float *)(ws + L.traj);
+    double *pa = (double *)(ws + L.pa), *pb = (double *)(ws + L.pb);
+    double *tcorr = (double *)(ws + L.tcorr), *tacc = (double *)(ws + L.tacc);
+    const size_t npx = tv_px_blocks(N, S);
+    const int nl = 2 * half_len - 1;
+    const double lam = lowdose ? tau * beta : tau;
+
+    // the scalars of the forward pass are still in the workspace; reset the accumulators
+    set_scalars(scal, scal2, tau, sigma, beta, mode, st);
+    cudaMemsetAsync(gm, 0, sizeof(float) * S * I, st);
+    cudaMemsetAsync(gmb, 0, sizeof(float) * S * I, st);
+    cudaMemsetAsync(gp, 0, sizeof(float) * S * 2 * J, st);
+    cudaMemsetAsync(tacc, 0, sizeof(double) * nl, st);
+    cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
+    for (int k = iters - 1; k >= 0; --k) {
+        CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
+        // recompute z_k and the prox trajectory p_k = traj[0] .. traj[n_tv]
+        launch_backproject(g, c.mubar, z, 1, c.x, scal, S, st);
+        cudaMemcpyAsync(traj, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
+        for (int l = 0; l < tv_iters; ++l)
+            launch_tv_step(z, traj + (size_t)l * S * 2 * J, traj + (size_t)(l + 1) * S * 2 * J, N, S, scal, st);
+        // adjoint of the dual step (needs A x_{k+1} for the residual)
+        launch_project_bands(g, n.x, band, S, st);
+        launch_dual_bwd_fft(g, hhat, band, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv, lowdose, scal, S, st);
+        launch_tapcorr_acc(gm1, rr, S * V, g->n_bins, half_len, sigma, tcorr, tacc, st);
+        if (lowdose) launch_tapcorr_acc(gmb, vv, S * V, g->n_bins, half_len, -sigma, tcorr, tacc, st);
+        // dL/dx_{k+1} += A^T dL/dr  (into gz, then swapped)
+        launch_backproject(g, gr, gz, 1, gx, scal2, S, st);
+        std::swap(gx, gz);
+        // adjoint of the prox: final step, then the n_tv steps in reverse
+        const float *trn = traj + (size_t)tv_iters * S * 2 * J;
+        launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, pb, st);
+        launch_sum_partials(pb, npx, scal, U_LAMACC, 1.0, st);
+        for (int l = tv_iters - 1; l >= 0; --l) {
+            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gq, gz, gp, N, S, scal, pa, pb, st);
+            launch_sum_partials(pa, npx, scal, U_INV8ACC, 1.0, st);
+            launch_sum_partials(pb, npx, scal, U_LAMACC, 1.0, st);
+            std::swap(gp, gp2);
+        }
+        std::swap(gp, gp2);   // gp: dL/dp_k
+        // x_k enters through z_k only: dL/dx_k = dL/dz_k; dL/dmubar_k = -tau A dL/dz_k
+        std::swap(gx, gz);
+        launch_project_bands(g, gx, band, S, st);
+        launch_band_reduce_scaled(g, band, gmb, scal + S_RED0, S, st);
+        std::swap(gm, gmu);   // dL/dmu_k
+    }
+    // mubar_0 = -sigma D b
+    launch_tapcorr_acc(gmb, b, S * V, g->n_bins, half_len, -sigma, tcorr, tacc, st);
+    // dL/dbeta = dL/dlambda dlambda/dbeta, dL/dlambda = lamacc + inv8acc d(1/(8 lam))/dlam
+    if (lam > 0.0) launch_scalars(scal, SC_AXPY_SLOT, -1.0 / (8.0 * lam * lam), (double)U_INV8ACC, 0, U_LAMACC, st);
+    launch_grad_out(tacc, nl, scal, U_LAMACC, lowdose ? tau : 0.0, grad, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("ct_unrolled_backward: %s", cudaGetErrorString(e));
+        return CT_ERR_CUDA;
+    }
+    return CT_OK;
+}

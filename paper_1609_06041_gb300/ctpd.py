@@ -60,6 +60,9 @@ EXPORTS = {
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
                        ctypes.POINTER(ct_pdtv_report), _vp], _i),
+    "ct_unrolled_workspace_bytes": ([_vp, _i, _i, _i, _i], ctypes.c_size_t),
+    "ct_unrolled_forward": ([_vp, _vp, _vp, _i, _vp, _i, _d, _d, _d, _i, _i, _i, _vp, _vp, _vp], _i),
+    "ct_unrolled_backward": ([_vp, _vp, _vp, _i, _vp, _i, _d, _d, _d, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
     "ct_pdtv_solve_batched": ([_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.POINTER(ct_pdtv_params), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.POINTER(ct_pdtv_report), _vp], _i),
@@ -299,3 +302,39 @@ def ct_pdtv_solve_batched(slices, reports=True):
     """Solve a list of (Geometry, b, w or None, PDTVParams) slices in one call."""
     bs = BatchedSolve(slices)
     return bs.run(reports=reports)
+
+
+def ct_unrolled_workspace_bytes(g: Geometry, batch: int, half_len: int, iters: int, tv_iters: int) -> int:
+    return int(_lib.ct_unrolled_workspace_bytes(g.handle, int(batch), int(half_len), int(iters), int(tv_iters)))
+
+
+def ct_unrolled_forward(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, taps: torch.Tensor,
+                        tau: float, sigma: float, beta: float, mode: int, iters: int, tv_iters: int,
+                        workspace: torch.Tensor, x_out: torch.Tensor | None = None) -> torch.Tensor:
+    """x_K of the unrolled iteration (batch over b's leading dims); the
+    per-iteration checkpoints stay in `workspace` for ct_unrolled_backward."""
+    pb = _dev(b, "b", (g.n_views, g.n_bins))
+    batch = _batch(b, 2)
+    pw = None if w is None else _dev(w, "w", (g.n_views, g.n_bins))
+    half = (taps.numel() + 1) // 2
+    if x_out is None:
+        x_out = torch.empty(*b.shape[:-2], g.n, g.n, device=b.device, dtype=torch.float32)
+    _check(_lib.ct_unrolled_forward(g.handle, pb, pw, batch, _dev(taps, "taps"), half, float(tau), float(sigma),
+                                    float(beta), int(mode), int(iters), int(tv_iters),
+                                    _dev(x_out, "x_out", (g.n, g.n)), ctypes.c_void_p(workspace.data_ptr()),
+                                    _stream()))
+    return x_out
+
+
+def ct_unrolled_backward(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, taps: torch.Tensor,
+                         tau: float, sigma: float, beta: float, mode: int, iters: int, tv_iters: int,
+                         grad_x: torch.Tensor, workspace: torch.Tensor) -> torch.Tensor:
+    """(dL/dtaps, dL/dbeta) as one float tensor of 2*half_len values."""
+    half = (taps.numel() + 1) // 2
+    grad = torch.empty(2 * half, device=b.device, dtype=torch.float32)
+    _check(_lib.ct_unrolled_backward(g.handle, _dev(b, "b", (g.n_views, g.n_bins)),
+                                     None if w is None else _dev(w, "w", (g.n_views, g.n_bins)), _batch(b, 2),
+                                     _dev(taps, "taps"), half, float(tau), float(sigma), float(beta), int(mode),
+                                     int(iters), int(tv_iters), _dev(grad_x.contiguous(), "grad_x", (g.n, g.n)),
+                                     _dev(grad, "grad"), ctypes.c_void_p(workspace.data_ptr()), _stream()))
+    return grad

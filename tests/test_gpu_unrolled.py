@@ -1,0 +1,122 @@
+"""The differentiable form: the unrolled solve's forward against the FP64
+oracle, and its hand-written backward (dL/dtaps, dL/dbeta) against FP64
+central finite differences of the oracle's loss."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_util import need_gpu, rel_l2, to_gpu, to_np, f32
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(N, V, B, S, seed, i0=1e4):
+    xs, bs, ws = [], [], []
+    for s in range(S):
+        x = synth.ellipse_phantom(N, 5, seed + s) * (2.0 / N)
+        b, w = synth.poisson_data(O.project(x, V, B), i0, seed + 50 + s)
+        xs.append(x)
+        bs.append(f32(b))
+        ws.append(f32(w))
+    return np.stack(xs), np.stack(bs), np.stack(ws)
+
+
+def steps_for(V, B, bs, ws, half):
+    kappa = float(np.mean(1.0 / ws))
+    tau = O.default_tau(0, V, kappa)
+    taps = f32(O.ramp_taps(0, V, B, tau, kappa, half=half))
+    return tau, taps
+
+
+def oracle_loss(bs, ws, xt, taps, beta, tau, sigma, K, ntv, N):
+    L = 0.0
+    for s in range(bs.shape[0]):
+        st, _ = O.pdtv(bs[s], ws[s], taps, 0, beta, tau, sigma, ntv, K, N)
+        L += float(((st.x - xt[s]) ** 2).sum())
+    return L / (bs.shape[0] * N * N)
+
+
+def test_unrolled_forward_matches_oracle():
+    P = need_gpu()
+    N, V, B, S, K, ntv, half = 32, 45, 47, 2, 5, 6, 16
+    xt, bs, ws = make_batch(N, V, B, S, 3)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.02
+    g = P.Geometry(N, V, B)
+    work = P.ct_pdtv_workspace_bytes  # noqa: F841  (keeps the binding import visible)
+    import torch
+    wsp = torch.empty(P.ct_unrolled_workspace_bytes(g, S, half, K, ntv), dtype=torch.uint8, device="cuda")
+    x = P.ct_unrolled_forward(g, to_gpu(bs), to_gpu(ws), to_gpu(taps), tau, sigma, beta, 0, K, ntv, wsp)
+    for s in range(S):
+        st, _ = O.pdtv(bs[s], ws[s], taps, 0, beta, tau, sigma, ntv, K, N)
+        assert rel_l2(to_np(x[s]), st.x) <= 1e-3
+
+
+def test_unrolled_gradients_match_fp64_finite_differences():
+    P = need_gpu()
+    import torch
+    N, V, B, S, K, ntv, half = 24, 30, 35, 2, 4, 5, 8
+    xt, bs, ws = make_batch(N, V, B, S, 7)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.05
+    g = P.Geometry(N, V, B)
+    t = to_gpu(taps).requires_grad_(True)
+    bt = torch.tensor(beta, device="cuda", requires_grad=True)
+    x = P.UnrolledPDTV.apply(t, bt, g, to_gpu(bs), to_gpu(ws), tau, sigma, 0, K, ntv)
+    loss = ((x - to_gpu(xt)) ** 2).sum() / (S * N * N)
+    loss.backward()
+    gt, gb = to_np(t.grad), float(bt.grad)
+    L0 = oracle_loss(bs, ws, xt, taps, beta, tau, sigma, K, ntv, N)
+    assert abs(float(loss.detach()) - L0) <= 1e-4 * L0
+    # beta
+    hb = 1e-3 * beta
+    fd_b = (oracle_loss(bs, ws, xt, taps, beta + hb, tau, sigma, K, ntv, N) -
+            oracle_loss(bs, ws, xt, taps, beta - hb, tau, sigma, K, ntv, N)) / (2 * hb)
+    assert gb == pytest.approx(fd_b, rel=2e-2, abs=1e-3 * abs(fd_b) + 1e-12)
+    # taps: two random directions and the centre tap
+    rng = np.random.default_rng(0)
+    dirs = [rng.standard_normal(taps.size), np.eye(taps.size)[half - 1]]
+    for d in dirs:
+        eps = 1e-3 * np.abs(taps).max() / np.abs(d).max()
+        fd = (oracle_loss(bs, ws, xt, taps + eps * d, beta, tau, sigma, K, ntv, N) -
+              oracle_loss(bs, ws, xt, taps - eps * d, beta, tau, sigma, K, ntv, N)) / (2 * eps)
+        got = float(gt @ d)
+        assert got == pytest.approx(fd, rel=2e-2, abs=1e-3 * np.abs(gt).sum() * np.abs(d).max())
+
+
+def test_project_backproject_autograd_are_adjoint():
+    P = need_gpu()
+    import torch
+    N, V, B = 40, 30, 57
+    g = P.Geometry(N, V, B)
+    x = to_gpu(synth.random_image(N, 1)).requires_grad_(True)
+    y = to_gpu(synth.random_sinogram(V, B, 2))
+    (P.project(g, x) * y).sum().backward()
+    assert rel_l2(to_np(x.grad), to_np(P.ct_backproject(g, y))) < 1e-6
+    y2 = y.clone().requires_grad_(True)
+    (P.backproject(g, y2) * x.detach()).sum().backward()
+    assert rel_l2(to_np(y2.grad), to_np(P.ct_project(g, x.detach()))) < 1e-6
+
+
+def test_unrolled_module_at_scale():
+    # batch 16 of 256^2, 180 views, 368 bins, 10 unrolled iterations,
+    # learnable log beta and 128 one-sided taps: forward and backward run and
+    # give finite gradients of the MSE loss.
+    P = need_gpu()
+    import torch
+    N, V, B, S = 256, 180, 368, 16
+    g = P.Geometry(N, V, B)
+    xt = torch.from_numpy(np.stack([synth.ellipse_phantom(N, 10, s) * (2.0 / N) for s in range(S)]).astype(np.float32)).cuda()
+    p = P.ct_project(g, xt).cpu().numpy()
+    b, w = synth.poisson_data(p, 1e4, 1)
+    b, w = to_gpu(b), to_gpu(w)
+    _, rep = P.ct_pdtv_solve(g, b[0], w[0], P.PDTVParams(mode=0, iters=0, beta=0.01))
+    taps0 = P.ct_ramp_taps(g, 0, rep["tau"], rep["kappa"])
+    m = P.UnrolledReconstructor(g, taps0, 0.01, rep["tau"], 0.9 * rep["sigma"], iters=10, tv_iters=10, half=128)
+    x = m(b, w)
+    loss = ((x - xt) ** 2).mean()
+    loss.backward()
+    assert torch.isfinite(loss)
+    assert torch.isfinite(m.taps_half.grad).all() and torch.isfinite(m.log_beta.grad)
+    assert float(m.taps_half.grad.abs().max()) > 0
