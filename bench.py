@@ -238,6 +238,58 @@ def measure_batched(P, steps=3, count=64, seed=0):
             "speedup": t_single / t_batched}
 
 
+def measure_unrolled(P, steps=3):
+    """Differentiable form: forward + backward of 10 unrolled iterations for a
+    batch of 16 slices (256^2, 180 views, 368 bins, I0 = 1e4) with learnable
+    log beta and 128 one-sided taps, MSE loss; against the plain solve of one
+    such slice (10 iterations, setup included)."""
+    import torch
+    N, V, B, S = 256, 180, 368, 16
+    g = P.Geometry(N, V, B)
+    xt = torch.from_numpy(np.stack([synth.ellipse_phantom(N, 10, s) * (2.0 / N) for s in range(S)])
+                          .astype(np.float32)).cuda()
+    p = P.ct_project(g, xt).cpu().numpy()
+    bb, ww = synth.poisson_data(p, 1e4, 1)
+    b = torch.from_numpy(bb.astype(np.float32)).cuda()
+    w = torch.from_numpy(ww.astype(np.float32)).cuda()
+    _, rep = P.ct_pdtv_solve(g, b[0], w[0], P.PDTVParams(mode=0, iters=0, beta=0.01))
+    taps0 = P.ct_ramp_taps(g, 0, rep["tau"], rep["kappa"])
+    m = P.UnrolledReconstructor(g, taps0, 0.01, rep["tau"], 0.9 * rep["sigma"], iters=10, tv_iters=10, half=128)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        m.zero_grad(set_to_none=True)
+        loss = ((m(b, w) - xt) ** 2).mean()
+        loss.backward()
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fb = e0.elapsed_time(e1) / steps
+    prm = P.PDTVParams(mode=0, iters=10, beta=0.01)
+    wsp = P.workspace_for(g, prm)
+    x1 = torch.empty(N, N, device="cuda")
+    for _ in range(2):
+        P.ct_pdtv_solve(g, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps * 4):
+        P.ct_pdtv_solve(g, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_one = e0.elapsed_time(e1) / (steps * 4)
+    return {"workload": "16 slices of 256^2, 180 views, 368 bins, I0 1e4, 10 unrolled iterations, "
+                        "learnable log beta + 128 taps, MSE loss, forward + backward",
+            "fwd_bwd_slices_per_s": S / (t_fb / 1e3), "fwd_bwd_ms": t_fb,
+            "plain_solve_slices_per_s": 1.0 / (t_one / 1e3), "plain_solve_ms": t_one}
+
+
 # ----------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------
@@ -376,7 +428,7 @@ def run_ours(args):
 
     forms = None
     if not args.no_forms:
-        forms = {"batched": measure_batched(P)}
+        forms = {"batched": measure_batched(P), "differentiable": measure_unrolled(P)}
 
     clocks = sampler.summary()
     if rank == 0:

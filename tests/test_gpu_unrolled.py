@@ -73,16 +73,16 @@ def test_unrolled_gradients_match_fp64_finite_differences():
     hb = 1e-3 * beta
     fd_b = (oracle_loss(bs, ws, xt, taps, beta + hb, tau, sigma, K, ntv, N) -
             oracle_loss(bs, ws, xt, taps, beta - hb, tau, sigma, K, ntv, N)) / (2 * hb)
-    assert gb == pytest.approx(fd_b, rel=2e-2, abs=1e-3 * abs(fd_b) + 1e-12)
+    assert gb == pytest.approx(fd_b, rel=1e-4)
     # taps: two random directions and the centre tap
     rng = np.random.default_rng(0)
     dirs = [rng.standard_normal(taps.size), np.eye(taps.size)[half - 1]]
     for d in dirs:
-        eps = 1e-3 * np.abs(taps).max() / np.abs(d).max()
+        eps = 1e-4 * np.abs(taps).max() / np.abs(d).max()
         fd = (oracle_loss(bs, ws, xt, taps + eps * d, beta, tau, sigma, K, ntv, N) -
               oracle_loss(bs, ws, xt, taps - eps * d, beta, tau, sigma, K, ntv, N)) / (2 * eps)
         got = float(gt @ d)
-        assert got == pytest.approx(fd, rel=2e-2, abs=1e-3 * np.abs(gt).sum() * np.abs(d).max())
+        assert got == pytest.approx(fd, rel=3e-3)
 
 
 def test_project_backproject_autograd_are_adjoint():
