@@ -51,6 +51,23 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(t_ms, device="cpu"):
+    """The slowest rank's time (replicas: no collective on the data path,
+    one all-reduce of this scalar after the timed region)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(t_ms)
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(units_per_rank, world, t_ms):
+    """Whole-job throughput: units all ranks processed / slowest rank's time."""
+    return units_per_rank * world / (t_ms / 1e3)
+
+
 def phantom(seed):
     return synth.ellipse_phantom(WORK["n"], WORK["ellipses"], seed) * (2.0 / WORK["n"])
 
@@ -350,13 +367,8 @@ def run_ours(args):
     launches = P.ct_kernel_launches() - launches0
     if world > 1:
         dist.barrier()
-    t_ms = sum(a.elapsed_time(c) for a, c in ev)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    iters_total = WORK["iters"] * args.steps * world
-    value = iters_total / (t_ms / 1e3)
+    t_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), device="cuda")
+    value = job_value(WORK["iters"] * args.steps, world, t_ms)
 
     # ---- breakdown: setup vs iterations (resume runs iterations only) ----
     _, rep = P.ct_pdtv_solve(g, b, w, prm, x_out=x, workspace=ws, report=True)
@@ -423,11 +435,11 @@ def run_ours(args):
         e2e_step()
         ee[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(c) for a, c in ee)
-    e2e_value = WORK["iters"] * args.steps * world / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ee), device="cuda")
+    e2e_value = job_value(WORK["iters"] * args.steps, world, e2e_ms)
 
     forms = None
-    if not args.no_forms:
+    if not args.no_forms and world == 1:
         forms = {"batched": measure_batched(P), "differentiable": measure_unrolled(P)}
 
     clocks = sampler.summary()
