@@ -73,7 +73,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, total;
+    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, total;
 };
 
 Layout layout(const Geometry *g)
@@ -95,6 +95,7 @@ Layout layout(const Geometry *g)
     L.p0 = o;       o += align256(sizeof(float) * 2 * J);
     L.p1 = o;       o += align256(sizeof(float) * 2 * J);
     L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
+    L.orb = o;      o += align256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, 1) : 1));
     L.total = o;
     return L;
 }
@@ -155,6 +156,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     g->n_bins = n_bins;
     g->n_fft = 1;
     while (g->n_fft < 2 * n_bins) g->n_fft <<= 1;
+    g->orbit = !angles && (n_views % 2 == 0) && (n % 2 == 0);
     cudaGetDevice(&g->device);
     g->h_angles = new double[n_views];
     // candidate-window margin of the backprojector (bins): a generous bound
@@ -271,7 +273,20 @@ ct_status ct_backproject(const ct_geometry *g, const float *sino, float *img, in
     if (batch == 0) return CT_OK;
     if (!img || !sino) return fail(CT_ERR_ARG, "ct_backproject: NULL pointer");
     if (!aligned16(img) || !aligned16(sino)) return fail(CT_ERR_ARG, "ct_backproject: pointers must be 16-byte aligned");
-    launch_backproject(g, sino, img, 0, nullptr, nullptr, batch, S(stream));
+    if (!orbit_ok(g)) {
+        launch_backproject(g, sino, img, 0, nullptr, nullptr, batch, S(stream));
+        return cuda_check("ct_backproject");
+    }
+    // slice images of the orbit form: stream-ordered scratch, freed after use
+    const size_t bytes = sizeof(float) * orbit_partial_floats(g, batch);
+    float *partial = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&partial, bytes, S(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CT_ERR_OOM, "ct_backproject: scratch allocation failed (%zu bytes)", bytes);
+    }
+    launch_backproject_orbit(g, sino, img, 0, nullptr, nullptr, batch, partial, S(stream));
+    cudaFreeAsync(partial, S(stream));
     return cuda_check("ct_backproject");
 }
 
@@ -360,6 +375,12 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
     float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u), *w3img = (float *)(ws + L.w3);
     float *band = (float *)(ws + L.band);
+    float *orb = (float *)(ws + L.orb);
+    // A^T, by rotation orbits when the geometry allows
+    auto backproject = [&](const float *yy, float *out, int md, const float *xin) {
+        if (orbit_ok(g)) launch_backproject_orbit(g, yy, out, md, xin, scal, 1, orb, st);
+        else launch_backproject(g, yy, out, md, xin, scal, 1, st);
+    };
     float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};
     const int half = prm->precond ? g->n_bins : 1;
     const int lowdose = mode == CT_LOWDOSE;
@@ -390,7 +411,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
                 if (use_fft) launch_filter_fft(g, hhat, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
                 else launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
-                launch_backproject(g, mubar, out, 0, nullptr, nullptr, 1, st);
+                backproject(mubar, out, 0, nullptr);
             };
             lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, partials, ticket, S_NADA, st);
             if (lowdose) {
@@ -426,7 +447,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     int cur = (int)((k0 * chunks) & 1);
     for (int k = 0; k < prm->iters; ++k) {
         // Step 2: z = x^k - tau A^T mu_bar ; x^{k+1} = prox_{tau g}(z)
-        launch_backproject(g, mubar, z, 1, x_out, scal, 1, st);
+        backproject(mubar, z, 1, x_out);
         int left = ntv;
         do {
             int steps = std::min(left, chunk);

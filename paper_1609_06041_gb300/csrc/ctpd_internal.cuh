@@ -39,6 +39,7 @@ struct Geometry {
     int *d_col_list;      // device, the n_col column-stepping view indices
     float4 *d_trig;       // device, per view (cos t, sin t, |a|, 1 - |a|/2) for A^T
     float2 *d_tw;         // device, n_fft twiddles e^{-2 pi i k / P} (from double precision)
+    int orbit;            // default angles with V and N even: A^T by rotation orbits
     double *h_angles;     // host copy
 };
 
@@ -108,7 +109,12 @@ void launch_band_reduce(const Geometry *g, const float *partial, float *out, int
                         const float *b, const float *winv, const float *mu, int batch,
                         cudaStream_t st);
 // Backprojection; mode 0: out = A^T y; mode 1: out = xin - tau*A^T y with
-// tau = (float)scal[S_TAU].
+// tau = (float)scal[S_TAU].  The orbit form needs orbit_partial_floats()
+// of scratch (ORB_SL partial images per image).
+bool orbit_ok(const Geometry *g);
+size_t orbit_partial_floats(const Geometry *g, int batch);
+void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
+                              const double *scal, int batch, float *partial, cudaStream_t st);
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
                         const float *xin, const double *scal, int batch, cudaStream_t st);
 

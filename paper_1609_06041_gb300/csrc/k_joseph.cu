@@ -346,6 +346,151 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
     }
 }
 
+// =====================================================================
+// Backprojection by rotation orbits (default angles, V and N even).
+// View v + V/2 is view v turned by 90 degrees and the detector mirror
+// d -> B-1-d is the turn by 180 degrees, so for a pixel P the detector
+// coordinate e of (P, view v) is also that of (R90 P, view v + V/2), and the
+// mirrored coordinate B-1-e is that of (R180 P, v) and (R270 P, v + V/2).
+// One weight evaluation (floor, fraction, two hat weights) therefore
+// serves four pixel-views; a block takes a 16 x 16 tile of one image
+// quadrant and evaluates, per base view v < V/2, the weights of P and of
+// R90 P, which cover all eight (pixel, view) pairs of the orbit
+// {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Base views are split into
+// ORB_SL slices (grid.z); each slice writes its own partial image and
+// k_orbit_reduce adds the slices in a fixed order.  The weights are the
+// pixel-side Joseph weights of k_backproject_tiles, so both kernels compute
+// the same A^T.
+// =====================================================================
+constexpr int ORB_T = 16;        // quadrant tile side
+constexpr int ORB_SL = 4;        // base-view slices
+constexpr int ORB_VC = 16;       // base views staged per chunk
+constexpr int ORB_WW = 32;       // staged ray pairs per window
+
+__global__ void __launch_bounds__(256)
+k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
+                    int N, int V, int B)
+{
+    // tab[view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][pair]
+    __shared__ float2 tab[ORB_VC][2][4][ORB_WW];
+    __shared__ float4 sv[ORB_VC];
+    __shared__ int wb[ORB_VC][2];     // window bases of e and e90
+    const int tid = threadIdx.y * ORB_T + threadIdx.x;
+    const int half = N / 2, V2 = V / 2;
+    const int slice = blockIdx.z % ORB_SL, img = blockIdx.z / ORB_SL;
+    const int r0 = blockIdx.y * ORB_T, c0 = half + blockIdx.x * ORB_T;   // quadrant r < N/2, c >= N/2
+    const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
+    const bool inside = r < half && c < N;
+    const float h = 0.5f * (float)(N - 1), hb_lo = 0.5f * (float)(B - 1) - 0.5f;
+    const float xq = (float)c - h, yq = (float)r - h;               // P = (x, y); R90 P = (-y, x)
+    const float *ys = y + (size_t)img * V * B;
+    const int vb0 = (int)((long long)V2 * slice / ORB_SL), vb1 = (int)((long long)V2 * (slice + 1) / ORB_SL);
+    float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
+
+    for (int v0 = vb0; v0 < vb1; v0 += ORB_VC) {
+        const int nv = min(ORB_VC, vb1 - v0);
+        __syncthreads();
+        if (tid < nv) {
+            const float4 T = trig[v0 + tid];
+            sv[tid] = T;
+            float emin = 3.0e38f, e9min = 3.0e38f;
+#pragma unroll
+            for (int cr = 0; cr < 4; ++cr) {
+                const float xx = (float)(c0 + (cr & 1) * (ORB_T - 1)) - h;
+                const float yy = (float)(r0 + (cr >> 1) * (ORB_T - 1)) - h;
+                emin = fminf(emin, xx * T.x + yy * T.y);
+                e9min = fminf(e9min, -yy * T.x + xx * T.y);
+            }
+            const float hb = 0.5f * (float)(B - 1);
+            emin = fminf(fmaxf(emin + hb, -1.0e6f), 1.0e6f);
+            e9min = fminf(fmaxf(e9min + hb, -1.0e6f), 1.0e6f);
+            wb[tid][0] = (int)floorf(emin) - 2;
+            wb[tid][1] = (int)floorf(e9min) - 2;
+        }
+        __syncthreads();
+        // window entries: (y[base + k], y[base + k + 1]) * |a|; the mirror
+        // window of base wb starts at B - 33 - wb and holds pair (B-2-f) at 31 - (f - wb)
+        for (int k = tid; k < nv * 2 * 4 * ORB_WW; k += 256) {
+            const int w = k % ORB_WW, win = (k / ORB_WW) % 4, row = (k / (ORB_WW * 4)) % 2, vi = k / (ORB_WW * 8);
+            const int base = wb[vi][win >> 1];
+            const int start = (win & 1) ? B - 33 - base : base;
+            const int d = start + w;
+            const float *yv = ys + (size_t)(v0 + vi + row * V2) * B;
+            const float sc = sv[vi].z;
+            const float y0 = (d >= 0 && d < B) ? yv[d] : 0.0f;
+            const float y1 = (d + 1 >= 0 && d + 1 < B) ? yv[d + 1] : 0.0f;
+            tab[vi][row][win][w] = make_float2(y0 * sc, y1 * sc);
+        }
+        __syncthreads();
+        if (inside) {
+            for (int vi = 0; vi < nv; ++vi) {
+                const float4 T = sv[vi];
+                // e - 1/2 of P and of R90 P
+                const float e = fmaf(xq, T.x, fmaf(yq, T.y, hb_lo));
+                const float e9 = fmaf(xq, T.y, fmaf(-yq, T.x, hb_lo));
+                const float t = __fadd_rn(e, JOSEPH_BIAS), t9 = __fadd_rn(e9, JOSEPH_BIAS);
+                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb[vi][0])), (unsigned)(ORB_WW - 1));
+                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb[vi][1])), (unsigned)(ORB_WW - 1));
+                const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
+                const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
+                const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
+                const float w09 = fmaxf(0.0f, fmaf(-g9, T.z, T.w)), w19 = fmaxf(0.0f, fmaf(g9, T.z, T.w));
+                const float2 pv = tab[vi][0][0][k], pvm = tab[vi][0][1][ORB_WW - 1 - k];
+                const float2 qv = tab[vi][1][0][k], qvm = tab[vi][1][1][ORB_WW - 1 - k];
+                const float2 pv9 = tab[vi][0][2][k9], pvm9 = tab[vi][0][3][ORB_WW - 1 - k9];
+                const float2 qv9 = tab[vi][1][2][k9], qvm9 = tab[vi][1][3][ORB_WW - 1 - k9];
+                aP = fmaf(w0, pv.x, fmaf(w1, pv.y, aP));           // P at v
+                a180 = fmaf(w1, pvm.x, fmaf(w0, pvm.y, a180));     // R180 P at v
+                a90 = fmaf(w0, qv.x, fmaf(w1, qv.y, a90));         // R90 P at v + V/2
+                a270 = fmaf(w1, qvm.x, fmaf(w0, qvm.y, a270));     // R270 P at v + V/2
+                a90 = fmaf(w09, pv9.x, fmaf(w19, pv9.y, a90));     // R90 P at v
+                a270 = fmaf(w19, pvm9.x, fmaf(w09, pvm9.y, a270)); // R270 P at v
+                a180 = fmaf(w09, qv9.x, fmaf(w19, qv9.y, a180));   // R180 P at v + V/2
+                aP = fmaf(w19, qvm9.x, fmaf(w09, qvm9.y, aP));     // P at v + V/2
+            }
+        }
+    }
+    if (inside) {
+        float *pp = partial + ((size_t)img * ORB_SL + slice) * N * N;
+        pp[(size_t)r * N + c] = aP;
+        pp[(size_t)c * N + (N - 1 - r)] = a90;                   // R90 (r, c) = (c, N-1-r)
+        pp[(size_t)(N - 1 - r) * N + (N - 1 - c)] = a180;        // R180 (r, c) = (N-1-r, N-1-c)
+        pp[(size_t)(N - 1 - c) * N + r] = a270;                  // R270 (r, c) = (N-1-c, r)
+    }
+}
+
+// out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
+template <int MODE>
+__global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restrict__ out, const float *xin,
+                               const double *__restrict__ scal, size_t NN)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= NN) return;
+    const float *pp = partial + (size_t)blockIdx.y * ORB_SL * NN + i;
+    float t = pp[0];
+#pragma unroll
+    for (int s = 1; s < ORB_SL; ++s) t += pp[s * NN];
+    const size_t o = (size_t)blockIdx.y * NN + i;
+    if (MODE == 0) out[o] = t;
+    else out[o] = xin[o] - (float)scal[S_TAU] * t;
+}
+
+bool orbit_ok(const Geometry *g) { return g->orbit; }
+size_t orbit_partial_floats(const Geometry *g, int batch) { return (size_t)ORB_SL * g->n * g->n * batch; }
+
+void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
+                              const double *scal, int batch, float *partial, cudaStream_t st)
+{
+    const int q = g->n / 2;
+    dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, ORB_SL * batch);
+    counted(2);
+    k_backproject_orbit<<<grd, dim3(ORB_T, ORB_T), 0, st>>>(y, partial, g->d_trig, g->n, g->n_views, g->n_bins);
+    const size_t NN = (size_t)g->n * g->n;
+    dim3 g2((unsigned)((NN + 255) / 256), batch);
+    if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
+    else k_orbit_reduce<1><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
+}
+
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
                         const float *xin, const double *scal, int batch, cudaStream_t st)
 {

@@ -24,7 +24,7 @@ namespace {
 
 struct UL {
     size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gq, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa, pb,
-        tcorr, tacc, total;
+        tcorr, tacc, orb, total;
     size_t ck_stride;   // floats per checkpoint
 };
 
@@ -60,6 +60,7 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.pb = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
     L.tcorr = o; o += a256(sizeof(double) * tapcorr_partials(S * g->n_views, half));
     L.tacc = o;  o += a256(sizeof(double) * (2 * (size_t)half - 1));
+    L.orb = o;   o += a256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, S) : 1));
     L.total = o;
     return L;
 }
@@ -111,6 +112,13 @@ void set_scalars(double *scal, double *scal2, double tau, double sigma, double b
     launch_scalars(scal2, SC_SET, -1.0, 0, 0, S_TAU, st);       // backprojection that adds
 }
 
+void backproject(const Geometry *g, const float *y, float *out, int mode, const float *xin, const double *scal,
+                 int S, char *ws, const UL &L, cudaStream_t st)
+{
+    if (orbit_ok(g)) launch_backproject_orbit(g, y, out, mode, xin, scal, S, (float *)(ws + L.orb), st);
+    else launch_backproject(g, y, out, mode, xin, scal, S, st);
+}
+
 }  // namespace
 
 extern "C" size_t ct_unrolled_workspace_bytes(const ct_geometry *geom, int batch, int half_len, int iters,
@@ -155,7 +163,7 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
     launch_filter_fft(g, hhat, b, c0.mubar, nullptr, nullptr, 1, scal, S, st);      // mubar_0 = -sigma D b
     for (int k = 0; k < iters; ++k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
-        launch_backproject(g, c.mubar, z, 1, c.x, scal, S, st);                     // z = x - tau A^T mubar
+        backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);                       // z = x - tau A^T mubar
         if (tv_iters == 0) {
             cudaMemcpyAsync(n.p, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
         } else {
@@ -223,7 +231,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
         // recompute z_k and the prox trajectory p_k = traj[0] .. traj[n_tv]
-        launch_backproject(g, c.mubar, z, 1, c.x, scal, S, st);
+        backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);
         cudaMemcpyAsync(traj, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
         for (int l = 0; l < tv_iters; ++l)
             launch_tv_step(z, traj + (size_t)l * S * 2 * J, traj + (size_t)(l + 1) * S * 2 * J, N, S, scal, st);
@@ -233,7 +241,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
         launch_tapcorr_acc(gm1, rr, S * V, g->n_bins, half_len, sigma, tcorr, tacc, st);
         if (lowdose) launch_tapcorr_acc(gmb, vv, S * V, g->n_bins, half_len, -sigma, tcorr, tacc, st);
         // dL/dx_{k+1} += A^T dL/dr  (into gz, then swapped)
-        launch_backproject(g, gr, gz, 1, gx, scal2, S, st);
+        backproject(g, gr, gz, 1, gx, scal2, S, ws, L, st);
         std::swap(gx, gz);
         // adjoint of the prox: final step, then the n_tv steps in reverse
         const float *trn = traj + (size_t)tv_iters * S * 2 * J;
