@@ -156,7 +156,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     g->n_bins = n_bins;
     g->n_fft = 1;
     while (g->n_fft < 2 * n_bins) g->n_fft <<= 1;
-    g->orbit = !angles && (n_views % 2 == 0) && (n % 2 == 0);
+    g->orbit = !angles && (n_views % 2 == 0) && (n % 2 == 0);   // V <= 8192, so a slice has <= 1024 base views
     cudaGetDevice(&g->device);
     g->h_angles = new double[n_views];
     // candidate-window margin of the backprojector (bins): a generous bound

@@ -174,13 +174,155 @@ k_project_bands(const float *__restrict__ x, const ViewP *__restrict__ views,
     }
 }
 
+// ---------------------------------------------------------------------
+// Forward projection with the detector mirror (N a multiple of 32, one
+// staged pass).  Ray B-1-d meets step N-1-s at the mirrored coordinate
+// N-1-u of ray d at step s, so a block staging band A (steps s0 .. s0+15)
+// and band B (steps N-1-s0-15 .. N-1-s0) turned by 180 degrees (step and
+// pair order reversed) reads, for one evaluation of (u', g) at (d, s), the
+// sample of ray d in band A and of ray B-1-d in band B at the same shared
+// offset.  A thread takes the ray pair (d, B-1-d) and walks both rays; each
+// ray's partial covers both bands.  Partial slots: N/32 per image, like the
+// plain kernel's 32-step bands.
+// ---------------------------------------------------------------------
+constexpr int MR = 16;           // steps per band (two bands per block)
+static_assert(PG * 64 == PT, "one view of the group per 64 threads");
+static_assert(2 * MR == 32, "staging maps 32 lines (two bands) to 32 thread rows");
+
+__global__ void __launch_bounds__(PT)
+k_project_mirror(const float *__restrict__ x, const ViewP *__restrict__ views,
+                 const int *__restrict__ row_list, int n_row, const int *__restrict__ col_list, int n_col,
+                 int N, int V, int B, float *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int CW = N + 3, SP = CW | 1;
+    float2 *PA = reinterpret_cast<float2 *>(smraw);
+    float2 *PB = PA + (size_t)MR * SP;
+    ViewP *sv = reinterpret_cast<ViewP *>(PB + (size_t)MR * SP);
+    int *svi = reinterpret_cast<int *>(sv + PG);
+
+    const int bp = blockIdx.x, nbp = gridDim.x;
+    const int row_groups = (n_row + PG - 1) / PG;
+    const bool rows = (int)blockIdx.y < row_groups;
+    const int grp = rows ? blockIdx.y : blockIdx.y - row_groups;
+    const int *list = rows ? row_list : col_list;
+    const int nl = rows ? n_row : n_col;
+    const int nv = min(PG, nl - grp * PG);
+    const float *img = x + (size_t)blockIdx.z * N * N;
+    float *out = partial + ((size_t)blockIdx.z * nbp + bp) * V * B;
+    const int s0 = bp * MR;
+    const float h = joseph_h(N), hq = joseph_hq(N);
+    const int tid = threadIdx.x;
+
+    if (tid < nv) {
+        svi[tid] = list[grp * PG + tid];
+        sv[tid] = views[svi[tid]];
+    }
+    // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
+    // the line N-1-s0-t read backwards (image value at N-1-i).  Threads as
+    // 32 x 32: rows class -> lanes along the line; column class -> lanes
+    // across the 32 lines of both bands (coalesced image rows).
+    {
+        const int lx = tid & 31, ly = tid >> 5;
+        if (rows) {
+            const int band = ly >= MR, t = ly - band * MR;
+            const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
+            const float *rowp = img + (size_t)line * N;
+            float2 *dst = (band == 0 ? PA : PB) + t * SP;
+            for (int ii = lx; ii < CW; ii += 32) {
+                const int i = ii - 2;
+                const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
+                const float a = (ia >= 0 && ia < N) ? rowp[ia] : 0.0f;
+                const float b = (ib >= 0 && ib < N) ? rowp[ib] : 0.0f;
+                dst[ii] = make_float2(0.5f * (a + b), b - a);
+            }
+        } else {
+            const int band = lx >= MR, t = lx - band * MR;
+            const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
+            float2 *dst = (band == 0 ? PA : PB) + t * SP;
+            for (int ii = ly; ii < CW; ii += 32) {
+                const int i = ii - 2;
+                const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
+                const float a = (ia >= 0 && ia < N) ? img[(size_t)ia * N + line] : 0.0f;
+                const float b = (ib >= 0 && ib < N) ? img[(size_t)ib * N + line] : 0.0f;
+                dst[ii] = make_float2(0.5f * (a + b), b - a);
+            }
+        }
+    }
+    __syncthreads();
+    const int npair = (B + 1) / 2;
+    const unsigned top = (unsigned)(N + 2);
+    // thread -> view tid / 64 of the group, ray pairs (tid % 64) + 64 j
+    const int vi = tid >> 6;
+    if (vi >= nv) return;
+    for (int d = tid & 63; d < npair; d += 64) {
+        const int dm = B - 1 - d;
+        const float a = sv[vi].a, m = sv[vi].m, inv_m = sv[vi].inv_m;
+        float accA[2] = {0.0f, 0.0f}, accB[2] = {0.0f, 0.0f};   // [0]: ray d, [1]: ray dm
+#pragma unroll
+        for (int which = 0; which < 2; ++which) {
+            if (which == 1 && dm == d) break;
+            const int dd = which == 0 ? d : dm;
+            const float q = joseph_q(joseph_dp(dd, B), a, hq);
+            int lo, hi;
+            step_range(q, m, inv_m, h, -2.5f, (float)N + 0.5f, s0, s0 + MR - 1, lo, hi);
+            const float qu1 = __fadd_rn(q, m);
+            float spk = (float)lo - h;
+            int ridx = (lo - s0) * SP;
+            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+            int s = lo;
+            for (; s + 1 <= hi; s += 2) {
+                const float up0 = joseph_u(spk, m, q), up1 = joseph_u(spk, m, qu1);
+                const float t0 = __fadd_rn(up0, JOSEPH_BIAS), t1 = __fadd_rn(up1, JOSEPH_BIAS);
+                const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
+                const unsigned i1 = min((unsigned)(__float_as_int(t1) - (JOSEPH_BIAS_BITS - 2)), top);
+                const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
+                const float g1 = __fsub_rn(up1, __fsub_rn(t1, JOSEPH_BIAS));
+                const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
+                const float2 pa1 = PA[ridx + SP + (int)i1], pb1 = PB[ridx + SP + (int)i1];
+                a0 += __fmaf_rn(g0, pa0.y, pa0.x);
+                b0 += __fmaf_rn(g0, pb0.y, pb0.x);
+                a1 += __fmaf_rn(g1, pa1.y, pa1.x);
+                b1 += __fmaf_rn(g1, pb1.y, pb1.x);
+                spk = __fadd_rn(spk, 2.0f);
+                ridx += 2 * SP;
+            }
+            if (s <= hi) {
+                const float up0 = joseph_u(spk, m, q);
+                const float t0 = __fadd_rn(up0, JOSEPH_BIAS);
+                const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
+                const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
+                const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
+                a0 += __fmaf_rn(g0, pa0.y, pa0.x);
+                b0 += __fmaf_rn(g0, pb0.y, pb0.x);
+            }
+            // band A sample of ray dd; band B sample of its mirror ray
+            accA[which] = a0 + a1;
+            accB[1 - which] = b0 + b1;
+        }
+        float *o = out + (size_t)svi[vi] * B;
+        if (dm == d) {
+            o[d] = accA[0] + accB[1];
+        } else {
+            o[d] = accA[0] + accB[0];
+            o[dm] = accA[1] + accB[1];
+        }
+    }
+}
+
 void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st)
 {
     const int N = g->n;
     dim3 grd(proj_bands(N), (g->n_row + PG - 1) / PG + (g->n_col + PG - 1) / PG, batch);
     const size_t smem = proj_smem(N);
     counted();
-    if (N + 3 <= PROJ_CW)
+    if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
+        // two mirrored 16-step bands per block: N/32 partial slots, as below
+        dim3 grd2(N / (2 * MR), grd.y, batch);
+        const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + 64;
+        k_project_mirror<<<grd2, PT, smem2, st>>>(x, g->d_views, g->d_row_list, g->n_row, g->d_col_list, g->n_col,
+                                                 N, g->n_views, g->n_bins, partial);
+    } else if (N + 3 <= PROJ_CW)
         k_project_bands<false><<<grd, PT, smem, st>>>(x, g->d_views, g->d_row_list, g->n_row, g->d_col_list,
                                                       g->n_col, N, g->n_views, g->n_bins, partial);
     else
@@ -367,6 +509,8 @@ constexpr int ORB_SL = 4;        // base-view slices
 constexpr int ORB_VC = 16;       // base views staged per chunk
 constexpr int ORB_WW = 32;       // staged ray pairs per window
 
+constexpr int ORB_MAXS = 1024;   // base views per slice (V <= 8192)
+
 __global__ void __launch_bounds__(256)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
                     int N, int V, int B)
@@ -374,63 +518,79 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     // tab[view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][pair]
     __shared__ float2 tab[ORB_VC][2][4][ORB_WW];
     __shared__ float4 sv[ORB_VC];
-    __shared__ int wb[ORB_VC][2];     // window bases of e and e90
+    __shared__ int wbs[ORB_MAXS][2];     // window bases of e and e90, every base view of the slice
+    __shared__ float scs[ORB_MAXS];      // |a| of every base view of the slice
     const int tid = threadIdx.y * ORB_T + threadIdx.x;
     const int half = N / 2, V2 = V / 2;
     const int slice = blockIdx.z % ORB_SL, img = blockIdx.z / ORB_SL;
     const int r0 = blockIdx.y * ORB_T, c0 = half + blockIdx.x * ORB_T;   // quadrant r < N/2, c >= N/2
     const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
     const bool inside = r < half && c < N;
-    const float h = 0.5f * (float)(N - 1), hb_lo = 0.5f * (float)(B - 1) - 0.5f;
+    const float h = 0.5f * (float)(N - 1), hb = 0.5f * (float)(B - 1), hb_lo = hb - 0.5f;
     const float xq = (float)c - h, yq = (float)r - h;               // P = (x, y); R90 P = (-y, x)
     const float *ys = y + (size_t)img * V * B;
     const int vb0 = (int)((long long)V2 * slice / ORB_SL), vb1 = (int)((long long)V2 * (slice + 1) / ORB_SL);
+    const int nvs = vb1 - vb0;
     float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
 
+    // window bases of the tile for every base view of this slice
+    for (int vi = tid; vi < nvs; vi += 256) {
+        const float4 T = trig[vb0 + vi];
+        float emin = 3.0e38f, e9min = 3.0e38f;
+#pragma unroll
+        for (int cr = 0; cr < 4; ++cr) {
+            const float xx = (float)(c0 + (cr & 1) * (ORB_T - 1)) - h;
+            const float yy = (float)(r0 + (cr >> 1) * (ORB_T - 1)) - h;
+            emin = fminf(emin, xx * T.x + yy * T.y);
+            e9min = fminf(e9min, -yy * T.x + xx * T.y);
+        }
+        emin = fminf(fmaxf(emin + hb, -1.0e6f), 1.0e6f);
+        e9min = fminf(fmaxf(e9min + hb, -1.0e6f), 1.0e6f);
+        wbs[vi][0] = (int)floorf(emin) - 2;
+        wbs[vi][1] = (int)floorf(e9min) - 2;
+        scs[vi] = T.z;
+    }
+    __syncthreads();
+
+    // this thread fills entry (row, win, w) of every view of a chunk:
+    // (y[base + w], y[base + w + 1]) * |a|; the mirror window of base wb starts
+    // at B - 33 - wb and holds pair (B-2-f) at 31 - (f - wb)
+    const int w_ = tid & 31, win = (tid >> 5) & 3, row = (tid >> 7) & 1;
+    float2 pre[ORB_VC];
+    auto prefetch = [&](int v0, int nv) {
+#pragma unroll
+        for (int j = 0; j < ORB_VC; ++j) {
+            if (j < nv) {
+                const int vi = v0 - vb0 + j;
+                const int base = wbs[vi][win >> 1];
+                const int d = ((win & 1) ? B - 33 - base : base) + w_;
+                const float *yv = ys + (size_t)(v0 + j + row * V2) * B;
+                const float y0 = (d >= 0 && d < B) ? __ldg(yv + d) : 0.0f;
+                const float y1 = (d + 1 >= 0 && d + 1 < B) ? __ldg(yv + d + 1) : 0.0f;
+                pre[j] = make_float2(y0 * scs[vi], y1 * scs[vi]);
+            }
+        }
+    };
+    prefetch(vb0, min(ORB_VC, nvs));
     for (int v0 = vb0; v0 < vb1; v0 += ORB_VC) {
         const int nv = min(ORB_VC, vb1 - v0);
         __syncthreads();
-        if (tid < nv) {
-            const float4 T = trig[v0 + tid];
-            sv[tid] = T;
-            float emin = 3.0e38f, e9min = 3.0e38f;
 #pragma unroll
-            for (int cr = 0; cr < 4; ++cr) {
-                const float xx = (float)(c0 + (cr & 1) * (ORB_T - 1)) - h;
-                const float yy = (float)(r0 + (cr >> 1) * (ORB_T - 1)) - h;
-                emin = fminf(emin, xx * T.x + yy * T.y);
-                e9min = fminf(e9min, -yy * T.x + xx * T.y);
-            }
-            const float hb = 0.5f * (float)(B - 1);
-            emin = fminf(fmaxf(emin + hb, -1.0e6f), 1.0e6f);
-            e9min = fminf(fmaxf(e9min + hb, -1.0e6f), 1.0e6f);
-            wb[tid][0] = (int)floorf(emin) - 2;
-            wb[tid][1] = (int)floorf(e9min) - 2;
-        }
+        for (int j = 0; j < ORB_VC; ++j)
+            if (j < nv) tab[j][row][win][w_] = pre[j];
+        if (tid < nv) sv[tid] = trig[v0 + tid];
         __syncthreads();
-        // window entries: (y[base + k], y[base + k + 1]) * |a|; the mirror
-        // window of base wb starts at B - 33 - wb and holds pair (B-2-f) at 31 - (f - wb)
-        for (int k = tid; k < nv * 2 * 4 * ORB_WW; k += 256) {
-            const int w = k % ORB_WW, win = (k / ORB_WW) % 4, row = (k / (ORB_WW * 4)) % 2, vi = k / (ORB_WW * 8);
-            const int base = wb[vi][win >> 1];
-            const int start = (win & 1) ? B - 33 - base : base;
-            const int d = start + w;
-            const float *yv = ys + (size_t)(v0 + vi + row * V2) * B;
-            const float sc = sv[vi].z;
-            const float y0 = (d >= 0 && d < B) ? yv[d] : 0.0f;
-            const float y1 = (d + 1 >= 0 && d + 1 < B) ? yv[d + 1] : 0.0f;
-            tab[vi][row][win][w] = make_float2(y0 * sc, y1 * sc);
-        }
-        __syncthreads();
+        if (v0 + ORB_VC < vb1) prefetch(v0 + ORB_VC, min(ORB_VC, vb1 - v0 - ORB_VC));
         if (inside) {
             for (int vi = 0; vi < nv; ++vi) {
                 const float4 T = sv[vi];
+                const int wb0 = wbs[v0 - vb0 + vi][0], wb1 = wbs[v0 - vb0 + vi][1];
                 // e - 1/2 of P and of R90 P
                 const float e = fmaf(xq, T.x, fmaf(yq, T.y, hb_lo));
                 const float e9 = fmaf(xq, T.y, fmaf(-yq, T.x, hb_lo));
                 const float t = __fadd_rn(e, JOSEPH_BIAS), t9 = __fadd_rn(e9, JOSEPH_BIAS);
-                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb[vi][0])), (unsigned)(ORB_WW - 1));
-                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb[vi][1])), (unsigned)(ORB_WW - 1));
+                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb0)), (unsigned)(ORB_WW - 1));
+                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb1)), (unsigned)(ORB_WW - 1));
                 const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
                 const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
                 const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
@@ -504,6 +664,7 @@ void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
 
 void kernel_attrs_joseph()
 {
+    cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }
