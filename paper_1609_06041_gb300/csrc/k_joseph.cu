@@ -510,16 +510,26 @@ constexpr int ORB_VC = 16;       // base views staged per chunk
 constexpr int ORB_WW = 32;       // staged ray pairs per window
 
 constexpr int ORB_MAXS = 1024;   // base views per slice (V <= 8192)
+constexpr int ORB_RW = 36;       // raw window values (33 used) per window
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
+{
+    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;   // 0: fill with zeros, read nothing
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sdst), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
 __global__ void __launch_bounds__(256)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
                     int N, int V, int B)
 {
-    // tab[view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][pair]
-    __shared__ float2 tab[ORB_VC][2][4][ORB_WW];
-    __shared__ float4 sv[ORB_VC];
-    __shared__ int wbs[ORB_MAXS][2];     // window bases of e and e90, every base view of the slice
-    __shared__ float scs[ORB_MAXS];      // |a| of every base view of the slice
+    // raw[buffer][view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][value]
+    extern __shared__ __align__(16) unsigned char osm[];
+    float *raw = reinterpret_cast<float *>(osm);                               // 2 x ORB_VC x 8 x ORB_RW
+    int *wbs = reinterpret_cast<int *>(raw + 2 * ORB_VC * 8 * ORB_RW);         // ORB_MAXS x 2
     const int tid = threadIdx.y * ORB_T + threadIdx.x;
     const int half = N / 2, V2 = V / 2;
     const int slice = blockIdx.z % ORB_SL, img = blockIdx.z / ORB_SL;
@@ -546,45 +556,44 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         }
         emin = fminf(fmaxf(emin + hb, -1.0e6f), 1.0e6f);
         e9min = fminf(fmaxf(e9min + hb, -1.0e6f), 1.0e6f);
-        wbs[vi][0] = (int)floorf(emin) - 2;
-        wbs[vi][1] = (int)floorf(e9min) - 2;
-        scs[vi] = T.z;
+        wbs[2 * vi] = (int)floorf(emin) - 2;
+        wbs[2 * vi + 1] = (int)floorf(e9min) - 2;
     }
     __syncthreads();
 
-    // this thread fills entry (row, win, w) of every view of a chunk:
-    // (y[base + w], y[base + w + 1]) * |a|; the mirror window of base wb starts
-    // at B - 33 - wb and holds pair (B-2-f) at 31 - (f - wb)
-    const int w_ = tid & 31, win = (tid >> 5) & 3, row = (tid >> 7) & 1;
-    float2 pre[ORB_VC];
-    auto prefetch = [&](int v0, int nv) {
-#pragma unroll
-        for (int j = 0; j < ORB_VC; ++j) {
-            if (j < nv) {
-                const int vi = v0 - vb0 + j;
-                const int base = wbs[vi][win >> 1];
-                const int d = ((win & 1) ? B - 33 - base : base) + w_;
-                const float *yv = ys + (size_t)(v0 + j + row * V2) * B;
-                const float y0 = (d >= 0 && d < B) ? __ldg(yv + d) : 0.0f;
-                const float y1 = (d + 1 >= 0 && d + 1 < B) ? __ldg(yv + d + 1) : 0.0f;
-                pre[j] = make_float2(y0 * scs[vi], y1 * scs[vi]);
-            }
+    // raw window values y[start + w], w < 33, start = wb (windows e, e90) or
+    // B - 33 - wb (their mirrors, holding pair B-2-f at 31 - (f - wb))
+    auto issue = [&](int v0, int nv, int buf) {
+        float *dst0 = raw + (size_t)buf * ORB_VC * 8 * ORB_RW;
+        for (int k = tid; k < nv * 8 * 33; k += 256) {
+            const int w = k % 33, q = k / 33;
+            const int win = q & 3, row = (q >> 2) & 1, vi = q >> 3;
+            const int base = wbs[2 * (v0 - vb0 + vi) + (win >> 1)];
+            const int d = ((win & 1) ? B - 33 - base : base) + w;
+            const bool ok = d >= 0 && d < B;
+            const float *src = ys + (size_t)(v0 + vi + row * V2) * B + (ok ? d : 0);
+            cp_async4(dst0 + (size_t)q * ORB_RW + w, src, ok);
         }
+        cp_async_commit();
     };
-    prefetch(vb0, min(ORB_VC, nvs));
-    for (int v0 = vb0; v0 < vb1; v0 += ORB_VC) {
-        const int nv = min(ORB_VC, vb1 - v0);
+    const int nch = (nvs + ORB_VC - 1) / ORB_VC;
+    if (nch > 0) issue(vb0, min(ORB_VC, nvs), 0);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int v0 = vb0 + ch * ORB_VC, nv = min(ORB_VC, vb1 - v0);
+        if (ch + 1 < nch) {
+            issue(v0 + ORB_VC, min(ORB_VC, vb1 - v0 - ORB_VC), (ch + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ORB_VC; ++j)
-            if (j < nv) tab[j][row][win][w_] = pre[j];
-        if (tid < nv) sv[tid] = trig[v0 + tid];
-        __syncthreads();
-        if (v0 + ORB_VC < vb1) prefetch(v0 + ORB_VC, min(ORB_VC, vb1 - v0 - ORB_VC));
+        const float *tb = raw + (size_t)(ch & 1) * ORB_VC * 8 * ORB_RW;
         if (inside) {
             for (int vi = 0; vi < nv; ++vi) {
-                const float4 T = sv[vi];
-                const int wb0 = wbs[v0 - vb0 + vi][0], wb1 = wbs[v0 - vb0 + vi][1];
+                const float4 T = trig[v0 + vi];
+                const float s2 = T.z * T.z, c1 = T.z * T.w;   // hat weights times |a|
+                const int wb0 = wbs[2 * (v0 - vb0 + vi)], wb1 = wbs[2 * (v0 - vb0 + vi) + 1];
+                const float *t8 = tb + (size_t)vi * 8 * ORB_RW;   // [row][win][value]
                 // e - 1/2 of P and of R90 P
                 const float e = fmaf(xq, T.x, fmaf(yq, T.y, hb_lo));
                 const float e9 = fmaf(xq, T.y, fmaf(-yq, T.x, hb_lo));
@@ -593,22 +602,23 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
                 const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb1)), (unsigned)(ORB_WW - 1));
                 const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
                 const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
-                const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
-                const float w09 = fmaxf(0.0f, fmaf(-g9, T.z, T.w)), w19 = fmaxf(0.0f, fmaf(g9, T.z, T.w));
-                const float2 pv = tab[vi][0][0][k], pvm = tab[vi][0][1][ORB_WW - 1 - k];
-                const float2 qv = tab[vi][1][0][k], qvm = tab[vi][1][1][ORB_WW - 1 - k];
-                const float2 pv9 = tab[vi][0][2][k9], pvm9 = tab[vi][0][3][ORB_WW - 1 - k9];
-                const float2 qv9 = tab[vi][1][2][k9], qvm9 = tab[vi][1][3][ORB_WW - 1 - k9];
-                aP = fmaf(w0, pv.x, fmaf(w1, pv.y, aP));           // P at v
-                a180 = fmaf(w1, pvm.x, fmaf(w0, pvm.y, a180));     // R180 P at v
-                a90 = fmaf(w0, qv.x, fmaf(w1, qv.y, a90));         // R90 P at v + V/2
-                a270 = fmaf(w1, qvm.x, fmaf(w0, qvm.y, a270));     // R270 P at v + V/2
-                a90 = fmaf(w09, pv9.x, fmaf(w19, pv9.y, a90));     // R90 P at v
-                a270 = fmaf(w19, pvm9.x, fmaf(w09, pvm9.y, a270)); // R270 P at v
-                a180 = fmaf(w09, qv9.x, fmaf(w19, qv9.y, a180));   // R180 P at v + V/2
-                aP = fmaf(w19, qvm9.x, fmaf(w09, qvm9.y, aP));     // P at v + V/2
+                const float w0 = fmaxf(0.0f, fmaf(-g, s2, c1)), w1 = fmaxf(0.0f, fmaf(g, s2, c1));
+                const float w09 = fmaxf(0.0f, fmaf(-g9, s2, c1)), w19 = fmaxf(0.0f, fmaf(g9, s2, c1));
+                const unsigned km = ORB_WW - 1 - k, km9 = ORB_WW - 1 - k9;
+                const float *e_v = t8, *m_v = t8 + ORB_RW, *e9_v = t8 + 2 * ORB_RW, *m9_v = t8 + 3 * ORB_RW;
+                const float *e_w = t8 + 4 * ORB_RW, *m_w = t8 + 5 * ORB_RW, *e9_w = t8 + 6 * ORB_RW,
+                            *m9_w = t8 + 7 * ORB_RW;
+                aP = fmaf(w0, e_v[k], fmaf(w1, e_v[k + 1], aP));             // P at v
+                a180 = fmaf(w1, m_v[km], fmaf(w0, m_v[km + 1], a180));       // R180 P at v
+                a90 = fmaf(w0, e_w[k], fmaf(w1, e_w[k + 1], a90));           // R90 P at v + V/2
+                a270 = fmaf(w1, m_w[km], fmaf(w0, m_w[km + 1], a270));       // R270 P at v + V/2
+                a90 = fmaf(w09, e9_v[k9], fmaf(w19, e9_v[k9 + 1], a90));     // R90 P at v
+                a270 = fmaf(w19, m9_v[km9], fmaf(w09, m9_v[km9 + 1], a270)); // R270 P at v
+                a180 = fmaf(w09, e9_w[k9], fmaf(w19, e9_w[k9 + 1], a180));   // R180 P at v + V/2
+                aP = fmaf(w19, m9_w[km9], fmaf(w09, m9_w[km9 + 1], aP));     // P at v + V/2
             }
         }
+        __syncthreads();   // the buffer is refilled two chunks later
     }
     if (inside) {
         float *pp = partial + ((size_t)img * ORB_SL + slice) * N * N;
@@ -618,6 +628,8 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         pp[(size_t)(N - 1 - c) * N + r] = a270;                  // R270 (r, c) = (N-1-c, r)
     }
 }
+
+static size_t orbit_smem() { return sizeof(float) * 2 * ORB_VC * 8 * ORB_RW + sizeof(int) * 2 * ORB_MAXS; }
 
 // out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
 template <int MODE>
@@ -644,7 +656,8 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     const int q = g->n / 2;
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, ORB_SL * batch);
     counted(2);
-    k_backproject_orbit<<<grd, dim3(ORB_T, ORB_T), 0, st>>>(y, partial, g->d_trig, g->n, g->n_views, g->n_bins);
+    k_backproject_orbit<<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n, g->n_views,
+                                                                       g->n_bins);
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
     if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
@@ -664,6 +677,7 @@ void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
 
 void kernel_attrs_joseph()
 {
+    cudaFuncSetAttribute(k_backproject_orbit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
