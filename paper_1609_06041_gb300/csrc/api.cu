@@ -158,6 +158,11 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     while (g->n_fft < 2 * n_bins) g->n_fft <<= 1;
     g->orbit = !angles && (n_views % 2 == 0) && (n % 2 == 0);   // V <= 8192, so a slice has <= 1024 base views
     cudaGetDevice(&g->device);
+    g->n_sm = 0;
+    if (cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || g->n_sm < 1) {
+        cudaGetLastError();
+        g->n_sm = 1;
+    }
     g->h_angles = new double[n_views];
     // candidate-window margin of the backprojector (bins): a generous bound
     // on the float rounding of the Joseph coordinates at this size
@@ -448,13 +453,14 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     for (int k = 0; k < prm->iters; ++k) {
         // Step 2: z = x^k - tau A^T mu_bar ; x^{k+1} = prox_{tau g}(z)
         backproject(mubar, z, 1, x_out);
+        // equal chunks of at most tv_max_steps() steps
         int left = ntv;
-        do {
-            int steps = std::min(left, chunk);
+        for (int c = chunks; c > 0; --c) {
+            const int steps = (left + c - 1) / c;
             left -= steps;
-            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, steps, left == 0, scal, st);
+            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, g->n_sm, steps, c == 1, scal, st);
             cur ^= 1;
-        } while (left > 0);
+        }
         // Step 3: A x^{k+1} (band partial sums); the dual update forms the
         // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
         // performs Step 1 of the next iteration

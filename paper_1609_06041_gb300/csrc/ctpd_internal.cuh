@@ -40,6 +40,7 @@ struct Geometry {
     float4 *d_trig;       // device, per view (cos t, sin t, |a|, 1 - |a|/2) for A^T
     float2 *d_tw;         // device, n_fft twiddles e^{-2 pi i k / P} (from double precision)
     int orbit;            // default angles with V and N even: A^T by rotation orbits
+    int n_sm;             // multiprocessors of the device
     double *h_angles;     // host copy
 };
 
@@ -176,11 +177,12 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
                         int n, int batch, const double *scal, double *part_inv8, double *part_lam, cudaStream_t st);
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
-// dual field p = (px, py)), temporal blocking in shared memory.
-// Runs `steps` dual steps reading p_in and writing p_out; when final != 0
-// also writes x = max(0, z + lam div p).
+// dual field p = (px, py)), temporally blocked tiles held in registers.
+// Runs `steps` <= tv_max_steps() dual steps reading p_in and writing p_out;
+// when final != 0 also writes x = max(0, z + lam div p).  n_sm (the
+// device's SM count) sizes the tiles.
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int steps, int final, const double *scal, cudaStream_t st);
+               int n, int n_sm, int steps, int final, const double *scal, cudaStream_t st);
 int tv_max_steps();
 
 // Small helpers

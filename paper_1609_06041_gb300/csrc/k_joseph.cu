@@ -506,11 +506,9 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // =====================================================================
 constexpr int ORB_T = 16;        // quadrant tile side
 constexpr int ORB_SL = 4;        // base-view slices
-constexpr int ORB_VC = 16;       // base views staged per chunk
-constexpr int ORB_WW = 32;       // staged ray pairs per window
-
+constexpr int ORB_VC = 8;        // base views staged per chunk
+constexpr int ORB_RW = 36;       // values per window: pairs (k, k+1), k <= ORB_RW - 2
 constexpr int ORB_MAXS = 1024;   // base views per slice (V <= 8192)
-constexpr int ORB_RW = 36;       // raw window values (33 used) per window
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
 {
@@ -518,18 +516,29 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool val
     const int n = valid ? 4 : 0;   // 0: fill with zeros, read nothing
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sdst), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool valid)
+{
+    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
-__global__ void __launch_bounds__(256)
+// AL: B % 4 == 0 and y 16-byte aligned, so every window (its base a
+// multiple of 4) is copied in aligned 16-byte pieces, each wholly on or
+// wholly off the detector.
+template <bool AL>
+__global__ void __launch_bounds__(256, 8)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
                     int N, int V, int B)
 {
     // raw[buffer][view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][value]
     extern __shared__ __align__(16) unsigned char osm[];
     float *raw = reinterpret_cast<float *>(osm);                               // 2 x ORB_VC x 8 x ORB_RW
-    int *wbs = reinterpret_cast<int *>(raw + 2 * ORB_VC * 8 * ORB_RW);         // ORB_MAXS x 2
+    float4 *tt = reinterpret_cast<float4 *>(raw + 2 * ORB_VC * 8 * ORB_RW);    // 2 x ORB_VC
+    int *wbs = reinterpret_cast<int *>(tt + 2 * ORB_VC);                       // ORB_MAXS x 2
     const int tid = threadIdx.y * ORB_T + threadIdx.x;
     const int half = N / 2, V2 = V / 2;
     const int slice = blockIdx.z % ORB_SL, img = blockIdx.z / ORB_SL;
@@ -543,7 +552,9 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     const int nvs = vb1 - vb0;
     float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
 
-    // window bases of the tile for every base view of this slice
+    // window bases (multiples of 4) of the tile for every base view of this
+    // slice: floor(e) - wb lies in [1, 29] for every pixel of the tile, as
+    // e spans at most 15 (|cos| + |sin|) < 21.3 over it
     for (int vi = tid; vi < nvs; vi += 256) {
         const float4 T = trig[vb0 + vi];
         float emin = 3.0e38f, e9min = 3.0e38f;
@@ -556,23 +567,30 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         }
         emin = fminf(fmaxf(emin + hb, -1.0e6f), 1.0e6f);
         e9min = fminf(fmaxf(e9min + hb, -1.0e6f), 1.0e6f);
-        wbs[2 * vi] = (int)floorf(emin) - 2;
-        wbs[2 * vi + 1] = (int)floorf(e9min) - 2;
+        wbs[2 * vi] = ((int)floorf(emin) - 2) & ~3;
+        wbs[2 * vi + 1] = ((int)floorf(e9min) - 2) & ~3;
     }
     __syncthreads();
 
-    // raw window values y[start + w], w < 33, start = wb (windows e, e90) or
-    // B - 33 - wb (their mirrors, holding pair B-2-f at 31 - (f - wb))
+    // raw window values y[start + w], w < ORB_RW, start = wb (windows e, e90)
+    // or B - ORB_RW - wb (their mirrors, holding pair B-2-f at ORB_RW-2 - (f - wb));
+    // per view (cos, sin, |a|^2, |a| (1 - |a|/2)): the hat weights times |a|
     auto issue = [&](int v0, int nv, int buf) {
         float *dst0 = raw + (size_t)buf * ORB_VC * 8 * ORB_RW;
-        for (int k = tid; k < nv * 8 * 33; k += 256) {
-            const int w = k % 33, q = k / 33;
+        if (tid < nv) {
+            const float4 T = trig[v0 + tid];
+            tt[buf * ORB_VC + tid] = make_float4(T.x, T.y, T.z * T.z, T.z * T.w);
+        }
+        constexpr int CH = AL ? ORB_RW / 4 : ORB_RW;   // copies per window
+        for (int k = tid; k < nv * 8 * CH; k += 256) {
+            const int q = k / CH, j = k - q * CH;
             const int win = q & 3, row = (q >> 2) & 1, vi = q >> 3;
             const int base = wbs[2 * (v0 - vb0 + vi) + (win >> 1)];
-            const int d = ((win & 1) ? B - 33 - base : base) + w;
+            const int d = ((win & 1) ? B - ORB_RW - base : base) + (AL ? 4 * j : j);
             const bool ok = d >= 0 && d < B;
             const float *src = ys + (size_t)(v0 + vi + row * V2) * B + (ok ? d : 0);
-            cp_async4(dst0 + (size_t)q * ORB_RW + w, src, ok);
+            if (AL) cp_async16(dst0 + (size_t)q * ORB_RW + 4 * j, src, ok);
+            else cp_async4(dst0 + (size_t)q * ORB_RW + j, src, ok);
         }
         cp_async_commit();
     };
@@ -588,23 +606,23 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         }
         __syncthreads();
         const float *tb = raw + (size_t)(ch & 1) * ORB_VC * 8 * ORB_RW;
+        const float4 *tv = tt + (ch & 1) * ORB_VC;
         if (inside) {
             for (int vi = 0; vi < nv; ++vi) {
-                const float4 T = trig[v0 + vi];
-                const float s2 = T.z * T.z, c1 = T.z * T.w;   // hat weights times |a|
-                const int wb0 = wbs[2 * (v0 - vb0 + vi)], wb1 = wbs[2 * (v0 - vb0 + vi) + 1];
+                const float4 T = tv[vi];
+                const int2 wb = *reinterpret_cast<const int2 *>(wbs + 2 * (v0 - vb0 + vi));
                 const float *t8 = tb + (size_t)vi * 8 * ORB_RW;   // [row][win][value]
                 // e - 1/2 of P and of R90 P
                 const float e = fmaf(xq, T.x, fmaf(yq, T.y, hb_lo));
                 const float e9 = fmaf(xq, T.y, fmaf(-yq, T.x, hb_lo));
                 const float t = __fadd_rn(e, JOSEPH_BIAS), t9 = __fadd_rn(e9, JOSEPH_BIAS);
-                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb0)), (unsigned)(ORB_WW - 1));
-                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb1)), (unsigned)(ORB_WW - 1));
+                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb.x)), (unsigned)(ORB_RW - 2));
+                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb.y)), (unsigned)(ORB_RW - 2));
                 const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
                 const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
-                const float w0 = fmaxf(0.0f, fmaf(-g, s2, c1)), w1 = fmaxf(0.0f, fmaf(g, s2, c1));
-                const float w09 = fmaxf(0.0f, fmaf(-g9, s2, c1)), w19 = fmaxf(0.0f, fmaf(g9, s2, c1));
-                const unsigned km = ORB_WW - 1 - k, km9 = ORB_WW - 1 - k9;
+                const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
+                const float w09 = fmaxf(0.0f, fmaf(-g9, T.z, T.w)), w19 = fmaxf(0.0f, fmaf(g9, T.z, T.w));
+                const unsigned km = ORB_RW - 2 - k, km9 = ORB_RW - 2 - k9;
                 const float *e_v = t8, *m_v = t8 + ORB_RW, *e9_v = t8 + 2 * ORB_RW, *m9_v = t8 + 3 * ORB_RW;
                 const float *e_w = t8 + 4 * ORB_RW, *m_w = t8 + 5 * ORB_RW, *e9_w = t8 + 6 * ORB_RW,
                             *m9_w = t8 + 7 * ORB_RW;
@@ -629,7 +647,10 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     }
 }
 
-static size_t orbit_smem() { return sizeof(float) * 2 * ORB_VC * 8 * ORB_RW + sizeof(int) * 2 * ORB_MAXS; }
+static size_t orbit_smem()
+{
+    return sizeof(float) * 2 * ORB_VC * 8 * ORB_RW + sizeof(float4) * 2 * ORB_VC + sizeof(int) * 2 * ORB_MAXS;
+}
 
 // out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
 template <int MODE>
@@ -656,8 +677,12 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     const int q = g->n / 2;
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, ORB_SL * batch);
     counted(2);
-    k_backproject_orbit<<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n, g->n_views,
-                                                                       g->n_bins);
+    if (g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0)
+        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
+                                                                                g->n_views, g->n_bins);
+    else
+        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
+                                                                                 g->n_views, g->n_bins);
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
     if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
@@ -677,7 +702,8 @@ void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
 
 void kernel_attrs_joseph()
 {
-    cudaFuncSetAttribute(k_backproject_orbit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
+    cudaFuncSetAttribute(k_backproject_orbit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
+    cudaFuncSetAttribute(k_backproject_orbit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));

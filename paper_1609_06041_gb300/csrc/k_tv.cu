@@ -4,111 +4,180 @@
 // then x = max(0, z + lam div p).  grad is the forward difference (zero
 // across the last row/column), div = -grad^T.  lam = 0 gives max(0, z).
 //
-// Temporal blocking: one block owns a TV_T x TV_T tile and loads it with a
-// halo of (steps + 1) pixels.  Each step invalidates one more ring of the
-// halo, so after `steps` steps the tile interior holds exactly what a
+// Temporal blocking: one block owns a tile of tc x tr pixels and holds it
+// with a halo of H = steps + 1 pixels on every side.  Each step spoils one
+// more ring of the halo (its outermost cells see zeros instead of their
+// neighbours), so after `steps` steps the tile holds exactly what a
 // whole-image iteration would give, with no grid-wide synchronisation and
 // one pass over global memory per call.  p is double-buffered (p_in ->
 // p_out) because neighbouring blocks read the old p in their halos.
+//
+// The held region is 64 columns (lane l owns columns 2l, 2l+1) by up to
+// TV_ROWS rows (warp w owns rows w + 16 j), so tc = 64 - 2H.  Every cell's
+// z, p and x stay in registers for the whole call; left/right neighbours
+// come from the adjacent lane by shuffle, and each phase publishes the one
+// field its vertical neighbours need (x for the dual step, p_y for the
+// divergence) in shared memory.  Outside the image, and where a forward
+// difference does not exist (p_x on the last column, p_y on the last row),
+// p is zero and stays zero: the dual step's factor is 0 there, so the
+// divergence needs no boundary tests.
+#include <algorithm>
+
 #include "ctpd_internal.cuh"
 
 namespace ctpd {
 
-constexpr int TV_T = 32;
-constexpr int TV_MAX_STEPS = 24;   // S = 32 + 2*25 = 82: 4*82*82*4 B = 105 KB
+constexpr int TV_WARPS = 16;
+constexpr int TV_THREADS = TV_WARPS * 32;
+constexpr int TV_J = 5;                     // region rows per warp
+constexpr int TV_ROWS = TV_WARPS * TV_J;    // 80
+constexpr int TV_MAX_STEPS = 16;            // H = 17: 30 interior columns
+constexpr int TV_MIN_TR = 16;               // fewest interior rows per tile
 
 int tv_max_steps() { return TV_MAX_STEPS; }
 
-static size_t tv_smem(int steps)
+struct TvTiles {
+    int tc, tr, ncb, nrb;
+};
+
+// Column tiles are as wide as the region allows; rows are split so that the
+// tiles of one image about fill the GPU once (one block per SM), but no
+// narrower than TV_MIN_TR rows and no taller than the region.
+static TvTiles tv_tiles(int N, int steps, int n_sm)
 {
-    int S = TV_T + 2 * (steps + 1);
-    return sizeof(float) * 4 * (size_t)S * S;
+    const int H = steps + 1;
+    TvTiles t;
+    t.tc = 64 - 2 * H;
+    t.ncb = (N + t.tc - 1) / t.tc;
+    const int tr_max = TV_ROWS - 2 * H;
+    int nrb = std::max(1, n_sm / t.ncb);
+    nrb = std::min(nrb, (N + TV_MIN_TR - 1) / TV_MIN_TR);
+    nrb = std::max(nrb, (N + tr_max - 1) / tr_max);
+    t.tr = (N + nrb - 1) / nrb;
+    t.nrb = (N + t.tr - 1) / t.tr;
+    return t;
 }
 
-constexpr int TV_THREADS = 512;   // 32 x 16
-
-__global__ void __launch_bounds__(TV_THREADS)
+__global__ void __launch_bounds__(TV_THREADS, 1)
 k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
-     float *__restrict__ x, int N, int steps, int final_,
-     const double *__restrict__ scal)
+     float *__restrict__ x, int N, int steps, int final_, int tc, int tr, const double *__restrict__ scal)
 {
-    extern __shared__ float sm[];
-    const int H = steps + 1;
-    const int S = TV_T + 2 * H;
-    float *sz = sm, *spx = sm + S * S, *spy = spx + S * S, *sx = spy + S * S;
-    const int R0 = blockIdx.y * TV_T - H, C0 = blockIdx.x * TV_T - H;
+    // row li of the region at index (li + 1) * 32 + lane; rows -1 and
+    // beyond the region read zeros
+    __shared__ float2 pub_x[(TV_ROWS + 2) * 32];
+    __shared__ float2 pub_y[(TV_ROWS + 2) * 32];
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int H = steps + 1, Sr = tr + 2 * H;
+    const int R0 = blockIdx.y * tr - H, C0 = blockIdx.x * tc - H;
+    const int c0 = C0 + 2 * lane;   // image columns c0, c0 + 1 of this lane
     const size_t NN = (size_t)N * N;
     const float lam = (float)scal[S_LAMBDA];
     const float inv8 = (float)scal[S_INV8LAM];
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 16
-    constexpr int TY = TV_THREADS / 32;
+    // forward differences: along x on columns 0..N-2, along y on columns 0..N-1
+    const bool cx0 = (unsigned)c0 < (unsigned)(N - 1), cx1 = (unsigned)(c0 + 1) < (unsigned)(N - 1);
+    const bool cy0 = (unsigned)c0 < (unsigned)N, cy1 = (unsigned)(c0 + 1) < (unsigned)N;
 
-    for (int li = ty; li < S; li += TY) {
-        const int rr = R0 + li;
-        for (int lj = tx; lj < S; lj += 32) {
-            const int cc = C0 + lj;
-            const bool in = rr >= 0 && rr < N && cc >= 0 && cc < N;
-            const size_t gi = (size_t)rr * N + cc;
-            const int i = li * S + lj;
-            sz[i] = in ? z[gi] : 0.0f;
-            spx[i] = in ? p_in[gi] : 0.0f;
-            spy[i] = in ? p_in[NN + gi] : 0.0f;
-            sx[i] = 0.0f;
+    for (int i = threadIdx.x; i < (TV_ROWS + 2) * 32; i += TV_THREADS) {
+        pub_x[i] = make_float2(0.0f, 0.0f);
+        pub_y[i] = make_float2(0.0f, 0.0f);
+    }
+    float zr[TV_J][2], pxr[TV_J][2], pyr[TV_J][2], xr[TV_J][2];
+    unsigned rowx = 0, rowy = 0;   // bit j: row in the image / row with a y difference
+#pragma unroll
+    for (int j = 0; j < TV_J; ++j) {
+        const int li = w + TV_WARPS * j, rr = R0 + li;
+        const bool rin = li < Sr && (unsigned)rr < (unsigned)N;
+        const bool ryd = li < Sr && (unsigned)rr < (unsigned)(N - 1);
+        rowx |= (unsigned)rin << j;
+        rowy |= (unsigned)ryd << j;
+        zr[j][0] = zr[j][1] = pxr[j][0] = pxr[j][1] = pyr[j][0] = pyr[j][1] = 0.0f;
+        xr[j][0] = xr[j][1] = 0.0f;
+        if (rin) {
+            const size_t gi = (size_t)rr * N + c0;   // c0 may be -1..: only valid columns are read
+            if (cy0) zr[j][0] = z[gi];
+            if (cy1) zr[j][1] = z[gi + 1];
+            if (cx0) pxr[j][0] = p_in[gi];
+            if (cx1) pxr[j][1] = p_in[gi + 1];
+            if (ryd && cy0) pyr[j][0] = p_in[NN + gi];
+            if (ryd && cy1) pyr[j][1] = p_in[NN + gi + 1];
         }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < TV_J; ++j) {
+        const int li = w + TV_WARPS * j;
+        if (li < Sr) pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
     }
     __syncthreads();
 
     if (lam > 0.0f) {
         for (int it = 0; it < steps; ++it) {
-            // x_l = max(0, z + lam div p) on rows/cols >= 1 of the region
-            for (int li = 1 + ty; li < S; li += TY) {
-                const int rr = R0 + li;
-                for (int lj = 1 + tx; lj < S; lj += 32) {
-                    const int cc = C0 + lj;
-                    const int i = li * S + lj;
-                    const float dvx = (cc < N - 1 ? spx[i] : 0.0f) - (cc > 0 ? spx[i - 1] : 0.0f);
-                    const float dvy = (rr < N - 1 ? spy[i] : 0.0f) - (rr > 0 ? spy[i - S] : 0.0f);
-                    sx[i] = fmaxf(0.0f, sz[i] + lam * (dvx + dvy));
+            // x = max(0, z + lam div p)
+#pragma unroll
+            for (int j = 0; j < TV_J; ++j) {
+                const int li = w + TV_WARPS * j;
+                if (li < Sr) {
+                    const float2 pa = pub_y[li * 32 + lane];   // p_y of row li - 1
+                    float pl = __shfl_up_sync(FULL, pxr[j][1], 1);
+                    if (lane == 0) pl = 0.0f;
+                    const float d0 = (pxr[j][0] - pl) + (pyr[j][0] - pa.x);
+                    const float d1 = (pxr[j][1] - pxr[j][0]) + (pyr[j][1] - pa.y);
+                    xr[j][0] = fmaxf(0.0f, fmaf(lam, d0, zr[j][0]));
+                    xr[j][1] = fmaxf(0.0f, fmaf(lam, d1, zr[j][1]));
+                    pub_x[(li + 1) * 32 + lane] = make_float2(xr[j][0], xr[j][1]);
                 }
             }
             __syncthreads();
-            // p <- Pi(p + grad x / (8 lam)) on rows/cols 1 .. S-2
-            for (int li = 1 + ty; li < S - 1; li += TY) {
-                const int rr = R0 + li;
-                for (int lj = 1 + tx; lj < S - 1; lj += 32) {
-                    const int cc = C0 + lj;
-                    const int i = li * S + lj;
-                    const float gx = (cc < N - 1) ? sx[i + 1] - sx[i] : 0.0f;
-                    const float gy = (rr < N - 1) ? sx[i + S] - sx[i] : 0.0f;
-                    const float qx = spx[i] + gx * inv8;
-                    const float qy = spy[i] + gy * inv8;
-                    // divide by max(1, |q|)
-                    const float sc = fminf(1.0f, rsqrtf(fmaf(qx, qx, qy * qy)));
-                    spx[i] = qx * sc;
-                    spy[i] = qy * sc;
+            // p = Pi(p + grad x / (8 lam)), Pi(q) = q / max(1, |q|)
+#pragma unroll
+            for (int j = 0; j < TV_J; ++j) {
+                const int li = w + TV_WARPS * j;
+                if (li < Sr) {
+                    const float2 xb = pub_x[(li + 2) * 32 + lane];   // x of row li + 1
+                    const float xrt = __shfl_down_sync(FULL, xr[j][0], 1);
+                    const bool rx = (rowx >> j) & 1u, ry = (rowy >> j) & 1u;
+                    const float mx0 = (rx && cx0) ? inv8 : 0.0f, mx1 = (rx && cx1) ? inv8 : 0.0f;
+                    const float my0 = (ry && cy0) ? inv8 : 0.0f, my1 = (ry && cy1) ? inv8 : 0.0f;
+                    const float qx0 = fmaf(xr[j][1] - xr[j][0], mx0, pxr[j][0]);
+                    const float qx1 = fmaf(xrt - xr[j][1], mx1, pxr[j][1]);
+                    const float qy0 = fmaf(xb.x - xr[j][0], my0, pyr[j][0]);
+                    const float qy1 = fmaf(xb.y - xr[j][1], my1, pyr[j][1]);
+                    const float s0 = fminf(1.0f, rsqrtf(fmaf(qx0, qx0, qy0 * qy0)));
+                    const float s1 = fminf(1.0f, rsqrtf(fmaf(qx1, qx1, qy1 * qy1)));
+                    pxr[j][0] = qx0 * s0;
+                    pxr[j][1] = qx1 * s1;
+                    pyr[j][0] = qy0 * s0;
+                    pyr[j][1] = qy1 * s1;
+                    pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
                 }
             }
             __syncthreads();
         }
     }
 
-    // write back the tile interior
-    for (int li = H + ty; li < H + TV_T; li += TY) {
-        const int rr = R0 + li;
-        for (int lj = H + tx; lj < H + TV_T; lj += 32) {
-            const int cc = C0 + lj;
-            const int i = li * S + lj;
-            if (rr < N && cc < N) {
-                const size_t gi = (size_t)rr * N + cc;
-                if (lam > 0.0f) {
-                    p_out[gi] = spx[i];
-                    p_out[NN + gi] = spy[i];
-                }
-                if (final_) {
-                    const float dvx = (cc < N - 1 ? spx[i] : 0.0f) - (cc > 0 ? spx[i - 1] : 0.0f);
-                    const float dvy = (rr < N - 1 ? spy[i] : 0.0f) - (rr > 0 ? spy[i - S] : 0.0f);
-                    const float xv = fmaxf(0.0f, sz[i] + lam * (dvx + dvy));
-                    x[gi] = xv;
+    // the tile interior: p, and x = max(0, z + lam div p) on the last chunk
+#pragma unroll
+    for (int j = 0; j < TV_J; ++j) {
+        const int li = w + TV_WARPS * j, rr = R0 + li;
+        if (li >= H && li < H + tr && rr < N) {
+            const float2 pa = pub_y[li * 32 + lane];
+            float pl = __shfl_up_sync(FULL, pxr[j][1], 1);
+            if (lane == 0) pl = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int lj = 2 * lane + e, cc = C0 + lj;
+                if (lj >= H && lj < H + tc && cc < N) {
+                    const size_t gi = (size_t)rr * N + cc;
+                    if (lam > 0.0f) {
+                        p_out[gi] = pxr[j][e];
+                        p_out[NN + gi] = pyr[j][e];
+                    }
+                    if (final_) {
+                        const float dv = e == 0 ? (pxr[j][0] - pl) + (pyr[j][0] - pa.x)
+                                                : (pxr[j][1] - pxr[j][0]) + (pyr[j][1] - pa.y);
+                        x[gi] = fmaxf(0.0f, fmaf(lam, dv, zr[j][e]));
+                    }
                 }
             }
         }
@@ -116,17 +185,14 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 }
 
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int steps, int final_, const double *scal, cudaStream_t st)
+               int n, int n_sm, int steps, int final_, const double *scal, cudaStream_t st)
 {
-    dim3 blk(32, TV_THREADS / 32), grd((n + TV_T - 1) / TV_T, (n + TV_T - 1) / TV_T);
+    const TvTiles t = tv_tiles(n, steps, n_sm);
     counted();
-    k_tv<<<grd, blk, tv_smem(steps), st>>>(z, p_in, p_out, x, n, steps, final_, scal);
+    k_tv<<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
 }
 
-void kernel_attrs_tv()
-{
-    cudaFuncSetAttribute(k_tv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tv_smem(TV_MAX_STEPS));
-}
+void kernel_attrs_tv() {}
 
 
 // =====================================================================
