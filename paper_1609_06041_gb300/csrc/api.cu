@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "ctpd_internal.cuh"
@@ -73,7 +74,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, total;
+    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, total;
 };
 
 Layout layout(const Geometry *g)
@@ -82,7 +83,7 @@ Layout layout(const Geometry *g)
     const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
     size_t o = 0;
     L.scal = o;     o += align256(sizeof(double) * S_COUNT);
-    L.partials = o; o += align256(sizeof(double) * dot_partials_doubles());
+    L.partials = o; o += align256(sizeof(double) * 2 * dot_partials_doubles());   // two concurrent reductions
     L.taps = o;     o += align256(sizeof(float) * (2 * (size_t)g->n_bins - 1));
     L.hhat = o;     o += align256(sizeof(float2) * (size_t)g->n_fft);
     L.winv = o;     o += align256(sizeof(float) * I);
@@ -96,6 +97,7 @@ Layout layout(const Geometry *g)
     L.p1 = o;       o += align256(sizeof(float) * 2 * J);
     L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
     L.orb = o;      o += align256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, 1) : 1));
+    L.aux = o;      o += align256(sizeof(float) * 2 * I);   // the sinogram-side Lanczos, run beside the image side
     L.total = o;
     return L;
 }
@@ -106,29 +108,56 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 // (n-vectors) by k Lanczos steps from the all-ones vector, into scal[slot]:
 //   w = op(q_j) - beta_{j-1} q_{j-1};  alpha_j = <w, q_j>;  w -= alpha_j q_j;
 //   beta_j = |w|;  q_{j+1} = w / beta_j,
-// then the largest eigenvalue of the tridiagonal (alpha, beta) (bisection,
-// double precision).  q, qp, w are n-vector buffers; the whole recurrence
-// stays on the device.
+// then the largest eigenvalue of the tridiagonal (alpha, beta) (Sturm
+// multisection).  The vectors are kept unnormalised (t_j = beta_{j-1} q_j,
+// t_0 = ones with norm sqrt(n)), the scaling folded into the two fused
+// update-and-reduce kernels of each step.  Coefficients go to scal[base ..
+// base + 2k), the norm of t_0 to scal[n0slot].  t, tp, w are n-vector
+// buffers; the whole recurrence stays on the device.
 template <class Op>
-void lanczos_norm(Op op, float *q, float *qp, float *w, size_t n, int k, double *scal, double *partials,
-                  unsigned *ticket, int slot, cudaStream_t st)
+void lanczos_norm(Op op, float *t, float *tp, float *w, size_t n, int k, double *scal, int base, int n0slot,
+                  double *partials, unsigned *ticket, int slot, cudaStream_t st)
 {
-    launch_fill(q, 1.0f, n, st);
-    launch_dot(q, q, n, scal, S_RED0, partials, st);
-    launch_normalize(q, q, n, scal, S_RED0, st);
+    launch_fill(t, 1.0f, n, st);
+    launch_scalars(scal, SC_SET, sqrt((double)n), 0, 0, n0slot, st);
     for (int j = 0; j < k; ++j) {
-        op(q, w);
-        // w -= beta_{j-1} q_{j-1};  alpha_j = <w, q_j>
-        launch_axpy_dot(w, qp, n, scal, j > 0 ? S_LZ + 2 * j - 1 : -1, q, S_LZ + 2 * j, partials, ticket, -1, st);
-        // w -= alpha_j q_j;  |w|^2 -> S_RED0, beta_j = |w|
-        launch_axpy_dot(w, q, n, scal, S_LZ + 2 * j, nullptr, S_RED0, partials, ticket, S_LZ + 2 * j + 1, st);
-        launch_normalize(w, w, n, scal, S_RED0, st);
-        float *t = qp;
-        qp = q;
-        q = w;
-        w = t;
+        op(t, w);
+        launch_lanczos_step(w, tp, t, n, scal, base, n0slot, j, 0, partials, ticket, st);
+        launch_lanczos_step(w, tp, t, n, scal, base, n0slot, j, 1, partials, ticket, st);
+        float *x = tp;
+        tp = t;
+        t = w;
+        w = x;
     }
-    launch_lanczos_max(scal, k, slot, st);
+    launch_lanczos_max(scal, base, k, slot, st);
+}
+
+// A second stream and two events per device for forking work inside one
+// solve (created on first use, kept until exit).
+struct Fork {
+    bool ready = false;
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+std::mutex g_fork_mu;
+Fork g_forks[64];
+
+Fork *fork_for(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_fork_mu);
+    Fork &f = g_forks[dev];
+    if (!f.ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        f.ready = true;
+    }
+    return &f;
 }
 
 }  // namespace
@@ -199,6 +228,18 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
         const double sc = 1.0 / fmax(fabs(c), fabs(s));
         ht[v] = make_float4((float)c, (float)s, (float)sc, (float)(1.0 - 0.5 * sc));
     }
+    // view-pair work items of the projector (default angles only)
+    g->vpair = !angles;
+    int2 *hri = new int2[n_views + 1], *hci = new int2[n_views + 1];
+    g->n_row_items = g->n_col_items = 0;
+    if (g->vpair) {
+        hri[g->n_row_items++] = make_int2(0, -1);
+        for (int v = 1; v < n_views; ++v) {
+            if (4 * v <= n_views) hri[g->n_row_items++] = make_int2(v, n_views - v);
+            else if (4 * v < 3 * n_views && 2 * v < n_views) hci[g->n_col_items++] = make_int2(v, n_views - v);
+            else if (2 * v == n_views) hci[g->n_col_items++] = make_int2(v, -1);
+        }
+    }
     float2 *htw = new float2[g->n_fft];
     for (int k = 0; k < g->n_fft; ++k) {
         const double ang = -2.0 * M_PI * (double)k / (double)g->n_fft;
@@ -214,6 +255,14 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     if (e == cudaSuccess) e = cudaMemcpy(g->d_views, hv, sizeof(ViewP) * n_views, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_row_list, rl, sizeof(int) * n_views, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_col_list, cl, sizeof(int) * n_views, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_row_items, sizeof(int2) * (n_views + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_col_items, sizeof(int2) * (n_views + 1));
+    if (e == cudaSuccess && g->n_row_items)
+        e = cudaMemcpy(g->d_row_items, hri, sizeof(int2) * g->n_row_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && g->n_col_items)
+        e = cudaMemcpy(g->d_col_items, hci, sizeof(int2) * g->n_col_items, cudaMemcpyHostToDevice);
+    delete[] hri;
+    delete[] hci;
     delete[] hv;
     delete[] ht;
     delete[] htw;
@@ -246,6 +295,8 @@ void ct_geometry_destroy(ct_geometry *g)
     if (g->d_col_list) cudaFree(g->d_col_list);
     if (g->d_trig) cudaFree(g->d_trig);
     if (g->d_tw) cudaFree(g->d_tw);
+    if (g->d_row_items) cudaFree(g->d_row_items);
+    if (g->d_col_items) cudaFree(g->d_col_items);
     delete[] g->h_angles;
     delete g;
 }
@@ -341,6 +392,14 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                         const ct_pdtv_params *prm, float *x_out, void *workspace,
                         ct_pdtv_report *report, void *stream)
 {
+    return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, report, stream, true);
+}
+
+}  // extern "C"
+
+ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
+                           float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork)
+{
     g_err[0] = 0;
     if (!g || !b || !prm || !x_out) return fail(CT_ERR_ARG, "ct_pdtv_solve: NULL argument");
     const int mode = prm->mode;
@@ -373,6 +432,9 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     double *scal = (double *)(ws + L.scal);
     double *partials = (double *)(ws + L.partials);
     unsigned *ticket = (unsigned *)(partials + dot_partials_doubles() - 64);
+    double *partials2 = partials + dot_partials_doubles();
+    unsigned *ticket2 = (unsigned *)(partials2 + dot_partials_doubles() - 64);
+    float *aux = (float *)(ws + L.aux);
     float *taps = (float *)(ws + L.taps);
     float2 *hhat = (float2 *)(ws + L.hhat);
     const bool use_fft = fft_supported(g);
@@ -400,6 +462,7 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         // ---- setup (Alg. 1 / Alg. 2 boxes): kappa, tau, D, sigma ----
         cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
         cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+        cudaMemsetAsync(ticket2, 0, sizeof(unsigned), st);
         if (lowdose) {
             launch_recip(w, winv, I, st);
             launch_dot(winv, nullptr, I, scal, S_RED0, partials, st);
@@ -410,24 +473,44 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         else launch_fill(taps, 1.0f, 1, st);
         if (use_fft) launch_hhat(g, taps, half, hhat, st);
         if (!(prm->sigma > 0.0)) {
+            // ||W^-1/2 D W^-1/2|| by Lanczos on the sinogram side (low-dose),
+            // on a second stream beside the image-side run when D is applied
+            // by FFT (the two then share no buffers)
+            Fork *fk = nullptr;
+            if (allow_fork && lowdose && use_fft) {
+                int dev = -1;
+                if (cudaGetDevice(&dev) == cudaSuccess) fk = fork_for(dev);
+            }
+            if (lowdose) {
+                cudaStream_t s2 = st;
+                if (fk) {
+                    cudaEventRecord(fk->fork, st);
+                    cudaStreamWaitEvent(fk->s, fk->fork, 0);
+                    s2 = fk->s;
+                }
+                float *sw = aux;
+                launch_sqrt(winv, sw, I, s2);
+                auto op_wdw = [&](const float *v, float *out) {
+                    if (use_fft) launch_filter_fft(g, hhat, v, out, sw, sw, 0, nullptr, 1, s2);
+                    else launch_filter(g, taps, half, v, out, sw, sw, 0, nullptr, 1, s2);
+                };
+                lanczos_norm(op_wdw, mu, r, aux + I, I, nlz, scal, S_LZ2, S_LN0B, partials2, ticket2, S_NWDW, s2);
+            }
             // ||A^T D A|| by Lanczos on the image side
             auto op_ada = [&](const float *v, float *out) {
                 launch_project_bands(g, v, band, 1, st);
-                launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
-                if (use_fft) launch_filter_fft(g, hhat, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
-                else launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
+                if (use_fft) {
+                    launch_filter_fft_bands(g, hhat, band, mubar, 1, st);
+                } else {
+                    launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
+                    launch_filter(g, taps, half, r, mubar, nullptr, nullptr, 0, nullptr, 1, st);
+                }
                 backproject(mubar, out, 0, nullptr);
             };
-            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, partials, ticket, S_NADA, st);
-            if (lowdose) {
-                // ||W^-1/2 D W^-1/2|| by Lanczos on the sinogram side
-                float *sw = mubar;
-                launch_sqrt(winv, sw, I, st);
-                auto op_wdw = [&](const float *v, float *out) {
-                    if (use_fft) launch_filter_fft(g, hhat, v, out, sw, sw, 0, nullptr, 1, st);
-                    else launch_filter(g, taps, half, v, out, sw, sw, 0, nullptr, 1, st);
-                };
-                lanczos_norm(op_wdw, mu, r, band, I, nlz, scal, partials, ticket, S_NWDW, st);
+            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, S_LZ, S_LN0, partials, ticket, S_NADA, st);
+            if (fk) {
+                cudaEventRecord(fk->join, fk->s);
+                cudaStreamWaitEvent(st, fk->join, 0);
             }
         }
         launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);
@@ -478,5 +561,3 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     if (owned) cudaFreeAsync(ws, st);
     return cs;
 }
-
-}  // extern "C"

@@ -86,8 +86,8 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
     for (int i = 0; i < used; ++i) cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
     ct_status result = CT_OK;
     for (int i = 0; i < n && result == CT_OK; ++i) {
-        result = ct_pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, &params[i], x_out[i], workspaces[i],
-                               nullptr, pool->s[i % POOL_STREAMS]);
+        result = ctpd::pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, &params[i], x_out[i], workspaces[i],
+                                  nullptr, pool->s[i % POOL_STREAMS], false);
         if (result != CT_OK) {
             char msg[400];
             snprintf(msg, sizeof(msg), "%s", ct_last_error());

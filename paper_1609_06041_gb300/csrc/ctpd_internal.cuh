@@ -40,6 +40,10 @@ struct Geometry {
     float4 *d_trig;       // device, per view (cos t, sin t, |a|, 1 - |a|/2) for A^T
     float2 *d_tw;         // device, n_fft twiddles e^{-2 pi i k / P} (from double precision)
     int orbit;            // default angles with V and N even: A^T by rotation orbits
+    int vpair;            // default angles: A by view pairs (v, V-v)
+    int n_row_items, n_col_items;
+    int2 *d_row_items;    // device, (v, V-v) for 1 <= v <= V/4, and (0, -1)
+    int2 *d_col_items;    // device, (v, V-v) for V/4 < v < V/2, and (V/2, -1) for even V
     int n_sm;             // multiprocessors of the device
     double *h_angles;     // host copy
 };
@@ -53,6 +57,13 @@ ct_status read_report(const void *workspace, ct_pdtv_report *report);
 
 // The opaque handle of the C ABI is the geometry itself.
 struct ct_geometry : public ctpd::Geometry {};
+
+namespace ctpd {
+// ct_pdtv_solve; allow_fork lets one solve run independent setup work on a
+// second stream of the device (off for solves already run side by side).
+ct_status pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
+                     float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork);
+}  // namespace ctpd
 
 namespace ctpd {
 
@@ -87,10 +98,19 @@ __device__ __forceinline__ void joseph_round(float up, int &i0, float &g)
 enum {
     S_KAPPA = 0, S_TAU, S_SIGMA, S_LAMBDA, S_INV8LAM, S_NADA, S_NWDW, S_K,
     S_RED0 = 16,   // reduction results
-    S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1
-    S_COUNT = 32 + 2 * 64
+    S_LN0 = 24,    // norm of the first Lanczos vector (image side)
+    S_LN0B = 25,   // and of the sinogram side
+    S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1 (image side)
+    S_LZ2 = 32 + 2 * 64,   // the same for the sinogram side
+    S_COUNT = 32 + 4 * 64
 };
 constexpr int LANCZOS_MAX = 64;
+// Float copies of the scalars the per-iteration kernels read (doubles 20-21
+// hold four floats; every scalar-program launch refreshes them), so those
+// kernels convert nothing on the slow FP64 pipe.
+constexpr int S_F32 = 20;
+enum { F_TAU = 0, F_SIGMA, F_LAMBDA, F_INV8LAM };
+__device__ __forceinline__ float fscal(const double *scal, int k) { return reinterpret_cast<const float *>(scal + S_F32)[k]; }
 
 // Number of kernels this library has enqueued (all threads), for callers
 // that account for launches.
@@ -143,6 +163,9 @@ void launch_hhat(const Geometry *g, const float *taps, int half, float2 *hhat, c
 void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, float *out,
                        const float *pre, const float *post, int mode, const double *scal, int batch,
                        cudaStream_t st);
+// out = D (A x) with A x given as the projector's band partial sums
+void launch_filter_fft_bands(const Geometry *g, const float2 *hhat, const float *partial, float *out, int batch,
+                             cudaStream_t st);
 // fused residual + Step 3 + next Step 1 (as launch_dual_update)
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
                      float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st);
@@ -193,21 +216,20 @@ void launch_scale_by(const float *in, const float *s, int sqrt_s, float *out, si
 // scal[slot] = sum(a .* b) (b may be NULL: sum(a)), deterministic two-pass.
 void launch_dot(const float *a, const float *b, size_t n, double *scal, int slot,
                 double *partials, cudaStream_t st);
-// out = in / sqrt(scal[slot])
-void launch_normalize(const float *in, float *out, size_t n, const double *scal, int slot,
-                      cudaStream_t st);
 // scalar program: set tau/sigma/lambda from norms and parameters
 void launch_scalars(double *scal, int op, double a0, double a1, double a2, int i0,
                     cudaStream_t st);
 enum { SC_KAPPA_FROM_SUM = 0, SC_TAU, SC_NORM_FROM_DOT, SC_SIGMA, SC_LAMBDA, SC_SET, SC_COPY,
        SC_NORM_SQRT, SC_AXPY_SLOT };
-// scal[out] = largest eigenvalue of the Lanczos tridiagonal of k steps
-void launch_lanczos_max(double *scal, int k, int out, cudaStream_t st);
-// w -= scal[cslot] q (cslot >= 0); scal[dslot] = <w, v or w>; scal[sqrt_out] =
-// sqrt of it (sqrt_out >= 0).  partials: dot_partials_doubles(); ticket: a
+// scal[out] = largest eigenvalue of the Lanczos tridiagonal of k steps with
+// coefficients at scal[base ..]
+void launch_lanczos_max(double *scal, int base, int k, int out, cudaStream_t st);
+// One half (phase 0 / 1) of a Lanczos step on unnormalised vectors: w holds
+// op(t_j), tp = t_{j-1}, tc = t_j; coefficients at scal[base ..], the norm of
+// t_0 at scal[n0slot].  partials: dot_partials_doubles(); ticket: a
 // zero-initialised counter (left at zero).
-void launch_axpy_dot(float *w, const float *q, size_t n, double *scal, int cslot, const float *v, int dslot,
-                     double *partials, unsigned *ticket, int sqrt_out, cudaStream_t st);
+void launch_lanczos_step(float *w, const float *tp, const float *tc, size_t n, double *scal, int base, int n0slot,
+                         int j, int phase, double *partials, unsigned *ticket, cudaStream_t st);
 // w -= scal[slot] * q
 void launch_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot, cudaStream_t st);
 

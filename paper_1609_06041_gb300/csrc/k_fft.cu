@@ -124,6 +124,31 @@ __device__ float2 *fft_block(float2 *a, float2 *b, int P, const float2 *__restri
     return src;
 }
 
+// Band partial sums of A x for two rays (p0[k VB], p1[k VB], k < nb),
+// added in band order; the loads of 16 bands are issued together.
+__device__ __forceinline__ void band_sum2(const float *__restrict__ p0, const float *__restrict__ p1, size_t VB,
+                                          int nb, float &s0, float &s1)
+{
+    s0 = 0.0f;
+    s1 = 0.0f;
+    for (int kb = 0; kb < nb; kb += 16) {
+        float a[16], c[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const bool ok = kb + k < nb;
+            a[k] = ok ? p0[(size_t)(kb + k) * VB] : 0.0f;
+            c[k] = ok ? p1[(size_t)(kb + k) * VB] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (kb + k < nb) {
+                s0 += a[k];
+                s1 += c[k];
+            }
+        }
+    }
+}
+
 // Hhat = DFT_P of the taps placed circularly (t[k] at k mod P).
 __global__ void __launch_bounds__(FFT_T)
 k_hhat(const float *__restrict__ taps, int half, int P, const float2 *__restrict__ tw, float2 *__restrict__ hhat)
@@ -149,11 +174,15 @@ void launch_hhat(const Geometry *g, const float *taps, int half, float2 *hhat, c
 }
 
 // out = post .* D(pre .* in) * sc, sc = 1 (mode 0) or -sigma (mode 1);
-// one block per pair of views (v, v+1) of image `blockIdx.y`.
+// one block per pair of views (v, v+1) of image `blockIdx.y`.  BANDS: the
+// input is A x given as band partial sums (in = partial, nb bands), added
+// in band order and scaled by the views' path lengths.
+template <bool BANDS>
 __global__ void __launch_bounds__(FFT_T)
 k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, float *__restrict__ out,
              const float *__restrict__ pre, const float *__restrict__ post, int mode,
-             const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
+             const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw, int nb,
+             const ViewP *__restrict__ views)
 {
     extern __shared__ float2 fsm[];
     float2 *a = fsm, *b = fsm + P;
@@ -164,11 +193,21 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float x0 = 0.0f, x1 = 0.0f;
         if (i < B) {
-            x0 = in[o0 + i];
-            if (pre) x0 *= pre[o0 + i];
-            if (has1) {
-                x1 = in[o1 + i];
-                if (pre) x1 *= pre[o1 + i];
+            if (BANDS) {
+                const size_t VB = (size_t)V * B;
+                const float *p0 = in + (size_t)blockIdx.y * nb * VB + (size_t)v0 * B + i;
+                const float *p1 = in + (size_t)blockIdx.y * nb * VB + (size_t)(has1 ? v1 : v0) * B + i;
+                float s0, s1;
+                band_sum2(p0, p1, VB, nb, s0, s1);
+                x0 = s0 * views[v0].scale;
+                x1 = has1 ? s1 * views[v1].scale : 0.0f;
+            } else {
+                x0 = in[o0 + i];
+                if (pre) x0 *= pre[o0 + i];
+                if (has1) {
+                    x1 = in[o1 + i];
+                    if (pre) x1 *= pre[o1 + i];
+                }
             }
         }
         a[i] = make_float2(x0, x1);
@@ -176,7 +215,7 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
     float2 *f = fft_block(a, b, P, tw, false);
     for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
     float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
-    const float sc = ((mode == 1) ? -(float)scal[S_SIGMA] : 1.0f) / (float)P;
+    const float sc = ((mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f) / (float)P;
     for (int i = threadIdx.x; i < B; i += blockDim.x) {
         float y0 = res[i].x * sc, y1 = res[i].y * sc;
         if (post) {
@@ -188,6 +227,18 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
     }
 }
 
+// out = D (A x) from the projector's band partial sums
+void launch_filter_fft_bands(const Geometry *g, const float2 *hhat, const float *partial, float *out, int batch,
+                             cudaStream_t st)
+{
+    const int P = g->n_fft;
+    dim3 grd((g->n_views + 1) / 2, batch);
+    counted();
+    k_filter_fft<true><<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, partial, out, nullptr, nullptr, 0, nullptr,
+                                                                   g->n_views, g->n_bins, P, g->d_tw,
+                                                                   proj_bands(g->n), g->d_views);
+}
+
 void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, float *out,
                        const float *pre, const float *post, int mode, const double *scal, int batch,
                        cudaStream_t st)
@@ -195,8 +246,8 @@ void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, f
     const int P = g->n_fft;
     dim3 grd((g->n_views + 1) / 2, batch);
     counted();
-    k_filter_fft<<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, in, out, pre, post, mode, scal,
-                                                             g->n_views, g->n_bins, P, g->d_tw);
+    k_filter_fft<false><<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, in, out, pre, post, mode, scal,
+                                                                    g->n_views, g->n_bins, P, g->d_tw, 0, nullptr);
 }
 
 // Fused Step 3 and next Step 1 for the pair of views (v, v+1):
@@ -229,26 +280,15 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
     const size_t VB = (size_t)V * B;
     const size_t o0 = (size_t)v0 * B, o1 = (size_t)v1 * B;
     const float sc0 = views[v0].scale, sc1 = has1 ? views[v1].scale : 0.0f;
-    const float sigma = (float)scal[S_SIGMA];
+    const float sigma = fscal(scal, F_SIGMA);
     const float invP = 1.0f / (float)P;
 
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float r0 = 0.0f, r1 = 0.0f;
         if (i < B) {
-            // band partial sums of A x, added in band order (loads issued ahead)
-            float s0 = 0.0f, s1 = 0.0f;
-            const float *p0 = partial + o0 + i, *p1 = partial + (has1 ? o1 : o0) + i;
-            int k = 0;
-            for (; k + 4 <= nb; k += 4) {
-                const float a0 = p0[k * VB], a1 = p0[(k + 1) * VB], a2 = p0[(k + 2) * VB], a3 = p0[(k + 3) * VB];
-                const float c0 = p1[k * VB], c1 = p1[(k + 1) * VB], c2 = p1[(k + 2) * VB], c3 = p1[(k + 3) * VB];
-                s0 = (((s0 + a0) + a1) + a2) + a3;
-                s1 = (((s1 + c0) + c1) + c2) + c3;
-            }
-            for (; k < nb; ++k) {
-                s0 += p0[k * VB];
-                s1 += p1[k * VB];
-            }
+            // band partial sums of A x, added in band order
+            float s0, s1;
+            band_sum2(partial + o0 + i, partial + (has1 ? o1 : o0) + i, VB, nb, s0, s1);
             if (!has1) s1 = 0.0f;
             const float mu0 = mu_in[o0 + i], mu1 = has1 ? mu_in[o1 + i] : 0.0f;
             m_old[i] = mu0;
@@ -353,7 +393,7 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
     const bool has1 = v1 < V;
     const size_t VB = (size_t)V * B;
     const size_t o0 = so + (size_t)v0 * B, o1 = so + (size_t)(has1 ? v1 : v0) * B;
-    const float sigma = (float)scal[S_SIGMA];
+    const float sigma = fscal(scal, F_SIGMA);
     const float invP = 1.0f / (float)P;
 
     // h = D^T gmb
@@ -436,7 +476,8 @@ void kernel_attrs_fft()
 {
     const int smax = (int)(sizeof(float2) * 2 * FFT_MAX_P + sizeof(float) * 4 * (FFT_MAX_P / 2));
     cudaFuncSetAttribute(k_hhat, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_filter_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_filter_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_filter_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_dual_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_dual_bwd_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
 }

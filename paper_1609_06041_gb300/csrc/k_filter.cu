@@ -56,7 +56,7 @@ k_filter(const float *__restrict__ taps, int half, const float *__restrict__ in,
         s_in[e] = val;
     }
     __syncthreads();
-    const float sc = (mode == 1) ? -(float)scal[S_SIGMA] : 1.0f;
+    const float sc = (mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f;
     for (int base = 0; base < B; base += FT * FR) {
         float acc[FR];
         conv_view(s_in, s_t, B, tpad, base, acc);
@@ -109,7 +109,7 @@ k_dual(const float *__restrict__ taps, int half, const float *__restrict__ parti
         s_in[e] = r;
     }
     __syncthreads();
-    const float sigma = (float)scal[S_SIGMA];
+    const float sigma = fscal(scal, F_SIGMA);
     // B <= FT*FR*MAXR handled by keeping the per-round results in registers
     constexpr int MAXR = 8;
     float mun[MAXR][FR], mo[MAXR][FR];
@@ -197,7 +197,7 @@ __global__ void k_taps(int mode, int m, int P, int B, const double *__restrict__
     const int lane = threadIdx.x & 31;
     if (warp >= B) return;
     const int k = warp;
-    const float tau = scal ? (float)scal[S_TAU] : tau_h;
+    const float tau = scal ? fscal(scal, F_TAU) : tau_h;
     const float kappa = scal ? (float)scal[S_KAPPA] : kappa_h;
     const float two_m_tau = 2.0f * (float)m * tau;
     float sum = 0.0f, comp = 0.0f;

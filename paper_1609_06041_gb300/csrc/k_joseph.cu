@@ -310,13 +310,216 @@ k_project_mirror(const float *__restrict__ x, const ViewP *__restrict__ views,
     }
 }
 
+// ---------------------------------------------------------------------
+// Forward projection with the detector mirror and the view mirror (default
+// angles t_v = v pi / V).  View V-v is view v reflected in the image's
+// vertical axis: its a and m are those of view v with the signs a row view
+// (a -> -a, m -> -m) or a column view (m -> -m) gets from t -> pi - t.
+// For a row view that puts ray d of view V-v at coordinate N-1-u on the
+// same row; for a column view ray d of view V-v meets column N-1-c where
+// ray d of view v meets column c, i.e. the other band's line.  Either way
+// the reflected sample sits at pair N-2-i0 of a staged line with weight
+// -g: one evaluation of (u', g) at (d, s) yields four samples, two of view
+// v (bands A, B as in k_project_mirror) and two of view V-v:
+//     rows:    A[i0] (v, d)  B[i0] (v, B-1-d)  A[N-2-i0] (V-v, d)    B[N-2-i0] (V-v, B-1-d)
+//     columns: A[i0] (v, d)  B[i0] (v, B-1-d)  A[N-2-i0] (V-v, B-1-d) B[N-2-i0] (V-v, d)
+// Work items are view pairs (v, V-v) and the views without a partner
+// (v = 0, and v = V/2 for even V), pg items per block, 64 threads per item.
+// ---------------------------------------------------------------------
+template <bool PAIR>
+__device__ __forceinline__ float4 quad_walk(const float2 *__restrict__ PA, const float2 *__restrict__ PB, int SP,
+                                            float q, float m, int lo, int hi, int s0, float h, unsigned top)
+{
+    const float qu1 = __fadd_rn(q, m);
+    float spk = (float)lo - h;
+    int ridx = (lo - s0) * SP;
+    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f, c0 = 0.0f, c1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
+    int s = lo;
+    for (; s + 1 <= hi; s += 2) {
+        const float up0 = joseph_u(spk, m, q), up1 = joseph_u(spk, m, qu1);
+        const float t0 = __fadd_rn(up0, JOSEPH_BIAS), t1 = __fadd_rn(up1, JOSEPH_BIAS);
+        const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
+        const unsigned i1 = min((unsigned)(__float_as_int(t1) - (JOSEPH_BIAS_BITS - 2)), top);
+        const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
+        const float g1 = __fsub_rn(up1, __fsub_rn(t1, JOSEPH_BIAS));
+        const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
+        const float2 pa1 = PA[ridx + SP + (int)i1], pb1 = PB[ridx + SP + (int)i1];
+        a0 += __fmaf_rn(g0, pa0.y, pa0.x);
+        b0 += __fmaf_rn(g0, pb0.y, pb0.x);
+        a1 += __fmaf_rn(g1, pa1.y, pa1.x);
+        b1 += __fmaf_rn(g1, pb1.y, pb1.x);
+        if (PAIR) {
+            const int j0 = (int)(top - i0), j1 = (int)(top - i1);
+            const float2 qa0 = PA[ridx + j0], qb0 = PB[ridx + j0];
+            const float2 qa1 = PA[ridx + SP + j1], qb1 = PB[ridx + SP + j1];
+            c0 += __fmaf_rn(-g0, qa0.y, qa0.x);
+            e0 += __fmaf_rn(-g0, qb0.y, qb0.x);
+            c1 += __fmaf_rn(-g1, qa1.y, qa1.x);
+            e1 += __fmaf_rn(-g1, qb1.y, qb1.x);
+        }
+        spk = __fadd_rn(spk, 2.0f);
+        ridx += 2 * SP;
+    }
+    if (s <= hi) {
+        const float up0 = joseph_u(spk, m, q);
+        const float t0 = __fadd_rn(up0, JOSEPH_BIAS);
+        const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
+        const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
+        const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
+        a0 += __fmaf_rn(g0, pa0.y, pa0.x);
+        b0 += __fmaf_rn(g0, pb0.y, pb0.x);
+        if (PAIR) {
+            const int j0 = (int)(top - i0);
+            const float2 qa0 = PA[ridx + j0], qb0 = PB[ridx + j0];
+            c0 += __fmaf_rn(-g0, qa0.y, qa0.x);
+            e0 += __fmaf_rn(-g0, qb0.y, qb0.x);
+        }
+    }
+    return make_float4(a0 + a1, b0 + b1, c0 + c1, e0 + e1);
+}
+
+__global__ void __launch_bounds__(PT)
+k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
+               const int2 *__restrict__ row_items, int n_row, const int2 *__restrict__ col_items, int n_col,
+               int N, int V, int B, int pg, float *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int CW = N + 3, SP = CW | 1;
+    float2 *PA = reinterpret_cast<float2 *>(smraw);
+    float2 *PB = PA + (size_t)MR * SP;
+    ViewP *sv = reinterpret_cast<ViewP *>(PB + (size_t)MR * SP);
+    int2 *sit = reinterpret_cast<int2 *>(sv + PG);
+
+    const int bp = blockIdx.x, nbp = gridDim.x;
+    const int row_groups = (n_row + pg - 1) / pg;
+    const bool rows = (int)blockIdx.y < row_groups;
+    const int grp = rows ? blockIdx.y : blockIdx.y - row_groups;
+    const int2 *list = rows ? row_items : col_items;
+    const int nl = rows ? n_row : n_col;
+    const int nv = min(pg, nl - grp * pg);
+    const float *img = x + (size_t)blockIdx.z * N * N;
+    float *out = partial + ((size_t)blockIdx.z * nbp + bp) * V * B;
+    const int s0 = bp * MR;
+    const float h = joseph_h(N), hq = joseph_hq(N);
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    if (tid < nv) {
+        sit[tid] = list[grp * pg + tid];
+        sv[tid] = views[sit[tid].x];
+    }
+    // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
+    // the line N-1-s0-t read backwards (image value at N-1-i)
+    {
+        const int lx = tid & 31;
+        if (rows) {
+            for (int ly = tid >> 5; ly < 2 * MR; ly += nth >> 5) {
+                const int band = ly >= MR, t = ly - band * MR;
+                const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
+                const float *rowp = img + (size_t)line * N;
+                float2 *dst = (band == 0 ? PA : PB) + t * SP;
+                for (int ii = lx; ii < CW; ii += 32) {
+                    const int i = ii - 2;
+                    const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
+                    const float a = (ia >= 0 && ia < N) ? rowp[ia] : 0.0f;
+                    const float b = (ib >= 0 && ib < N) ? rowp[ib] : 0.0f;
+                    dst[ii] = make_float2(0.5f * (a + b), b - a);
+                }
+            }
+        } else {
+            const int band = lx >= MR, t = lx - band * MR;
+            const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
+            float2 *dst = (band == 0 ? PA : PB) + t * SP;
+            for (int ii = tid >> 5; ii < CW; ii += nth >> 5) {
+                const int i = ii - 2;
+                const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
+                const float a = (ia >= 0 && ia < N) ? img[(size_t)ia * N + line] : 0.0f;
+                const float b = (ib >= 0 && ib < N) ? img[(size_t)ib * N + line] : 0.0f;
+                dst[ii] = make_float2(0.5f * (a + b), b - a);
+            }
+        }
+    }
+    __syncthreads();
+    const int npair = (B + 1) / 2;
+    const unsigned top = (unsigned)(N + 2);
+    const int vi = tid >> 6;
+    if (vi >= nv) return;
+    const int v = sit[vi].x, vp = sit[vi].y;
+    const float a = sv[vi].a, m = sv[vi].m, inv_m = sv[vi].inv_m;
+    for (int d = tid & 63; d < npair; d += 64) {
+        const int dm = B - 1 - d;
+        float ov[2] = {0.0f, 0.0f}, op[2] = {0.0f, 0.0f};   // view v / V-v: [0] ray d, [1] ray dm
+#pragma unroll
+        for (int which = 0; which < 2; ++which) {
+            if (which == 1 && dm == d) break;
+            const int dd = which == 0 ? d : dm;
+            const float q = joseph_q(joseph_dp(dd, B), a, hq);
+            int lo, hi;
+            step_range(q, m, inv_m, h, -2.5f, (float)N + 0.5f, s0, s0 + MR - 1, lo, hi);
+            const float4 r = vp >= 0 ? quad_walk<true>(PA, PB, SP, q, m, lo, hi, s0, h, top)
+                                     : quad_walk<false>(PA, PB, SP, q, m, lo, hi, s0, h, top);
+            ov[which] += r.x;
+            ov[1 - which] += r.y;
+            if (rows) {
+                op[which] += r.z;
+                op[1 - which] += r.w;
+            } else {
+                op[1 - which] += r.z;
+                op[which] += r.w;
+            }
+        }
+        float *o = out + (size_t)v * B;
+        if (dm == d) {
+            o[d] = ov[0] + ov[1];
+        } else {
+            o[d] = ov[0];
+            o[dm] = ov[1];
+        }
+        if (vp >= 0) {
+            float *o2 = out + (size_t)vp * B;
+            if (dm == d) {
+                o2[d] = op[0] + op[1];
+            } else {
+                o2[d] = op[0];
+                o2[dm] = op[1];
+            }
+        }
+    }
+}
+
+// items per block of k_project_quad: the fewest waves of blocks (one block
+// per SM, shared memory) times the per-block work, staging counted as two items
+static int quad_pg(const Geometry *g, int batch)
+{
+    const long bands = g->n / (2 * MR);
+    int best = PG;
+    long best_cost = -1;
+    for (int pg = 4; pg <= PG; ++pg) {
+        const long groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
+        const long blocks = bands * groups * batch;
+        const long cost = ((blocks + g->n_sm - 1) / g->n_sm) * (pg + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = pg;
+        }
+    }
+    return best;
+}
+
 void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st)
 {
     const int N = g->n;
     dim3 grd(proj_bands(N), (g->n_row + PG - 1) / PG + (g->n_col + PG - 1) / PG, batch);
     const size_t smem = proj_smem(N);
     counted();
-    if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
+    if (g->vpair && N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
+        // view pairs and two mirrored 16-step bands per block: N/32 partial slots
+        const int pg = quad_pg(g, batch);
+        const int groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
+        const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
+        k_project_quad<<<dim3(N / (2 * MR), groups, batch), pg * 64, smem2, st>>>(
+            x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
+            pg, partial);
+    } else if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // two mirrored 16-step bands per block: N/32 partial slots, as below
         dim3 grd2(N / (2 * MR), grd.y, batch);
         const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + 64;
@@ -483,7 +686,7 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
             for (int k = 1; k < BSL; ++k) tot += red[k][tid];
             const size_t o = (size_t)blockIdx.z * N * N + (size_t)rr * N + cc;
             if (MODE == 0) out[o] = tot;
-            else out[o] = xin[o] - (float)scal[S_TAU] * tot;
+            else out[o] = xin[o] - fscal(scal, F_TAU) * tot;
         }
     }
 }
@@ -665,7 +868,7 @@ __global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restr
     for (int s = 1; s < ORB_SL; ++s) t += pp[s * NN];
     const size_t o = (size_t)blockIdx.y * NN + i;
     if (MODE == 0) out[o] = t;
-    else out[o] = xin[o] - (float)scal[S_TAU] * t;
+    else out[o] = xin[o] - fscal(scal, F_TAU) * t;
 }
 
 bool orbit_ok(const Geometry *g) { return g->orbit; }
@@ -705,6 +908,7 @@ void kernel_attrs_joseph()
     cudaFuncSetAttribute(k_backproject_orbit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_backproject_orbit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }

@@ -61,64 +61,72 @@ void launch_scale_by(const float *in, const float *s, int sqrt_s, float *out, si
     k_scale_by<<<grid_for(n, 256), 256, 0, st>>>(in, s, sqrt_s, out, n);
 }
 
-// Deterministic dot product: a fixed grid of DOT_BLOCKS blocks writes one
-// double partial each (fixed grid-stride order, fixed tree), then one block
-// adds the partials in a fixed order.
-constexpr int DOT_BLOCKS = 304;
+// Deterministic reductions: a fixed grid of DOT_BLOCKS blocks; each thread
+// sums its grid-stride elements in float, warps add their lanes by a fixed
+// shuffle tree, the warp sums of a block are added in order, and the block
+// partials the same way.  Everything is float (FP64 arithmetic is slow on
+// this GPU); the relative error stays near 1e-6, well inside what the
+// step-size setup needs.
+constexpr int DOT_BLOCKS = 1216;   // 8 blocks per SM of 152: one element group per thread
+constexpr int DOT_THREADS = 256;
 size_t dot_partials_doubles() { return DOT_BLOCKS + 64; }   // + room for the ticket counter
 
-__global__ void __launch_bounds__(256)
-k_dot_partial(const float *a, const float *b, size_t n, double *partials)
+__device__ __forceinline__ float warp_sum(float v)
 {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        acc += (double)a[i] * (b ? (double)b[i] : 1.0);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
 }
 
-__global__ void k_dot_final(const double *partials, int np, double *scal, int slot)
+// block total (valid in thread 0) of the float per-thread sums: warp trees,
+// then the warp sums in order
+__device__ __forceinline__ float block_sum(float v)
 {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
-    red[threadIdx.x] = acc;
+    __shared__ float wsum[DOT_THREADS / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < DOT_THREADS / 32; ++k) t += wsum[k];
     }
-    if (threadIdx.x == 0) scal[slot] = red[0];
+    return t;
+}
+
+// sum of the np block partials (strided runs per thread, then block_sum),
+// valid in thread 0; every thread of the block calls it.  The partials are
+// read from L2 (written by other blocks before their fence).
+__device__ __forceinline__ float partials_sum(const double *partials, int np)
+{
+    float t = 0.0f;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t += (float)__ldcg(partials + i);
+    return block_sum(t);
+}
+
+__global__ void __launch_bounds__(DOT_THREADS)
+k_dot_partial(const float *a, const float *b, size_t n, double *partials)
+{
+    float acc = 0.0f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc = fmaf(a[i], b ? b[i] : 1.0f, acc);
+    const float t = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = (double)t;
+}
+
+__global__ void __launch_bounds__(DOT_THREADS) k_dot_final(const double *partials, int np, double *scal, int slot)
+{
+    const float t = partials_sum(partials, np);
+    if (threadIdx.x == 0) scal[slot] = (double)t;
 }
 
 void launch_dot(const float *a, const float *b, size_t n, double *scal, int slot,
                 double *partials, cudaStream_t st)
 {
     counted();
-    k_dot_partial<<<DOT_BLOCKS, 256, 0, st>>>(a, b, n, partials);
+    k_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(a, b, n, partials);
     counted();
-    k_dot_final<<<1, 256, 0, st>>>(partials, DOT_BLOCKS, scal, slot);
-}
-
-__global__ void k_normalize(const float *in, float *out, size_t n, const double *scal, int slot)
-{
-    const float s2 = (float)scal[slot];
-    const float inv = s2 > 0.0f ? rsqrtf(s2) : 0.0f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = in[i] * inv;
-}
-
-void launch_normalize(const float *in, float *out, size_t n, const double *scal, int slot,
-                      cudaStream_t st)
-{
-    counted();
-    k_normalize<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, scal, slot);
+    k_dot_final<<<1, DOT_THREADS, 0, st>>>(partials, DOT_BLOCKS, scal, slot);
 }
 
 // One-thread scalar program (keeps the whole setup on the device, so a
@@ -162,104 +170,160 @@ __global__ void k_scalars(double *s, int op, double a0, double a1, double a2, in
         s[i0] += a0 * s[(int)a1];
         break;
     }
+    float *f = reinterpret_cast<float *>(s + S_F32);
+    f[F_TAU] = (float)s[S_TAU];
+    f[F_SIGMA] = (float)s[S_SIGMA];
+    f[F_LAMBDA] = (float)s[S_LAMBDA];
+    f[F_INV8LAM] = (float)s[S_INV8LAM];
 }
 
-// Largest eigenvalue of the Lanczos tridiagonal T_k (diagonal s[S_LZ + 2j],
-// off-diagonal s[S_LZ + 2j + 1]) into s[out]: multisection on the Sturm
+// Largest eigenvalue of the Lanczos tridiagonal T_k (diagonal s[base + 2j],
+// off-diagonal s[base + 2j + 1]) into s[out]: multisection on the Sturm
 // count of T - x I (the number of negative pivots of its LDL^T is the
-// number of eigenvalues below x), 32 points per round, in double precision.
-__global__ void k_lanczos_max(double *s, int k, int out)
+// number of eigenvalues below x), 32 points per round.  The count runs in
+// float on T scaled by its Gershgorin bound (backward stable: the count is
+// exact for a matrix within a few float ulps of T); the result is the upper
+// end of the final bracket, so it errs high.
+__global__ void k_lanczos_max(double *s, int base, int k, int out)
 {
+    __shared__ float ta[LANCZOS_MAX], tb[LANCZOS_MAX];
     const int lane = threadIdx.x;
-    double lo = 0.0, hi = 0.0;
-    for (int j = 0; j < k; ++j) {   // Gershgorin interval
-        const double al = s[S_LZ + 2 * j];
-        const double rad = (j > 0 ? fabs(s[S_LZ + 2 * j - 1]) : 0.0) + (j + 1 < k ? fabs(s[S_LZ + 2 * j + 1]) : 0.0);
-        lo = j == 0 ? al - rad : fmin(lo, al - rad);
-        hi = j == 0 ? al + rad : fmax(hi, al + rad);
+    for (int j = lane; j < k; j += 32) {
+        ta[j] = (float)s[base + 2 * j];
+        tb[j] = (float)s[base + 2 * j + 1];
     }
-    for (int round = 0; round < 12 && hi - lo > 1e-13 * fmax(fabs(hi), 1e-300); ++round) {
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    __syncwarp();
+    float glo = 0.0f, ghi = 0.0f;
+    for (int j = 0; j < k; ++j) {   // Gershgorin interval
+        const float rad = (j > 0 ? fabsf(tb[j - 1]) : 0.0f) + (j + 1 < k ? fabsf(tb[j]) : 0.0f);
+        glo = j == 0 ? ta[j] - rad : fminf(glo, ta[j] - rad);
+        ghi = j == 0 ? ta[j] + rad : fmaxf(ghi, ta[j] + rad);
+    }
+    const float big = fmaxf(fabsf(glo), fabsf(ghi));
+    if (!(big > 0.0f)) {
+        if (lane == 0) s[out] = 0.0;
+        return;
+    }
+    const float inv = 1.0f / big;
+    float lo = glo * inv, hi = ghi * inv;
+    for (int round = 0; round < 8 && hi - lo > 4e-7f * fmaxf(fabsf(hi), 1e-30f); ++round) {
+        const float x = lo + (hi - lo) * (float)(lane + 1) * (1.0f / 33.0f);
         int below = 0;
-        double d = 1.0;
+        float d = 1.0f;
         for (int j = 0; j < k; ++j) {
-            const double b = j > 0 ? s[S_LZ + 2 * j - 1] : 0.0;
-            d = (s[S_LZ + 2 * j] - x) - (j > 0 ? b * b / d : 0.0);
-            if (d == 0.0) d = -1e-300;
-            if (d < 0.0) ++below;
+            const float b = j > 0 ? tb[j - 1] * inv : 0.0f;
+            d = (ta[j] * inv - x) - (j > 0 ? b * b / d : 0.0f);
+            if (d == 0.0f) d = -1e-30f;
+            if (d < 0.0f) ++below;
         }
         // lowest point with all k eigenvalues below it bounds lambda_max from above
         const unsigned all = __ballot_sync(0xffffffffu, below == k);
         const int first = all ? __ffs(all) - 1 : 32;     // lanes >= first have below == k
-        const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / 33.0;
-        const double nhi = first == 32 ? hi : lo + (hi - lo) * (double)(first + 1) / 33.0;
+        const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first * (1.0f / 33.0f);
+        const float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) * (1.0f / 33.0f);
         lo = nlo;
-        hi = nhi;
+        hi = fmaxf(nhi, nlo);
     }
-    if (lane == 0) s[out] = hi;
+    if (lane == 0) s[out] = (double)(hi * big) * (1.0 + 1e-6);
 }
 
-void launch_lanczos_max(double *scal, int k, int out, cudaStream_t st)
+void launch_lanczos_max(double *scal, int base, int k, int out, cudaStream_t st)
 {
     counted();
-    k_lanczos_max<<<1, 32, 0, st>>>(scal, k, out);
+    k_lanczos_max<<<1, 32, 0, st>>>(scal, base, k, out);
 }
 
-// w -= c q (c = scal[cslot], skipped when cslot < 0), then scal[dslot] =
-// <w, v> (v = w when NULL): a fixed grid writes per-block partials; the
-// last block to finish (ticket counter) adds them in block order and
-// resets the counter, so the sum is deterministic and nothing waits.
-constexpr int AXD_BLOCKS = 304;
-__global__ void __launch_bounds__(256)
-k_axpy_dot(float *w, const float *q, size_t n, double *scal, int cslot, const float *v, int dslot,
-           double *partials, unsigned *ticket, int sqrt_out)
+// One half of a Lanczos step on unnormalised vectors (t_j = n_j q_j with
+// n_0 = s[n0slot] and n_j = beta_{j-1} = s[base + 2j - 1]):
+//   phase 0:  w = w / n_j - (n_j / n_{j-1}) t_{j-1}   (w held op(t_j));
+//             alpha_j = <w, t_j> / n_j                 -> s[base + 2j]
+//   phase 1:  w -= (alpha_j / n_j) t_j;  beta_j = |w|  -> s[base + 2j + 1]
+// The dot is the deterministic reduction above; the last block to finish
+// (ticket counter) adds the partials in block order and resets the counter.
+__global__ void __launch_bounds__(DOT_THREADS)
+k_lanczos_step(float *__restrict__ w, const float *__restrict__ tp, const float *__restrict__ tc, size_t n,
+               double *s, int base, int n0slot, int j, int phase, double *partials, unsigned *ticket)
 {
-    __shared__ double red[256];
     __shared__ bool last;
-    const float c = cslot >= 0 ? (float)scal[cslot] : 0.0f;
-    double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float wi = w[i];
-        if (cslot >= 0) {
-            wi = fmaf(-c, q[i], wi);
-            w[i] = wi;
-        }
-        acc += (double)wi * (double)(v ? v[i] : wi);
+    __shared__ float coef[3];
+    const float *x2 = phase == 0 ? tp : tc;
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(tc) |
+                       reinterpret_cast<uintptr_t>(x2)) & 15) == 0;
+    const size_t n4 = vec ? n / 4 : 0;   // four elements per load
+    float4 *w4 = reinterpret_cast<float4 *>(w);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x2), *t4 = reinterpret_cast<const float4 *>(tc);
+    // the first group's loads go out before the coefficients are known
+    const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 a0 = zero, xa = zero, ta = zero;
+    if (tid < n4) {
+        a0 = w4[tid];
+        xa = x4[tid];
+        if (phase == 0) ta = t4[tid];
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
+    // coefficients from the double slots, once per block (FP64 is slow here)
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = red[0];
+        const float nj = (float)(j == 0 ? s[n0slot] : s[base + 2 * j - 1]);
+        float c1 = 1.0f, c2 = 0.0f;
+        if (phase == 0) {
+            const float njm1 = (float)(j <= 1 ? s[n0slot] : s[base + 2 * j - 3]);
+            c1 = nj > 0.0f ? 1.0f / nj : 0.0f;
+            c2 = (j > 0 && njm1 > 0.0f) ? nj / njm1 : 0.0f;
+        } else {
+            c2 = nj > 0.0f ? (float)s[base + 2 * j] / nj : 0.0f;
+        }
+        coef[0] = c1;
+        coef[1] = c2;
+        coef[2] = nj;
+    }
+    __syncthreads();
+    const float c1 = coef[0], c2 = coef[1];
+    float acc = 0.0f;
+    auto group = [&](float4 a, float4 x, float4 t, size_t i) {
+        if (c2 == 0.0f) x = zero;   // t_{-1} is never read (it may hold anything)
+        a.x = fmaf(-c2, x.x, a.x * c1);
+        a.y = fmaf(-c2, x.y, a.y * c1);
+        a.z = fmaf(-c2, x.z, a.z * c1);
+        a.w = fmaf(-c2, x.w, a.w * c1);
+        w4[i] = a;
+        const float4 d = phase == 0 ? t : a;
+        acc = fmaf(a.x, d.x, acc);
+        acc = fmaf(a.y, d.y, acc);
+        acc = fmaf(a.z, d.z, acc);
+        acc = fmaf(a.w, d.w, acc);
+    };
+    if (tid < n4) group(a0, xa, ta, tid);
+    for (size_t i = tid + stride; i < n4; i += stride) group(w4[i], x4[i], phase == 0 ? t4[i] : zero, i);
+    const size_t done = n4 * 4;
+    for (size_t i = done + tid; i < n; i += stride) {
+        float wi = w[i] * c1;
+        if (c2 != 0.0f) wi = fmaf(-c2, x2[i], wi);
+        w[i] = wi;
+        acc = fmaf(wi, phase == 0 ? tc[i] : wi, acc);
+    }
+    const float t = block_sum(acc);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = (double)t;
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double t = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile double *)partials)[i];
-    red[threadIdx.x] = t;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
+    const float tf = partials_sum(partials, gridDim.x);
     if (threadIdx.x == 0) {
-        scal[dslot] = red[0];
-        if (sqrt_out >= 0) scal[sqrt_out] = sqrt(red[0]);
+        const float nj = coef[2];
+        if (phase == 0) s[base + 2 * j] = nj > 0.0f ? (double)(tf / nj) : 0.0;
+        else s[base + 2 * j + 1] = (double)sqrtf(fmaxf(tf, 0.0f));
         *ticket = 0u;
     }
 }
 
-void launch_axpy_dot(float *w, const float *q, size_t n, double *scal, int cslot, const float *v, int dslot,
-                     double *partials, unsigned *ticket, int sqrt_out, cudaStream_t st)
+void launch_lanczos_step(float *w, const float *tp, const float *tc, size_t n, double *scal, int base, int n0slot,
+                         int j, int phase, double *partials, unsigned *ticket, cudaStream_t st)
 {
     counted();
-    k_axpy_dot<<<AXD_BLOCKS, 256, 0, st>>>(w, q, n, scal, cslot, v, dslot, partials, ticket, sqrt_out);
+    k_lanczos_step<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(w, tp, tc, n, scal, base, n0slot, j, phase, partials, ticket);
 }
 
 __global__ void k_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot)

@@ -72,8 +72,8 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     const int R0 = blockIdx.y * tr - H, C0 = blockIdx.x * tc - H;
     const int c0 = C0 + 2 * lane;   // image columns c0, c0 + 1 of this lane
     const size_t NN = (size_t)N * N;
-    const float lam = (float)scal[S_LAMBDA];
-    const float inv8 = (float)scal[S_INV8LAM];
+    const float lam = fscal(scal, F_LAMBDA);
+    const float inv8 = fscal(scal, F_INV8LAM);
     // forward differences: along x on columns 0..N-2, along y on columns 0..N-1
     const bool cx0 = (unsigned)c0 < (unsigned)(N - 1), cx1 = (unsigned)(c0 + 1) < (unsigned)(N - 1);
     const bool cy0 = (unsigned)c0 < (unsigned)N, cy1 = (unsigned)(c0 + 1) < (unsigned)N;
@@ -267,7 +267,7 @@ k_tv_step(const float *__restrict__ z, const float *__restrict__ p_in, float *__
     const float *zz = z + blockIdx.z * NN;
     const float *px = p_in + blockIdx.z * 2 * NN, *py = px + NN;
     float *ox = p_out + blockIdx.z * 2 * NN, *oy = ox + NN;
-    const float lam = (float)scal[S_LAMBDA], inv8 = (float)scal[S_INV8LAM];
+    const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
     const float2 q = tv_q(zz, px, py, r, c, N, lam, inv8);
     const float sc = fminf(1.0f, rsqrtf(fmaf(q.x, q.x, q.y * q.y)));
     ox[j] = q.x * sc;
@@ -284,7 +284,7 @@ k_tv_final(const float *__restrict__ z, const float *__restrict__ p, float *__re
     const size_t NN = (size_t)N * N;
     const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
     x[blockIdx.z * NN + (size_t)r * N + c] =
-        fmaxf(0.0f, tv_s(z + blockIdx.z * NN, px, py, r, c, N, (float)scal[S_LAMBDA]));
+        fmaxf(0.0f, tv_s(z + blockIdx.z * NN, px, py, r, c, N, fscal(scal, F_LAMBDA)));
 }
 
 // Adjoint of x = max(0, s), s = z + lam div p, with the adjoint gp_next of p
@@ -301,7 +301,7 @@ k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const f
         const size_t NN = (size_t)N * N, j = (size_t)r * N + c;
         const float *zz = z + blockIdx.z * NN, *g = gx + blockIdx.z * NN;
         const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
-        const float lam = (float)scal[S_LAMBDA];
+        const float lam = fscal(scal, F_LAMBDA);
         auto gs_at = [&](int rr, int cc) {
             return tv_s(zz, px, py, rr, cc, N, lam) > 0.0f ? g[(size_t)rr * N + cc] : 0.0f;
         };
@@ -330,7 +330,7 @@ k_tv_step_bwd_a(const float *__restrict__ z, const float *__restrict__ p, const 
         const size_t NN = (size_t)N * N, j = (size_t)r * N + c;
         const float *zz = z + blockIdx.z * NN;
         const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
-        const float lam = (float)scal[S_LAMBDA], inv8 = (float)scal[S_INV8LAM];
+        const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
         const float2 q = tv_q(zz, px, py, r, c, N, lam, inv8);
         const float *gnx = gp_next + blockIdx.z * 2 * NN, *gny = gnx + NN;
         const float2 g = proj_adj(q, make_float2(gnx[j], gny[j]));
@@ -360,7 +360,7 @@ k_tv_step_bwd_b(const float *__restrict__ z, const float *__restrict__ p, const 
         const float *zz = z + blockIdx.z * NN;
         const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
         const float *qx = gq + blockIdx.z * 2 * NN, *qy = qx + NN;
-        const float lam = (float)scal[S_LAMBDA], inv8 = (float)scal[S_INV8LAM];
+        const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
         auto gs_at = [&](int rr, int cc) {
             const float gxv = -inv8 * tv_div(qx, qy, rr, cc, N);
             return tv_s(zz, px, py, rr, cc, N, lam) > 0.0f ? gxv : 0.0f;
