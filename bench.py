@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from the full ncu capture in profiles/kernels_lowdose_512_v720_b736.md
 # (update together with the kernels; None when no capture of the current kernel exists)
-TRAFFIC_BYTES = {"A": 1.087488e6, "AT": 3.053568e6}
+TRAFFIC_BYTES = {"A": 1.095936e6, "AT": 2.025728e6}
 
 
 def dist_info():
@@ -221,7 +221,7 @@ def measure_batched(P, steps=3, count=64, seed=0):
             b, w = p, None
         slices.append((g, b, w, P.PDTVParams(mode=mode, iters=30, beta=0.005)))
     stream = torch.cuda.current_stream()
-    bs = P.BatchedSolve(slices)
+    bs = P.BatchedSolve(slices, autotune=True)   # one autotune per distinct geometry, before capture
     bs.run()
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -329,6 +329,7 @@ def run_ours(args):
 
     N, V, B = WORK["n"], WORK["views"], WORK["bins"]
     g = P.Geometry(N, V, B)
+    tuning = g.autotune()   # launch shapes by measurement, once per geometry (untimed, like its creation)
     # synthetic slice for this rank: phantom -> A (on the GPU) -> Poisson data
     xt = torch.from_numpy(phantom(rank).astype(np.float32)).cuda()
     p = P.ct_project(g, xt).cpu().numpy()
@@ -407,9 +408,10 @@ def run_ours(args):
     nnz = joseph_nnz(N, V, B)
     flops = 2.0 * nnz
     # dominant operator: the slower of A (ct_project: band kernel + reduction)
-    # and A^T (ct_backproject); both carry 2 nnz(A) algorithmic flops
-    dom_name, dom_ms, dom_key = ("ct_backproject (A^T, k_backproject_tiles)", at_ms, "AT") if at_ms >= a_ms else \
-        ("ct_project (A, k_project_bands + k_band_reduce)", a_ms, "A")
+    # and A^T (ct_backproject: orbit kernel + slice reduction); both carry
+    # 2 nnz(A) algorithmic flops
+    dom_name, dom_ms, dom_key = ("ct_backproject (A^T, k_backproject_orbit + k_orbit_reduce)", at_ms, "AT") \
+        if at_ms >= a_ms else ("ct_project (A, k_project_quad + k_band_reduce)", a_ms, "A")
     achieved = flops / (dom_ms / 1e3) / 1e12
 
     # ---- end to end through the public API with host buffers ----
@@ -455,7 +457,7 @@ def run_ours(args):
                        "beta": WORK["beta"], "i0": WORK["i0"], "iters_per_step": WORK["iters"],
                        "tv_iters": WORK["tv_iters"], "norm_iters": WORK["norm_iters"],
                        "l2": "flushed between steps (512 MB write, untimed)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tuning": tuning},
             "breakdown_ms": {"solve": step_ms, "iterations_only": loop_ms,
                              "setup": step_ms - loop_ms, "per_iteration": loop_ms / WORK["iters"],
                              "A_launch": a_ms, "AT_launch": at_ms},
@@ -489,6 +491,7 @@ def run_ncu_case(args):
     import paper_1609_06041_gb300 as P
     N, V, B = WORK["n"], WORK["views"], WORK["bins"]
     g = P.Geometry(N, V, B)
+    g.autotune()
     xt = torch.from_numpy(phantom(0).astype(np.float32)).cuda()
     p = P.ct_project(g, xt).cpu().numpy()
     b_np, w_np = synth.poisson_data(p, WORK["i0"], 100)

@@ -85,6 +85,36 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins,
 void ct_geometry_destroy(ct_geometry *geom);
 
 /*
+ * Launch-shape tuning (no counterpart in the paper: it picks how the work of
+ * A, A^T and the TV prox of Eq. 17 is cut into thread blocks, never what is
+ * computed).  Three shapes are held by the geometry:
+ *   items_per_block  view pairs (v, V-v) sharing one staged band pair in the
+ *                    projector, 64 threads each (4..16);
+ *   orbit_slices     base-view slices of the rotation-orbit backprojector,
+ *                    one partial image each (1..8, at most 1024 base views
+ *                    per slice);
+ *   tv_rows          fewest interior rows of a TV prox tile (4..64).
+ * 0 selects the built-in rule (a wave-count model for items_per_block, 4
+ * slices, 16 rows).  A shape changes the order in which independent
+ * partial sums are added, so results can differ in the last float bits
+ * between shapes; for one shape they are deterministic.
+ *
+ * ct_geometry_autotune times every candidate of each shape on synthetic data
+ * of the geometry's size (batch images for A and A^T) on `stream`, with
+ * CUDA events, and stores the fastest.  It allocates and frees device
+ * memory and synchronises the stream: call it before capturing a graph and
+ * not while other calls use the geometry.  On error the previous shapes
+ * are kept.  Errors: CT_ERR_ARG (NULL geometry, batch outside [1, 64]),
+ * CT_ERR_OOM, CT_ERR_CUDA.
+ * ct_geometry_set_tuning validates and stores shapes (CT_ERR_ARG when one is
+ * out of range); ct_geometry_get_tuning reads them (NULL outputs skipped).
+ */
+ct_status ct_geometry_autotune(ct_geometry *geom, int batch, void *stream);
+ct_status ct_geometry_set_tuning(ct_geometry *geom, int items_per_block, int orbit_slices, int tv_rows);
+ct_status ct_geometry_get_tuning(const ct_geometry *geom, int *items_per_block, int *orbit_slices,
+                                 int *tv_rows);
+
+/*
  * Forward projection sino = A img (A of Eq. 1; Joseph interpolation).
  * img: batch x N x N, sino: batch x V x B (overwritten).
  */

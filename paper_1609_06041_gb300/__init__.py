@@ -12,8 +12,11 @@ from .ctpd import (  # noqa: F401
     Geometry,
     PDTVParams,
     ct_backproject,
+    ct_geometry_autotune,
     ct_geometry_create,
     ct_geometry_destroy,
+    ct_geometry_get_tuning,
+    ct_geometry_set_tuning,
     ct_kernel_launches,
     ct_last_error,
     ct_pdtv_solve,

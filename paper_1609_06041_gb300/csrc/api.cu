@@ -541,7 +541,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         for (int c = chunks; c > 0; --c) {
             const int steps = (left + c - 1) / c;
             left -= steps;
-            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, g->n_sm, steps, c == 1, scal, st);
+            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, g->n_sm, g->tune_tv, steps, c == 1, scal, st);
             cur ^= 1;
         }
         // Step 3: A x^{k+1} (band partial sums); the dual update forms the

@@ -45,6 +45,10 @@ struct Geometry {
     int2 *d_row_items;    // device, (v, V-v) for 1 <= v <= V/4, and (0, -1)
     int2 *d_col_items;    // device, (v, V-v) for V/4 < v < V/2, and (V/2, -1) for even V
     int n_sm;             // multiprocessors of the device
+    // launch shapes chosen by ct_geometry_autotune (0: the built-in rule)
+    int tune_pg;          // projector view items per block (4..16)
+    int tune_orb;         // A^T orbit base-view slices (1..8)
+    int tune_tv;          // fewest interior rows of a TV tile (4..64)
     double *h_angles;     // host copy
 };
 
@@ -134,6 +138,7 @@ void launch_band_reduce(const Geometry *g, const float *partial, float *out, int
 // of scratch (ORB_SL partial images per image).
 bool orbit_ok(const Geometry *g);
 size_t orbit_partial_floats(const Geometry *g, int batch);
+bool orbit_slices_ok(const Geometry *g, int nsl);
 void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
                               const double *scal, int batch, float *partial, cudaStream_t st);
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
@@ -203,9 +208,10 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
 // dual field p = (px, py)), temporally blocked tiles held in registers.
 // Runs `steps` <= tv_max_steps() dual steps reading p_in and writing p_out;
 // when final != 0 also writes x = max(0, z + lam div p).  n_sm (the
-// device's SM count) sizes the tiles.
+// device's SM count) and min_rows (fewest interior rows per tile, 0: the
+// default) size the tiles.
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int n_sm, int steps, int final, const double *scal, cudaStream_t st);
+               int n, int n_sm, int min_rows, int steps, int final, const double *scal, cudaStream_t st);
 int tv_max_steps();
 
 // Small helpers

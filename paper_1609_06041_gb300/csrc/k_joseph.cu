@@ -1,6 +1,8 @@
 // k_joseph.cu -- Joseph forward projector A (ray-driven) and its transpose
 // A^T (pixel-driven gather), the A and A^T of Eqs. 18-20 / 29-31.  Both are
 // deterministic (fixed summation orders, no atomics).
+#include <algorithm>
+
 #include "ctpd_internal.cuh"
 
 namespace ctpd {
@@ -513,7 +515,7 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
     counted();
     if (g->vpair && N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // view pairs and two mirrored 16-step bands per block: N/32 partial slots
-        const int pg = quad_pg(g, batch);
+        const int pg = g->tune_pg > 0 ? std::min(g->tune_pg, PG) : quad_pg(g, batch);
         const int groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
         const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
         k_project_quad<<<dim3(N / (2 * MR), groups, batch), pg * 64, smem2, st>>>(
@@ -702,13 +704,15 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // quadrant and evaluates, per base view v < V/2, the weights of P and of
 // R90 P, which cover all eight (pixel, view) pairs of the orbit
 // {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Base views are split into
-// ORB_SL slices (grid.z); each slice writes its own partial image and
-// k_orbit_reduce adds the slices in a fixed order.  The weights are the
+// nsl slices (grid.z; 4 unless tuned, at most ORB_SL_MAX); each slice
+// writes its own partial image and k_orbit_reduce adds the slices in a
+// fixed order.  The weights are the
 // pixel-side Joseph weights of k_backproject_tiles, so both kernels compute
 // the same A^T.
 // =====================================================================
 constexpr int ORB_T = 16;        // quadrant tile side
-constexpr int ORB_SL = 4;        // base-view slices
+constexpr int ORB_SL = 4;        // base-view slices unless tuned
+constexpr int ORB_SL_MAX = 8;
 constexpr int ORB_VC = 8;        // base views staged per chunk
 constexpr int ORB_RW = 36;       // values per window: pairs (k, k+1), k <= ORB_RW - 2
 constexpr int ORB_MAXS = 1024;   // base views per slice (V <= 8192)
@@ -735,7 +739,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <bool AL>
 __global__ void __launch_bounds__(256, 8)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
-                    int N, int V, int B)
+                    int N, int V, int B, int nsl)
 {
     // raw[buffer][view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][value]
     extern __shared__ __align__(16) unsigned char osm[];
@@ -744,14 +748,14 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     int *wbs = reinterpret_cast<int *>(tt + 2 * ORB_VC);                       // ORB_MAXS x 2
     const int tid = threadIdx.y * ORB_T + threadIdx.x;
     const int half = N / 2, V2 = V / 2;
-    const int slice = blockIdx.z % ORB_SL, img = blockIdx.z / ORB_SL;
+    const int slice = blockIdx.z % nsl, img = blockIdx.z / nsl;
     const int r0 = blockIdx.y * ORB_T, c0 = half + blockIdx.x * ORB_T;   // quadrant r < N/2, c >= N/2
     const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
     const bool inside = r < half && c < N;
     const float h = 0.5f * (float)(N - 1), hb = 0.5f * (float)(B - 1), hb_lo = hb - 0.5f;
     const float xq = (float)c - h, yq = (float)r - h;               // P = (x, y); R90 P = (-y, x)
     const float *ys = y + (size_t)img * V * B;
-    const int vb0 = (int)((long long)V2 * slice / ORB_SL), vb1 = (int)((long long)V2 * (slice + 1) / ORB_SL);
+    const int vb0 = (int)((long long)V2 * slice / nsl), vb1 = (int)((long long)V2 * (slice + 1) / nsl);
     const int nvs = vb1 - vb0;
     float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
 
@@ -842,7 +846,7 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         __syncthreads();   // the buffer is refilled two chunks later
     }
     if (inside) {
-        float *pp = partial + ((size_t)img * ORB_SL + slice) * N * N;
+        float *pp = partial + ((size_t)img * nsl + slice) * N * N;
         pp[(size_t)r * N + c] = aP;
         pp[(size_t)c * N + (N - 1 - r)] = a90;                   // R90 (r, c) = (c, N-1-r)
         pp[(size_t)(N - 1 - r) * N + (N - 1 - c)] = a180;        // R180 (r, c) = (N-1-r, N-1-c)
@@ -858,38 +862,45 @@ static size_t orbit_smem()
 // out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
 template <int MODE>
 __global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restrict__ out, const float *xin,
-                               const double *__restrict__ scal, size_t NN)
+                               const double *__restrict__ scal, size_t NN, int nsl)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= NN) return;
-    const float *pp = partial + (size_t)blockIdx.y * ORB_SL * NN + i;
+    const float *pp = partial + (size_t)blockIdx.y * nsl * NN + i;
     float t = pp[0];
-#pragma unroll
-    for (int s = 1; s < ORB_SL; ++s) t += pp[s * NN];
+    for (int s = 1; s < nsl; ++s) t += pp[s * NN];
     const size_t o = (size_t)blockIdx.y * NN + i;
     if (MODE == 0) out[o] = t;
     else out[o] = xin[o] - fscal(scal, F_TAU) * t;
 }
 
 bool orbit_ok(const Geometry *g) { return g->orbit; }
-size_t orbit_partial_floats(const Geometry *g, int batch) { return (size_t)ORB_SL * g->n * g->n * batch; }
+size_t orbit_partial_floats(const Geometry *g, int batch) { return (size_t)ORB_SL_MAX * g->n * g->n * batch; }
+
+// base-view slices of the orbit kernel: a slice holds at most ORB_MAXS base views
+bool orbit_slices_ok(const Geometry *g, int nsl)
+{
+    return nsl >= 1 && nsl <= ORB_SL_MAX && (g->n_views / 2 + nsl - 1) / nsl <= ORB_MAXS;
+}
+static int orbit_slices(const Geometry *g) { return g->tune_orb > 0 ? g->tune_orb : ORB_SL; }
 
 void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
                               const double *scal, int batch, float *partial, cudaStream_t st)
 {
     const int q = g->n / 2;
-    dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, ORB_SL * batch);
+    const int nsl = orbit_slices(g);
+    dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, nsl * batch);
     counted(2);
     if (g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0)
         k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
-                                                                                g->n_views, g->n_bins);
+                                                                                g->n_views, g->n_bins, nsl);
     else
         k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
-                                                                                 g->n_views, g->n_bins);
+                                                                                 g->n_views, g->n_bins, nsl);
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
-    if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
-    else k_orbit_reduce<1><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN);
+    if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN, nsl);
+    else k_orbit_reduce<1><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN, nsl);
 }
 
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,

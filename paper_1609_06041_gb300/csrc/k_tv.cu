@@ -43,7 +43,7 @@ struct TvTiles {
 // Column tiles are as wide as the region allows; rows are split so that the
 // tiles of one image about fill the GPU once (one block per SM), but no
 // narrower than TV_MIN_TR rows and no taller than the region.
-static TvTiles tv_tiles(int N, int steps, int n_sm)
+static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr)
 {
     const int H = steps + 1;
     TvTiles t;
@@ -51,7 +51,7 @@ static TvTiles tv_tiles(int N, int steps, int n_sm)
     t.ncb = (N + t.tc - 1) / t.tc;
     const int tr_max = TV_ROWS - 2 * H;
     int nrb = std::max(1, n_sm / t.ncb);
-    nrb = std::min(nrb, (N + TV_MIN_TR - 1) / TV_MIN_TR);
+    nrb = std::min(nrb, (N + min_tr - 1) / min_tr);
     nrb = std::max(nrb, (N + tr_max - 1) / tr_max);
     t.tr = (N + nrb - 1) / nrb;
     t.nrb = (N + t.tr - 1) / t.tr;
@@ -185,9 +185,9 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 }
 
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int n_sm, int steps, int final_, const double *scal, cudaStream_t st)
+               int n, int n_sm, int min_rows, int steps, int final_, const double *scal, cudaStream_t st)
 {
-    const TvTiles t = tv_tiles(n, steps, n_sm);
+    const TvTiles t = tv_tiles(n, steps, n_sm, min_rows > 0 ? min_rows : TV_MIN_TR);
     counted();
     k_tv<<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
 }

@@ -52,6 +52,9 @@ EXPORTS = {
     "ct_kernel_launches": ([], ctypes.c_ulonglong),
     "ct_geometry_create": ([_i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
     "ct_geometry_destroy": ([_vp], None),
+    "ct_geometry_autotune": ([_vp, _i, _vp], _i),
+    "ct_geometry_set_tuning": ([_vp, _i, _i, _i], _i),
+    "ct_geometry_get_tuning": ([_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "ct_project": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
@@ -145,6 +148,21 @@ class Geometry:
             _lib.ct_geometry_destroy(self._h)
             self._h = ctypes.c_void_p()
 
+    def autotune(self, batch: int = 1) -> dict:
+        """ct_geometry_autotune on the current stream; returns the chosen shapes."""
+        _check(_lib.ct_geometry_autotune(self.handle, int(batch), _stream()))
+        return self.tuning
+
+    @property
+    def tuning(self) -> dict:
+        """Launch shapes held by the geometry (0: built-in rule)."""
+        a, b, c = _i(), _i(), _i()
+        _check(_lib.ct_geometry_get_tuning(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"items_per_block": a.value, "orbit_slices": b.value, "tv_rows": c.value}
+
+    def set_tuning(self, items_per_block: int = 0, orbit_slices: int = 0, tv_rows: int = 0) -> None:
+        _check(_lib.ct_geometry_set_tuning(self.handle, int(items_per_block), int(orbit_slices), int(tv_rows)))
+
     def __del__(self):
         try:
             self.close()
@@ -158,6 +176,18 @@ def ct_geometry_create(n, n_views, n_bins, angles=None) -> Geometry:
 
 def ct_geometry_destroy(g: Geometry) -> None:
     g.close()
+
+
+def ct_geometry_autotune(g: Geometry, batch: int = 1) -> dict:
+    return g.autotune(batch)
+
+
+def ct_geometry_set_tuning(g: Geometry, items_per_block: int = 0, orbit_slices: int = 0, tv_rows: int = 0) -> None:
+    g.set_tuning(items_per_block, orbit_slices, tv_rows)
+
+
+def ct_geometry_get_tuning(g: Geometry) -> dict:
+    return g.tuning
 
 
 def ct_project(g: Geometry, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -272,10 +302,18 @@ class BatchedSolve:
     workspaces and outputs are allocated once here, so run() enqueues only
     device work (and can be captured in a CUDA graph)."""
 
-    def __init__(self, slices):
-        # slices: list of (Geometry, b, w or None, PDTVParams)
+    def __init__(self, slices, autotune=False):
+        # slices: list of (Geometry, b, w or None, PDTVParams).  autotune:
+        # run ct_geometry_autotune once per distinct geometry first (not
+        # capturable; do it here, before any graph capture of run()).
         self.slices = list(slices)
         n = len(self.slices)
+        if autotune:
+            seen = set()
+            for g, _, _, _ in self.slices:
+                if id(g) not in seen:
+                    seen.add(id(g))
+                    g.autotune()
         self.x = [torch.empty(g.n, g.n, device=b.device, dtype=torch.float32) for g, b, w, p in self.slices]
         self.ws = [workspace_for(g, p, b.device) for g, b, w, p in self.slices]
         for g, b, w, p in self.slices:

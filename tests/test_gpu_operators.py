@@ -21,6 +21,12 @@ SHAPES = [
     (5, 3, 9),         # tiny
     (1, 1, 1),         # single pixel, single ray
     (130, 32, 190),    # several 128-bin tiles + tail
+    # N a multiple of 32: the view-pair projector; V = 33 (odd), 12 (V/4 a
+    # row pair, V/2 a single), 16; even N and V: the orbit backprojector,
+    # with B % 4 = 0 (aligned window copies) and not
+    (96, 33, 140),
+    (32, 12, 47),
+    (64, 16, 92),
 ]
 
 

@@ -1,0 +1,90 @@
+"""Launch-shape tuning (ct_geometry_autotune / set / get): every shape must
+give the same operators and the same solve as the oracle, within the
+per-pass and per-solve tolerances; out-of-range shapes are rejected."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_util import need_gpu, rel_l2, to_gpu, to_np, f32
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.mark.parametrize("N,V,B", [(64, 90, 95), (96, 12, 140)])
+@pytest.mark.parametrize("items,slices", [(4, 1), (7, 2), (13, 8), (16, 4)])
+def test_operator_shapes_parity(N, V, B, items, slices):
+    P = need_gpu()
+    g = P.Geometry(N, V, B)
+    g.set_tuning(items_per_block=items, orbit_slices=slices)
+    assert g.tuning == {"items_per_block": items, "orbit_slices": slices, "tv_rows": 0}
+    x = f32(synth.ellipse_phantom(N, 6, 3))
+    assert rel_l2(to_np(P.ct_project(g, to_gpu(x))), O.project(x, V, B)) <= TOL
+    y = f32(synth.random_sinogram(V, B, 4))
+    assert rel_l2(to_np(P.ct_backproject(g, to_gpu(y))), O.backproject(y, N)) <= TOL
+
+
+@pytest.mark.parametrize("rows", [4, 16, 64])
+def test_tv_rows_solve_parity(rows):
+    # the low-dose 64^2 / 90 / 95 solve (20 iterations, n_tv = 10) under
+    # three TV tile shapes, against the oracle run with the same tau, sigma, taps
+    P = need_gpu()
+    N, V, B = 64, 90, 95
+    x_true = synth.ellipse_phantom(N, 10, 0) * (2.0 / N)
+    b, w = synth.poisson_data(O.project(x_true, V, B), 1e4, 100)
+    b, w = f32(b), f32(w)
+    kappa = float(np.mean(1.0 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    g = P.Geometry(N, V, B)
+    g.set_tuning(tv_rows=rows)
+    prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=20, tv_iters=10, precond=1, beta=0.01, tau=tau, sigma=0.5)
+    xg, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    st, _ = O.pdtv(b, w, taps, 0, 0.01, tau, 0.5, 10, 20, N)
+    assert rel_l2(to_np(xg), st.x) <= 1e-3
+
+
+def test_autotune_picks_valid_shapes_and_keeps_parity():
+    P = need_gpu()
+    N, V, B = 128, 60, 185
+    g = P.Geometry(N, V, B)
+    t = g.autotune(batch=2)
+    assert 4 <= t["items_per_block"] <= 16
+    assert t["orbit_slices"] in (1, 2, 4, 8)
+    assert t["tv_rows"] in (4, 8, 16, 32, 64)
+    x = f32(synth.ellipse_phantom(N, 8, 5))
+    assert rel_l2(to_np(P.ct_project(g, to_gpu(x))), O.project(x, V, B)) <= TOL
+    y = f32(synth.random_sinogram(V, B, 6))
+    assert rel_l2(to_np(P.ct_backproject(g, to_gpu(y))), O.backproject(y, N)) <= TOL
+
+
+def test_autotune_without_shared_paths():
+    # custom angles and odd N: neither the view-pair projector nor the orbit
+    # backprojector applies; only the TV shape is tuned
+    P = need_gpu()
+    g = P.Geometry(37, 13, 53, angles=np.linspace(0.0, 3.0, 13))
+    t = g.autotune()
+    assert t["items_per_block"] == 0 and t["orbit_slices"] == 0
+    assert t["tv_rows"] in (4, 8, 16, 32, 64)
+
+
+@pytest.mark.parametrize("bad", [dict(items_per_block=3), dict(items_per_block=17), dict(orbit_slices=9),
+                                 dict(orbit_slices=-1), dict(tv_rows=2), dict(tv_rows=65)])
+def test_set_tuning_rejects_out_of_range(bad):
+    P = need_gpu()
+    g = P.Geometry(64, 90, 95)
+    with pytest.raises(P.CTError):
+        g.set_tuning(**bad)
+    assert g.tuning == {"items_per_block": 0, "orbit_slices": 0, "tv_rows": 0}
+
+
+def test_orbit_slices_limit_large_view_count():
+    # 8192 views: a slice holds at most 1024 base views, so 1 and 2 slices are refused
+    P = need_gpu()
+    g = P.Geometry(32, 8192, 46)
+    with pytest.raises(P.CTError):
+        g.set_tuning(orbit_slices=2)
+    g.set_tuning(orbit_slices=4)
+    assert g.tuning["orbit_slices"] == 4
