@@ -66,6 +66,12 @@ __device__ __forceinline__ void dft8(float2 *v, bool inv)
     v[7] = csub(e3, w3o);
 }
 
+// Shared-memory FFT buffers hold element i at fp(i) = i + i/16: one pad slot
+// per 16 elements makes the strided stores of the first stages (stride R
+// and R Ns) and the contiguous loads free of bank conflicts.
+__host__ __device__ __forceinline__ int fp(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int fft_elems(int P) { return P + (P >> 4); }
+
 // One radix-R Stockham stage: butterfly j reads src[j + r P/R], applies the
 // twiddles w^(r k P/(Ns R)) (k = j mod Ns) and writes dst[(j - k) R + k + r Ns].
 template <int R>
@@ -78,7 +84,7 @@ __device__ __forceinline__ void fft_stage(const float2 *src, float2 *dst, int P,
         const int k = j & (Ns - 1);
         const int step = (P / (Ns * R)) * k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+        for (int r = 0; r < R; ++r) v[r] = src[fp(j + r * nb)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -92,7 +98,7 @@ __device__ __forceinline__ void fft_stage(const float2 *src, float2 *dst, int P,
         else dft2(v[0], v[1]);
         const int d0 = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[d0 + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[fp(d0 + r * Ns)] = v[r];
     }
 }
 
@@ -154,23 +160,23 @@ __global__ void __launch_bounds__(FFT_T)
 k_hhat(const float *__restrict__ taps, int half, int P, const float2 *__restrict__ tw, float2 *__restrict__ hhat)
 {
     extern __shared__ float2 fsm[];
-    float2 *a = fsm, *b = fsm + P;
+    float2 *a = fsm, *b = fsm + fft_elems(P);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         // index i holds t[k] with k = i (i < half) or k = i - P (i > P - half)
         float v = 0.0f;
         if (i < half) v = taps[half - 1 + i];
         else if (i > P - half) v = taps[half - 1 + (i - P)];
-        a[i] = make_float2(v, 0.0f);
+        a[fp(i)] = make_float2(v, 0.0f);
     }
     const float2 *res = fft_block(a, b, P, tw, false);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) hhat[i] = res[i];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) hhat[i] = res[fp(i)];
 }
 
 void launch_hhat(const Geometry *g, const float *taps, int half, float2 *hhat, cudaStream_t st)
 {
     const int P = g->n_fft;
     counted();
-    k_hhat<<<1, FFT_T, sizeof(float2) * 2 * P, st>>>(taps, half, P, g->d_tw, hhat);
+    k_hhat<<<1, FFT_T, sizeof(float2) * 2 * fft_elems(P), st>>>(taps, half, P, g->d_tw, hhat);
 }
 
 // out = post .* D(pre .* in) * sc, sc = 1 (mode 0) or -sigma (mode 1);
@@ -185,7 +191,7 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
              const ViewP *__restrict__ views)
 {
     extern __shared__ float2 fsm[];
-    float2 *a = fsm, *b = fsm + P;
+    float2 *a = fsm, *b = fsm + fft_elems(P);
     const int v0 = 2 * blockIdx.x, v1 = v0 + 1;
     const bool has1 = v1 < V;
     const size_t base = (size_t)blockIdx.y * V * B;
@@ -210,14 +216,14 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
                 }
             }
         }
-        a[i] = make_float2(x0, x1);
+        a[fp(i)] = make_float2(x0, x1);
     }
     float2 *f = fft_block(a, b, P, tw, false);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
     float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
     const float sc = ((mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f) / (float)P;
     for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        float y0 = res[i].x * sc, y1 = res[i].y * sc;
+        float y0 = res[fp(i)].x * sc, y1 = res[fp(i)].y * sc;
         if (post) {
             y0 *= post[o0 + i];
             if (has1) y1 *= post[o1 + i];
@@ -234,7 +240,7 @@ void launch_filter_fft_bands(const Geometry *g, const float2 *hhat, const float 
     const int P = g->n_fft;
     dim3 grd((g->n_views + 1) / 2, batch);
     counted();
-    k_filter_fft<true><<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, partial, out, nullptr, nullptr, 0, nullptr,
+    k_filter_fft<true><<<grd, FFT_T, sizeof(float2) * 2 * fft_elems(P), st>>>(hhat, partial, out, nullptr, nullptr, 0, nullptr,
                                                                    g->n_views, g->n_bins, P, g->d_tw,
                                                                    proj_bands(g->n), g->d_views);
 }
@@ -246,7 +252,7 @@ void launch_filter_fft(const Geometry *g, const float2 *hhat, const float *in, f
     const int P = g->n_fft;
     dim3 grd((g->n_views + 1) / 2, batch);
     counted();
-    k_filter_fft<false><<<grd, FFT_T, sizeof(float2) * 2 * P, st>>>(hhat, in, out, pre, post, mode, scal,
+    k_filter_fft<false><<<grd, FFT_T, sizeof(float2) * 2 * fft_elems(P), st>>>(hhat, in, out, pre, post, mode, scal,
                                                                     g->n_views, g->n_bins, P, g->d_tw, 0, nullptr);
 }
 
@@ -272,8 +278,8 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
         if (winv) winv += so;
     }
     extern __shared__ float2 fsm[];
-    float2 *a = fsm, *bb = fsm + P;
-    float *m_old = reinterpret_cast<float *>(fsm + 2 * P);   // 2 x B
+    float2 *a = fsm, *bb = fsm + fft_elems(P);
+    float *m_old = reinterpret_cast<float *>(fsm + 2 * fft_elems(P));   // 2 x B
     float *m_new = m_old + 2 * B;                            // 2 x B
     const int v0 = 2 * blockIdx.x, v1 = v0 + 1;
     const bool has1 = v1 < V;
@@ -300,17 +306,17 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
                 if (lowdose) r1 -= winv[o1 + i] * mu1;
             }
         }
-        a[i] = make_float2(r0, r1);
+        a[fp(i)] = make_float2(r0, r1);
     }
     float2 *f = fft_block(a, bb, P, tw, false);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
     float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
     float2 *other = res == a ? bb : a;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float d0 = 0.0f, d1 = 0.0f;
         if (i < B) {
-            const float n0 = m_old[i] + sigma * (res[i].x * invP);
-            const float n1 = m_old[B + i] + sigma * (res[i].y * invP);
+            const float n0 = m_old[i] + sigma * (res[fp(i)].x * invP);
+            const float n1 = m_old[B + i] + sigma * (res[fp(i)].y * invP);
             m_new[i] = n0;
             m_new[B + i] = n1;
             if (lowdose) {
@@ -318,11 +324,11 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
                 if (has1) d1 = winv[o1 + i] * (n1 - m_old[B + i]);
             }
         }
-        other[i] = make_float2(d0, d1);
+        other[fp(i)] = make_float2(d0, d1);
     }
     if (lowdose) {
         f = fft_block(other, res, P, tw, false);
-        for (int i = threadIdx.x; i < P; i += blockDim.x) f[i] = cmul(f[i], hhat[i]);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
         res = fft_block(f, f == a ? bb : a, P, tw, true);
     } else {
         __syncthreads();
@@ -331,8 +337,8 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
         const float n0 = m_new[i], n1 = m_new[B + i];
         float mb0 = 2.0f * n0 - m_old[i], mb1 = 2.0f * n1 - m_old[B + i];
         if (lowdose) {
-            mb0 -= sigma * (res[i].x * invP);
-            mb1 -= sigma * (res[i].y * invP);
+            mb0 -= sigma * (res[fp(i)].x * invP);
+            mb1 -= sigma * (res[fp(i)].y * invP);
         }
         mu[o0 + i] = n0;
         mu_bar[o0 + i] = mb0;
@@ -343,7 +349,7 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
     }
 }
 
-size_t dual_fft_smem(const Geometry *g) { return sizeof(float2) * 2 * g->n_fft + sizeof(float) * 4 * g->n_bins; }
+size_t dual_fft_smem(const Geometry *g) { return sizeof(float2) * 2 * fft_elems(g->n_fft) + sizeof(float) * 4 * g->n_bins; }
 
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
                      float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st)
@@ -384,8 +390,8 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
                const float2 *__restrict__ tw)
 {
     extern __shared__ float2 fsm[];
-    float2 *a = fsm, *bb = fsm + P;
-    float *h_s = reinterpret_cast<float *>(fsm + 2 * P);   // 2 x B: D^T gmb
+    float2 *a = fsm, *bb = fsm + fft_elems(P);
+    float *h_s = reinterpret_cast<float *>(fsm + 2 * fft_elems(P));   // 2 x B: D^T gmb
     float *g1_s = h_s + 2 * B;                             // 2 x B: gm1
     const size_t so = (size_t)blockIdx.y * V * B;
     partial += (size_t)blockIdx.y * nb * V * B;
@@ -398,11 +404,11 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
 
     // h = D^T gmb
     for (int i = threadIdx.x; i < P; i += blockDim.x)
-        a[i] = i < B ? make_float2(gmb[o0 + i], has1 ? gmb[o1 + i] : 0.0f) : make_float2(0.0f, 0.0f);
+        a[fp(i)] = i < B ? make_float2(gmb[o0 + i], has1 ? gmb[o1 + i] : 0.0f) : make_float2(0.0f, 0.0f);
     float2 *f = fft_block(a, bb, P, tw, false);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const float2 h = hhat[i];
-        f[i] = cmul(f[i], make_float2(h.x, -h.y));
+        f[fp(i)] = cmul(f[fp(i)], make_float2(h.x, -h.y));
     }
     float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
     float2 *other = res == a ? bb : a;
@@ -410,7 +416,7 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float g0 = 0.0f, g1v = 0.0f;
         if (i < B) {
-            const float h0 = res[i].x * invP, h1 = res[i].y * invP;
+            const float h0 = res[fp(i)].x * invP, h1 = res[fp(i)].y * invP;
             h_s[i] = h0;
             h_s[B + i] = h1;
             g0 = gm[o0 + i] + 2.0f * gmb[o0 + i];
@@ -422,12 +428,12 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
             g1_s[i] = g0;
             g1_s[B + i] = g1v;
         }
-        other[i] = make_float2(g0, g1v);
+        other[fp(i)] = make_float2(g0, g1v);
     }
     f = fft_block(other, res, P, tw, false);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const float2 h = hhat[i];
-        f[i] = cmul(f[i], make_float2(h.x, -h.y));
+        f[fp(i)] = cmul(f[fp(i)], make_float2(h.x, -h.y));
     }
     res = fft_block(f, f == a ? bb : a, P, tw, true);
     const float sc0 = views[v0].scale, sc1 = has1 ? views[v1].scale : 0.0f;
@@ -435,7 +441,7 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
         // two views: k = 0 -> v0, k = 1 -> v1
         for (int k = 0; k < (has1 ? 2 : 1); ++k) {
             const size_t o = (k == 0 ? o0 : o1) + i;
-            const float gr = sigma * ((k == 0 ? res[i].x : res[i].y) * invP);
+            const float gr = sigma * ((k == 0 ? res[fp(i)].x : res[fp(i)].y) * invP);
             const float g1v = g1_s[k * B + i], hv = h_s[k * B + i];
             float gmu = g1v - gmb[o];
             float acc = 0.0f;
@@ -457,7 +463,7 @@ k_dual_bwd_fft(const float2 *__restrict__ hhat, const float *__restrict__ partia
     }
 }
 
-size_t dual_bwd_smem(const Geometry *g) { return sizeof(float2) * 2 * g->n_fft + sizeof(float) * 4 * g->n_bins; }
+size_t dual_bwd_smem(const Geometry *g) { return sizeof(float2) * 2 * fft_elems(g->n_fft) + sizeof(float) * 4 * g->n_bins; }
 
 void launch_dual_bwd_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
                          const float *winv, const float *mu, const float *mu1, const float *gm, const float *gmb,
@@ -474,7 +480,7 @@ bool fft_supported(const Geometry *g) { return g->n_fft <= FFT_MAX_P; }
 
 void kernel_attrs_fft()
 {
-    const int smax = (int)(sizeof(float2) * 2 * FFT_MAX_P + sizeof(float) * 4 * (FFT_MAX_P / 2));
+    const int smax = (int)(sizeof(float2) * 2 * fft_elems(FFT_MAX_P) + sizeof(float) * 4 * (FFT_MAX_P / 2));
     cudaFuncSetAttribute(k_hhat, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_filter_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_filter_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
