@@ -87,15 +87,18 @@ void ct_geometry_destroy(ct_geometry *geom);
 /*
  * Launch-shape tuning (no counterpart in the paper: it picks how the work of
  * A, A^T and the TV prox of Eq. 17 is cut into thread blocks, never what is
- * computed).  Three shapes are held by the geometry:
+ * computed).  Four shapes are held by the geometry:
  *   items_per_block  view pairs (v, V-v) sharing one staged band pair in the
- *                    projector, 64 threads each (4..16);
+ *                    projector, 64 threads each (4..16; 4..12 when
+ *                    proj_rows is 4);
+ *   proj_rows        steps a projector thread evaluates per pass of a ray
+ *                    walk (2 or 4: more loads in flight, more registers);
  *   orbit_slices     base-view slices of the rotation-orbit backprojector,
  *                    one partial image each (1..8, at most 1024 base views
  *                    per slice);
  *   tv_rows          fewest interior rows of a TV prox tile (4..64).
- * 0 selects the built-in rule (a wave-count model for items_per_block, 4
- * slices, 16 rows).  A shape changes the order in which independent
+ * 0 selects the built-in rule (a wave-count model for items_per_block, 2
+ * steps per pass, 4 slices, 16 rows).  A shape changes the order in which independent
  * partial sums are added, so results can differ in the last float bits
  * between shapes; for one shape they are deterministic.
  *
@@ -110,9 +113,10 @@ void ct_geometry_destroy(ct_geometry *geom);
  * out of range); ct_geometry_get_tuning reads them (NULL outputs skipped).
  */
 ct_status ct_geometry_autotune(ct_geometry *geom, int batch, void *stream);
-ct_status ct_geometry_set_tuning(ct_geometry *geom, int items_per_block, int orbit_slices, int tv_rows);
-ct_status ct_geometry_get_tuning(const ct_geometry *geom, int *items_per_block, int *orbit_slices,
-                                 int *tv_rows);
+ct_status ct_geometry_set_tuning(ct_geometry *geom, int items_per_block, int proj_rows, int orbit_slices,
+                                 int tv_rows);
+ct_status ct_geometry_get_tuning(const ct_geometry *geom, int *items_per_block, int *proj_rows,
+                                 int *orbit_slices, int *tv_rows);
 
 /*
  * Forward projection sino = A img (A of Eq. 1; Joseph interpolation).

@@ -1,11 +1,12 @@
 // autotune.cu -- ct_geometry_autotune / ct_geometry_get_tuning /
 // ct_geometry_set_tuning: launch shapes per geometry picked by measurement.
 //
-// Three shapes are tuned, each by timing every candidate on synthetic data
+// Four shapes are tuned, each by timing every candidate on synthetic data
 // of the geometry's size with CUDA events (one warm-up launch, then the mean
 // of three):
 //   - the projector's view items per block (k_project_quad: 64 threads per
-//     view pair, pg pairs share one staged band pair), pg = 4 .. 16;
+//     view pair, pg pairs share one staged band pair), pg = 4 .. 16, jointly
+//     with its steps per pass of a ray walk (2, or 4 with pg <= 12);
 //   - the backprojector's base-view slices (k_backproject_orbit: grid.z,
 //     one partial image per slice), 1, 2, 4 or 8;
 //   - the TV prox's fewest interior rows per tile (k_tv), 4 .. 64, which
@@ -53,27 +54,33 @@ bool quad_path(const Geometry *g) { return g->vpair && g->n % 32 == 0 && g->n + 
 
 }  // namespace
 
-extern "C" ct_status ct_geometry_get_tuning(const ct_geometry *g, int *items_per_block, int *orbit_slices,
-                                            int *tv_rows)
+extern "C" ct_status ct_geometry_get_tuning(const ct_geometry *g, int *items_per_block, int *proj_rows,
+                                            int *orbit_slices, int *tv_rows)
 {
     if (!g) {
         set_error("ct_geometry_get_tuning: NULL geometry");
         return CT_ERR_ARG;
     }
     if (items_per_block) *items_per_block = g->tune_pg;
+    if (proj_rows) *proj_rows = g->tune_qrows;
     if (orbit_slices) *orbit_slices = g->tune_orb;
     if (tv_rows) *tv_rows = g->tune_tv;
     return CT_OK;
 }
 
-extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block, int orbit_slices, int tv_rows)
+extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block, int proj_rows, int orbit_slices,
+                                            int tv_rows)
 {
     if (!g) {
         set_error("ct_geometry_set_tuning: NULL geometry");
         return CT_ERR_ARG;
     }
-    if (items_per_block != 0 && (items_per_block < 4 || items_per_block > 16)) {
-        set_error("ct_geometry_set_tuning: items_per_block must be 0 or in [4, 16]");
+    if (proj_rows != 0 && proj_rows != 2 && proj_rows != 4) {
+        set_error("ct_geometry_set_tuning: proj_rows must be 0, 2 or 4");
+        return CT_ERR_ARG;
+    }
+    if (items_per_block != 0 && (items_per_block < 4 || items_per_block > (proj_rows == 4 ? 12 : 16))) {
+        set_error("ct_geometry_set_tuning: items_per_block must be 0 or in [4, 16] ([4, 12] with proj_rows 4)");
         return CT_ERR_ARG;
     }
     if (orbit_slices != 0 && !orbit_slices_ok(g, orbit_slices)) {
@@ -86,6 +93,7 @@ extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block,
         return CT_ERR_ARG;
     }
     g->tune_pg = items_per_block;
+    g->tune_qrows = proj_rows;
     g->tune_orb = orbit_slices;
     g->tune_tv = tv_rows;
     return CT_OK;
@@ -101,7 +109,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int N = g->n;
     const size_t J = (size_t)N * N, I = (size_t)g->n_views * g->n_bins;
-    const int old_pg = g->tune_pg, old_orb = g->tune_orb, old_tv = g->tune_tv;
+    const int old_pg = g->tune_pg, old_rows = g->tune_qrows, old_orb = g->tune_orb, old_tv = g->tune_tv;
     Buffers buf;
     float *x = nullptr, *sino = nullptr, *band = nullptr, *orb = nullptr, *img = nullptr, *tvb = nullptr;
     float *scalf = nullptr;
@@ -136,17 +144,22 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     float t;
     if (quad_path(g)) {
         float best = -1.0f;
-        int best_pg = 0;
-        for (int pg = 4; pg <= 16 && result == CT_OK; ++pg) {
-            g->tune_pg = pg;
-            t = time_launches([&] { launch_project_bands(g, x, band, batch, st); }, st, e0, e1);
-            if (t < 0.0f) result = CT_ERR_CUDA;
-            else if (best < 0.0f || t < best) {
-                best = t;
-                best_pg = pg;
+        int best_pg = 0, best_rows = 0;
+        for (int rows = 2; rows <= 4 && result == CT_OK; rows += 2) {
+            for (int pg = 4; pg <= (rows == 4 ? 12 : 16) && result == CT_OK; ++pg) {
+                g->tune_pg = pg;
+                g->tune_qrows = rows;
+                t = time_launches([&] { launch_project_bands(g, x, band, batch, st); }, st, e0, e1);
+                if (t < 0.0f) result = CT_ERR_CUDA;
+                else if (best < 0.0f || t < best) {
+                    best = t;
+                    best_pg = pg;
+                    best_rows = rows;
+                }
             }
         }
         g->tune_pg = best_pg;
+        g->tune_qrows = best_rows;
     }
     if (result == CT_OK && orbit_ok(g)) {
         float best = -1.0f;
@@ -184,6 +197,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     cudaEventDestroy(e1);
     if (result != CT_OK) {
         g->tune_pg = old_pg;
+        g->tune_qrows = old_rows;
         g->tune_orb = old_orb;
         g->tune_tv = old_tv;
         cudaError_t le = cudaGetLastError();

@@ -46,7 +46,8 @@ struct Geometry {
     int2 *d_col_items;    // device, (v, V-v) for V/4 < v < V/2, and (V/2, -1) for even V
     int n_sm;             // multiprocessors of the device
     // launch shapes chosen by ct_geometry_autotune (0: the built-in rule)
-    int tune_pg;          // projector view items per block (4..16)
+    int tune_pg;          // projector view items per block (4..16; 4..12 with 4 steps per pass)
+    int tune_qrows;       // projector steps per pass of a ray walk (2 or 4)
     int tune_orb;         // A^T orbit base-view slices (1..8)
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     double *h_angles;     // host copy

@@ -328,68 +328,83 @@ k_project_mirror(const float *__restrict__ x, const ViewP *__restrict__ views,
 // Work items are view pairs (v, V-v) and the views without a partner
 // (v = 0, and v = V/2 for even V), pg items per block, 64 threads per item.
 // ---------------------------------------------------------------------
-template <bool PAIR>
-__device__ __forceinline__ float4 quad_walk(const float2 *__restrict__ PA, const float2 *__restrict__ PB, int SP,
-                                            float q, float m, int lo, int hi, int s0, float h, unsigned top)
+// Walks one ray through the staged steps lo..hi (ROWS steps per pass, one
+// coordinate evaluation per step) and returns its four sums: band A and
+// band B at the pair i0, and (PAIR) at the reflected pair N-2-i0.  Q holds
+// per step and pair (A mid, A delta, B mid, B delta), so one 16-byte load
+// serves both bands.
+template <bool PAIR, int ROWS>
+__device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP, float q, float m, int lo, int hi,
+                                            int s0, float h, unsigned top)
 {
-    const float qu1 = __fadd_rn(q, m);
+    float qk[ROWS];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) qk[k] = __fmaf_rn((float)k, m, q);
     float spk = (float)lo - h;
     int ridx = (lo - s0) * SP;
-    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f, c0 = 0.0f, c1 = 0.0f, e0 = 0.0f, e1 = 0.0f;
+    float a[ROWS], b[ROWS], c[ROWS], e[ROWS];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) a[k] = b[k] = c[k] = e[k] = 0.0f;
     int s = lo;
-    for (; s + 1 <= hi; s += 2) {
-        const float up0 = joseph_u(spk, m, q), up1 = joseph_u(spk, m, qu1);
-        const float t0 = __fadd_rn(up0, JOSEPH_BIAS), t1 = __fadd_rn(up1, JOSEPH_BIAS);
-        const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
-        const unsigned i1 = min((unsigned)(__float_as_int(t1) - (JOSEPH_BIAS_BITS - 2)), top);
-        const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
-        const float g1 = __fsub_rn(up1, __fsub_rn(t1, JOSEPH_BIAS));
-        const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
-        const float2 pa1 = PA[ridx + SP + (int)i1], pb1 = PB[ridx + SP + (int)i1];
-        a0 += __fmaf_rn(g0, pa0.y, pa0.x);
-        b0 += __fmaf_rn(g0, pb0.y, pb0.x);
-        a1 += __fmaf_rn(g1, pa1.y, pa1.x);
-        b1 += __fmaf_rn(g1, pb1.y, pb1.x);
-        if (PAIR) {
-            const int j0 = (int)(top - i0), j1 = (int)(top - i1);
-            const float2 qa0 = PA[ridx + j0], qb0 = PB[ridx + j0];
-            const float2 qa1 = PA[ridx + SP + j1], qb1 = PB[ridx + SP + j1];
-            c0 += __fmaf_rn(-g0, qa0.y, qa0.x);
-            e0 += __fmaf_rn(-g0, qb0.y, qb0.x);
-            c1 += __fmaf_rn(-g1, qa1.y, qa1.x);
-            e1 += __fmaf_rn(-g1, qb1.y, qb1.x);
+    for (; s + ROWS - 1 <= hi; s += ROWS) {
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k) {
+            const float up = joseph_u(spk, m, qk[k]);
+            const float t = __fadd_rn(up, JOSEPH_BIAS);
+            const unsigned i = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
+            const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
+            const float4 pv = Q[ridx + k * SP + (int)i];
+            a[k] += __fmaf_rn(g, pv.y, pv.x);
+            b[k] += __fmaf_rn(g, pv.w, pv.z);
+            if (PAIR) {
+                const float4 rv = Q[ridx + k * SP + (int)(top - i)];
+                c[k] += __fmaf_rn(-g, rv.y, rv.x);
+                e[k] += __fmaf_rn(-g, rv.w, rv.z);
+            }
         }
-        spk = __fadd_rn(spk, 2.0f);
-        ridx += 2 * SP;
+        spk = __fadd_rn(spk, (float)ROWS);
+        ridx += ROWS * SP;
     }
-    if (s <= hi) {
-        const float up0 = joseph_u(spk, m, q);
-        const float t0 = __fadd_rn(up0, JOSEPH_BIAS);
-        const unsigned i0 = min((unsigned)(__float_as_int(t0) - (JOSEPH_BIAS_BITS - 2)), top);
-        const float g0 = __fsub_rn(up0, __fsub_rn(t0, JOSEPH_BIAS));
-        const float2 pa0 = PA[ridx + (int)i0], pb0 = PB[ridx + (int)i0];
-        a0 += __fmaf_rn(g0, pa0.y, pa0.x);
-        b0 += __fmaf_rn(g0, pb0.y, pb0.x);
+    for (; s <= hi; ++s) {
+        const float up = joseph_u(spk, m, qk[0]);
+        const float t = __fadd_rn(up, JOSEPH_BIAS);
+        const unsigned i = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
+        const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
+        const float4 pv = Q[ridx + (int)i];
+        a[0] += __fmaf_rn(g, pv.y, pv.x);
+        b[0] += __fmaf_rn(g, pv.w, pv.z);
         if (PAIR) {
-            const int j0 = (int)(top - i0);
-            const float2 qa0 = PA[ridx + j0], qb0 = PB[ridx + j0];
-            c0 += __fmaf_rn(-g0, qa0.y, qa0.x);
-            e0 += __fmaf_rn(-g0, qb0.y, qb0.x);
+            const float4 rv = Q[ridx + (int)(top - i)];
+            c[0] += __fmaf_rn(-g, rv.y, rv.x);
+            e[0] += __fmaf_rn(-g, rv.w, rv.z);
         }
+        spk = __fadd_rn(spk, 1.0f);
+        ridx += SP;
     }
-    return make_float4(a0 + a1, b0 + b1, c0 + c1, e0 + e1);
+    float4 r = make_float4(a[0], b[0], c[0], e[0]);
+#pragma unroll
+    for (int k = 1; k < ROWS; ++k) {
+        r.x += a[k];
+        r.y += b[k];
+        r.z += c[k];
+        r.w += e[k];
+    }
+    return r;
 }
 
-__global__ void __launch_bounds__(PT)
+// ROWS = 2: up to 16 items (1024 threads, 64 registers); ROWS = 4: more
+// loads in flight per thread, up to 12 items (768 threads, 85 registers).
+template <int ROWS>
+__global__ void __launch_bounds__(ROWS == 2 ? 1024 : 768)
 k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                const int2 *__restrict__ row_items, int n_row, const int2 *__restrict__ col_items, int n_col,
                int N, int V, int B, int pg, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int CW = N + 3, SP = CW | 1;
-    float2 *PA = reinterpret_cast<float2 *>(smraw);
-    float2 *PB = PA + (size_t)MR * SP;
-    ViewP *sv = reinterpret_cast<ViewP *>(PB + (size_t)MR * SP);
+    float4 *Q = reinterpret_cast<float4 *>(smraw);   // [step][pair]: band A pair, band B pair
+    float2 *Q2 = reinterpret_cast<float2 *>(smraw);
+    ViewP *sv = reinterpret_cast<ViewP *>(Q + (size_t)MR * SP);
     int2 *sit = reinterpret_cast<int2 *>(sv + PG);
 
     const int bp = blockIdx.x, nbp = gridDim.x;
@@ -418,25 +433,25 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                 const int band = ly >= MR, t = ly - band * MR;
                 const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
                 const float *rowp = img + (size_t)line * N;
-                float2 *dst = (band == 0 ? PA : PB) + t * SP;
+                float2 *dst = Q2 + 2 * (size_t)t * SP + band;
                 for (int ii = lx; ii < CW; ii += 32) {
                     const int i = ii - 2;
                     const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
-                    const float a = (ia >= 0 && ia < N) ? rowp[ia] : 0.0f;
-                    const float b = (ib >= 0 && ib < N) ? rowp[ib] : 0.0f;
-                    dst[ii] = make_float2(0.5f * (a + b), b - a);
+                    const float av = (ia >= 0 && ia < N) ? rowp[ia] : 0.0f;
+                    const float bv = (ib >= 0 && ib < N) ? rowp[ib] : 0.0f;
+                    dst[2 * ii] = make_float2(0.5f * (av + bv), bv - av);
                 }
             }
         } else {
             const int band = lx >= MR, t = lx - band * MR;
             const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
-            float2 *dst = (band == 0 ? PA : PB) + t * SP;
+            float2 *dst = Q2 + 2 * (size_t)t * SP + band;
             for (int ii = tid >> 5; ii < CW; ii += nth >> 5) {
                 const int i = ii - 2;
                 const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
-                const float a = (ia >= 0 && ia < N) ? img[(size_t)ia * N + line] : 0.0f;
-                const float b = (ib >= 0 && ib < N) ? img[(size_t)ib * N + line] : 0.0f;
-                dst[ii] = make_float2(0.5f * (a + b), b - a);
+                const float av = (ia >= 0 && ia < N) ? img[(size_t)ia * N + line] : 0.0f;
+                const float bv = (ib >= 0 && ib < N) ? img[(size_t)ib * N + line] : 0.0f;
+                dst[2 * ii] = make_float2(0.5f * (av + bv), bv - av);
             }
         }
     }
@@ -457,8 +472,8 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
             const float q = joseph_q(joseph_dp(dd, B), a, hq);
             int lo, hi;
             step_range(q, m, inv_m, h, -2.5f, (float)N + 0.5f, s0, s0 + MR - 1, lo, hi);
-            const float4 r = vp >= 0 ? quad_walk<true>(PA, PB, SP, q, m, lo, hi, s0, h, top)
-                                     : quad_walk<false>(PA, PB, SP, q, m, lo, hi, s0, h, top);
+            const float4 r = vp >= 0 ? quad_walk<true, ROWS>(Q, SP, q, m, lo, hi, s0, h, top)
+                                     : quad_walk<false, ROWS>(Q, SP, q, m, lo, hi, s0, h, top);
             ov[which] += r.x;
             ov[1 - which] += r.y;
             if (rows) {
@@ -490,12 +505,12 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
 
 // items per block of k_project_quad: the fewest waves of blocks (one block
 // per SM, shared memory) times the per-block work, staging counted as two items
-static int quad_pg(const Geometry *g, int batch)
+static int quad_pg(const Geometry *g, int batch, int max_pg)
 {
     const long bands = g->n / (2 * MR);
-    int best = PG;
+    int best = max_pg;
     long best_cost = -1;
-    for (int pg = 4; pg <= PG; ++pg) {
+    for (int pg = 4; pg <= max_pg; ++pg) {
         const long groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
         const long blocks = bands * groups * batch;
         const long cost = ((blocks + g->n_sm - 1) / g->n_sm) * (pg + 2);
@@ -515,12 +530,20 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
     counted();
     if (g->vpair && N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // view pairs and two mirrored 16-step bands per block: N/32 partial slots
-        const int pg = g->tune_pg > 0 ? std::min(g->tune_pg, PG) : quad_pg(g, batch);
+        const int rows4 = g->tune_qrows == 4;
+        const int max_pg = rows4 ? 12 : PG;
+        const int pg = g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : quad_pg(g, batch, max_pg);
         const int groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
         const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
-        k_project_quad<<<dim3(N / (2 * MR), groups, batch), pg * 64, smem2, st>>>(
-            x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
-            pg, partial);
+        const dim3 grd2(N / (2 * MR), groups, batch);
+        if (rows4)
+            k_project_quad<4><<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items,
+                                                            g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
+                                                            pg, partial);
+        else
+            k_project_quad<2><<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items,
+                                                            g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
+                                                            pg, partial);
     } else if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // two mirrored 16-step bands per block: N/32 partial slots, as below
         dim3 grd2(N / (2 * MR), grd.y, batch);
@@ -919,7 +942,8 @@ void kernel_attrs_joseph()
     cudaFuncSetAttribute(k_backproject_orbit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_backproject_orbit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
-    cudaFuncSetAttribute(k_project_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }

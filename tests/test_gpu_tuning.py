@@ -13,13 +13,15 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4
 
 
-@pytest.mark.parametrize("N,V,B", [(64, 90, 95), (96, 12, 140)])
-@pytest.mark.parametrize("items,slices", [(4, 1), (7, 2), (13, 8), (16, 4)])
-def test_operator_shapes_parity(N, V, B, items, slices):
+@pytest.mark.parametrize("N,V,B", [(64, 90, 95), (96, 12, 140), (64, 33, 93)])
+@pytest.mark.parametrize("items,rows,slices", [(4, 2, 1), (7, 4, 2), (13, 2, 8), (16, 2, 4), (12, 4, 4)])
+def test_operator_shapes_parity(N, V, B, items, rows, slices):
     P = need_gpu()
     g = P.Geometry(N, V, B)
-    g.set_tuning(items_per_block=items, orbit_slices=slices)
-    assert g.tuning == {"items_per_block": items, "orbit_slices": slices, "tv_rows": 0}
+    if V % 2:
+        slices = 0   # odd V: no orbit backprojector
+    g.set_tuning(items_per_block=items, orbit_slices=slices, proj_rows=rows)
+    assert g.tuning == {"items_per_block": items, "proj_rows": rows, "orbit_slices": slices, "tv_rows": 0}
     x = f32(synth.ellipse_phantom(N, 6, 3))
     assert rel_l2(to_np(P.ct_project(g, to_gpu(x))), O.project(x, V, B)) <= TOL
     y = f32(synth.random_sinogram(V, B, 4))
@@ -51,7 +53,8 @@ def test_autotune_picks_valid_shapes_and_keeps_parity():
     N, V, B = 128, 60, 185
     g = P.Geometry(N, V, B)
     t = g.autotune(batch=2)
-    assert 4 <= t["items_per_block"] <= 16
+    assert 4 <= t["items_per_block"] <= (12 if t["proj_rows"] == 4 else 16)
+    assert t["proj_rows"] in (2, 4)
     assert t["orbit_slices"] in (1, 2, 4, 8)
     assert t["tv_rows"] in (4, 8, 16, 32, 64)
     x = f32(synth.ellipse_phantom(N, 8, 5))
@@ -66,18 +69,19 @@ def test_autotune_without_shared_paths():
     P = need_gpu()
     g = P.Geometry(37, 13, 53, angles=np.linspace(0.0, 3.0, 13))
     t = g.autotune()
-    assert t["items_per_block"] == 0 and t["orbit_slices"] == 0
+    assert t["items_per_block"] == 0 and t["proj_rows"] == 0 and t["orbit_slices"] == 0
     assert t["tv_rows"] in (4, 8, 16, 32, 64)
 
 
 @pytest.mark.parametrize("bad", [dict(items_per_block=3), dict(items_per_block=17), dict(orbit_slices=9),
-                                 dict(orbit_slices=-1), dict(tv_rows=2), dict(tv_rows=65)])
+                                 dict(orbit_slices=-1), dict(tv_rows=2), dict(tv_rows=65), dict(proj_rows=3),
+                                 dict(items_per_block=13, proj_rows=4)])
 def test_set_tuning_rejects_out_of_range(bad):
     P = need_gpu()
     g = P.Geometry(64, 90, 95)
     with pytest.raises(P.CTError):
         g.set_tuning(**bad)
-    assert g.tuning == {"items_per_block": 0, "orbit_slices": 0, "tv_rows": 0}
+    assert g.tuning == {"items_per_block": 0, "proj_rows": 0, "orbit_slices": 0, "tv_rows": 0}
 
 
 def test_orbit_slices_limit_large_view_count():
