@@ -307,6 +307,93 @@ def measure_unrolled(P, steps=3):
             "plain_solve_slices_per_s": 1.0 / (t_one / 1e3), "plain_solve_ms": t_one}
 
 
+CHECKPOINTS = (1, 3, 10, 30, 100, 300, 1000)
+
+
+def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale):
+    """Iterates of one solve at CHECKPOINTS (resumed solves continue the
+    same iteration exactly): RMSE of x / scale against the phantom v_true
+    and the relative data residual |A x - b| / |b|."""
+    import torch
+    prm = P.PDTVParams(mode=mode, iters=CHECKPOINTS[0], tv_iters=10, precond=precond, beta=beta,
+                       norm_iters=16)
+    ws = P.workspace_for(g, prm)
+    x = torch.empty(g.n, g.n, device="cuda")
+    xs, rmse, resid = {}, {}, {}
+    done = 0
+    bn = float(torch.linalg.norm(b))
+    for k in CHECKPOINTS:
+        q = P.PDTVParams(**{**prm.__dict__, "iters": k - done, "resume": 1 if done else 0})
+        P.ct_pdtv_solve(g, b, w, q, x_out=x, workspace=ws, report=False)
+        done = k
+        xs[k] = x.clone()
+        rmse[k] = float(torch.sqrt(torch.mean((x.double() / scale - v_true) ** 2)))
+        resid[k] = float(torch.linalg.norm(P.ct_project(g, x) - b)) / bn
+    return xs, rmse, resid
+
+
+def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3):
+    """iterations/s of a whole solve (setup included), CUDA events."""
+    import torch
+    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=16)
+    ws = P.workspace_for(g, prm)
+    x = torch.empty(g.n, g.n, device="cuda")
+    for _ in range(2):
+        P.ct_pdtv_solve(g, b, w, prm, x_out=x, workspace=ws, report=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        P.ct_pdtv_solve(g, b, w, prm, x_out=x, workspace=ws, report=False)
+    e1.record()
+    torch.cuda.synchronize()
+    return iters * steps / (e0.elapsed_time(e1) / 1e3)
+
+
+def measure_convergence(P):
+    """The ramp preconditioner against plain Chambolle-Pock (D = I) on the
+    same GPU kernels: RMSE to the phantom, data residual and distance to the
+    preconditioned 1000-iteration iterate x* after 1 .. 1000 iterations, for
+    the low-dose workload (512^2, 720 views, I0 5e3, beta 0.005) and the
+    few-view one (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2),
+    plus the few-view solve rates at 100 iterations."""
+    import torch
+    out = {}
+    cases = [("lowdose", WORK["views"], 0, WORK["beta"]), ("fewview", 32, 1, 0.0)]
+    for name, V, mode, beta in cases:
+        N, B = WORK["n"], WORK["bins"]
+        g = P.Geometry(N, V, B)
+        g.autotune()
+        v_true = synth.ellipse_phantom(N, WORK["ellipses"], 0)
+        scale = (2.0 / N) if mode == 0 else 1.0
+        p = P.ct_project(g, torch.from_numpy((v_true * scale).astype(np.float32)).cuda())
+        if mode == 0:
+            bb, ww = synth.poisson_data(p.cpu().numpy(), WORK["i0"], 100)
+            b = torch.from_numpy(bb.astype(np.float32)).cuda()
+            w = torch.from_numpy(ww.astype(np.float32)).cuda()
+        else:
+            b, w = p, None
+        vt = torch.from_numpy(v_true).cuda()
+        runs = {}
+        for label, pc in (("preconditioned", 1), ("plain_cp", 0)):
+            runs[label] = _trajectory(P, g, b, w, mode, pc, beta, vt, scale)
+        xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
+        xn = float(torch.linalg.norm(xstar))
+        entry = {"workload": f"512^2, {V} views, {B} bins, " +
+                             ("Poisson I0 5e3, beta 0.005, Alg. 1" if mode == 0 else "noiseless b = A v, Alg. 2"),
+                 "checkpoints": list(CHECKPOINTS)}
+        for label, (xs, rmse, resid) in runs.items():
+            entry[label] = {"rmse": [rmse[k] for k in CHECKPOINTS],
+                            "rel_residual": [resid[k] for k in CHECKPOINTS],
+                            "rel_dist_to_xstar": [float(torch.linalg.norm(xs[k] - xstar)) / xn
+                                                  for k in CHECKPOINTS]}
+        if mode == 1:
+            entry["iterations_per_s_100"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, 100)
+                                             for label, pc in (("preconditioned", 1), ("plain_cp", 0))}
+        out[name] = entry
+    return out
+
+
 # ----------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------
@@ -442,7 +529,8 @@ def run_ours(args):
 
     forms = None
     if not args.no_forms and world == 1:
-        forms = {"batched": measure_batched(P), "differentiable": measure_unrolled(P)}
+        forms = {"batched": measure_batched(P), "differentiable": measure_unrolled(P),
+                 "convergence": measure_convergence(P)}
 
     clocks = sampler.summary()
     if rank == 0:
@@ -462,6 +550,9 @@ def run_ours(args):
                              "setup": step_ms - loop_ms, "per_iteration": loop_ms / WORK["iters"],
                              "A_launch": a_ms, "AT_launch": at_ms},
             "loop_iterations_per_s": WORK["iters"] / (loop_ms / 1e3) * world,
+            # the survey's effective operator bandwidth, (4 N^2 + 4 V B) bytes per pass
+            "operator_GBps": {"A": (4.0 * N * N + 4.0 * V * B) / (a_ms / 1e3) / 1e9,
+                              "AT": (4.0 * N * N + 4.0 * V * B) / (at_ms / 1e3) / 1e9},
             "report": {k: rep[k] for k in ("tau", "sigma", "kappa", "norm_ADA", "norm_WDW")},
             "roofline": {"kernel": dom_name, "bound": "alu", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
@@ -491,7 +582,13 @@ def run_ncu_case(args):
     import paper_1609_06041_gb300 as P
     N, V, B = WORK["n"], WORK["views"], WORK["bins"]
     g = P.Geometry(N, V, B)
-    g.autotune()
+    if args.tuning:
+        # fixed launch shapes (items_per_block, proj_rows, orbit_slices, tv_rows),
+        # so the captured launches are not the tuner's trial launches
+        ip, pr, osl, tvr = (int(t) for t in args.tuning.split(","))
+        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr)
+    else:
+        g.autotune()
     xt = torch.from_numpy(phantom(0).astype(np.float32)).cuda()
     p = P.ct_project(g, xt).cpu().numpy()
     b_np, w_np = synth.poisson_data(p, WORK["i0"], 100)
@@ -512,9 +609,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched, differentiable and convergence measurements")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
+    ap.add_argument("--tuning", default="",
+                    help="with --ncu-case: fixed launch shapes 'items,rows,orbit_slices,tv_rows'")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

@@ -403,7 +403,6 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int CW = N + 3, SP = CW | 1;
     float4 *Q = reinterpret_cast<float4 *>(smraw);   // [step][pair]: band A pair, band B pair
-    float2 *Q2 = reinterpret_cast<float2 *>(smraw);
     ViewP *sv = reinterpret_cast<ViewP *>(Q + (size_t)MR * SP);
     int2 *sit = reinterpret_cast<int2 *>(sv + PG);
 
@@ -425,33 +424,39 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
         sv[tid] = views[sit[tid].x];
     }
     // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
-    // the line N-1-s0-t read backwards (image value at N-1-i)
+    // the line N-1-s0-t read backwards (image value at N-1-i); one thread
+    // forms both bands' pairs of (t, i) and stores them as one float4
     {
-        const int lx = tid & 31;
+        const int lx = tid & 31, nw = nth >> 5;
         if (rows) {
-            for (int ly = tid >> 5; ly < 2 * MR; ly += nth >> 5) {
-                const int band = ly >= MR, t = ly - band * MR;
-                const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
-                const float *rowp = img + (size_t)line * N;
-                float2 *dst = Q2 + 2 * (size_t)t * SP + band;
-                for (int ii = lx; ii < CW; ii += 32) {
+            // warps take 32-pair chunks of the 16 steps, lanes neighbouring pairs
+            const int nch = (CW + 31) >> 5;
+            for (int c = tid >> 5; c < MR * nch; c += nw) {
+                const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
+                if (ii < CW) {
                     const int i = ii - 2;
-                    const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
-                    const float av = (ia >= 0 && ia < N) ? rowp[ia] : 0.0f;
-                    const float bv = (ib >= 0 && ib < N) ? rowp[ib] : 0.0f;
-                    dst[2 * ii] = make_float2(0.5f * (av + bv), bv - av);
+                    const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
+                    const float a0 = (i >= 0 && i < N) ? ra[i] : 0.0f;
+                    const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
+                    const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
+                    const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
+                    Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
                 }
             }
         } else {
-            const int band = lx >= MR, t = lx - band * MR;
-            const int line = band == 0 ? s0 + t : N - 1 - s0 - t;
-            float2 *dst = Q2 + 2 * (size_t)t * SP + band;
-            for (int ii = tid >> 5; ii < CW; ii += nth >> 5) {
-                const int i = ii - 2;
-                const int ia = band == 0 ? i : N - 1 - i, ib = band == 0 ? i + 1 : N - 2 - i;
-                const float av = (ia >= 0 && ia < N) ? img[(size_t)ia * N + line] : 0.0f;
-                const float bv = (ib >= 0 && ib < N) ? img[(size_t)ib * N + line] : 0.0f;
-                dst[2 * ii] = make_float2(0.5f * (av + bv), bv - av);
+            // lanes take the 16 steps (columns) of two neighbouring pairs:
+            // 64-byte row segments in, conflict-free float4 stores (odd SP)
+            const int t = lx & 15, ca = s0 + t, cb = N - 1 - s0 - t;
+            for (int c = tid >> 5; 2 * c < CW; c += nw) {
+                const int ii = 2 * c + (lx >> 4);
+                if (ii < CW) {
+                    const int i = ii - 2;
+                    const float a0 = (i >= 0 && i < N) ? img[(size_t)i * N + ca] : 0.0f;
+                    const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
+                    const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
+                    const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
+                    Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+                }
             }
         }
     }
