@@ -731,7 +731,10 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // serves four pixel-views; a block takes a 16 x 16 tile of one image
 // quadrant and evaluates, per base view v < V/2, the weights of P and of
 // R90 P, which cover all eight (pixel, view) pairs of the orbit
-// {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Base views are split into
+// {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Each of the block's 128
+// threads takes the orbits of two pixels of the tile, rows r and r + 8 of
+// one column, so the per-view constants, window bases and loop control
+// are shared by sixteen pixel-views.  Base views are split into
 // nsl slices (grid.z; 4 unless tuned, at most ORB_SL_MAX); each slice
 // writes its own partial image and k_orbit_reduce adds the slices in a
 // fixed order.  The weights are the
@@ -739,6 +742,8 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // the same A^T.
 // =====================================================================
 constexpr int ORB_T = 16;        // quadrant tile side
+constexpr int ORB_TY = 8;        // thread rows of a block: two tile rows (r, r + 8) each
+constexpr int ORB_TH = ORB_T * ORB_TY;
 constexpr int ORB_SL = 4;        // base-view slices unless tuned
 constexpr int ORB_SL_MAX = 8;
 constexpr int ORB_VC = 8;        // base views staged per chunk
@@ -765,7 +770,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // multiple of 4) is copied in aligned 16-byte pieces, each wholly on or
 // wholly off the detector.
 template <bool AL>
-__global__ void __launch_bounds__(256, 8)
+__global__ void __launch_bounds__(ORB_TH, 8)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
                     int N, int V, int B, int nsl)
 {
@@ -774,23 +779,25 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     float *raw = reinterpret_cast<float *>(osm);                               // 2 x ORB_VC x 8 x ORB_RW
     float4 *tt = reinterpret_cast<float4 *>(raw + 2 * ORB_VC * 8 * ORB_RW);    // 2 x ORB_VC
     int *wbs = reinterpret_cast<int *>(tt + 2 * ORB_VC);                       // ORB_MAXS x 2
-    const int tid = threadIdx.y * ORB_T + threadIdx.x;
+    const int tid = threadIdx.y * ORB_T + threadIdx.x;   // threadIdx.y < ORB_TY
     const int half = N / 2, V2 = V / 2;
     const int slice = blockIdx.z % nsl, img = blockIdx.z / nsl;
     const int r0 = blockIdx.y * ORB_T, c0 = half + blockIdx.x * ORB_T;   // quadrant r < N/2, c >= N/2
-    const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
-    const bool inside = r < half && c < N;
+    const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;            // pixels (r, c) and (r + 8, c)
+    const bool inside = r < half && c < N, inside2 = r + ORB_TY < half && c < N;
     const float h = 0.5f * (float)(N - 1), hb = 0.5f * (float)(B - 1), hb_lo = hb - 0.5f;
     const float xq = (float)c - h, yq = (float)r - h;               // P = (x, y); R90 P = (-y, x)
+    const float yq2 = yq + (float)ORB_TY;
     const float *ys = y + (size_t)img * V * B;
     const int vb0 = (int)((long long)V2 * slice / nsl), vb1 = (int)((long long)V2 * (slice + 1) / nsl);
     const int nvs = vb1 - vb0;
     float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
+    float bP = 0.0f, b90 = 0.0f, b180 = 0.0f, b270 = 0.0f;   // the second pixel's orbit
 
     // window bases (multiples of 4) of the tile for every base view of this
     // slice: floor(e) - wb lies in [1, 29] for every pixel of the tile, as
     // e spans at most 15 (|cos| + |sin|) < 21.3 over it
-    for (int vi = tid; vi < nvs; vi += 256) {
+    for (int vi = tid; vi < nvs; vi += ORB_TH) {
         const float4 T = trig[vb0 + vi];
         float emin = 3.0e38f, e9min = 3.0e38f;
 #pragma unroll
@@ -817,7 +824,7 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
             tt[buf * ORB_VC + tid] = make_float4(T.x, T.y, T.z * T.z, T.z * T.w);
         }
         constexpr int CH = AL ? ORB_RW / 4 : ORB_RW;   // copies per window
-        for (int k = tid; k < nv * 8 * CH; k += 256) {
+        for (int k = tid; k < nv * 8 * CH; k += ORB_TH) {
             const int q = k / CH, j = k - q * CH;
             const int win = q & 3, row = (q >> 2) & 1, vi = q >> 3;
             const int base = wbs[2 * (v0 - vb0 + vi) + (win >> 1)];
@@ -847,38 +854,51 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
                 const float4 T = tv[vi];
                 const int2 wb = *reinterpret_cast<const int2 *>(wbs + 2 * (v0 - vb0 + vi));
                 const float *t8 = tb + (size_t)vi * 8 * ORB_RW;   // [row][win][value]
-                // e - 1/2 of P and of R90 P
-                const float e = fmaf(xq, T.x, fmaf(yq, T.y, hb_lo));
-                const float e9 = fmaf(xq, T.y, fmaf(-yq, T.x, hb_lo));
-                const float t = __fadd_rn(e, JOSEPH_BIAS), t9 = __fadd_rn(e9, JOSEPH_BIAS);
-                const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb.x)), (unsigned)(ORB_RW - 2));
-                const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb.y)), (unsigned)(ORB_RW - 2));
-                const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
-                const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
-                const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
-                const float w09 = fmaxf(0.0f, fmaf(-g9, T.z, T.w)), w19 = fmaxf(0.0f, fmaf(g9, T.z, T.w));
-                const unsigned km = ORB_RW - 2 - k, km9 = ORB_RW - 2 - k9;
                 const float *e_v = t8, *m_v = t8 + ORB_RW, *e9_v = t8 + 2 * ORB_RW, *m9_v = t8 + 3 * ORB_RW;
                 const float *e_w = t8 + 4 * ORB_RW, *m_w = t8 + 5 * ORB_RW, *e9_w = t8 + 6 * ORB_RW,
                             *m9_w = t8 + 7 * ORB_RW;
-                aP = fmaf(w0, e_v[k], fmaf(w1, e_v[k + 1], aP));             // P at v
-                a180 = fmaf(w1, m_v[km], fmaf(w0, m_v[km + 1], a180));       // R180 P at v
-                a90 = fmaf(w0, e_w[k], fmaf(w1, e_w[k + 1], a90));           // R90 P at v + V/2
-                a270 = fmaf(w1, m_w[km], fmaf(w0, m_w[km + 1], a270));       // R270 P at v + V/2
-                a90 = fmaf(w09, e9_v[k9], fmaf(w19, e9_v[k9 + 1], a90));     // R90 P at v
-                a270 = fmaf(w19, m9_v[km9], fmaf(w09, m9_v[km9 + 1], a270)); // R270 P at v
-                a180 = fmaf(w09, e9_w[k9], fmaf(w19, e9_w[k9 + 1], a180));   // R180 P at v + V/2
-                aP = fmaf(w19, m9_w[km9], fmaf(w09, m9_w[km9 + 1], aP));     // P at v + V/2
+                // the orbit of the pixel at (x, y) = (xq, yy): e - 1/2 of P and of R90 P
+                auto orbit = [&](float yy, float &cP, float &c90, float &c180, float &c270) {
+                    const float e = fmaf(xq, T.x, fmaf(yy, T.y, hb_lo));
+                    const float e9 = fmaf(xq, T.y, fmaf(-yy, T.x, hb_lo));
+                    const float t = __fadd_rn(e, JOSEPH_BIAS), t9 = __fadd_rn(e9, JOSEPH_BIAS);
+                    const unsigned k = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS + wb.x)),
+                                           (unsigned)(ORB_RW - 2));
+                    const unsigned k9 = min((unsigned)(__float_as_int(t9) - (JOSEPH_BIAS_BITS + wb.y)),
+                                            (unsigned)(ORB_RW - 2));
+                    const float g = __fsub_rn(e, __fsub_rn(t, JOSEPH_BIAS));
+                    const float g9 = __fsub_rn(e9, __fsub_rn(t9, JOSEPH_BIAS));
+                    const float w0 = fmaxf(0.0f, fmaf(-g, T.z, T.w)), w1 = fmaxf(0.0f, fmaf(g, T.z, T.w));
+                    const float w09 = fmaxf(0.0f, fmaf(-g9, T.z, T.w)), w19 = fmaxf(0.0f, fmaf(g9, T.z, T.w));
+                    const unsigned km = ORB_RW - 2 - k, km9 = ORB_RW - 2 - k9;
+                    cP = fmaf(w0, e_v[k], fmaf(w1, e_v[k + 1], cP));             // P at v
+                    c180 = fmaf(w1, m_v[km], fmaf(w0, m_v[km + 1], c180));       // R180 P at v
+                    c90 = fmaf(w0, e_w[k], fmaf(w1, e_w[k + 1], c90));           // R90 P at v + V/2
+                    c270 = fmaf(w1, m_w[km], fmaf(w0, m_w[km + 1], c270));       // R270 P at v + V/2
+                    c90 = fmaf(w09, e9_v[k9], fmaf(w19, e9_v[k9 + 1], c90));     // R90 P at v
+                    c270 = fmaf(w19, m9_v[km9], fmaf(w09, m9_v[km9 + 1], c270)); // R270 P at v
+                    c180 = fmaf(w09, e9_w[k9], fmaf(w19, e9_w[k9 + 1], c180));   // R180 P at v + V/2
+                    cP = fmaf(w19, m9_w[km9], fmaf(w09, m9_w[km9 + 1], cP));     // P at v + V/2
+                };
+                orbit(yq, aP, a90, a180, a270);
+                if (inside2) orbit(yq2, bP, b90, b180, b270);
             }
         }
         __syncthreads();   // the buffer is refilled two chunks later
     }
+    float *pp = partial + ((size_t)img * nsl + slice) * N * N;
     if (inside) {
-        float *pp = partial + ((size_t)img * nsl + slice) * N * N;
         pp[(size_t)r * N + c] = aP;
         pp[(size_t)c * N + (N - 1 - r)] = a90;                   // R90 (r, c) = (c, N-1-r)
         pp[(size_t)(N - 1 - r) * N + (N - 1 - c)] = a180;        // R180 (r, c) = (N-1-r, N-1-c)
         pp[(size_t)(N - 1 - c) * N + r] = a270;                  // R270 (r, c) = (N-1-c, r)
+    }
+    if (inside2) {
+        const int r2 = r + ORB_TY;
+        pp[(size_t)r2 * N + c] = bP;
+        pp[(size_t)c * N + (N - 1 - r2)] = b90;
+        pp[(size_t)(N - 1 - r2) * N + (N - 1 - c)] = b180;
+        pp[(size_t)(N - 1 - c) * N + r2] = b270;
     }
 }
 
@@ -920,10 +940,10 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, nsl * batch);
     counted(2);
     if (g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0)
-        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
+        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
                                                                                 g->n_views, g->n_bins, nsl);
     else
-        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_T), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
+        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
                                                                                  g->n_views, g->n_bins, nsl);
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
