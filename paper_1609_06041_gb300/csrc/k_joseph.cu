@@ -731,10 +731,10 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // serves four pixel-views; a block takes a 16 x 16 tile of one image
 // quadrant and evaluates, per base view v < V/2, the weights of P and of
 // R90 P, which cover all eight (pixel, view) pairs of the orbit
-// {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Each of the block's 128
-// threads takes the orbits of two pixels of the tile, rows r and r + 8 of
-// one column, so the per-view constants, window bases and loop control
-// are shared by sixteen pixel-views.  Base views are split into
+// {P, R90 P, R180 P, R270 P} x {v, v + V/2}.  Each of the block's
+// 16 ORB_TY threads takes the orbits of ORB_PX pixels of one tile column
+// (rows r, r + ORB_TY, ..), so the per-view constants, window bases and
+// loop control are shared by 8 ORB_PX pixel-views.  Base views are split into
 // nsl slices (grid.z; 4 unless tuned, at most ORB_SL_MAX); each slice
 // writes its own partial image and k_orbit_reduce adds the slices in a
 // fixed order.  The weights are the
@@ -742,8 +742,9 @@ k_backproject_tiles(const float *__restrict__ y, float *__restrict__ out,
 // the same A^T.
 // =====================================================================
 constexpr int ORB_T = 16;        // quadrant tile side
-constexpr int ORB_TY = 8;        // thread rows of a block: two tile rows (r, r + 8) each
+constexpr int ORB_TY = 8;        // thread rows of a block: tile rows r, r + ORB_TY, ... each
 constexpr int ORB_TH = ORB_T * ORB_TY;
+constexpr int ORB_PX = ORB_T / ORB_TY;   // pixel orbits per thread
 constexpr int ORB_SL = 4;        // base-view slices unless tuned
 constexpr int ORB_SL_MAX = 8;
 constexpr int ORB_VC = 8;        // base views staged per chunk
@@ -783,16 +784,16 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
     const int half = N / 2, V2 = V / 2;
     const int slice = blockIdx.z % nsl, img = blockIdx.z / nsl;
     const int r0 = blockIdx.y * ORB_T, c0 = half + blockIdx.x * ORB_T;   // quadrant r < N/2, c >= N/2
-    const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;            // pixels (r, c) and (r + 8, c)
-    const bool inside = r < half && c < N, inside2 = r + ORB_TY < half && c < N;
+    const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;            // pixels (r + j ORB_TY, c)
+    const bool inside = r < half && c < N;
     const float h = 0.5f * (float)(N - 1), hb = 0.5f * (float)(B - 1), hb_lo = hb - 0.5f;
     const float xq = (float)c - h, yq = (float)r - h;               // P = (x, y); R90 P = (-y, x)
-    const float yq2 = yq + (float)ORB_TY;
     const float *ys = y + (size_t)img * V * B;
     const int vb0 = (int)((long long)V2 * slice / nsl), vb1 = (int)((long long)V2 * (slice + 1) / nsl);
     const int nvs = vb1 - vb0;
-    float aP = 0.0f, a90 = 0.0f, a180 = 0.0f, a270 = 0.0f;
-    float bP = 0.0f, b90 = 0.0f, b180 = 0.0f, b270 = 0.0f;   // the second pixel's orbit
+    float acc[ORB_PX][4];   // per pixel orbit: P, R90 P, R180 P, R270 P
+#pragma unroll
+    for (int j = 0; j < ORB_PX; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
 
     // window bases (multiples of 4) of the tile for every base view of this
     // slice: floor(e) - wb lies in [1, 29] for every pixel of the tile, as
@@ -880,25 +881,24 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
                     c180 = fmaf(w09, e9_w[k9], fmaf(w19, e9_w[k9 + 1], c180));   // R180 P at v + V/2
                     cP = fmaf(w19, m9_w[km9], fmaf(w09, m9_w[km9 + 1], cP));     // P at v + V/2
                 };
-                orbit(yq, aP, a90, a180, a270);
-                if (inside2) orbit(yq2, bP, b90, b180, b270);
+#pragma unroll
+                for (int j = 0; j < ORB_PX; ++j)
+                    if (j == 0 || r + j * ORB_TY < half)
+                        orbit(yq + (float)(j * ORB_TY), acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
             }
         }
         __syncthreads();   // the buffer is refilled two chunks later
     }
     float *pp = partial + ((size_t)img * nsl + slice) * N * N;
-    if (inside) {
-        pp[(size_t)r * N + c] = aP;
-        pp[(size_t)c * N + (N - 1 - r)] = a90;                   // R90 (r, c) = (c, N-1-r)
-        pp[(size_t)(N - 1 - r) * N + (N - 1 - c)] = a180;        // R180 (r, c) = (N-1-r, N-1-c)
-        pp[(size_t)(N - 1 - c) * N + r] = a270;                  // R270 (r, c) = (N-1-c, r)
-    }
-    if (inside2) {
-        const int r2 = r + ORB_TY;
-        pp[(size_t)r2 * N + c] = bP;
-        pp[(size_t)c * N + (N - 1 - r2)] = b90;
-        pp[(size_t)(N - 1 - r2) * N + (N - 1 - c)] = b180;
-        pp[(size_t)(N - 1 - c) * N + r2] = b270;
+#pragma unroll
+    for (int j = 0; j < ORB_PX; ++j) {
+        const int rj = r + j * ORB_TY;
+        if (rj < half && c < N) {
+            pp[(size_t)rj * N + c] = acc[j][0];
+            pp[(size_t)c * N + (N - 1 - rj)] = acc[j][1];              // R90 (r, c) = (c, N-1-r)
+            pp[(size_t)(N - 1 - rj) * N + (N - 1 - c)] = acc[j][2];    // R180 (r, c) = (N-1-r, N-1-c)
+            pp[(size_t)(N - 1 - c) * N + rj] = acc[j][3];              // R270 (r, c) = (N-1-c, r)
+        }
     }
 }
 
