@@ -71,9 +71,10 @@ def _load():
                 "orc_tv_prox": [_i, _p, _d, _i, _p, _p, _p],
                 "orc_cost": [_i, _i, _i, _p, _p, _p, _d, _p],
                 "orc_residual": [_i, _i, _i, _p, _p, _p],
-                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i,
+                "orc_apply_d": [_i, _i, _p, _p, _i, _p, _p, _p],
+                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i,
                              _i, _i, _p, _p, _p, _p, _p, _p],
-                "orc_power_norm": [_i, _i, _i, _i, _p, _p, _i, _p, _i],
+                "orc_power_norm": [_i, _i, _i, _i, _p, _p, _p, _p, _i, _p, _i],
                 "orc_cp_reference": [_i, _i, _i, _p, _p, _p, _i, _d, _d, _d, _i, _p],
             }
             for name, args in sig.items():
@@ -126,8 +127,10 @@ def fft_len(n_bins):
 
 
 def ramp_taps(mode, n_views, n_bins, tau, kappa=0.0, half=None, period=None):
-    """Taps of D (Eq. 24 mode 0, Eq. 32 mode 1); returns 2*half-1 values,
-    centre at index half-1.  Defaults: half = n_bins, period = fft_len."""
+    """Taps of D (Eq. 24 mode 0, Eq. 32 mode 1; modes 2 and 3 the low and
+    high bands of the shift-variant split, which add up to mode 0); returns
+    2*half-1 values, centre at index half-1.  Defaults: half = n_bins,
+    period = fft_len."""
     half = n_bins if half is None else half
     P = fft_len(n_bins) if period is None else period
     out = np.empty(2 * half - 1)
@@ -143,6 +146,28 @@ def filt(sino, taps):
     half = (taps.size + 1) // 2
     out = np.empty_like(sino)
     _load().orc_filter(V, B, _ptr(taps), half, _ptr(sino), _ptr(out))
+    return out
+
+
+def shift_variant_scale(w):
+    """s_i = sqrt(kappa w_i), kappa = mean(1/w) (Eq. 24 text): the diagonal
+    that scales the high band of the shift-variant preconditioner."""
+    w = _f64(w)
+    kappa = float(np.mean(1.0 / w))
+    return np.sqrt(kappa * w)
+
+
+def apply_d(sino, taps, taps_hi=None, s=None):
+    """The iteration's preconditioner: filt(sino, taps), or with taps_hi the
+    shift-variant D = T_lo + S T_hi S (taps = low band, S = diag(s))."""
+    sino = _f64(sino)
+    V, B = sino.shape
+    taps = _f64(taps)
+    half = (taps.size + 1) // 2
+    out = np.empty_like(sino)
+    th = None if taps_hi is None else _f64(taps_hi)
+    sv = None if taps_hi is None else _f64(s)
+    _load().orc_apply_d(V, B, _ptr(taps), _ptr(th), half, _ptr(sv), _ptr(sino), _ptr(out))
     return out
 
 
@@ -207,17 +232,21 @@ class PDState:
 
 
 def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
-         state=None, trace=False):
+         state=None, trace=False, taps_hi=None, s=None):
     """Run `iters` iterations of Algorithm 1 (mode 0) / 2 (mode 1) from
-    `state` (fresh zero state if None).  Returns (state, trace or None)."""
+    `state` (fresh zero state if None).  With taps_hi (and s) the
+    preconditioner is the shift-variant D = T_lo + S T_hi S (apply_d).
+    Returns (state, trace or None)."""
     b = _f64(b)
     V, B = b.shape
     w = None if w is None else _f64(w)
     taps = _f64(taps)
     half = (taps.size + 1) // 2
+    th = None if taps_hi is None else _f64(taps_hi)
+    sv = None if taps_hi is None else _f64(s)
     st = PDState(n, V, B) if state is None else state
     tr = np.empty(iters) if trace else None
-    _load().orc_pdtv(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), _ptr(taps), half,
+    _load().orc_pdtv(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), _ptr(taps), _ptr(th), _ptr(sv), half,
                      int(mode), float(beta), float(tau), float(sigma), int(n_tv),
                      int(st.k), int(iters), _ptr(st.x), _ptr(st.mu), _ptr(st.mu_prev),
                      _ptr(st.px), _ptr(st.py), _ptr(tr))
@@ -225,13 +254,15 @@ def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
     return st, tr
 
 
-def power_norm(which, n, n_views, n_bins, taps=None, w=None, iters=50, angles=None):
-    """which=0: ||A^T D A||; which=1: ||W^-1/2 D W^-1/2||."""
+def power_norm(which, n, n_views, n_bins, taps=None, w=None, iters=50, angles=None, taps_hi=None, s=None):
+    """which=0: ||A^T D A||; which=1: ||W^-1/2 D W^-1/2|| (D as in apply_d)."""
     taps = np.ones(1) if taps is None else _f64(taps)
     half = (taps.size + 1) // 2
     w = None if w is None else _f64(w)
+    th = None if taps_hi is None else _f64(taps_hi)
+    sv = None if taps_hi is None else _f64(s)
     return float(_load().orc_power_norm(int(which), n, n_views, n_bins, _ptr(_angles(angles)),
-                                        _ptr(taps), half, _ptr(w), int(iters)))
+                                        _ptr(taps), _ptr(th), _ptr(sv), half, _ptr(w), int(iters)))
 
 
 def cp_reference(b, w, mode, beta, s, t, iters, n, angles=None):
@@ -251,13 +282,14 @@ def default_tau(mode, n_views, kappa):
     return np.pi * kappa / (2.0 * n_views) if mode == 0 else 0.01
 
 
-def step_sizes(mode, n, n_views, n_bins, taps, w, tau, rho=0.95, iters=50, angles=None):
+def step_sizes(mode, n, n_views, n_bins, taps, w, tau, rho=0.95, iters=50, angles=None, taps_hi=None, s=None):
     """sigma from the step rule of the Alg. 1 / Alg. 2 boxes with safety rho:
     low-dose sigma = rho*min(2/||W^-1/2 D W^-1/2||, 1/(tau ||A^T D A||)),
     few-view sigma = rho/(tau ||A^T D A||).  Returns (sigma, nADA, nWDW)."""
-    nada = power_norm(0, n, n_views, n_bins, taps=taps, iters=iters, angles=angles)
+    nada = power_norm(0, n, n_views, n_bins, taps=taps, iters=iters, angles=angles, taps_hi=taps_hi, s=s)
     if mode == 0:
-        nwdw = power_norm(1, n, n_views, n_bins, taps=taps, w=w, iters=iters, angles=angles)
+        nwdw = power_norm(1, n, n_views, n_bins, taps=taps, w=w, iters=iters, angles=angles,
+                          taps_hi=taps_hi, s=s)
         sigma = rho * min(2.0 / nwdw, 1.0 / (tau * nada))
     else:
         nwdw = 0.0

@@ -163,12 +163,20 @@ int orc_fft_len(int B)
 }
 
 /* H(w): mode 0 smoothed ramp |w|/(2 m tau + kappa |w|) (Eq. 24);
- *       mode 1 pure ramp |w|/(2 m tau) (Eq. 32). */
+ *       mode 1 pure ramp |w|/(2 m tau) (Eq. 32);
+ *       modes 2 and 3 split the smoothed ramp into a low band and a high
+ *       band, H_lo + H_hi = H (mode 0), for the shift-variant preconditioner
+ *       (Sec. 5 names one approximating D = (tau A A^T + W^-1)^-1 of Eq. 23
+ *       better; its form is this project's):
+ *         H_lo = 2 m tau |w| / (2 m tau + kappa |w|)^2,
+ *         H_hi = kappa w^2 / (2 m tau + kappa |w|)^2. */
 static double H_of(int mode, double w, int m, double tau, double kappa)
 {
-    double aw = fabs(w);
-    if (mode == 0) return aw / (2.0 * m * tau + kappa * aw);
-    return aw / (2.0 * m * tau);
+    double aw = fabs(w), den = 2.0 * m * tau + kappa * aw;
+    if (mode == 0) return aw / den;
+    if (mode == 1) return aw / (2.0 * m * tau);
+    if (mode == 2) return 2.0 * m * tau * aw / (den * den);
+    return kappa * aw * aw / (den * den);
 }
 
 /* taps[k + half - 1] = t[k] for |k| <= half - 1, by the direct cosine sum. */
@@ -205,6 +213,34 @@ void orc_filter(int V, int B, const double *taps, int half,
             o[d] = acc;
         }
     }
+}
+
+/* The preconditioner applied in the iteration.  taps_hi == NULL: the
+ * convolution D of Eqs. 24 / 32 with `taps`.  Otherwise the shift-variant
+ * form D = T_lo + S T_hi S: `taps` holds the low band (H_lo), taps_hi the
+ * high band (H_hi), and S = diag(s), s_i = sqrt(kappa w_i), scales the high
+ * band so that, as the frequency grows, D tends to W = diag(w), the high-
+ * frequency limit of (tau A A^T + W^-1)^-1 (Eq. 23), where Eq. 24 tends to
+ * I/kappa.  With s = 1 (w_i = 1/kappa) it is the convolution of Eq. 24.
+ * tmp: two scratch sinograms. */
+static void apply_d(int V, int B, const double *taps, const double *taps_hi, int half,
+                    const double *s, const double *in, double *out, double *tmp)
+{
+    orc_filter(V, B, taps, half, in, out);
+    if (!taps_hi) return;
+    size_t I = (size_t)V * B;
+    double *t1 = tmp, *t2 = tmp + I;
+    for (size_t i = 0; i < I; ++i) t1[i] = s[i] * in[i];
+    orc_filter(V, B, taps_hi, half, t1, t2);
+    for (size_t i = 0; i < I; ++i) out[i] += s[i] * t2[i];
+}
+
+void orc_apply_d(int V, int B, const double *taps, const double *taps_hi, int half,
+                 const double *s, const double *in, double *out)
+{
+    double *tmp = malloc(sizeof(double) * 2 * (size_t)V * B);
+    apply_d(V, B, taps, taps_hi, half, s, in, out, tmp);
+    free(tmp);
 }
 
 /* ------------------------------------------------------------------ */
@@ -337,7 +373,7 @@ double orc_residual(int N, int V, int B, const double *angles,
 
 void orc_pdtv(int N, int V, int B, const double *angles,
               const double *b, const double *w,
-              const double *taps, int half, int mode,
+              const double *taps, const double *taps_hi, const double *sv, int half, int mode,
               double beta, double tau, double sigma, int n_tv,
               int k0, int iters,
               double *x, double *mu, double *mu_prev, double *px, double *py,
@@ -347,6 +383,7 @@ void orc_pdtv(int N, int V, int B, const double *angles,
     double *mubar = malloc(sizeof(double) * I);
     double *t1 = malloc(sizeof(double) * I), *t2 = malloc(sizeof(double) * I);
     double *z = malloc(sizeof(double) * J);
+    double *dtmp = malloc(sizeof(double) * 2 * I);
     double lam = (mode == 0) ? tau * beta : tau;
     if (k0 == 0) {
         memset(x, 0, sizeof(double) * J);
@@ -358,11 +395,11 @@ void orc_pdtv(int N, int V, int B, const double *angles,
     for (int k = k0; k < k0 + iters; ++k) {
         /* Step 1: extrapolation */
         if (k == 0) {
-            orc_filter(V, B, taps, half, b, t1);
+            apply_d(V, B, taps, taps_hi, half, sv, b, t1, dtmp);
             for (size_t i = 0; i < I; ++i) mubar[i] = -sigma * t1[i];
         } else if (mode == 0) {
             for (size_t i = 0; i < I; ++i) t2[i] = (mu[i] - mu_prev[i]) / w[i];
-            orc_filter(V, B, taps, half, t2, t1);
+            apply_d(V, B, taps, taps_hi, half, sv, t2, t1, dtmp);
             for (size_t i = 0; i < I; ++i)
                 mubar[i] = 2.0 * mu[i] - mu_prev[i] - sigma * t1[i];
         } else {
@@ -378,7 +415,7 @@ void orc_pdtv(int N, int V, int B, const double *angles,
             t2[i] -= b[i];
             if (mode == 0) t2[i] -= mu[i] / w[i];
         }
-        orc_filter(V, B, taps, half, t2, t1);
+        apply_d(V, B, taps, taps_hi, half, sv, t2, t1, dtmp);
         for (size_t i = 0; i < I; ++i) {
             mu_prev[i] = mu[i];
             mu[i] = mu[i] + sigma * t1[i];
@@ -393,6 +430,7 @@ void orc_pdtv(int N, int V, int B, const double *angles,
     free(t1);
     free(t2);
     free(z);
+    free(dtmp);
 }
 
 /* ------------------------------------------------------------------ */
@@ -403,12 +441,14 @@ void orc_pdtv(int N, int V, int B, const double *angles,
 /* ------------------------------------------------------------------ */
 
 double orc_power_norm(int which, int N, int V, int B, const double *angles,
-                      const double *taps, int half, const double *w, int iters)
+                      const double *taps, const double *taps_hi, const double *sv, int half,
+                      const double *w, int iters)
 {
     size_t I = (size_t)V * B, J = (size_t)N * N;
     size_t n = which == 0 ? J : I;
     double *v = malloc(sizeof(double) * n), *u = malloc(sizeof(double) * n);
     double *s1 = malloc(sizeof(double) * I), *s2 = malloc(sizeof(double) * I);
+    double *dtmp = malloc(sizeof(double) * 2 * I);
     double lam = 0.0;
     for (size_t i = 0; i < n; ++i) v[i] = 1.0;
     for (int it = 0; it < iters; ++it) {
@@ -418,11 +458,11 @@ double orc_power_norm(int which, int N, int V, int B, const double *angles,
         for (size_t i = 0; i < n; ++i) v[i] /= nv;
         if (which == 0) {
             orc_project(N, V, B, angles, v, s1);
-            orc_filter(V, B, taps, half, s1, s2);
+            apply_d(V, B, taps, taps_hi, half, sv, s1, s2, dtmp);
             orc_backproject(N, V, B, angles, s2, u);
         } else {
             for (size_t i = 0; i < I; ++i) s1[i] = v[i] / sqrt(w[i]);
-            orc_filter(V, B, taps, half, s1, s2);
+            apply_d(V, B, taps, taps_hi, half, sv, s1, s2, dtmp);
             for (size_t i = 0; i < I; ++i) u[i] = s2[i] / sqrt(w[i]);
         }
         lam = 0.0;
@@ -433,6 +473,7 @@ double orc_power_norm(int which, int N, int V, int B, const double *angles,
     free(u);
     free(s1);
     free(s2);
+    free(dtmp);
     return lam;
 }
 
