@@ -60,6 +60,8 @@ typedef enum {
 } ct_status;
 
 enum { CT_LOWDOSE = 0, CT_FEWVIEW = 1 };
+/* Band taps of the shift-variant preconditioner (ct_ramp_taps modes). */
+enum { CT_TAPS_LOW_BAND = 2, CT_TAPS_HIGH_BAND = 3 };
 
 typedef struct ct_geometry ct_geometry;
 
@@ -141,6 +143,10 @@ ct_status ct_backproject(const ct_geometry *geom, const float *sino, float *img,
  * with t[k] = (1/P) sum_j H(w_j) cos(2 pi j k / P), |k| <= B-1, on the
  * period P = 2^ceil(log2(2B)), w_j = 2 pi min(j, P-j)/P.  taps (device,
  * 2B-1 floats) receives t[-(B-1)] .. t[B-1] (centre at index B-1).
+ * Modes CT_TAPS_LOW_BAND and CT_TAPS_HIGH_BAND give the two bands of the
+ * shift-variant preconditioner (see ct_ramp_filter_split), which add up to
+ * the CT_LOWDOSE taps:
+ *     H_lo = 2 m tau |w| / (2 m tau + kappa |w|)^2,  H_hi = kappa w^2 / (2 m tau + kappa |w|)^2.
  * tau > 0, kappa >= 0 (kappa ignored for CT_FEWVIEW).
  */
 ct_status ct_ramp_taps(const ct_geometry *geom, int mode, double tau, double kappa,
@@ -154,6 +160,26 @@ ct_status ct_ramp_taps(const ct_geometry *geom, int mode, double tau, double kap
  */
 ct_status ct_ramp_filter(const ct_geometry *geom, const float *taps, int half_len,
                          const float *in, float *out, int batch, void *stream);
+
+/*
+ * The shift-variant preconditioner: out = T_lo in + s .* T_hi (s .* in), per
+ * view, with T_lo, T_hi the linear convolutions with taps_lo and taps_hi
+ * (layout as ct_ramp_filter) and s elementwise.  Sec. 5 reports that a
+ * shift-variant preconditioner approximating D = (tau A A^T + W^-1)^-1
+ * (Eq. 23) better than Eq. 24 improves the low-dose iteration, without
+ * giving its form; this is the project's form: with the band taps of
+ * ct_ramp_taps and s_i = sqrt(kappa w_i) it tends to the pure ramp of Eq. 32
+ * at low frequency and to W = diag(w) at high frequency, the two limits of
+ * Eq. 23, and equals Eq. 24 when all w_i = 1/kappa.  It is symmetric
+ * positive definite, so the iteration keeps its limit (Sec. 2.2).
+ * s: device, V x B floats (one slice; the same s for every batch image).
+ * in, out: batch x V x B, in == out not allowed.  Needs n_bins <= 4096 (an
+ * FFT of at most 8192 points); CT_ERR_ARG otherwise.  Allocates two
+ * frequency responses of n_fft complex values from the stream-ordered
+ * allocator and frees them after use (CT_ERR_OOM if that fails).
+ */
+ct_status ct_ramp_filter_split(const ct_geometry *geom, const float *taps_lo, const float *taps_hi, int half_len,
+                               const float *s, const float *in, float *out, int batch, void *stream);
 
 /*
  * ct_ramp_filter without any device memory allocation.  The paper has no
@@ -186,7 +212,9 @@ typedef struct {
     int tv_iters;     /* inner projected-gradient steps of the TV prox (Eq. 17),
                          0 -> 10; warm-started across outer iterations       */
     int precond;      /* 1: ramp preconditioner D (Eq. 24 / Eq. 32);
-                         0: D = I (the unpreconditioned iteration)           */
+                         0: D = I (the unpreconditioned iteration);
+                         2: the shift-variant D of ct_ramp_filter_split with
+                            s = sqrt(kappa w) (CT_LOWDOSE, n_bins <= 4096) */
     int norm_iters;   /* Lanczos steps for the operator norms of the automatic
                          sigma (0 -> 16, at most 64)                          */
     int resume;       /* 1: continue from the state held in `workspace`       */

@@ -7,6 +7,8 @@ C ABI of include/ctpd.h; ``ctpd`` is its thin Python binding.
 from .ctpd import (  # noqa: F401
     CT_FEWVIEW,
     CT_LOWDOSE,
+    CT_TAPS_HIGH_BAND,
+    CT_TAPS_LOW_BAND,
     BatchedSolve,
     CTError,
     Geometry,
@@ -25,6 +27,7 @@ from .ctpd import (  # noqa: F401
     ct_project,
     ct_ramp_filter,
     ct_ramp_filter_noalloc,
+    ct_ramp_filter_split,
     ct_ramp_taps,
     ct_version,
     workspace_for,

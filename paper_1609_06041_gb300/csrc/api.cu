@@ -74,7 +74,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, hhat, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, total;
+    size_t scal, partials, taps, hhat, taps2, hhat2, sv, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, total;
 };
 
 Layout layout(const Geometry *g)
@@ -86,6 +86,10 @@ Layout layout(const Geometry *g)
     L.partials = o; o += align256(sizeof(double) * 2 * dot_partials_doubles());   // two concurrent reductions
     L.taps = o;     o += align256(sizeof(float) * (2 * (size_t)g->n_bins - 1));
     L.hhat = o;     o += align256(sizeof(float2) * (size_t)g->n_fft);
+    // the shift-variant D: its high band's taps and response, and s
+    L.taps2 = o;    o += align256(sizeof(float) * (2 * (size_t)g->n_bins - 1));
+    L.hhat2 = o;    o += align256(sizeof(float2) * (size_t)g->n_fft);
+    L.sv = o;       o += align256(sizeof(float) * I);
     L.winv = o;     o += align256(sizeof(float) * I);
     L.mu = o;       o += align256(sizeof(float) * I);
     L.mubar = o;    o += align256(sizeof(float) * I);
@@ -349,11 +353,34 @@ ct_status ct_backproject(const ct_geometry *g, const float *sino, float *img, in
 ct_status ct_ramp_taps(const ct_geometry *g, int mode, double tau, double kappa, float *taps, void *stream)
 {
     g_err[0] = 0;
-    if (!g || !taps || (mode != CT_LOWDOSE && mode != CT_FEWVIEW) || !(tau > 0.0) ||
-        (mode == CT_LOWDOSE && !(kappa >= 0.0)))
+    if (!g || !taps || mode < CT_LOWDOSE || mode > CT_TAPS_HIGH_BAND || !(tau > 0.0) ||
+        (mode != CT_FEWVIEW && !(kappa >= 0.0)))
         return fail(CT_ERR_ARG, "ct_ramp_taps: bad argument");
     launch_taps(g, mode, nullptr, tau, kappa, taps, S(stream));
     return cuda_check("ct_ramp_taps");
+}
+
+ct_status ct_ramp_filter_split(const ct_geometry *g, const float *taps_lo, const float *taps_hi, int half_len,
+                               const float *sv, const float *in, float *out, int batch, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || half_len < 1 || half_len > g->n_bins || batch < 0 || batch > 65535)
+        return fail(CT_ERR_ARG, "ct_ramp_filter_split: bad argument");
+    if (!fft_supported(g)) return fail(CT_ERR_ARG, "ct_ramp_filter_split: needs n_bins <= 4096");
+    if (batch == 0) return CT_OK;
+    if (!taps_lo || !taps_hi || !sv || !in || !out || in == out)
+        return fail(CT_ERR_ARG, "ct_ramp_filter_split: bad pointer");
+    // the bands' frequency responses: stream-ordered scratch, freed after use
+    float2 *hs = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&hs, sizeof(float2) * 2 * g->n_fft, S(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CT_ERR_OOM, "ct_ramp_filter_split: scratch allocation failed");
+    }
+    launch_sv_hhat(g, taps_lo, taps_hi, half_len, hs, hs + g->n_fft, S(stream));
+    launch_filter_sv(g, hs, hs + g->n_fft, sv, in, out, nullptr, nullptr, 0, nullptr, batch, S(stream));
+    cudaFreeAsync(hs, S(stream));
+    return cuda_check("ct_ramp_filter_split");
 }
 
 ct_status ct_ramp_filter(const ct_geometry *g, const float *taps, int half_len, const float *in,
@@ -409,6 +436,9 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         return fail(CT_ERR_ARG, "ct_pdtv_solve: negative iteration count");
     if (mode == CT_LOWDOSE && !(prm->beta >= 0.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: beta must be >= 0");
     if (prm->resume && !workspace) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
+    if (prm->precond < 0 || prm->precond > 2) return fail(CT_ERR_ARG, "ct_pdtv_solve: precond must be 0, 1 or 2");
+    if (prm->precond == 2 && (mode != CT_LOWDOSE || !fft_supported(g)))
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: the shift-variant preconditioner needs CT_LOWDOSE and n_bins <= 4096");
     if (!aligned16(b) || !aligned16(x_out) || (w && !aligned16(w)) || (workspace && !aligned16(workspace)))
         return fail(CT_ERR_ARG, "ct_pdtv_solve: pointers must be 16-byte aligned");
     const double rho = prm->rho > 0.0 ? prm->rho : 0.95;
@@ -438,6 +468,16 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     float *taps = (float *)(ws + L.taps);
     float2 *hhat = (float2 *)(ws + L.hhat);
     const bool use_fft = fft_supported(g);
+    // precond 2: hhat / hhat2 hold (H_lo +- H_hi) / 2, sv = sqrt(kappa w)
+    const bool sv_d = prm->precond == 2;
+    float *taps2 = (float *)(ws + L.taps2), *sv = (float *)(ws + L.sv);
+    float2 *hhat2 = (float2 *)(ws + L.hhat2);
+    // out = post .* D(pre .* in) * (mode 1 ? -sigma : 1), and D applied to A x given as band sums
+    auto filter = [&](const float *in, float *out, const float *pre, const float *post, int md, cudaStream_t s_) {
+        if (sv_d) launch_filter_sv(g, hhat, hhat2, sv, in, out, pre, post, md, scal, 1, s_);
+        else if (use_fft) launch_filter_fft(g, hhat, in, out, pre, post, md, scal, 1, s_);
+        else launch_filter(g, taps, prm->precond ? g->n_bins : 1, in, out, pre, post, md, scal, 1, s_);
+    };
     float *winv = (float *)(ws + L.winv);
     float *mu = (float *)(ws + L.mu), *mubar = (float *)(ws + L.mubar), *r = (float *)(ws + L.r);
     float *z = (float *)(ws + L.z), *uimg = (float *)(ws + L.u), *w3img = (float *)(ws + L.w3);
@@ -469,9 +509,16 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             launch_scalars(scal, SC_KAPPA_FROM_SUM, (double)I, 0, 0, 0, st);
         }
         launch_scalars(scal, SC_TAU, prm->tau, (double)g->n_views, 0, mode, st);
-        if (prm->precond) launch_taps(g, mode, scal, 0.0, 0.0, taps, st);
-        else launch_fill(taps, 1.0f, 1, st);
-        if (use_fft) launch_hhat(g, taps, half, hhat, st);
+        if (sv_d) {
+            launch_taps(g, CT_TAPS_LOW_BAND, scal, 0.0, 0.0, taps, st);
+            launch_taps(g, CT_TAPS_HIGH_BAND, scal, 0.0, 0.0, taps2, st);
+            launch_sv_hhat(g, taps, taps2, half, hhat, hhat2, st);
+            launch_sv_scale(w, scal, sv, I, st);
+        } else {
+            if (prm->precond) launch_taps(g, mode, scal, 0.0, 0.0, taps, st);
+            else launch_fill(taps, 1.0f, 1, st);
+            if (use_fft) launch_hhat(g, taps, half, hhat, st);
+        }
         if (!(prm->sigma > 0.0)) {
             // ||W^-1/2 D W^-1/2|| by Lanczos on the sinogram side (low-dose),
             // on a second stream beside the image-side run when D is applied
@@ -490,16 +537,15 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 }
                 float *sw = aux;
                 launch_sqrt(winv, sw, I, s2);
-                auto op_wdw = [&](const float *v, float *out) {
-                    if (use_fft) launch_filter_fft(g, hhat, v, out, sw, sw, 0, nullptr, 1, s2);
-                    else launch_filter(g, taps, half, v, out, sw, sw, 0, nullptr, 1, s2);
-                };
+                auto op_wdw = [&](const float *v, float *out) { filter(v, out, sw, sw, 0, s2); };
                 lanczos_norm(op_wdw, mu, r, aux + I, I, nlz, scal, S_LZ2, S_LN0B, partials2, ticket2, S_NWDW, s2);
             }
             // ||A^T D A|| by Lanczos on the image side
             auto op_ada = [&](const float *v, float *out) {
                 launch_project_bands(g, v, band, 1, st);
-                if (use_fft) {
+                if (sv_d) {
+                    launch_filter_sv_bands(g, hhat, hhat2, sv, band, mubar, 1, st);
+                } else if (use_fft) {
                     launch_filter_fft_bands(g, hhat, band, mubar, 1, st);
                 } else {
                     launch_band_reduce(g, band, r, 0, nullptr, nullptr, nullptr, 1, st);
@@ -520,8 +566,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         launch_fill(pbuf[0], 0.0f, 2 * J, st);
         launch_fill(pbuf[1], 0.0f, 2 * J, st);
         launch_fill(mu, 0.0f, I, st);
-        if (use_fft) launch_filter_fft(g, hhat, b, mubar, nullptr, nullptr, 1, scal, 1, st);
-        else launch_filter(g, taps, half, b, mubar, nullptr, nullptr, 1, scal, 1, st);
+        filter(b, mubar, nullptr, nullptr, 1, st);
     }
     ct_status cs = cuda_check("ct_pdtv_solve setup");
     if (cs != CT_OK) {
@@ -548,7 +593,8 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
         // performs Step 1 of the next iteration
         launch_project_bands(g, x_out, band, 1, st);
-        if (use_fft) launch_dual_fft(g, hhat, band, b, mu, mubar, winv, lowdose, scal, st);
+        if (sv_d) launch_dual_sv(g, hhat, hhat2, sv, band, b, mu, mubar, winv, scal, st);
+        else if (use_fft) launch_dual_fft(g, hhat, band, b, mu, mubar, winv, lowdose, scal, st);
         else launch_dual_update(g, taps, half, band, b, mu, mubar, winv, lowdose, scal, st);
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);

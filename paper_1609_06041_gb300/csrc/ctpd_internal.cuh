@@ -175,6 +175,21 @@ void launch_filter_fft_bands(const Geometry *g, const float2 *hhat, const float 
 // fused residual + Step 3 + next Step 1 (as launch_dual_update)
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
                      float *mu_bar, const float *winv, int lowdose, const double *scal, cudaStream_t st);
+// The shift-variant preconditioner D = T_lo + S T_hi S (k_fft.cu; low-dose,
+// FFT path).  hs, hd (n_fft complex each) = (H_lo +- H_hi) / 2 from the band
+// taps; sv = s (V x B), s_i = sqrt(kappa w_i).
+void launch_sv_hhat(const Geometry *g, const float *taps_lo, const float *taps_hi, int half, float2 *hs, float2 *hd,
+                    cudaStream_t st);
+void launch_filter_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *in,
+                      float *out, const float *pre, const float *post, int mode, const double *scal, int batch,
+                      cudaStream_t st);
+void launch_filter_sv_bands(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv,
+                            const float *partial, float *out, int batch, cudaStream_t st);
+void launch_dual_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *partial,
+                    const float *b, float *mu, float *mu_bar, const float *winv, const double *scal,
+                    cudaStream_t st);
+// s = sqrt(kappa w), kappa = scal[S_KAPPA]
+void launch_sv_scale(const float *w, const double *scal, float *s, size_t n, cudaStream_t st);
 void kernel_attrs_fft();
 void launch_dual_fft_batched(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
                              const float *mu_in, float *mu_out, float *mu_bar, const float *winv, int lowdose,

@@ -349,6 +349,182 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
     }
 }
 
+// =====================================================================
+// The shift-variant preconditioner D = T_lo + S T_hi S (S = diag(s),
+// s_i = sqrt(kappa w_i)): T_lo and T_hi are the convolutions with the taps
+// of the low and high bands H_lo + H_hi = H of Eq. 24, so that D tends to
+// the pure ramp of Eq. 32 at low frequency and to W at high frequency, the
+// two limits of D = (tau A A^T + W^-1)^-1 (Eq. 23).  One view y per block:
+// the real sequences y and S y travel as one complex sequence,
+//     Z = FFT(y + i S y),  F y = (Z + conj Z(-k)) / 2,  F(S y) = (Z - conj Z(-k)) / 2i,
+// and one inverse transform of
+//     Y = H_lo F y + i H_hi F(S y) = hs Z + hd conj Z(-k),   hs, hd = (H_lo +- H_hi) / 2,
+// returns u + i v with u = P T_lo y and v = P T_hi S y (both real, as
+// H_lo and H_hi are Hermitian), so D y = (u + s v) / P.
+// =====================================================================
+__global__ void k_sv_combine(float2 *__restrict__ hs, float2 *__restrict__ hd, int P)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const float2 lo = hs[k], hi = hd[k];
+    hs[k] = make_float2(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y));
+    hd[k] = make_float2(0.5f * (lo.x - hi.x), 0.5f * (lo.y - hi.y));
+}
+
+void launch_sv_hhat(const Geometry *g, const float *taps_lo, const float *taps_hi, int half, float2 *hs, float2 *hd,
+                    cudaStream_t st)
+{
+    launch_hhat(g, taps_lo, half, hs, st);
+    launch_hhat(g, taps_hi, half, hd, st);
+    counted();
+    k_sv_combine<<<(g->n_fft + 255) / 256, 256, 0, st>>>(hs, hd, g->n_fft);
+}
+
+// Y(k) = hs(k) Z(k) + hd(k) conj Z(P-k), in place: each thread takes the pair (k, P-k)
+__device__ __forceinline__ void sv_spectrum(float2 *f, const float2 *__restrict__ hs, const float2 *__restrict__ hd,
+                                            int P)
+{
+    for (int k = threadIdx.x; k <= P / 2; k += blockDim.x) {
+        const int k2 = (P - k) & (P - 1);
+        const float2 z1 = f[fp(k)], z2 = f[fp(k2)];
+        const float2 c1 = make_float2(z1.x, -z1.y), c2 = make_float2(z2.x, -z2.y);
+        f[fp(k)] = cadd(cmul(hs[k], z1), cmul(hd[k], c2));
+        if (k2 != k) f[fp(k2)] = cadd(cmul(hs[k2], z2), cmul(hd[k2], c1));
+    }
+}
+
+// out = post .* D(pre .* in) * sc, sc = 1 (mode 0) or -sigma (mode 1), D the
+// shift-variant form; one block per view v = blockIdx.x of image blockIdx.y.
+// BANDS: the input is A x as the projector's nb band partial sums.
+template <bool BANDS>
+__global__ void __launch_bounds__(FFT_T)
+k_filter_sv(const float2 *__restrict__ hs, const float2 *__restrict__ hd, const float *__restrict__ sv,
+            const float *__restrict__ in, float *__restrict__ out, const float *__restrict__ pre,
+            const float *__restrict__ post, int mode, const double *__restrict__ scal, int V, int B, int P,
+            const float2 *__restrict__ tw, int nb, const ViewP *__restrict__ views)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *b = fsm + fft_elems(P);
+    const int v = blockIdx.x;
+    const size_t VB = (size_t)V * B;
+    const size_t o = (size_t)blockIdx.y * VB + (size_t)v * B;
+    const float *s = sv + (size_t)v * B;   // the weights, so S, are one slice's
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float y = 0.0f, sy = 0.0f;
+        if (i < B) {
+            if (BANDS) {
+                const float *pp = in + (size_t)blockIdx.y * nb * VB + (size_t)v * B + i;
+                float acc = 0.0f;
+                for (int q = 0; q < nb; ++q) acc += pp[q * VB];
+                y = acc * views[v].scale;
+            } else {
+                y = in[o + i];
+                if (pre) y *= pre[o + i];
+            }
+            sy = s[i] * y;
+        }
+        a[fp(i)] = make_float2(y, sy);
+    }
+    float2 *f = fft_block(a, b, P, tw, false);
+    sv_spectrum(f, hs, hd, P);
+    float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
+    const float sc = ((mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f) / (float)P;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        const float2 uv = res[fp(i)];
+        float y = fmaf(s[i], uv.y, uv.x) * sc;
+        if (post) y *= post[o + i];
+        out[o + i] = y;
+    }
+}
+
+void launch_filter_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *in,
+                      float *out, const float *pre, const float *post, int mode, const double *scal, int batch,
+                      cudaStream_t st)
+{
+    counted();
+    k_filter_sv<false><<<dim3(g->n_views, batch), FFT_T, sizeof(float2) * 2 * fft_elems(g->n_fft), st>>>(
+        hs, hd, sv, in, out, pre, post, mode, scal, g->n_views, g->n_bins, g->n_fft, g->d_tw, 0, nullptr);
+}
+
+void launch_filter_sv_bands(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv,
+                            const float *partial, float *out, int batch, cudaStream_t st)
+{
+    counted();
+    k_filter_sv<true><<<dim3(g->n_views, batch), FFT_T, sizeof(float2) * 2 * fft_elems(g->n_fft), st>>>(
+        hs, hd, sv, partial, out, nullptr, nullptr, 0, nullptr, g->n_views, g->n_bins, g->n_fft, g->d_tw,
+        proj_bands(g->n), g->d_views);
+}
+
+// Fused Step 3 and next Step 1 of Algorithm 1 with the shift-variant D, one
+// view per block (the form of k_dual_fft):
+//   r = scale_v sum_b partial[b] - b - winv mu;  mu' = mu + sigma D r;
+//   mubar = 2 mu' - mu - sigma D (winv .* (mu' - mu)).
+__global__ void __launch_bounds__(FFT_T)
+k_dual_sv(const float2 *__restrict__ hs, const float2 *__restrict__ hd, const float *__restrict__ sv,
+          const float *__restrict__ partial, int nb, const float *__restrict__ b, float *mu,
+          float *__restrict__ mu_bar, const float *__restrict__ winv, const ViewP *__restrict__ views,
+          const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
+{
+    extern __shared__ float2 fsm[];
+    float2 *a = fsm, *bb = fsm + fft_elems(P);
+    float *m_old = reinterpret_cast<float *>(fsm + 2 * fft_elems(P));   // B
+    float *m_new = m_old + B;                                          // B
+    const int v = blockIdx.x;
+    const size_t VB = (size_t)V * B, o = (size_t)v * B;
+    const float *s = sv + o;
+    const float sc = views[v].scale;
+    const float sigma = fscal(scal, F_SIGMA);
+    const float invP = 1.0f / (float)P;
+
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float r = 0.0f, sr = 0.0f;
+        if (i < B) {
+            const float *pp = partial + o + i;
+            float acc = 0.0f;
+            for (int q = 0; q < nb; ++q) acc += pp[q * VB];
+            const float m0 = mu[o + i];
+            m_old[i] = m0;
+            r = acc * sc - b[o + i] - winv[o + i] * m0;
+            sr = s[i] * r;
+        }
+        a[fp(i)] = make_float2(r, sr);
+    }
+    float2 *f = fft_block(a, bb, P, tw, false);
+    sv_spectrum(f, hs, hd, P);
+    float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
+    float2 *other = res == a ? bb : a;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float d = 0.0f, sd = 0.0f;
+        if (i < B) {
+            const float2 uv = res[fp(i)];
+            const float n0 = m_old[i] + sigma * (fmaf(s[i], uv.y, uv.x) * invP);
+            m_new[i] = n0;
+            d = winv[o + i] * (n0 - m_old[i]);
+            sd = s[i] * d;
+        }
+        other[fp(i)] = make_float2(d, sd);
+    }
+    f = fft_block(other, res, P, tw, false);
+    sv_spectrum(f, hs, hd, P);
+    res = fft_block(f, f == a ? bb : a, P, tw, true);
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        const float2 uv = res[fp(i)];
+        const float n0 = m_new[i];
+        mu[o + i] = n0;
+        mu_bar[o + i] = 2.0f * n0 - m_old[i] - sigma * (fmaf(s[i], uv.y, uv.x) * invP);
+    }
+}
+
+void launch_dual_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *partial,
+                    const float *b, float *mu, float *mu_bar, const float *winv, const double *scal,
+                    cudaStream_t st)
+{
+    counted();
+    const size_t smem = sizeof(float2) * 2 * fft_elems(g->n_fft) + sizeof(float) * 2 * g->n_bins;
+    k_dual_sv<<<g->n_views, FFT_T, smem, st>>>(hs, hd, sv, partial, proj_bands(g->n), b, mu, mu_bar, winv,
+                                               g->d_views, scal, g->n_views, g->n_bins, g->n_fft, g->d_tw);
+}
+
 size_t dual_fft_smem(const Geometry *g) { return sizeof(float2) * 2 * fft_elems(g->n_fft) + sizeof(float) * 4 * g->n_bins; }
 
 void launch_dual_fft(const Geometry *g, const float2 *hhat, const float *partial, const float *b, float *mu,
@@ -486,6 +662,9 @@ void kernel_attrs_fft()
     cudaFuncSetAttribute(k_filter_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_dual_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_dual_bwd_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_filter_sv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_filter_sv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_dual_sv, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
 }
 
 }  // namespace ctpd

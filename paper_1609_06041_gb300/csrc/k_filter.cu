@@ -189,7 +189,9 @@ void kernel_attrs_filter()
 // mirrored into taps[B-1 +- k].  One warp per k; the cosine argument is
 // reduced exactly in integers ((j*k) mod P) and evaluated with cospif;
 // compensated summation keeps the float sum at full precision.
-// H(w) = |w|/(2 m tau + kappa |w|) (mode 0, Eq. 24) or |w|/(2 m tau) (mode 1, Eq. 32).
+// H(w) = |w|/(2 m tau + kappa |w|) (mode 0, Eq. 24) or |w|/(2 m tau) (mode 1, Eq. 32);
+// modes 2 and 3 split mode 0 into the low band 2 m tau |w| / (2 m tau + kappa |w|)^2
+// and the high band kappa w^2 / (2 m tau + kappa |w|)^2 of the shift-variant D.
 __global__ void k_taps(int mode, int m, int P, int B, const double *__restrict__ scal,
                        float tau_h, float kappa_h, float *__restrict__ taps)
 {
@@ -204,7 +206,11 @@ __global__ void k_taps(int mode, int m, int P, int B, const double *__restrict__
     for (int j = lane; j < P; j += 32) {
         const int jj = j < P - j ? j : P - j;
         const float w = 6.28318530717958647692f * (float)jj / (float)P;
-        const float Hj = (mode == 0) ? w / (two_m_tau + kappa * w) : w / two_m_tau;
+        const float den = two_m_tau + kappa * w;
+        // modes 2, 3: the low and high bands of mode 0 (shift-variant preconditioner)
+        const float Hj = (mode == 0) ? w / den
+                       : (mode == 1) ? w / two_m_tau
+                       : (mode == 2) ? two_m_tau * w / (den * den) : kappa * w * w / (den * den);
         const int ph = (int)(((long long)j * k) % P);
         const float term = Hj * cospif(2.0f * (float)ph / (float)P);
         const float y = term - comp;

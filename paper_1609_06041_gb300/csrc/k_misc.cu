@@ -48,6 +48,20 @@ void launch_sqrt(const float *a, float *out, size_t n, cudaStream_t st)
     k_sqrt<<<grid_for(n, 256), 256, 0, st>>>(a, out, n);
 }
 
+// s = sqrt(kappa w): the diagonal of the shift-variant preconditioner
+__global__ void k_sv_scale(const float *w, const double *scal, float *s, size_t n)
+{
+    const float kappa = (float)scal[S_KAPPA];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        s[i] = sqrtf(kappa * w[i]);
+}
+
+void launch_sv_scale(const float *w, const double *scal, float *s, size_t n, cudaStream_t st)
+{
+    counted();
+    k_sv_scale<<<grid_for(n, 256), 256, 0, st>>>(w, scal, s, n);
+}
+
 // out = in * s (sqrt_s: in * sqrt(s))
 __global__ void k_scale_by(const float *in, const float *s, int sqrt_s, float *out, size_t n)
 {

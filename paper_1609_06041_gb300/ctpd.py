@@ -28,6 +28,7 @@ _d = ctypes.c_double
 
 CT_OK, CT_ERR_ARG, CT_ERR_CUDA, CT_ERR_OOM, CT_ERR_TIMEOUT, CT_ERR_NONFINITE = range(6)
 CT_LOWDOSE, CT_FEWVIEW = 0, 1
+CT_TAPS_LOW_BAND, CT_TAPS_HIGH_BAND = 2, 3   # ct_ramp_taps: bands of the shift-variant D
 
 
 class ct_pdtv_params(ctypes.Structure):
@@ -60,6 +61,7 @@ EXPORTS = {
     "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
     "ct_ramp_filter": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
+    "ct_ramp_filter_split": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_filter_noalloc": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
@@ -216,7 +218,8 @@ def ct_backproject(g: Geometry, sino: torch.Tensor, out: torch.Tensor | None = N
 
 
 def ct_ramp_taps(g: Geometry, mode: int, tau: float, kappa: float = 0.0, out=None) -> torch.Tensor:
-    """Taps of D (Eq. 24 / Eq. 32), 2B-1 values centred at B-1."""
+    """Taps of D (Eq. 24 / Eq. 32; modes CT_TAPS_LOW_BAND / CT_TAPS_HIGH_BAND the
+    bands of the shift-variant D), 2B-1 values centred at B-1."""
     if out is None:
         out = torch.empty(2 * g.n_bins - 1, device="cuda", dtype=torch.float32)
     _check(_lib.ct_ramp_taps(g.handle, int(mode), float(tau), float(kappa), _dev(out, "taps"), _stream()))
@@ -234,6 +237,22 @@ def ct_ramp_filter(g: Geometry, taps: torch.Tensor, sino: torch.Tensor, out=None
         out = torch.empty_like(sino)
     po = _dev(out, "out", (g.n_views, g.n_bins))
     _check(_lib.ct_ramp_filter(g.handle, pt, half, ps, po, _batch(sino, 2), _stream()))
+    return out
+
+
+def ct_ramp_filter_split(g: Geometry, taps_lo: torch.Tensor, taps_hi: torch.Tensor, s: torch.Tensor,
+                         sino: torch.Tensor, out=None) -> torch.Tensor:
+    """The shift-variant preconditioner: out = T_lo sino + s * T_hi (s * sino)."""
+    if taps_lo.numel() % 2 != 1 or taps_hi.numel() != taps_lo.numel():
+        raise ValueError("taps_lo, taps_hi must have the same odd length 2*half-1")
+    half = (taps_lo.numel() + 1) // 2
+    pl, ph = _dev(taps_lo, "taps_lo"), _dev(taps_hi, "taps_hi")
+    pv = _dev(s, "s", (g.n_views, g.n_bins))
+    ps = _dev(sino, "sino", (g.n_views, g.n_bins))
+    if out is None:
+        out = torch.empty_like(sino)
+    po = _dev(out, "out", (g.n_views, g.n_bins))
+    _check(_lib.ct_ramp_filter_split(g.handle, pl, ph, half, pv, ps, po, _batch(sino, 2), _stream()))
     return out
 
 
