@@ -351,21 +351,25 @@ def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3):
 
 
 def measure_convergence(P):
-    """The ramp preconditioner against plain Chambolle-Pock (D = I) on the
-    same GPU kernels: RMSE to the phantom, data residual and distance to the
-    preconditioned 1000-iteration iterate x* after 1 .. 1000 iterations, for
-    the low-dose workload (512^2, 720 views, I0 5e3, beta 0.005) and the
-    few-view one (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2),
-    plus the few-view solve rates at 100 iterations."""
+    """Preconditioners on the same GPU kernels: the ramp D of Eq. 24 / Eq. 32,
+    plain Chambolle-Pock (D = I) and, for low-dose, the shift-variant split D
+    (precond 2).  RMSE to the phantom, data residual and distance to the
+    1000-iteration iterate x* of the Eq. 24 run after 1 .. 1000 iterations,
+    for three workloads: low-dose at the bench size (512^2, 720 views, I0
+    5e3, beta 0.005), the same with the phantom's attenuation times 5 (a
+    dense object: counts spread over two decades), and few-view (512^2,
+    32 views, 736 bins, noiseless b = A v, Alg. 2); plus whole-solve rates
+    (iterations/s, setup included, 30 iterations low-dose, 100 few-view)."""
     import torch
     out = {}
-    cases = [("lowdose", WORK["views"], 0, WORK["beta"]), ("fewview", 32, 1, 0.0)]
-    for name, V, mode, beta in cases:
+    cases = [("lowdose", WORK["views"], 0, WORK["beta"], 1.0), ("lowdose_dense", WORK["views"], 0, WORK["beta"], 5.0),
+             ("fewview", 32, 1, 0.0, 1.0)]
+    for name, V, mode, beta, dense in cases:
         N, B = WORK["n"], WORK["bins"]
         g = P.Geometry(N, V, B)
         g.autotune()
         v_true = synth.ellipse_phantom(N, WORK["ellipses"], 0)
-        scale = (2.0 / N) if mode == 0 else 1.0
+        scale = (2.0 / N) * dense if mode == 0 else 1.0
         p = P.ct_project(g, torch.from_numpy((v_true * scale).astype(np.float32)).cuda())
         if mode == 0:
             bb, ww = synth.poisson_data(p.cpu().numpy(), WORK["i0"], 100)
@@ -374,22 +378,25 @@ def measure_convergence(P):
         else:
             b, w = p, None
         vt = torch.from_numpy(v_true).cuda()
-        runs = {}
-        for label, pc in (("preconditioned", 1), ("plain_cp", 0)):
-            runs[label] = _trajectory(P, g, b, w, mode, pc, beta, vt, scale)
+        arms = (("preconditioned", 1), ("shift_variant", 2), ("plain_cp", 0)) if mode == 0 else \
+            (("preconditioned", 1), ("plain_cp", 0))
+        runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale) for label, pc in arms}
         xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
         xn = float(torch.linalg.norm(xstar))
         entry = {"workload": f"512^2, {V} views, {B} bins, " +
-                             ("Poisson I0 5e3, beta 0.005, Alg. 1" if mode == 0 else "noiseless b = A v, Alg. 2"),
+                             (f"Poisson I0 5e3, attenuation x{dense}, beta 0.005, Alg. 1" if mode == 0
+                              else "noiseless b = A v, Alg. 2"),
                  "checkpoints": list(CHECKPOINTS)}
+        if mode == 0:
+            entry["weight_range"] = [float(w.min()), float(w.max())]
         for label, (xs, rmse, resid) in runs.items():
             entry[label] = {"rmse": [rmse[k] for k in CHECKPOINTS],
                             "rel_residual": [resid[k] for k in CHECKPOINTS],
                             "rel_dist_to_xstar": [float(torch.linalg.norm(xs[k] - xstar)) / xn
                                                   for k in CHECKPOINTS]}
-        if mode == 1:
-            entry["iterations_per_s_100"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, 100)
-                                             for label, pc in (("preconditioned", 1), ("plain_cp", 0))}
+        iters = 100 if mode == 1 else WORK["iters"]
+        entry[f"iterations_per_s_{iters}"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, iters)
+                                              for label, pc in arms}
         out[name] = entry
     return out
 
