@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from the full ncu capture in profiles/kernels_lowdose_512_v720_b736.md
 # (update together with the kernels; None when no capture of the current kernel exists)
-TRAFFIC_BYTES = {"A": 1.098240e6, "AT": 2.027776e6}
+TRAFFIC_BYTES = {"A": 1.098240e6, "AT": 2.022912e6}
 
 
 def dist_info():
