@@ -69,10 +69,11 @@ def _load():
                 "orc_div": [_i, _p, _p, _p],
                 "orc_tv": [_i, _p],
                 "orc_tv_prox": [_i, _p, _d, _i, _p, _p, _p],
+                "orc_tv_prox_fgp": [_i, _p, _d, _i, _p, _p, _p],
                 "orc_cost": [_i, _i, _i, _p, _p, _p, _d, _p],
                 "orc_residual": [_i, _i, _i, _p, _p, _p],
                 "orc_apply_d": [_i, _i, _p, _p, _i, _p, _p, _p],
-                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i,
+                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i, _i,
                              _i, _i, _p, _p, _p, _p, _p, _p],
                 "orc_power_norm": [_i, _i, _i, _i, _p, _p, _p, _p, _i, _p, _i],
                 "orc_cp_reference": [_i, _i, _i, _p, _p, _p, _i, _d, _d, _d, _i, _p],
@@ -192,15 +193,17 @@ def tv(x):
     return float(_load().orc_tv(x.shape[-1], _ptr(x)))
 
 
-def tv_prox(z, lam, n_tv, px=None, py=None):
-    """prox of lam*TV + i(x>=0) by n_tv projected-gradient dual steps.
-    Returns (x, px, py); px, py are the warm-started dual fields."""
+def tv_prox(z, lam, n_tv, px=None, py=None, fgp=False):
+    """prox of lam*TV + i(x>=0) by n_tv projected-gradient dual steps (fgp:
+    the fast gradient projection with momentum).  Returns (x, px, py); px,
+    py are the warm-started dual fields."""
     z = _f64(z)
     N = z.shape[-1]
     px = np.zeros_like(z) if px is None else _f64(px).copy()
     py = np.zeros_like(z) if py is None else _f64(py).copy()
     x = np.empty_like(z)
-    _load().orc_tv_prox(N, _ptr(z), float(lam), int(n_tv), _ptr(px), _ptr(py), _ptr(x))
+    fn = _load().orc_tv_prox_fgp if fgp else _load().orc_tv_prox
+    fn(N, _ptr(z), float(lam), int(n_tv), _ptr(px), _ptr(py), _ptr(x))
     return x, px, py
 
 
@@ -232,11 +235,12 @@ class PDState:
 
 
 def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
-         state=None, trace=False, taps_hi=None, s=None):
+         state=None, trace=False, taps_hi=None, s=None, fgp=False):
     """Run `iters` iterations of Algorithm 1 (mode 0) / 2 (mode 1) from
     `state` (fresh zero state if None).  With taps_hi (and s) the
-    preconditioner is the shift-variant D = T_lo + S T_hi S (apply_d).
-    Returns (state, trace or None)."""
+    preconditioner is the shift-variant D = T_lo + S T_hi S (apply_d); with
+    fgp the prox runs the fast gradient projection.  Returns (state, trace
+    or None)."""
     b = _f64(b)
     V, B = b.shape
     w = None if w is None else _f64(w)
@@ -247,7 +251,7 @@ def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
     st = PDState(n, V, B) if state is None else state
     tr = np.empty(iters) if trace else None
     _load().orc_pdtv(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), _ptr(taps), _ptr(th), _ptr(sv), half,
-                     int(mode), float(beta), float(tau), float(sigma), int(n_tv),
+                     int(mode), float(beta), float(tau), float(sigma), int(n_tv), int(bool(fgp)),
                      int(st.k), int(iters), _ptr(st.x), _ptr(st.mu), _ptr(st.mu_prev),
                      _ptr(st.px), _ptr(st.py), _ptr(tr))
     st.k += iters

@@ -327,6 +327,63 @@ void orc_tv_prox(int N, const double *z, double lam, int n_tv,
     free(gy);
 }
 
+/* The same prox by the fast gradient projection (FGP) of Beck and      */
+/* Teboulle (2009) on the dual field: the projected-gradient step above */
+/* taken at an extrapolated point r, with the momentum of Nesterov:     */
+/*   r_1 = p_0, t_1 = 1;  for k = 1..n_tv:                              */
+/*     p_k = Pi(r_k + grad max(0, z + lam div r_k) / (8 lam)),          */
+/*     t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,                           */
+/*     r_{k+1} = p_k + ((t_k - 1) / t_{k+1}) (p_k - p_{k-1});           */
+/*   x = max(0, z + lam div p_n).                                       */
+/* p_0 (px, py on entry) warm-starts it; px, py receive p_n.            */
+void orc_tv_prox_fgp(int N, const double *z, double lam, int n_tv,
+                     double *px, double *py, double *x)
+{
+    size_t J = (size_t)N * N;
+    if (lam <= 0.0) {
+        for (size_t j = 0; j < J; ++j) x[j] = z[j] > 0.0 ? z[j] : 0.0;
+        return;
+    }
+    double *dv = malloc(sizeof(double) * J);
+    double *gx = malloc(sizeof(double) * J), *gy = malloc(sizeof(double) * J);
+    double *rx = malloc(sizeof(double) * J), *ry = malloc(sizeof(double) * J);
+    memcpy(rx, px, sizeof(double) * J);
+    memcpy(ry, py, sizeof(double) * J);
+    double t = 1.0;
+    for (int it = 0; it < n_tv; ++it) {
+        orc_div(N, rx, ry, dv);
+        for (size_t j = 0; j < J; ++j) {
+            double v = z[j] + lam * dv[j];
+            x[j] = v > 0.0 ? v : 0.0;
+        }
+        orc_grad(N, x, gx, gy);
+        double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        double th = (t - 1.0) / t1;
+        for (size_t j = 0; j < J; ++j) {
+            double qx = rx[j] + gx[j] / (8.0 * lam);
+            double qy = ry[j] + gy[j] / (8.0 * lam);
+            double nrm = sqrt(qx * qx + qy * qy);
+            double s = nrm > 1.0 ? nrm : 1.0;
+            double nx = qx / s, ny = qy / s;      /* p_k */
+            rx[j] = nx + th * (nx - px[j]);       /* r_{k+1}, px = p_{k-1} */
+            ry[j] = ny + th * (ny - py[j]);
+            px[j] = nx;
+            py[j] = ny;
+        }
+        t = t1;
+    }
+    orc_div(N, px, py, dv);
+    for (size_t j = 0; j < J; ++j) {
+        double v = z[j] + lam * dv[j];
+        x[j] = v > 0.0 ? v : 0.0;
+    }
+    free(dv);
+    free(gx);
+    free(gy);
+    free(rx);
+    free(ry);
+}
+
 /* ------------------------------------------------------------------ */
 /* Algorithm 1 (low-dose, Eqs. 18-20), Algorithm 1' (beta = 0) and     */
 /* Algorithm 2 (few-view, Eqs. 29-31), in the order of their boxes:    */
@@ -340,6 +397,7 @@ void orc_tv_prox(int N, const double *z, double lam, int n_tv,
 /* filter with the given taps (taps = {1}, half = 1 gives D = I, the   */
 /* unpreconditioned iteration).  Iterations k0 .. k0+iters-1 run from  */
 /* the state (x, mu, mu_prev, px, py); k0 = 0 starts from x = mu = p = 0. */
+/* fgp: the prox by orc_tv_prox_fgp instead of orc_tv_prox.            */
 /* trace[i] (optional) receives f(x) (Eq. 1) for mode 0 or ||Ax-b||    */
 /* for mode 1 after iteration i.                                       */
 /* ------------------------------------------------------------------ */
@@ -374,7 +432,7 @@ double orc_residual(int N, int V, int B, const double *angles,
 void orc_pdtv(int N, int V, int B, const double *angles,
               const double *b, const double *w,
               const double *taps, const double *taps_hi, const double *sv, int half, int mode,
-              double beta, double tau, double sigma, int n_tv,
+              double beta, double tau, double sigma, int n_tv, int fgp,
               int k0, int iters,
               double *x, double *mu, double *mu_prev, double *px, double *py,
               double *trace)
@@ -408,7 +466,8 @@ void orc_pdtv(int N, int V, int B, const double *angles,
         /* Step 2: primal update through the prox of tau*g */
         orc_backproject(N, V, B, angles, mubar, z);
         for (size_t j = 0; j < J; ++j) z[j] = x[j] - tau * z[j];
-        orc_tv_prox(N, z, lam, n_tv, px, py, x);
+        if (fgp) orc_tv_prox_fgp(N, z, lam, n_tv, px, py, x);
+        else orc_tv_prox(N, z, lam, n_tv, px, py, x);
         /* Step 3: dual update */
         orc_project(N, V, B, angles, x, t2);
         for (size_t i = 0; i < I; ++i) {

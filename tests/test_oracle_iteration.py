@@ -149,3 +149,21 @@ def test_power_norm_matches_matrix_norm():
     Mw = np.diag(w ** -0.5) @ DD @ np.diag(w ** -0.5)
     got = O.power_norm(1, N, V, B, taps=taps, w=w.reshape(V, B), iters=2000)
     assert got == pytest.approx(np.linalg.norm(Mw, 2), rel=1e-6)
+
+
+def test_fgp_prox_keeps_the_limit():
+    # the prox by fast gradient projection (warm-started, momentum restarted
+    # at every outer iteration) reaches the same minimiser of Eq. 1
+    N, V, B = 12, 18, 17
+    rng = np.random.default_rng(2)
+    xt = synth.ellipse_phantom(N, 3, 1)
+    b = O.project(xt, V, B) + 0.2 * rng.standard_normal((V, B))
+    w = rng.uniform(0.5, 2.0, (V, B))
+    beta = 0.3
+    kappa = float(np.mean(1 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    sigma, _, _ = O.step_sizes(0, N, V, B, taps, w, tau)
+    xg = O.pdtv(b, w, taps, 0, beta, tau, sigma, 10, 3000, N)[0].x
+    xf = O.pdtv(b, w, taps, 0, beta, tau, sigma, 10, 3000, N, fgp=True)[0].x
+    assert np.linalg.norm(xf - xg) / np.linalg.norm(xg) < 1e-6

@@ -81,3 +81,61 @@ def test_prox_special_cases():
     z = synth.random_image(6, 4)
     x, _, _ = O.tv_prox(z, 0.0, 10)            # lam = 0: projection onto x >= 0
     np.testing.assert_array_equal(x, np.maximum(z, 0))
+
+
+# ---- the fast gradient projection (FGP) form of the same prox ----
+
+@pytest.mark.parametrize("a,b,lam", [(2.0, 1.2, 0.1), (1.0, 3.0, 0.25), (2.0, 1.9, 0.1)])
+def test_fgp_two_level_closed_form(a, b, lam):
+    z = np.array([[a, b], [a, b]])
+    x, _, _ = O.tv_prox(z, lam, 2000, fgp=True)
+    if abs(a - b) > 2 * lam:
+        s = np.sign(a - b)
+        expect = [a - lam * s, b + lam * s]
+    else:
+        expect = [(a + b) / 2] * 2
+    np.testing.assert_allclose(x, [expect, expect], atol=1e-9)
+
+
+def test_fgp_duality_gap_certificate_and_same_prox():
+    rng = np.random.default_rng(0)
+    z = rng.standard_normal((8, 8))
+    lam = 0.3
+    x, px, py = O.tv_prox(z, lam, 4000, fgp=True)
+    assert np.sqrt(px ** 2 + py ** 2).max() <= 1 + 1e-12
+    gx, gy = O.grad(x)
+    gap = lam * (O.tv(x) - float((px * gx + py * gy).sum()))
+    assert -1e-12 <= gap < 1e-9
+    xg, _, _ = O.tv_prox(z, lam, 20000)
+    np.testing.assert_allclose(x, xg, atol=1e-7)
+
+
+def test_fgp_first_step_is_a_gradient_projection_step():
+    # t_1 = 1: the first extrapolation weight is 0, so one FGP step from any
+    # warm start is one step of the plain projected gradient
+    z = synth.random_image(9, 5)
+    p0x, p0y = 0.3 * synth.random_image(9, 6), 0.3 * synth.random_image(9, 7)
+    a = O.tv_prox(z, 0.2, 1, p0x, p0y, fgp=True)
+    b = O.tv_prox(z, 0.2, 1, p0x, p0y)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_fgp_special_cases():
+    z = np.full((5, 5), -0.3)
+    assert (O.tv_prox(z, 0.2, 10, fgp=True)[0] == 0).all()
+    z = np.full((5, 5), 0.7)
+    assert (O.tv_prox(z, 0.2, 10, fgp=True)[0] == 0.7).all()
+    z = synth.random_image(6, 4)
+    np.testing.assert_array_equal(O.tv_prox(z, 0.0, 10, fgp=True)[0], np.maximum(z, 0))
+
+
+def test_fgp_approaches_the_prox_faster():
+    # the dual objective converges as O(1/k^2) with momentum against O(1/k)
+    z = synth.ellipse_phantom(24, 5, 2) + 0.3 * synth.random_image(24, 8)
+    lam = 0.4
+    xs, _, _ = O.tv_prox(z, lam, 40000)
+    for k in (10, 30):
+        d_gp = np.linalg.norm(O.tv_prox(z, lam, k)[0] - xs)
+        d_fgp = np.linalg.norm(O.tv_prox(z, lam, k, fgp=True)[0] - xs)
+        assert d_fgp < 0.7 * d_gp
