@@ -437,6 +437,8 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     if (mode == CT_LOWDOSE && !(prm->beta >= 0.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: beta must be >= 0");
     if (prm->resume && !workspace) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
     if (prm->precond < 0 || prm->precond > 2) return fail(CT_ERR_ARG, "ct_pdtv_solve: precond must be 0, 1 or 2");
+    if (prm->tv_accel != 0 && (prm->tv_accel != 1 || prm->tv_iters > tv_max_steps()))
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: tv_accel must be 0 or 1 (1 needs tv_iters <= %d)", tv_max_steps());
     if (prm->precond == 2 && (mode != CT_LOWDOSE || !fft_supported(g)))
         return fail(CT_ERR_ARG, "ct_pdtv_solve: the shift-variant preconditioner needs CT_LOWDOSE and n_bins <= 4096");
     if (!aligned16(b) || !aligned16(x_out) || (w && !aligned16(w)) || (workspace && !aligned16(workspace)))
@@ -586,7 +588,8 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         for (int c = chunks; c > 0; --c) {
             const int steps = (left + c - 1) / c;
             left -= steps;
-            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, g->n_sm, g->tune_tv, steps, c == 1, scal, st);
+            launch_tv(z, pbuf[cur], pbuf[cur ^ 1], x_out, g->n, g->n_sm, g->tune_tv, steps, c == 1, scal, st,
+                      prm->tv_accel == 1);
             cur ^= 1;
         }
         // Step 3: A x^{k+1} (band partial sums); the dual update forms the

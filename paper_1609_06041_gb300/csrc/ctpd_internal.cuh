@@ -227,7 +227,8 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
 // device's SM count) and min_rows (fewest interior rows per tile, 0: the
 // default) size the tiles.
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int n_sm, int min_rows, int steps, int final, const double *scal, cudaStream_t st);
+               int n, int n_sm, int min_rows, int steps, int final, const double *scal, cudaStream_t st,
+               bool fgp = false);
 int tv_max_steps();
 
 // Small helpers

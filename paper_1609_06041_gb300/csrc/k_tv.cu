@@ -58,6 +58,12 @@ static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr)
     return t;
 }
 
+// FGP: the fast gradient projection (Beck and Teboulle): each step is the
+// projected-gradient step taken at r = p + theta (p - p_prev) instead of p,
+// with theta_k = (t_k - 1) / t_{k+1}, t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+// (momentum restarted at every call).  Each cell keeps p_prev as well, and
+// the field published for the divergence is r_y (p_y after the last step).
+template <bool FGP>
 __global__ void __launch_bounds__(TV_THREADS, 1)
 k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
      float *__restrict__ x, int N, int steps, int final_, int tc, int tr, const double *__restrict__ scal)
@@ -83,6 +89,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
         pub_y[i] = make_float2(0.0f, 0.0f);
     }
     float zr[TV_J][2], pxr[TV_J][2], pyr[TV_J][2], xr[TV_J][2];
+    float pxo[TV_J][2], pyo[TV_J][2];   // FGP: p of the previous step
     unsigned rowx = 0, rowy = 0;   // bit j: row in the image / row with a y difference
 #pragma unroll
     for (int j = 0; j < TV_J; ++j) {
@@ -103,6 +110,13 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
             if (ryd && cy1) pyr[j][1] = p_in[NN + gi + 1];
         }
     }
+#pragma unroll
+    for (int j = 0; j < TV_J; ++j) {
+        pxo[j][0] = pxr[j][0];
+        pxo[j][1] = pxr[j][1];
+        pyo[j][0] = pyr[j][0];
+        pyo[j][1] = pyr[j][1];
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < TV_J; ++j) {
@@ -112,23 +126,32 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     __syncthreads();
 
     if (lam > 0.0f) {
+        float t = 1.0f, th = 0.0f;   // FGP: t_k and theta_{k-1} (theta_0 = 0)
         for (int it = 0; it < steps; ++it) {
-            // x = max(0, z + lam div p)
+            // x = max(0, z + lam div r), r = p (GP) or p + theta (p - p_prev) (FGP)
 #pragma unroll
             for (int j = 0; j < TV_J; ++j) {
                 const int li = w + TV_WARPS * j;
                 if (li < Sr) {
-                    const float2 pa = pub_y[li * 32 + lane];   // p_y of row li - 1
-                    float pl = __shfl_up_sync(FULL, pxr[j][1], 1);
+                    const float2 pa = pub_y[li * 32 + lane];   // r_y of row li - 1
+                    const float rx0 = FGP ? fmaf(th, pxr[j][0] - pxo[j][0], pxr[j][0]) : pxr[j][0];
+                    const float rx1 = FGP ? fmaf(th, pxr[j][1] - pxo[j][1], pxr[j][1]) : pxr[j][1];
+                    const float ry0 = FGP ? fmaf(th, pyr[j][0] - pyo[j][0], pyr[j][0]) : pyr[j][0];
+                    const float ry1 = FGP ? fmaf(th, pyr[j][1] - pyo[j][1], pyr[j][1]) : pyr[j][1];
+                    float pl = __shfl_up_sync(FULL, rx1, 1);
                     if (lane == 0) pl = 0.0f;
-                    const float d0 = (pxr[j][0] - pl) + (pyr[j][0] - pa.x);
-                    const float d1 = (pxr[j][1] - pxr[j][0]) + (pyr[j][1] - pa.y);
+                    const float d0 = (rx0 - pl) + (ry0 - pa.x);
+                    const float d1 = (rx1 - rx0) + (ry1 - pa.y);
                     xr[j][0] = fmaxf(0.0f, fmaf(lam, d0, zr[j][0]));
                     xr[j][1] = fmaxf(0.0f, fmaf(lam, d1, zr[j][1]));
                     pub_x[(li + 1) * 32 + lane] = make_float2(xr[j][0], xr[j][1]);
                 }
             }
             __syncthreads();
+            // FGP: theta_k for the next extrapolation
+            const float t1 = FGP ? 0.5f * (1.0f + sqrtf(fmaf(4.0f * t, t, 1.0f))) : 1.0f;
+            const float thn = FGP ? (t - 1.0f) / t1 : 0.0f;
+            const bool last = it + 1 == steps;
             // p = Pi(p + grad x / (8 lam)), Pi(q) = q / max(1, |q|)
 #pragma unroll
             for (int j = 0; j < TV_J; ++j) {
@@ -139,20 +162,37 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                     const bool rx = (rowx >> j) & 1u, ry = (rowy >> j) & 1u;
                     const float mx0 = (rx && cx0) ? inv8 : 0.0f, mx1 = (rx && cx1) ? inv8 : 0.0f;
                     const float my0 = (ry && cy0) ? inv8 : 0.0f, my1 = (ry && cy1) ? inv8 : 0.0f;
-                    const float qx0 = fmaf(xr[j][1] - xr[j][0], mx0, pxr[j][0]);
-                    const float qx1 = fmaf(xrt - xr[j][1], mx1, pxr[j][1]);
-                    const float qy0 = fmaf(xb.x - xr[j][0], my0, pyr[j][0]);
-                    const float qy1 = fmaf(xb.y - xr[j][1], my1, pyr[j][1]);
+                    const float rx0 = FGP ? fmaf(th, pxr[j][0] - pxo[j][0], pxr[j][0]) : pxr[j][0];
+                    const float rx1 = FGP ? fmaf(th, pxr[j][1] - pxo[j][1], pxr[j][1]) : pxr[j][1];
+                    const float ry0 = FGP ? fmaf(th, pyr[j][0] - pyo[j][0], pyr[j][0]) : pyr[j][0];
+                    const float ry1 = FGP ? fmaf(th, pyr[j][1] - pyo[j][1], pyr[j][1]) : pyr[j][1];
+                    const float qx0 = fmaf(xr[j][1] - xr[j][0], mx0, rx0);
+                    const float qx1 = fmaf(xrt - xr[j][1], mx1, rx1);
+                    const float qy0 = fmaf(xb.x - xr[j][0], my0, ry0);
+                    const float qy1 = fmaf(xb.y - xr[j][1], my1, ry1);
                     const float s0 = fminf(1.0f, rsqrtf(fmaf(qx0, qx0, qy0 * qy0)));
                     const float s1 = fminf(1.0f, rsqrtf(fmaf(qx1, qx1, qy1 * qy1)));
+                    if (FGP) {
+                        pxo[j][0] = pxr[j][0];
+                        pxo[j][1] = pxr[j][1];
+                        pyo[j][0] = pyr[j][0];
+                        pyo[j][1] = pyr[j][1];
+                    }
                     pxr[j][0] = qx0 * s0;
                     pxr[j][1] = qx1 * s1;
                     pyr[j][0] = qy0 * s0;
                     pyr[j][1] = qy1 * s1;
-                    pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
+                    if (FGP && !last)   // r_y of the next step
+                        pub_y[(li + 1) * 32 + lane] =
+                            make_float2(fmaf(thn, pyr[j][0] - pyo[j][0], pyr[j][0]),
+                                        fmaf(thn, pyr[j][1] - pyo[j][1], pyr[j][1]));
+                    else
+                        pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
                 }
             }
             __syncthreads();
+            t = t1;
+            th = thn;
         }
     }
 
@@ -185,11 +225,14 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 }
 
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int n_sm, int min_rows, int steps, int final_, const double *scal, cudaStream_t st)
+               int n, int n_sm, int min_rows, int steps, int final_, const double *scal, cudaStream_t st, bool fgp)
 {
     const TvTiles t = tv_tiles(n, steps, n_sm, min_rows > 0 ? min_rows : TV_MIN_TR);
     counted();
-    k_tv<<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
+    if (fgp)
+        k_tv<true><<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
+    else
+        k_tv<false><<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
 }
 
 void kernel_attrs_tv() {}

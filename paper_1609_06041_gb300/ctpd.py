@@ -34,7 +34,7 @@ CT_TAPS_LOW_BAND, CT_TAPS_HIGH_BAND = 2, 3   # ct_ramp_taps: bands of the shift-
 class ct_pdtv_params(ctypes.Structure):
     _fields_ = [("mode", _i), ("iters", _i), ("tv_iters", _i), ("precond", _i),
                 ("norm_iters", _i), ("resume", _i), ("beta", _d), ("tau", _d),
-                ("sigma", _d), ("rho", _d)]
+                ("sigma", _d), ("rho", _d), ("tv_accel", _i)]
 
 
 class ct_pdtv_report(ctypes.Structure):
@@ -281,11 +281,12 @@ class PDTVParams:
     tau: float = 0.0
     sigma: float = 0.0
     rho: float = 0.95
+    tv_accel: int = 0
 
     def to_c(self):
         return ct_pdtv_params(int(self.mode), int(self.iters), int(self.tv_iters), int(self.precond),
                               int(self.norm_iters), int(self.resume), float(self.beta),
-                              float(self.tau), float(self.sigma), float(self.rho))
+                              float(self.tau), float(self.sigma), float(self.rho), int(self.tv_accel))
 
 
 def ct_pdtv_workspace_bytes(g: Geometry, params: PDTVParams) -> int:
