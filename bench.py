@@ -310,13 +310,13 @@ def measure_unrolled(P, steps=3):
 CHECKPOINTS = (1, 3, 10, 30, 100, 300, 1000)
 
 
-def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale):
+def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0):
     """Iterates of one solve at CHECKPOINTS (resumed solves continue the
     same iteration exactly): RMSE of x / scale against the phantom v_true
     and the relative data residual |A x - b| / |b|."""
     import torch
     prm = P.PDTVParams(mode=mode, iters=CHECKPOINTS[0], tv_iters=10, precond=precond, beta=beta,
-                       norm_iters=16)
+                       norm_iters=16, tv_accel=tv_accel)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     xs, rmse, resid = {}, {}, {}
@@ -332,10 +332,11 @@ def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale):
     return xs, rmse, resid
 
 
-def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3):
+def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3, tv_accel=0):
     """iterations/s of a whole solve (setup included), CUDA events."""
     import torch
-    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=16)
+    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=16,
+                       tv_accel=tv_accel)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     for _ in range(2):
@@ -351,19 +352,22 @@ def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3):
 
 
 def measure_convergence(P):
-    """Preconditioners on the same GPU kernels: the ramp D of Eq. 24 / Eq. 32,
-    plain Chambolle-Pock (D = I) and, for low-dose, the shift-variant split D
-    (precond 2).  RMSE to the phantom, data residual and distance to the
-    1000-iteration iterate x* of the Eq. 24 run after 1 .. 1000 iterations,
-    for three workloads: low-dose at the bench size (512^2, 720 views, I0
-    5e3, beta 0.005), the same with the phantom's attenuation times 5 (a
-    dense object: counts spread over two decades), and few-view (512^2,
-    32 views, 736 bins, noiseless b = A v, Alg. 2); plus whole-solve rates
-    (iterations/s, setup included, 30 iterations low-dose, 100 few-view)."""
+    """Preconditioners and prox forms on the same GPU kernels: the ramp D of
+    Eq. 24 / Eq. 32 with the projected-gradient prox, the same with the FGP
+    prox (tv_accel 1), plain Chambolle-Pock (D = I) and, for low-dose, the
+    shift-variant split D (precond 2).  RMSE to the phantom, data residual
+    and distance to the 1000-iteration iterate x* of the Eq. 24 run after
+    1 .. 1000 iterations, for four workloads: low-dose at the bench size
+    (512^2, 720 views, I0 5e3, beta 0.005), the same with the phantom's
+    attenuation times 5 (a dense object: counts spread over two decades),
+    the same slice with beta 500 (a TV weight that shapes the image), and
+    few-view (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2); plus
+    whole-solve rates (iterations/s, setup included, 30 iterations
+    low-dose, 100 few-view)."""
     import torch
     out = {}
     cases = [("lowdose", WORK["views"], 0, WORK["beta"], 1.0), ("lowdose_dense", WORK["views"], 0, WORK["beta"], 5.0),
-             ("fewview", 32, 1, 0.0, 1.0)]
+             ("lowdose_tv", WORK["views"], 0, 500.0, 1.0), ("fewview", 32, 1, 0.0, 1.0)]
     for name, V, mode, beta, dense in cases:
         N, B = WORK["n"], WORK["bins"]
         g = P.Geometry(N, V, B)
@@ -378,13 +382,14 @@ def measure_convergence(P):
         else:
             b, w = p, None
         vt = torch.from_numpy(v_true).cuda()
-        arms = (("preconditioned", 1), ("shift_variant", 2), ("plain_cp", 0)) if mode == 0 else \
-            (("preconditioned", 1), ("plain_cp", 0))
-        runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale) for label, pc in arms}
+        arms = [("preconditioned", 1, 0), ("preconditioned_fgp", 1, 1), ("plain_cp", 0, 0)]
+        if mode == 0:
+            arms.insert(2, ("shift_variant", 2, 0))
+        runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale, acc) for label, pc, acc in arms}
         xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
         xn = float(torch.linalg.norm(xstar))
         entry = {"workload": f"512^2, {V} views, {B} bins, " +
-                             (f"Poisson I0 5e3, attenuation x{dense}, beta 0.005, Alg. 1" if mode == 0
+                             (f"Poisson I0 5e3, attenuation x{dense}, beta {beta}, Alg. 1" if mode == 0
                               else "noiseless b = A v, Alg. 2"),
                  "checkpoints": list(CHECKPOINTS)}
         if mode == 0:
@@ -395,8 +400,8 @@ def measure_convergence(P):
                             "rel_dist_to_xstar": [float(torch.linalg.norm(xs[k] - xstar)) / xn
                                                   for k in CHECKPOINTS]}
         iters = 100 if mode == 1 else WORK["iters"]
-        entry[f"iterations_per_s_{iters}"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, iters)
-                                              for label, pc in arms}
+        entry[f"iterations_per_s_{iters}"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, iters, tv_accel=acc)
+                                              for label, pc, acc in arms}
         out[name] = entry
     return out
 
