@@ -224,9 +224,10 @@ typedef struct {
     double sigma;     /* dual step; <= 0: rho * the bound of the Alg. 1 / Alg. 2
                          box from Lanczos estimates of the operator norms     */
     double rho;       /* safety factor for the automatic sigma (0 -> 0.95)    */
-    int tv_accel;     /* 1: the TV prox by fast gradient projection (momentum
-                         on the dual field, restarted at every outer
-                         iteration; tv_iters <= 16); 0: projected gradient  */
+    int tv_accel;     /* prox of Eq. 17: 0 projected gradient on the dual
+                         field; 1 its fast form (Beck-Teboulle FGP: Nesterov
+                         momentum, restarted every outer iteration;
+                         tv_iters <= 16)                                      */
 } ct_pdtv_params;
 
 /* Scalars of a solve, copied to the host at the end when requested. */
