@@ -130,6 +130,67 @@ __device__ float2 *fft_block(float2 *a, float2 *b, int P, const float2 *__restri
     return src;
 }
 
+// fft_block with the work that follows the transform fused into its last
+// stage: instead of storing output d, the last stage calls
+// store(d, value, dst), dst being the buffer it would have written, which
+// the call returns.  This saves one pass over shared memory and one block
+// barrier per transform.
+template <int R, class Store>
+__device__ __forceinline__ void fft_stage_last(const float2 *src, float2 *dst, int P, int Ns,
+                                               const float2 *__restrict__ tw, bool inv, Store store)
+{
+    const int nb = P / R;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        float2 v[R];
+        const int k = j & (Ns - 1);
+        const int step = (P / (Ns * R)) * k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[fp(j + r * nb)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(tw + r * step);
+                if (inv) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        if (R == 8) dft8(v, inv);
+        else if (R == 4) dft4(v[0], v[1], v[2], v[3], inv);
+        else dft2(v[0], v[1]);
+        const int d0 = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) store(d0 + r * Ns, v[r], dst);
+    }
+}
+
+template <class Store>
+__device__ __forceinline__ float2 *fft_block_out(float2 *a, float2 *b, int P, const float2 *__restrict__ tw,
+                                                 bool inv, Store store)
+{
+    int Ns = 1;
+    float2 *src = a, *dst = b;
+    while (Ns < P) {
+        const int rem = P / Ns;
+        const int R = rem >= 8 ? 8 : (rem == 4 ? 4 : 2);
+        __syncthreads();
+        if (Ns * R == P) {
+            if (R == 8) fft_stage_last<8>(src, dst, P, Ns, tw, inv, store);
+            else if (R == 4) fft_stage_last<4>(src, dst, P, Ns, tw, inv, store);
+            else fft_stage_last<2>(src, dst, P, Ns, tw, inv, store);
+        } else {
+            if (R == 8) fft_stage<8>(src, dst, P, Ns, tw, inv);
+            else if (R == 4) fft_stage<4>(src, dst, P, Ns, tw, inv);
+            else fft_stage<2>(src, dst, P, Ns, tw, inv);
+        }
+        float2 *t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    __syncthreads();
+    return src;
+}
+
 // Band partial sums of A x for two rays (p0[k VB], p1[k VB], k < nb),
 // added in band order; the loads of 16 bands are issued together.
 __device__ __forceinline__ void band_sum2(const float *__restrict__ p0, const float *__restrict__ p1, size_t VB,
@@ -218,19 +279,22 @@ k_filter_fft(const float2 *__restrict__ hhat, const float *__restrict__ in, floa
         }
         a[fp(i)] = make_float2(x0, x1);
     }
-    float2 *f = fft_block(a, b, P, tw, false);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
-    float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
+    // the response and the output scaling fused into the transforms' last stages
+    auto mul_h = [&](int d, float2 v, float2 *dst) { dst[fp(d)] = cmul(v, hhat[d]); };
+    float2 *f = fft_block_out(a, b, P, tw, false, mul_h);
     const float sc = ((mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f) / (float)P;
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        float y0 = res[fp(i)].x * sc, y1 = res[fp(i)].y * sc;
-        if (post) {
-            y0 *= post[o0 + i];
-            if (has1) y1 *= post[o1 + i];
+    auto outp = [&](int d, float2 v, float2 *) {
+        if (d < B) {
+            float y0 = v.x * sc, y1 = v.y * sc;
+            if (post) {
+                y0 *= post[o0 + d];
+                if (has1) y1 *= post[o1 + d];
+            }
+            out[o0 + d] = y0;
+            if (has1) out[o1 + d] = y1;
         }
-        out[o0 + i] = y0;
-        if (has1) out[o1 + i] = y1;
-    }
+    };
+    fft_block_out(f, f == a ? b : a, P, tw, true, outp);
 }
 
 // out = D (A x) from the projector's band partial sums
@@ -308,45 +372,48 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
         }
         a[fp(i)] = make_float2(r0, r1);
     }
-    float2 *f = fft_block(a, bb, P, tw, false);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
-    float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
-    float2 *other = res == a ? bb : a;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    // D r: forward transform with the response fused into its last stage,
+    // inverse transform with the dual update fused into its last stage
+    // (which also stages the second filter's input in the buffer it writes)
+    auto mul_h = [&](int d, float2 v, float2 *dst) { dst[fp(d)] = cmul(v, hhat[d]); };
+    float2 *f = fft_block_out(a, bb, P, tw, false, mul_h);   // H . FFT(r), in f
+    auto upd = [&](int d, float2 v, float2 *dst) {
         float d0 = 0.0f, d1 = 0.0f;
-        if (i < B) {
-            const float n0 = m_old[i] + sigma * (res[fp(i)].x * invP);
-            const float n1 = m_old[B + i] + sigma * (res[fp(i)].y * invP);
-            m_new[i] = n0;
-            m_new[B + i] = n1;
+        if (d < B) {
+            const float n0 = m_old[d] + sigma * (v.x * invP);
+            const float n1 = m_old[B + d] + sigma * (v.y * invP);
             if (lowdose) {
-                d0 = winv[o0 + i] * (n0 - m_old[i]);
-                if (has1) d1 = winv[o1 + i] * (n1 - m_old[B + i]);
+                m_new[d] = n0;
+                m_new[B + d] = n1;
+                d0 = winv[o0 + d] * (n0 - m_old[d]);
+                if (has1) d1 = winv[o1 + d] * (n1 - m_old[B + d]);
+            } else {
+                // Alg. 2: mu_bar = 2 mu' - mu, no second filter
+                mu[o0 + d] = n0;
+                mu_bar[o0 + d] = 2.0f * n0 - m_old[d];
+                if (has1) {
+                    mu[o1 + d] = n1;
+                    mu_bar[o1 + d] = 2.0f * n1 - m_old[B + d];
+                }
             }
         }
-        other[fp(i)] = make_float2(d0, d1);
-    }
-    if (lowdose) {
-        f = fft_block(other, res, P, tw, false);
-        for (int i = threadIdx.x; i < P; i += blockDim.x) f[fp(i)] = cmul(f[fp(i)], hhat[i]);
-        res = fft_block(f, f == a ? bb : a, P, tw, true);
-    } else {
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        const float n0 = m_new[i], n1 = m_new[B + i];
-        float mb0 = 2.0f * n0 - m_old[i], mb1 = 2.0f * n1 - m_old[B + i];
-        if (lowdose) {
-            mb0 -= sigma * (res[fp(i)].x * invP);
-            mb1 -= sigma * (res[fp(i)].y * invP);
+        if (lowdose) dst[fp(d)] = make_float2(d0, d1);
+    };
+    f = fft_block_out(f, f == a ? bb : a, P, tw, true, upd);   // the second filter's input, in f
+    if (!lowdose) return;
+    f = fft_block_out(f, f == a ? bb : a, P, tw, false, mul_h);
+    auto fin = [&](int d, float2 v, float2 *) {
+        if (d < B) {
+            const float n0 = m_new[d], n1 = m_new[B + d];
+            mu[o0 + d] = n0;
+            mu_bar[o0 + d] = 2.0f * n0 - m_old[d] - sigma * (v.x * invP);
+            if (has1) {
+                mu[o1 + d] = n1;
+                mu_bar[o1 + d] = 2.0f * n1 - m_old[B + d] - sigma * (v.y * invP);
+            }
         }
-        mu[o0 + i] = n0;
-        mu_bar[o0 + i] = mb0;
-        if (has1) {
-            mu[o1 + i] = n1;
-            mu_bar[o1 + i] = mb1;
-        }
-    }
+    };
+    fft_block_out(f, f == a ? bb : a, P, tw, true, fin);
 }
 
 // =====================================================================
@@ -427,14 +494,15 @@ k_filter_sv(const float2 *__restrict__ hs, const float2 *__restrict__ hd, const 
     }
     float2 *f = fft_block(a, b, P, tw, false);
     sv_spectrum(f, hs, hd, P);
-    float2 *res = fft_block(f, f == a ? b : a, P, tw, true);
     const float sc = ((mode == 1) ? -fscal(scal, F_SIGMA) : 1.0f) / (float)P;
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        const float2 uv = res[fp(i)];
-        float y = fmaf(s[i], uv.y, uv.x) * sc;
-        if (post) y *= post[o + i];
-        out[o + i] = y;
-    }
+    auto outp = [&](int d, float2 uv, float2 *) {   // fused into the inverse transform's last stage
+        if (d < B) {
+            float y = fmaf(s[d], uv.y, uv.x) * sc;
+            if (post) y *= post[o + d];
+            out[o + d] = y;
+        }
+    };
+    fft_block_out(f, f == a ? b : a, P, tw, true, outp);
 }
 
 void launch_filter_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *in,
@@ -491,28 +559,29 @@ k_dual_sv(const float2 *__restrict__ hs, const float2 *__restrict__ hd, const fl
     }
     float2 *f = fft_block(a, bb, P, tw, false);
     sv_spectrum(f, hs, hd, P);
-    float2 *res = fft_block(f, f == a ? bb : a, P, tw, true);
-    float2 *other = res == a ? bb : a;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    // the dual update fused into the inverse transform's last stage, which
+    // also stages the second filter's input (d, s d) in the buffer it writes
+    auto upd = [&](int i, float2 uv, float2 *dst) {
         float d = 0.0f, sd = 0.0f;
         if (i < B) {
-            const float2 uv = res[fp(i)];
             const float n0 = m_old[i] + sigma * (fmaf(s[i], uv.y, uv.x) * invP);
             m_new[i] = n0;
             d = winv[o + i] * (n0 - m_old[i]);
             sd = s[i] * d;
         }
-        other[fp(i)] = make_float2(d, sd);
-    }
-    f = fft_block(other, res, P, tw, false);
+        dst[fp(i)] = make_float2(d, sd);
+    };
+    f = fft_block_out(f, f == a ? bb : a, P, tw, true, upd);
+    f = fft_block(f, f == a ? bb : a, P, tw, false);
     sv_spectrum(f, hs, hd, P);
-    res = fft_block(f, f == a ? bb : a, P, tw, true);
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        const float2 uv = res[fp(i)];
-        const float n0 = m_new[i];
-        mu[o + i] = n0;
-        mu_bar[o + i] = 2.0f * n0 - m_old[i] - sigma * (fmaf(s[i], uv.y, uv.x) * invP);
-    }
+    auto fin = [&](int i, float2 uv, float2 *) {
+        if (i < B) {
+            const float n0 = m_new[i];
+            mu[o + i] = n0;
+            mu_bar[o + i] = 2.0f * n0 - m_old[i] - sigma * (fmaf(s[i], uv.y, uv.x) * invP);
+        }
+    };
+    fft_block_out(f, f == a ? bb : a, P, tw, true, fin);
 }
 
 void launch_dual_sv(const Geometry *g, const float2 *hs, const float2 *hd, const float *sv, const float *partial,
