@@ -357,19 +357,25 @@ def measure_convergence(P):
     prox (tv_accel 1), plain Chambolle-Pock (D = I) and, for low-dose, the
     shift-variant split D (precond 2).  RMSE to the phantom, data residual
     and distance to the 1000-iteration iterate x* of the Eq. 24 run after
-    1 .. 1000 iterations, for four workloads: low-dose at the bench size
+    1 .. 1000 iterations, for six workloads: low-dose at the bench size
     (512^2, 720 views, I0 5e3, beta 0.005), the same with the phantom's
     attenuation times 5 (a dense object: counts spread over two decades),
-    the same slice with beta 500 (a TV weight that shapes the image), and
-    few-view (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2); plus
-    whole-solve rates (iterations/s, setup included, 30 iterations
-    low-dose, 100 few-view)."""
+    the same slice with beta 500 (a TV weight that shapes the image),
+    few-view (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2), and the
+    paper's shapes (256^2 with 1200 views low-dose at beta 500, and with 32
+    views few-view; 369 bins); plus whole-solve rates (iterations/s, setup
+    included, 30 iterations low-dose, 100 few-view)."""
     import torch
     out = {}
-    cases = [("lowdose", WORK["views"], 0, WORK["beta"], 1.0), ("lowdose_dense", WORK["views"], 0, WORK["beta"], 5.0),
-             ("lowdose_tv", WORK["views"], 0, 500.0, 1.0), ("fewview", 32, 1, 0.0, 1.0)]
-    for name, V, mode, beta, dense in cases:
-        N, B = WORK["n"], WORK["bins"]
+    # (name, N, views, bins, mode, beta, attenuation factor); the last two are
+    # the paper's own shapes (Sec. 4: 256^2, 1200 views low-dose; 32 views few-view)
+    cases = [("lowdose", WORK["n"], WORK["views"], WORK["bins"], 0, WORK["beta"], 1.0),
+             ("lowdose_dense", WORK["n"], WORK["views"], WORK["bins"], 0, WORK["beta"], 5.0),
+             ("lowdose_tv", WORK["n"], WORK["views"], WORK["bins"], 0, 500.0, 1.0),
+             ("fewview", WORK["n"], 32, WORK["bins"], 1, 0.0, 1.0),
+             ("paper_lowdose_256_v1200", 256, 1200, 369, 0, 500.0, 1.0),
+             ("paper_fewview_256_v32", 256, 32, 369, 1, 0.0, 1.0)]
+    for name, N, V, B, mode, beta, dense in cases:
         g = P.Geometry(N, V, B)
         g.autotune()
         v_true = synth.ellipse_phantom(N, WORK["ellipses"], 0)
@@ -388,7 +394,7 @@ def measure_convergence(P):
         runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale, acc) for label, pc, acc in arms}
         xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
         xn = float(torch.linalg.norm(xstar))
-        entry = {"workload": f"512^2, {V} views, {B} bins, " +
+        entry = {"workload": f"{N}^2, {V} views, {B} bins, " +
                              (f"Poisson I0 5e3, attenuation x{dense}, beta {beta}, Alg. 1" if mode == 0
                               else "noiseless b = A v, Alg. 2"),
                  "checkpoints": list(CHECKPOINTS)}
@@ -428,7 +434,13 @@ def run_ours(args):
 
     N, V, B = WORK["n"], WORK["views"], WORK["bins"]
     g = P.Geometry(N, V, B)
-    tuning = g.autotune()   # launch shapes by measurement, once per geometry (untimed, like its creation)
+    if args.tuning:
+        # fixed launch shapes (for profiler runs, whose timing would mislead the tuner)
+        ip, pr, osl, tvr = (int(t) for t in args.tuning.split(","))
+        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr)
+        tuning = {**g.tuning, "source": "fixed"}
+    else:
+        tuning = {**g.autotune(), "source": "autotune"}   # by measurement, once per geometry, untimed
     # synthetic slice for this rank: phantom -> A (on the GPU) -> Poisson data
     xt = torch.from_numpy(phantom(rank).astype(np.float32)).cuda()
     p = P.ct_project(g, xt).cpu().numpy()
@@ -625,7 +637,7 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     ap.add_argument("--tuning", default="",
-                    help="with --ncu-case: fixed launch shapes 'items,rows,orbit_slices,tv_rows'")
+                    help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)
