@@ -280,6 +280,18 @@ def cp_reference(b, w, mode, beta, s, t, iters, n, angles=None):
     return x
 
 
+def fewview_ell(n, n_views, n_bins, angles=None):
+    """l = (2/3) (N^2 / B) mean_v |a_v|, |a_v| = 1 / max(|cos t_v|, |sin t_v|):
+    the mean over rays of diag(A A^T) for Joseph's weights (one pixel's
+    weights in a view add up to 1, so a view's rays carry N^2 of weight in
+    total, |a_v| per step, and the squared interpolation weights of a step
+    average 2/3 of |a_v|^2).  It sets kappa = tau l of the few-view smoothed
+    ramp (precond 3)."""
+    t = np.arange(n_views) * np.pi / n_views if angles is None else _f64(angles)
+    a = 1.0 / np.maximum(np.abs(np.cos(t)), np.abs(np.sin(t)))
+    return (2.0 / 3.0) * (n * n / n_bins) * float(np.mean(a))
+
+
 def default_tau(mode, n_views, kappa):
     """tau defaults: low-dose pi*kappa/(2m) puts the knee of H (Eq. 24) at the
     Nyquist frequency; few-view 0.01 (image-intensity units)."""

@@ -167,3 +167,48 @@ def test_fgp_prox_keeps_the_limit():
     xg = O.pdtv(b, w, taps, 0, beta, tau, sigma, 10, 3000, N)[0].x
     xf = O.pdtv(b, w, taps, 0, beta, tau, sigma, 10, 3000, N, fgp=True)[0].x
     assert np.linalg.norm(xf - xg) / np.linalg.norm(xg) < 1e-6
+
+
+def test_fewview_ell_is_mean_diagonal_of_AAt():
+    # l of the few-view smoothed ramp against the explicit matrix: the mean
+    # over the rays that meet the image of sum_j a_ij^2, times the hit fraction
+    N, V, B = 16, 24, 23
+    A = explicit_A(N, V, B)
+    diag = (A ** 2).sum(axis=1)
+    assert O.fewview_ell(N, V, B) == pytest.approx(diag.mean(), rel=0.05)
+
+
+def fewview_problem(N, V, B, seed):
+    x = synth.ellipse_phantom(N, 8, seed)
+    return x, O.project(x, V, B)
+
+
+def test_fewview_smoothed_ramp_keeps_the_limit():
+    # Theorem (Sec. 2.2): injective few-view (N = 8, V = 16, B = 13): the
+    # smoothed ramp with kappa = tau l also converges to x_true
+    N, V, B = 8, 16, 13
+    rng = np.random.default_rng(3)
+    xt = 0.5 + 0.5 * rng.uniform(size=(N, N))
+    b = O.project(xt, V, B)
+    tau = O.default_tau(1, V, 0.0)
+    taps = O.ramp_taps(0, V, B, tau, tau * O.fewview_ell(N, V, B))
+    sigma, _, _ = O.step_sizes(1, N, V, B, taps, None, tau)
+    st, _ = O.pdtv(b, None, taps, 1, 0.0, tau, sigma, 10, 12000, N)
+    assert np.linalg.norm(st.x - xt) / np.linalg.norm(xt) < 1e-8
+
+
+def test_fewview_smoothed_ramp_converges_faster_than_eq32():
+    # 64^2 from 32 views: the pure ramp of Eq. 32 over-amplifies the detector
+    # frequencies that sparse views leave to the same-view part of A A^T
+    N, V, B = 64, 32, 95
+    x, b = fewview_problem(N, V, B, 0)
+    tau = O.default_tau(1, V, 0.0)
+    t32 = O.ramp_taps(1, V, B, tau)
+    tsm = O.ramp_taps(0, V, B, tau, tau * O.fewview_ell(N, V, B))
+    s32, n32, _ = O.step_sizes(1, N, V, B, t32, None, tau)
+    ssm, nsm, _ = O.step_sizes(1, N, V, B, tsm, None, tau)
+    assert tau * nsm < 0.5 * tau * n32          # the step-size bound is far less restrictive
+    xs = O.pdtv(b, None, t32, 1, 0.0, tau, s32, 10, 2000, N)[0].x
+    d32 = np.linalg.norm(O.pdtv(b, None, t32, 1, 0.0, tau, s32, 10, 30, N)[0].x - xs)
+    dsm = np.linalg.norm(O.pdtv(b, None, tsm, 1, 0.0, tau, ssm, 10, 30, N)[0].x - xs)
+    assert dsm < 0.5 * d32
