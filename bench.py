@@ -355,7 +355,8 @@ def measure_convergence(P):
     """Preconditioners and prox forms on the same GPU kernels: the ramp D of
     Eq. 24 / Eq. 32 with the projected-gradient prox, the same with the FGP
     prox (tv_accel 1), plain Chambolle-Pock (D = I) and, for low-dose, the
-    shift-variant split D (precond 2).  RMSE to the phantom, data residual
+    shift-variant split D (precond 2), for few-view the smoothed ramp with
+    kappa = tau l (precond 3).  RMSE to the phantom, data residual
     and distance to the 1000-iteration iterate x* of the Eq. 24 run after
     1 .. 1000 iterations, for six workloads: low-dose at the bench size
     (512^2, 720 views, I0 5e3, beta 0.005), the same with the phantom's
@@ -389,8 +390,7 @@ def measure_convergence(P):
             b, w = p, None
         vt = torch.from_numpy(v_true).cuda()
         arms = [("preconditioned", 1, 0), ("preconditioned_fgp", 1, 1), ("plain_cp", 0, 0)]
-        if mode == 0:
-            arms.insert(2, ("shift_variant", 2, 0))
+        arms.insert(2, ("shift_variant", 2, 0) if mode == 0 else ("smoothed_ramp", 3, 0))
         runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale, acc) for label, pc, acc in arms}
         xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
         xn = float(torch.linalg.norm(xstar))

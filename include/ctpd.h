@@ -214,7 +214,12 @@ typedef struct {
     int precond;      /* 1: ramp preconditioner D (Eq. 24 / Eq. 32);
                          0: D = I (the unpreconditioned iteration);
                          2: the shift-variant D of ct_ramp_filter_split with
-                            s = sqrt(kappa w) (CT_LOWDOSE, n_bins <= 4096) */
+                            s = sqrt(kappa w) (CT_LOWDOSE, n_bins <= 4096);
+                         3: few-view smoothed ramp, the form of Eq. 24 with
+                            kappa = tau l, l = (2/3)(N^2/B) mean_v |a_v| the
+                            mean diagonal of A A^T (CT_FEWVIEW): Eq. 32 adds
+                            the same-view part of A A^T that sparse views
+                            leave out of 2m/|w|                              */
     int norm_iters;   /* Lanczos steps for the operator norms of the automatic
                          sigma (0 -> 16, at most 64)                          */
     int resume;       /* 1: continue from the state held in `workspace`       */

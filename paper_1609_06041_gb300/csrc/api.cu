@@ -436,7 +436,9 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         return fail(CT_ERR_ARG, "ct_pdtv_solve: negative iteration count");
     if (mode == CT_LOWDOSE && !(prm->beta >= 0.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: beta must be >= 0");
     if (prm->resume && !workspace) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
-    if (prm->precond < 0 || prm->precond > 2) return fail(CT_ERR_ARG, "ct_pdtv_solve: precond must be 0, 1 or 2");
+    if (prm->precond < 0 || prm->precond > 3) return fail(CT_ERR_ARG, "ct_pdtv_solve: precond must be 0, 1, 2 or 3");
+    if (prm->precond == 3 && mode != CT_FEWVIEW)
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: the few-view smoothed ramp (precond 3) needs CT_FEWVIEW");
     if (prm->tv_accel != 0 && (prm->tv_accel != 1 || prm->tv_iters > tv_max_steps()))
         return fail(CT_ERR_ARG, "ct_pdtv_solve: tv_accel must be 0 or 1 (1 needs tv_iters <= %d)", tv_max_steps());
     if (prm->precond == 2 && (mode != CT_LOWDOSE || !fft_supported(g)))
@@ -516,6 +518,19 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             launch_taps(g, CT_TAPS_HIGH_BAND, scal, 0.0, 0.0, taps2, st);
             launch_sv_hhat(g, taps, taps2, half, hhat, hhat2, st);
             launch_sv_scale(w, scal, sv, I, st);
+        } else if (prm->precond == 3) {
+            // few-view smoothed ramp: Eq. 24's form with kappa = tau l (l the mean
+            // diagonal of A A^T, from the view constants), tau as SC_TAU sets it
+            double sa = 0.0;
+            for (int v = 0; v < g->n_views; ++v) {
+                const double t = g->h_angles[v];
+                sa += 1.0 / std::max(fabs(cos(t)), fabs(sin(t)));
+            }
+            const double ell = (2.0 / 3.0) * ((double)g->n * g->n / g->n_bins) * (sa / g->n_views);
+            const double tau_h = prm->tau > 0.0 ? prm->tau : 0.01;
+            launch_scalars(scal, SC_SET, tau_h * ell, 0, 0, S_KAPPA, st);
+            launch_taps(g, CT_LOWDOSE, scal, 0.0, 0.0, taps, st);
+            if (use_fft) launch_hhat(g, taps, half, hhat, st);
         } else {
             if (prm->precond) launch_taps(g, mode, scal, 0.0, 0.0, taps, st);
             else launch_fill(taps, 1.0f, 1, st);

@@ -169,3 +169,38 @@ def test_full_size_two_iterations():
     tau = O.default_tau(0, V, float(np.mean(1.0 / w)))
     xg, st, _, _, _ = run_both(P, N, V, B, b, w, 0, 0.005, 2, 10, tau, 0.5)
     assert rel_l2(xg, st.x) <= TOL
+
+
+def test_fewview_smoothed_ramp_parity():
+    # precond 3: Eq. 24's form with kappa = tau l (the few-view smoothed ramp),
+    # against the oracle with the same taps, tau, sigma; and its automatic
+    # sigma against the oracle's power-method bound
+    P = need_gpu()
+    N, V, B = 48, 16, 70
+    x = synth.ellipse_phantom(N, 6, 2)
+    b = f32(O.project(x, V, B))
+    tau = O.default_tau(1, V, 0.0)
+    taps = O.ramp_taps(0, V, B, tau, tau * O.fewview_ell(N, V, B))
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=1, iters=20, tv_iters=10, precond=3, tau=tau, sigma=0.3)
+    xg, rep = P.ct_pdtv_solve(g, to_gpu(b), None, prm)
+    assert rep["kappa"] == pytest.approx(tau * O.fewview_ell(N, V, B), rel=1e-6)
+    st, _ = O.pdtv(b, None, taps, 1, 0.0, tau, 0.3, 10, 20, N)
+    assert rel_l2(to_np(xg), st.x) <= TOL
+    # automatic sigma: rho / (tau ||A^T D A||), the norm against the 2-norm of
+    # the explicitly built operator (a smaller case)
+    N2, V2, B2 = 24, 16, 35
+    g2 = P.Geometry(N2, V2, B2)
+    b2 = f32(O.project(synth.ellipse_phantom(N2, 4, 1), V2, B2))
+    _, rep = P.ct_pdtv_solve(g2, to_gpu(b2), None, P.PDTVParams(mode=1, iters=1, precond=3, norm_iters=40))
+    t2 = O.ramp_taps(0, V2, B2, tau, tau * O.fewview_ell(N2, V2, B2))
+    cols = []
+    for j in range(N2 * N2):
+        e = np.zeros(N2 * N2)
+        e[j] = 1.0
+        cols.append(O.backproject(O.filt(O.project(e.reshape(N2, N2), V2, B2), t2), N2).ravel())
+    nada = np.linalg.norm(np.stack(cols, axis=1), 2)
+    assert rep["norm_ADA"] == pytest.approx(nada, rel=2e-4)
+    assert rep["sigma"] == pytest.approx(0.95 / (tau * nada), rel=3e-4)
+    with pytest.raises(P.CTError):
+        P.ct_pdtv_solve(g, to_gpu(b), to_gpu(np.ones((V, B))), P.PDTVParams(mode=0, iters=1, precond=3))
