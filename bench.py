@@ -38,6 +38,7 @@ METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory bytes per clock x max clock
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from the full ncu capture in profiles/kernels_lowdose_512_v720_b736.md
 # (update together with the kernels; None when no capture of the current kernel exists)
@@ -583,6 +584,12 @@ def run_ours(args):
                          "traffic": TRAFFIC_BYTES.get(dom_key), "traffic_unit": "bytes/launch",
                          "algorithmic_flops": flops, "nnz": nnz, "launch_ms": dom_ms,
                          "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+            # the projector's binding resource: every Joseph sample reads one
+            # interpolation pair (8 bytes) from shared memory; samples = nnz / 2
+            "roofline_shared_memory": {"kernel": "ct_project (A)", "achieved": 8.0 * (nnz / 2) / (a_ms / 1e3) / 1e12,
+                                       "peak": SMEM_PEAK_TBPS, "unit": "TB/s",
+                                       "frac": 8.0 * (nnz / 2) / (a_ms / 1e3) / 1e12 / SMEM_PEAK_TBPS,
+                                       "peak_source": "152 SMs x 128 B/clock x 2070 MHz"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 2 * V * B * 4, "d2h_bytes_per_step": N * N * 4},
