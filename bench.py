@@ -575,7 +575,7 @@ def run_ours(args):
                              "setup": step_ms - loop_ms, "per_iteration": loop_ms / WORK["iters"],
                              "A_launch": a_ms, "AT_launch": at_ms},
             "loop_iterations_per_s": WORK["iters"] / (loop_ms / 1e3) * world,
-            # the survey's effective operator bandwidth, (4 N^2 + 4 V B) bytes per pass
+            # effective operator bandwidth: (4 N^2 + 4 V B) bytes per pass
             "operator_GBps": {"A": (4.0 * N * N + 4.0 * V * B) / (a_ms / 1e3) / 1e9,
                               "AT": (4.0 * N * N + 4.0 * V * B) / (at_ms / 1e3) / 1e9},
             "report": {k: rep[k] for k in ("tau", "sigma", "kappa", "norm_ADA", "norm_WDW")},
