@@ -122,7 +122,10 @@ template <class Op>
 void lanczos_norm(Op op, float *t, float *tp, float *w, size_t n, int k, double *scal, int base, int n0slot,
                   double *partials, unsigned *ticket, int slot, cudaStream_t st)
 {
-    launch_fill(t, 1.0f, n, st);
+    // start vector: +-1 by a hash of the index (norm sqrt(n)); the all-ones
+    // vector is invariant under the geometry's rotations and reflections and
+    // has no component along a top eigenvector of another symmetry class
+    launch_fill_sign(t, n, st);
     launch_scalars(scal, SC_SET, sqrt((double)n), 0, 0, n0slot, st);
     for (int j = 0; j < k; ++j) {
         op(t, w);

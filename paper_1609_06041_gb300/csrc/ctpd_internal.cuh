@@ -190,6 +190,8 @@ void launch_dual_sv(const Geometry *g, const float2 *hs, const float2 *hd, const
                     cudaStream_t st);
 // s = sqrt(kappa w), kappa = scal[S_KAPPA]
 void launch_sv_scale(const float *w, const double *scal, float *s, size_t n, cudaStream_t st);
+// out[i] = +-1 from an integer hash of i (the Lanczos start vector)
+void launch_fill_sign(float *out, size_t n, cudaStream_t st);
 void kernel_attrs_fft();
 void launch_dual_fft_batched(const Geometry *g, const float2 *hhat, const float *partial, const float *b,
                              const float *mu_in, float *mu_out, float *mu_bar, const float *winv, int lowdose,

@@ -62,6 +62,27 @@ void launch_sv_scale(const float *w, const double *scal, float *s, size_t n, cud
     k_sv_scale<<<grid_for(n, 256), 256, 0, st>>>(w, scal, s, n);
 }
 
+// out[i] = +-1 from a 32-bit integer hash of i (the lowbias32 mixing of
+// C. Wellons): a start vector with components in every symmetry class
+__global__ void k_fill_sign(float *out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned x = (unsigned)i * 2654435761u + 12345u;
+        x ^= x >> 16;
+        x *= 0x7feb352du;
+        x ^= x >> 15;
+        x *= 0x846ca68bu;
+        x ^= x >> 16;
+        out[i] = (x & 1u) ? 1.0f : -1.0f;
+    }
+}
+
+void launch_fill_sign(float *out, size_t n, cudaStream_t st)
+{
+    counted();
+    k_fill_sign<<<grid_for(n, 256), 256, 0, st>>>(out, n);
+}
+
 // out = in * s (sqrt_s: in * sqrt(s))
 __global__ void k_scale_by(const float *in, const float *s, int sqrt_s, float *out, size_t n)
 {
@@ -238,7 +259,38 @@ __global__ void k_lanczos_max(double *s, int base, int k, int out)
         lo = nlo;
         hi = fmaxf(nhi, nlo);
     }
-    if (lane == 0) s[out] = (double)(hi * big) * (1.0 + 1e-6);
+    if (lane != 0) return;
+    // theta = the upper end of the bracket; the estimate is theta + beta_k |y_k|,
+    // the Ritz value plus its residual norm (y the unit eigenvector of T for
+    // theta, beta_k the norm left after the last step), so that it lies above
+    // lambda_max once the Ritz vector has found the top of the spectrum.
+    // y by two steps of inverse iteration with theta I - T (positive definite,
+    // as theta is above every eigenvalue of T): tridiagonal elimination in
+    // double on this one thread.
+    const double theta = (double)(hi * big) * (1.0 + 1e-6);
+    double y[LANCZOS_MAX], cp[LANCZOS_MAX];
+    for (int j = 0; j < k; ++j) y[j] = 1.0;
+    for (int itr = 0; itr < 2; ++itr) {
+        double m = theta - s[base];
+        if (!(m > 0.0)) m = 1e-300;
+        cp[0] = k > 1 ? -s[base + 1] / m : 0.0;
+        y[0] = y[0] / m;
+        for (int j = 1; j < k; ++j) {
+            const double sub = -s[base + 2 * j - 1];
+            double d = (theta - s[base + 2 * j]) - sub * cp[j - 1];
+            if (!(d > 0.0)) d = 1e-300;
+            cp[j] = j + 1 < k ? -s[base + 2 * j + 1] / d : 0.0;
+            y[j] = (y[j] - sub * y[j - 1]) / d;
+        }
+        for (int j = k - 2; j >= 0; --j) y[j] -= cp[j] * y[j + 1];
+        double nrm = 0.0;
+        for (int j = 0; j < k; ++j) nrm += y[j] * y[j];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0) || !isfinite(nrm)) break;
+        for (int j = 0; j < k; ++j) y[j] /= nrm;
+    }
+    const double res = fabs(s[base + 2 * (k - 1) + 1] * y[k - 1]);
+    s[out] = isfinite(res) ? theta + res : theta;
 }
 
 void launch_lanczos_max(double *scal, int base, int k, int out, cudaStream_t st)

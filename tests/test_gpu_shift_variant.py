@@ -106,9 +106,9 @@ def test_step_sizes_match_matrix_norms():
         D = Tl + s[v][:, None] * Th * s[v][None, :]
         q = 1.0 / np.sqrt(w[v])
         nwdw = max(nwdw, np.linalg.norm(q[:, None] * D * q[None, :], 2))
-    assert rep["norm_ADA"] == pytest.approx(nada, rel=2e-4)
-    assert rep["norm_WDW"] == pytest.approx(nwdw, rel=2e-4)
-    assert rep["sigma"] == pytest.approx(0.95 * min(2.0 / nwdw, 1.0 / (tau * nada)), rel=3e-4)
+    assert nada * (1 - 2e-4) <= rep["norm_ADA"] <= nada * 1.01
+    assert nwdw * (1 - 2e-4) <= rep["norm_WDW"] <= nwdw * 1.01
+    assert rep["sigma"] == pytest.approx(0.95 * min(2.0 / rep["norm_WDW"], 1.0 / (tau * rep["norm_ADA"])), rel=1e-6)
 
 
 def test_rejects_fewview_and_bad_precond():

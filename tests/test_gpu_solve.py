@@ -126,23 +126,28 @@ def test_auto_step_sizes_match_matrix_norms():
     D = np.array([[taps[B - 1 + (i - j)] for j in range(B)] for i in range(B)])
     s = 1.0 / np.sqrt(w)
     nwdw = max(np.linalg.norm(s[v][:, None] * D * s[v][None, :], 2) for v in range(V))
-    assert rep["norm_ADA"] == pytest.approx(nada, rel=2e-4)
-    assert rep["norm_WDW"] == pytest.approx(nwdw, rel=2e-4)
-    assert rep["sigma"] == pytest.approx(0.95 * min(2.0 / nwdw, 1.0 / (tau * nada)), rel=3e-4)
+    # the estimates (Ritz value + residual norm) lie at or just above the norms
+    assert nada * (1 - 2e-4) <= rep["norm_ADA"] <= nada * 1.01
+    assert nwdw * (1 - 2e-4) <= rep["norm_WDW"] <= nwdw * 1.01
+    assert rep["sigma"] == pytest.approx(0.95 * min(2.0 / rep["norm_WDW"], 1.0 / (tau * rep["norm_ADA"])), rel=1e-6)
+    assert rep["sigma"] <= 0.95 * min(2.0 / nwdw, 1.0 / (tau * nada)) * (1 + 2e-4)
 
 
-def test_default_step_sizes_are_valid_at_scale():
-    # 512^2 / 720 views with the default Lanczos depth: the estimate is a
-    # lower bound of the norm that the safety factor rho = 0.95 covers.
+@pytest.mark.parametrize("N,V,B", [(512, 720, 736), (384, 90, 553)])
+def test_default_step_sizes_are_valid_at_scale(N, V, B):
+    # the default Lanczos depth (16 steps from a +-1 start, Ritz value plus
+    # residual norm): the estimates lie above the 64-step ones and close to
+    # them, so sigma keeps the step conditions of the Alg. 1 box
     P = need_gpu()
-    N, V, B = 512, 720, 736
     x, b, w = lowdose_case(N, V, B, 0, n_ell=20, i0=5e3)
     g = P.Geometry(N, V, B)
     _, rep16 = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), P.PDTVParams(mode=0, iters=0, beta=0.005))
     _, rep64 = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), P.PDTVParams(mode=0, iters=0, beta=0.005, norm_iters=64))
-    assert rep16["norm_ADA"] <= rep64["norm_ADA"] * (1 + 1e-5)
-    assert rep16["norm_ADA"] >= 0.99 * rep64["norm_ADA"]
-    assert rep16["sigma"] * rep16["tau"] * rep64["norm_ADA"] < 0.96
+    for key in ("norm_ADA", "norm_WDW"):
+        assert rep16[key] >= rep64[key] * (1 - 1e-3)
+        assert rep16[key] <= rep64[key] * 1.05
+    assert rep16["sigma"] * rep16["tau"] * rep64["norm_ADA"] <= 0.95 * (1 + 1e-3)
+    assert rep16["sigma"] * rep64["norm_WDW"] <= 2 * 0.95 * (1 + 1e-3)
 
 
 def test_solve_converges_on_gpu():
@@ -200,7 +205,7 @@ def test_fewview_smoothed_ramp_parity():
         e[j] = 1.0
         cols.append(O.backproject(O.filt(O.project(e.reshape(N2, N2), V2, B2), t2), N2).ravel())
     nada = np.linalg.norm(np.stack(cols, axis=1), 2)
-    assert rep["norm_ADA"] == pytest.approx(nada, rel=2e-4)
-    assert rep["sigma"] == pytest.approx(0.95 / (tau * nada), rel=3e-4)
+    assert nada * (1 - 2e-4) <= rep["norm_ADA"] <= nada * 1.01
+    assert rep["sigma"] == pytest.approx(0.95 / (tau * rep["norm_ADA"]), rel=1e-6)
     with pytest.raises(P.CTError):
         P.ct_pdtv_solve(g, to_gpu(b), to_gpu(np.ones((V, B))), P.PDTVParams(mode=0, iters=1, precond=3))
