@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORK = dict(name="lowdose_512x512_v720_b736", n=512, views=720, bins=736, ellipses=20,
-            i0=5e3, beta=0.005, iters=30, tv_iters=10, norm_iters=16)
+            i0=5e3, beta=0.005, iters=30, tv_iters=10, norm_iters=12)
 METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
@@ -317,7 +317,7 @@ def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0):
     and the relative data residual |A x - b| / |b|."""
     import torch
     prm = P.PDTVParams(mode=mode, iters=CHECKPOINTS[0], tv_iters=10, precond=precond, beta=beta,
-                       norm_iters=16, tv_accel=tv_accel)
+                       norm_iters=WORK["norm_iters"], tv_accel=tv_accel)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     xs, rmse, resid = {}, {}, {}
@@ -336,7 +336,7 @@ def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0):
 def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3, tv_accel=0):
     """iterations/s of a whole solve (setup included), CUDA events."""
     import torch
-    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=16,
+    prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=WORK["norm_iters"],
                        tv_accel=tv_accel)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")

@@ -221,7 +221,8 @@ typedef struct {
                             the same-view part of A A^T that sparse views
                             leave out of 2m/|w|                              */
     int norm_iters;   /* Lanczos steps for the operator norms of the automatic
-                         sigma (0 -> 16, at most 64)                          */
+                         sigma (0 -> 12, at most 64); the estimate is the
+                         Ritz value plus its residual norm, from a +-1 start */
     int resume;       /* 1: continue from the state held in `workspace`       */
     double beta;      /* TV weight of Eq. 1 (low-dose)                         */
     double tau;       /* primal step; <= 0: low-dose pi*kappa/(2m) with

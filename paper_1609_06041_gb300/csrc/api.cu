@@ -451,7 +451,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const double rho = prm->rho > 0.0 ? prm->rho : 0.95;
     if (!(rho < 1.0)) return fail(CT_ERR_ARG, "ct_pdtv_solve: rho must be in (0, 1)");
     const int ntv = prm->tv_iters > 0 ? prm->tv_iters : 10;
-    const int nlz = std::min(prm->norm_iters > 0 ? prm->norm_iters : 16, (int)LANCZOS_MAX);
+    const int nlz = std::min(prm->norm_iters > 0 ? prm->norm_iters : 12, (int)LANCZOS_MAX);
     cudaStream_t st = S(stream);
     const Layout L = layout(g);
     const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;

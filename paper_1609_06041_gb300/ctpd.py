@@ -275,7 +275,7 @@ class PDTVParams:
     iters: int = 20
     tv_iters: int = 10
     precond: int = 1
-    norm_iters: int = 20
+    norm_iters: int = 0          # 0: the library default (12 Lanczos steps)
     resume: int = 0
     beta: float = 0.0
     tau: float = 0.0

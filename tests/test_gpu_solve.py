@@ -135,13 +135,13 @@ def test_auto_step_sizes_match_matrix_norms():
 
 @pytest.mark.parametrize("N,V,B", [(512, 720, 736), (384, 90, 553)])
 def test_default_step_sizes_are_valid_at_scale(N, V, B):
-    # the default Lanczos depth (16 steps from a +-1 start, Ritz value plus
+    # the default Lanczos depth (12 steps from a +-1 start, Ritz value plus
     # residual norm): the estimates lie above the 64-step ones and close to
     # them, so sigma keeps the step conditions of the Alg. 1 box
     P = need_gpu()
     x, b, w = lowdose_case(N, V, B, 0, n_ell=20, i0=5e3)
     g = P.Geometry(N, V, B)
-    _, rep16 = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), P.PDTVParams(mode=0, iters=0, beta=0.005))
+    _, rep16 = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), P.PDTVParams(mode=0, iters=0, beta=0.005))   # default depth
     _, rep64 = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), P.PDTVParams(mode=0, iters=0, beta=0.005, norm_iters=64))
     for key in ("norm_ADA", "norm_WDW"):
         assert rep16[key] >= rep64[key] * (1 - 1e-3)
