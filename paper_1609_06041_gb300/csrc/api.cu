@@ -285,6 +285,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     kernel_attrs_tv();
     kernel_attrs_joseph();
     kernel_attrs_fft();
+    kernel_attrs_grad();
     ct_status st = cuda_check("ct_geometry_create");
     if (st != CT_OK) {
         ct_geometry_destroy(g);

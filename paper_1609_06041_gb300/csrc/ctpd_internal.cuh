@@ -202,10 +202,12 @@ void launch_dual_bwd_fft(const Geometry *g, const float2 *hhat, const float *par
                          int batch, cudaStream_t st);
 
 // Reductions of the adjoint (k_grad.cu).
-size_t tapcorr_partials(int nviews, int half);
-void launch_tapcorr_acc(const float *g, const float *s, int nviews, int B, int half, double coef,
-                        double *partial, double *acc, cudaStream_t st);
-void launch_sum_partials(const double *partials, size_t n, double *scal, int slot, double coef, cudaStream_t st);
+// acc[half - 1 + k] += c0 <g0, T_k s0> + c1 <g1, T_k s1> over nviews rows of B
+// bins (T_k: shift by k, |k| < half); g1 = NULL drops the second pair.
+size_t tapcorr_partial_bytes(int nviews, int B, int half);
+void launch_tapcorr_acc(const float *g0, const float *s0, double c0, const float *g1, const float *s1, double c1,
+                        int nviews, int B, int half, float *partial, double *acc, cudaStream_t st);
+void kernel_attrs_grad();
 void launch_grad_out(const double *acc, int nl, const double *scal, int slot, double fac, float *grad,
                      cudaStream_t st);
 // out = fac[0] * scale_v * sum_b partial[b]
@@ -217,10 +219,15 @@ size_t tv_px_blocks(int n, int batch);
 void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int batch, const double *scal,
                     cudaStream_t st);
 void launch_tv_final(const float *z, const float *p, float *x, int n, int batch, const double *scal, cudaStream_t st);
+// The adjoints add their lambda (and inv8) derivative terms into scal[slot_*]
+// through the block partials part[tv_px_blocks] (doubles) and a zeroed ticket counter,
+// which the last block resets.
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, const double *scal, double *part_lam, cudaStream_t st);
-void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gq, float *gz, float *gp,
-                        int n, int batch, const double *scal, double *part_inv8, double *part_lam, cudaStream_t st);
+                         float *gp, int n, int batch, double *scal, int slot_lam, double *part, unsigned *ticket,
+                         cudaStream_t st);
+void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
+                        int batch, double *scal, int slot_inv8, int slot_lam, double *part, unsigned *ticket,
+                        cudaStream_t st);
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
 // dual field p = (px, py)), temporally blocked tiles held in registers.
@@ -228,9 +235,12 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
 // when final != 0 also writes x = max(0, z + lam div p).  n_sm (the
 // device's SM count) and min_rows (fewest interior rows per tile, 0: the
 // default) size the tiles.
+// batch > 1 runs that many images (z, x: n x n each; p: 2 n x n each);
+// traj, when not NULL (plain projected-gradient steps), receives p after each of the first
+// steps - 1 steps: step l + 1 at traj + (l * batch + image) * 2 n n.
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                int n, int n_sm, int min_rows, int steps, int final, const double *scal, cudaStream_t st,
-               bool fgp = false);
+               bool fgp = false, int batch = 1, float *traj = nullptr);
 int tv_max_steps();
 
 // Small helpers

@@ -58,15 +58,20 @@ static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr)
     return t;
 }
 
+// blockIdx.z selects the image of a batch (z, x: N x N each; p: 2 N x N).
+// traj, when not NULL, receives p after each of the first steps - 1 steps:
+// step l + 1 (l = 0 .. steps - 2) at traj + (l * gridDim.z + image) * 2 N N.
+//
 // FGP: the fast gradient projection (Beck and Teboulle): each step is the
 // projected-gradient step taken at r = p + theta (p - p_prev) instead of p,
 // with theta_k = (t_k - 1) / t_{k+1}, t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
 // (momentum restarted at every call).  Each cell keeps p_prev as well, and
 // the field published for the divergence is r_y (p_y after the last step).
-template <bool FGP>
+template <bool FGP, bool TRAJ>
 __global__ void __launch_bounds__(TV_THREADS, 1)
 k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
-     float *__restrict__ x, int N, int steps, int final_, int tc, int tr, const double *__restrict__ scal)
+     float *__restrict__ x, int N, int steps, int final_, int tc, int tr, const double *__restrict__ scal,
+     float *__restrict__ traj)
 {
     // row li of the region at index (li + 1) * 32 + lane; rows -1 and
     // beyond the region read zeros
@@ -77,7 +82,11 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     const int H = steps + 1, Sr = tr + 2 * H;
     const int R0 = blockIdx.y * tr - H, C0 = blockIdx.x * tc - H;
     const int c0 = C0 + 2 * lane;   // image columns c0, c0 + 1 of this lane
-    const size_t NN = (size_t)N * N;
+    const size_t NN = (size_t)N * N, img = blockIdx.z;
+    z += img * NN;
+    p_in += img * 2 * NN;
+    p_out += img * 2 * NN;
+    if (final_) x += img * NN;
     const float lam = fscal(scal, F_LAMBDA);
     const float inv8 = fscal(scal, F_INV8LAM);
     // forward differences: along x on columns 0..N-2, along y on columns 0..N-1
@@ -190,6 +199,24 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                         pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
                 }
             }
+            if (TRAJ && !last) {   // the tile interior's p after this step
+                float *tp = traj + ((size_t)it * gridDim.z + img) * 2 * NN;
+#pragma unroll
+                for (int j = 0; j < TV_J; ++j) {
+                    const int li = w + TV_WARPS * j, rr = R0 + li;
+                    if (li >= H && li < H + tr && rr < N) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int lj = 2 * lane + e, cc = C0 + lj;
+                            if (lj >= H && lj < H + tc && cc < N) {
+                                const size_t gi = (size_t)rr * N + cc;
+                                tp[gi] = pxr[j][e];
+                                tp[NN + gi] = pyr[j][e];
+                            }
+                        }
+                    }
+                }
+            }
             __syncthreads();
             t = t1;
             th = thn;
@@ -225,14 +252,20 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 }
 
 void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
-               int n, int n_sm, int min_rows, int steps, int final_, const double *scal, cudaStream_t st, bool fgp)
+               int n, int n_sm, int min_rows, int steps, int final_, const double *scal, cudaStream_t st, bool fgp,
+               int batch, float *traj)
 {
-    const TvTiles t = tv_tiles(n, steps, n_sm, min_rows > 0 ? min_rows : TV_MIN_TR);
+    // a batch fills the GPU with its images: the tiles of one image only
+    // need to cover n_sm / batch SMs
+    const TvTiles t = tv_tiles(n, steps, std::max(1, n_sm / std::max(1, batch)), min_rows > 0 ? min_rows : TV_MIN_TR);
+    const dim3 grid(t.ncb, t.nrb, std::max(1, batch));
     counted();
-    if (fgp)
-        k_tv<true><<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
+    if (traj)
+        k_tv<false, true><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
+    else if (fgp)
+        k_tv<true, false><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
     else
-        k_tv<false><<<dim3(t.ncb, t.nrb), TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal);
+        k_tv<false, false><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
 }
 
 void kernel_attrs_tv() {}
@@ -283,18 +316,85 @@ __device__ __forceinline__ float2 proj_adj(float2 q, float2 g)
     return make_float2((g.x - hx * d) * inv, (g.y - hy * d) * inv);
 }
 
-__device__ __forceinline__ void block_sum_to(double v, double *partials)
+// Adds the per-thread float terms va (vb) of the whole grid into
+// scal[slot_a] (scal[slot_b]), in double, deterministically: a fixed
+// shuffle tree per warp (float), the block's warp sums in order (double)
+// into part[2 block], part[2 block + 1]; the last block to finish (ticket
+// counter) adds the partials in block order, adds the totals to the slots
+// and resets the counter.  FP64 arithmetic is slow on this GPU, so only the
+// per-warp sums and the final pass are double.  slot_b < 0: one value.
+// Blocks of 256 threads.
+__device__ __forceinline__ void grid_sum2_to(float va, float vb, double *part, unsigned *ticket, double *scal,
+                                             int slot_a, int slot_b)
 {
-    __shared__ double red[256];
-    const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    red[t] = v;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (t < s) red[t] += red[t + s];
-        __syncthreads();
+    __shared__ double wa[8], wb[8];
+    __shared__ bool last;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, nblk = gridDim.x * gridDim.y * gridDim.z;
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        va += __shfl_down_sync(0xffffffffu, va, o);
+        vb += __shfl_down_sync(0xffffffffu, vb, o);
     }
-    if (t == 0)
-        partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
+    if ((t & 31) == 0) {
+        wa[t >> 5] = (double)va;
+        wb[t >> 5] = (double)vb;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double sa = 0.0, sb = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            sa += wa[k];
+            sb += wb[k];
+        }
+        part[2 * blk] = sa;
+        part[2 * blk + 1] = sb;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // four independent runs per thread, so the loads overlap
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = t;
+    for (; i + 3 * 256 < nblk; i += 4 * 256) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + i + u * 256);
+            a[u] += v.x;
+            b[u] += v.y;
+        }
+    }
+    for (; i < nblk; i += 256) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + i);
+        a[0] += v.x;
+        b[0] += v.y;
+    }
+    double sa = (a[0] + a[1]) + (a[2] + a[3]), sb = (b[0] + b[1]) + (b[2] + b[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    __syncthreads();
+    if ((t & 31) == 0) {
+        wa[t >> 5] = sa;
+        wb[t >> 5] = sb;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double ta = 0.0, tb = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            ta += wa[k];
+            tb += wb[k];
+        }
+        scal[slot_a] += ta;
+        if (slot_b >= 0) scal[slot_b] += tb;
+        *ticket = 0u;
+    }
 }
 
 }  // namespace
@@ -336,10 +436,10 @@ k_tv_final(const float *__restrict__ z, const float *__restrict__ p, float *__re
 __global__ void __launch_bounds__(256)
 k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gx,
                const float *__restrict__ gp_next, float *__restrict__ gz, float *__restrict__ gp, int N,
-               const double *__restrict__ scal, double *__restrict__ part_lam)
+               double *scal, int slot_lam, double *__restrict__ part, unsigned *ticket)
 {
     const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
-    double contrib = 0.0;
+    float contrib = 0.0f;
     if (r < N && c < N) {
         const size_t NN = (size_t)N * N, j = (size_t)r * N + c;
         const float *zz = z + blockIdx.z * NN, *g = gx + blockIdx.z * NN;
@@ -356,75 +456,114 @@ k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const f
         float *ox = gp + blockIdx.z * 2 * NN, *oy = ox + NN;
         ox[j] = gnx[j] - lam * (c < N - 1 ? gsr - gs0 : 0.0f);
         oy[j] = gny[j] - lam * (r < N - 1 ? gsd - gs0 : 0.0f);
-        contrib = (double)gs0 * (double)tv_div(px, py, r, c, N);
+        contrib = gs0 * tv_div(px, py, r, c, N);
     }
-    block_sum_to(contrib, part_lam);
+    grid_sum2_to(contrib, 0.0f, part, ticket, scal, slot_lam, -1);
 }
 
-// Adjoint of one step p' = Pi(q), q = p + inv8 grad x, x = max(0, s), part a:
-// gq = J_Pi(q)^T gp_next, and partial sums of <gq, grad x> (the inv8 derivative).
-__global__ void __launch_bounds__(256)
-k_tv_step_bwd_a(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
-                float *__restrict__ gq, int N, const double *__restrict__ scal, double *__restrict__ part_inv8)
-{
-    const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
-    double contrib = 0.0;
-    if (r < N && c < N) {
-        const size_t NN = (size_t)N * N, j = (size_t)r * N + c;
-        const float *zz = z + blockIdx.z * NN;
-        const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
-        const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
-        const float2 q = tv_q(zz, px, py, r, c, N, lam, inv8);
-        const float *gnx = gp_next + blockIdx.z * 2 * NN, *gny = gnx + NN;
-        const float2 g = proj_adj(q, make_float2(gnx[j], gny[j]));
-        float *ox = gq + blockIdx.z * 2 * NN, *oy = ox + NN;
-        ox[j] = g.x;
-        oy[j] = g.y;
-        // grad x = (q - p) / inv8 without the division: recompute it
-        const float x0 = fmaxf(0.0f, tv_s(zz, px, py, r, c, N, lam));
-        const float gxv = c < N - 1 ? fmaxf(0.0f, tv_s(zz, px, py, r, c + 1, N, lam)) - x0 : 0.0f;
-        const float gyv = r < N - 1 ? fmaxf(0.0f, tv_s(zz, px, py, r + 1, c, N, lam)) - x0 : 0.0f;
-        contrib = (double)g.x * gxv + (double)g.y * gyv;
-    }
-    block_sum_to(contrib, part_inv8);
-}
+// Adjoint of one step p' = Pi(q), q = p + inv8 grad x, x = max(0, s),
+// s = z + lam div p, with the adjoint gp_next of p' flowing in from later:
+//   gq = J_Pi(q)^T gp_next;   gx = -inv8 div gq;   gs = gx [s > 0];
+//   gz += gs;   gp = gq - lam grad gs;
+// and the derivative terms <gq, grad x> (for inv8) and <gs, div p> (for
+// lam).  One block per BT_W x BT_H tile: p is staged with a halo of two,
+// s with a halo of one (one more column and row on the far side), gq with
+// a halo of one and gs one column and row past the tile, each phase
+// reading only shared memory and the phase before.
+constexpr int BT_W = 32, BT_H = 16;
+constexpr int BP_W = BT_W + 4, BP_H = BT_H + 4;   // p: origin (r0 - 2, c0 - 2)
+constexpr int BS_W = BT_W + 3, BS_H = BT_H + 3;   // s: origin (r0 - 1, c0 - 1)
+constexpr int BQ_W = BT_W + 2, BQ_H = BT_H + 2;   // gq: origin (r0 - 1, c0 - 1)
+constexpr int BG_W = BT_W + 1, BG_H = BT_H + 1;   // gs: origin (r0, c0)
 
-// Part b: gx = -inv8 div gq; gs = gx [s > 0]; gz += gs; gp = gq - lam grad gs;
-// partial sums of <gs, div p> (the lam derivative).
 __global__ void __launch_bounds__(256)
-k_tv_step_bwd_b(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gq,
-                float *__restrict__ gz, float *__restrict__ gp, int N, const double *__restrict__ scal,
-                double *__restrict__ part_lam)
+k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
+              float *__restrict__ gz, float *__restrict__ gp, int N, double *scal, int slot_inv8, int slot_lam,
+              double *__restrict__ part, unsigned *ticket)
 {
-    const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
-    double contrib = 0.0;
-    if (r < N && c < N) {
-        const size_t NN = (size_t)N * N, j = (size_t)r * N + c;
-        const float *zz = z + blockIdx.z * NN;
-        const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
-        const float *qx = gq + blockIdx.z * 2 * NN, *qy = qx + NN;
-        const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
-        auto gs_at = [&](int rr, int cc) {
-            const float gxv = -inv8 * tv_div(qx, qy, rr, cc, N);
-            return tv_s(zz, px, py, rr, cc, N, lam) > 0.0f ? gxv : 0.0f;
-        };
-        const float gs0 = gs_at(r, c);
-        const float gsr = c < N - 1 ? gs_at(r, c + 1) : 0.0f;
-        const float gsd = r < N - 1 ? gs_at(r + 1, c) : 0.0f;
-        gz[blockIdx.z * NN + j] += gs0;
-        float *ox = gp + blockIdx.z * 2 * NN, *oy = ox + NN;
-        ox[j] = qx[j] - lam * (c < N - 1 ? gsr - gs0 : 0.0f);
-        oy[j] = qy[j] - lam * (r < N - 1 ? gsd - gs0 : 0.0f);
-        contrib = (double)gs0 * (double)tv_div(px, py, r, c, N);
+    __shared__ float PX[BP_H][BP_W], PY[BP_H][BP_W], SS[BS_H][BS_W], QX[BQ_H][BQ_W], QY[BQ_H][BQ_W],
+        GS[BG_H][BG_W];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * BT_H, c0 = blockIdx.x * BT_W;
+    const size_t NN = (size_t)N * N;
+    z += blockIdx.z * NN;
+    gz += blockIdx.z * NN;
+    const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
+    const float *gnx = gp_next + blockIdx.z * 2 * NN, *gny = gnx + NN;
+    float *ox = gp + blockIdx.z * 2 * NN, *oy = ox + NN;
+    const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
+    auto inside = [&](int a, int b) { return (unsigned)a < (unsigned)N && (unsigned)b < (unsigned)N; };
+    // div p at image cell (a, b) from the staged p (zero outside the image)
+    auto div_p = [&](int a, int b) {
+        const int i = a - r0 + 2, j = b - c0 + 2;
+        return ((b < N - 1 ? PX[i][j] : 0.0f) - (b > 0 ? PX[i][j - 1] : 0.0f)) +
+               ((a < N - 1 ? PY[i][j] : 0.0f) - (a > 0 ? PY[i - 1][j] : 0.0f));
+    };
+
+    for (int k = t; k < BP_H * BP_W; k += 256) {
+        const int i = k / BP_W, j = k - i * BP_W, a = r0 - 2 + i, b = c0 - 2 + j;
+        const bool in = inside(a, b);
+        const size_t gi = (size_t)a * N + b;
+        PX[i][j] = in ? px[gi] : 0.0f;
+        PY[i][j] = in ? py[gi] : 0.0f;
     }
-    block_sum_to(contrib, part_lam);
+    for (int k = t; k < BS_H * BS_W; k += 256) {
+        const int i = k / BS_W, j = k - i * BS_W, a = r0 - 1 + i, b = c0 - 1 + j;
+        SS[i][j] = inside(a, b) ? z[(size_t)a * N + b] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = t; k < BS_H * BS_W; k += 256) {   // s = z + lam div p
+        const int i = k / BS_W, j = k - i * BS_W, a = r0 - 1 + i, b = c0 - 1 + j;
+        if (inside(a, b)) SS[i][j] = fmaf(lam, div_p(a, b), SS[i][j]);
+    }
+    __syncthreads();
+    float c_inv8 = 0.0f, c_lam = 0.0f;
+    for (int k = t; k < BQ_H * BQ_W; k += 256) {   // gq = J_Pi(q)^T gp_next
+        const int i = k / BQ_W, j = k - i * BQ_W, a = r0 - 1 + i, b = c0 - 1 + j;
+        float2 g = make_float2(0.0f, 0.0f);
+        if (inside(a, b)) {
+            const float x0 = fmaxf(0.0f, SS[i][j]);
+            const float gxv = b < N - 1 ? fmaxf(0.0f, SS[i][j + 1]) - x0 : 0.0f;
+            const float gyv = a < N - 1 ? fmaxf(0.0f, SS[i + 1][j]) - x0 : 0.0f;
+            const float2 q = make_float2(PX[i + 1][j + 1] + gxv * inv8, PY[i + 1][j + 1] + gyv * inv8);
+            const size_t gi = (size_t)a * N + b;
+            g = proj_adj(q, make_float2(gnx[gi], gny[gi]));
+            if (i >= 1 && i <= BT_H && j >= 1 && j <= BT_W) c_inv8 = fmaf(g.x, gxv, fmaf(g.y, gyv, c_inv8));
+        }
+        QX[i][j] = g.x;
+        QY[i][j] = g.y;
+    }
+    __syncthreads();
+    for (int k = t; k < BG_H * BG_W; k += 256) {   // gs = [s > 0] (-inv8 div gq)
+        const int i = k / BG_W, j = k - i * BG_W, a = r0 + i, b = c0 + j;
+        float v = 0.0f;
+        if (inside(a, b) && SS[i + 1][j + 1] > 0.0f) {
+            const float d = ((b < N - 1 ? QX[i + 1][j + 1] : 0.0f) - (b > 0 ? QX[i + 1][j] : 0.0f)) +
+                            ((a < N - 1 ? QY[i + 1][j + 1] : 0.0f) - (a > 0 ? QY[i][j + 1] : 0.0f));
+            v = -inv8 * d;
+        }
+        GS[i][j] = v;
+    }
+    __syncthreads();
+    for (int k = t; k < BT_H * BT_W; k += 256) {
+        const int i = k / BT_W, j = k - i * BT_W, a = r0 + i, b = c0 + j;
+        if (!inside(a, b)) continue;
+        const size_t gi = (size_t)a * N + b;
+        const float gs0 = GS[i][j];
+        gz[gi] += gs0;
+        ox[gi] = QX[i + 1][j + 1] - lam * (b < N - 1 ? GS[i][j + 1] - gs0 : 0.0f);
+        oy[gi] = QY[i + 1][j + 1] - lam * (a < N - 1 ? GS[i + 1][j] - gs0 : 0.0f);
+        c_lam = fmaf(gs0, div_p(a, b), c_lam);
+    }
+    grid_sum2_to(c_inv8, c_lam, part, ticket, scal, slot_inv8, slot_lam);
 }
 
 namespace {
 dim3 tv_px_grid(int n, int batch) { return dim3((n + 31) / 32, (n + 7) / 8, batch); }
 }
 
-size_t tv_px_blocks(int n, int batch) { return (size_t)((n + 31) / 32) * ((n + 7) / 8) * batch; }
+// partials (two doubles per block) of the adjoint kernels
+size_t tv_px_blocks(int n, int batch) { return 2 * (size_t)((n + 31) / 32) * ((n + 7) / 8) * batch; }
 
 void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int batch, const double *scal,
                     cudaStream_t st)
@@ -440,18 +579,21 @@ void launch_tv_final(const float *z, const float *p, float *x, int n, int batch,
 }
 
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, const double *scal, double *part_lam, cudaStream_t st)
+                         float *gp, int n, int batch, double *scal, int slot_lam, double *part, unsigned *ticket,
+                         cudaStream_t st)
 {
     counted();
-    k_tv_final_bwd<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gx, gp_next, gz, gp, n, scal, part_lam);
+    k_tv_final_bwd<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gx, gp_next, gz, gp, n, scal, slot_lam,
+                                                                  part, ticket);
 }
 
-void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gq, float *gz, float *gp,
-                        int n, int batch, const double *scal, double *part_inv8, double *part_lam, cudaStream_t st)
+void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
+                        int batch, double *scal, int slot_inv8, int slot_lam, double *part, unsigned *ticket,
+                        cudaStream_t st)
 {
-    counted(2);
-    k_tv_step_bwd_a<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gp_next, gq, n, scal, part_inv8);
-    k_tv_step_bwd_b<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gq, gz, gp, n, scal, part_lam);
+    counted();
+    k_tv_step_bwd<<<dim3((n + BT_W - 1) / BT_W, (n + BT_H - 1) / BT_H, batch), dim3(32, 8), 0, st>>>(
+        z, p, gp_next, gz, gp, n, scal, slot_inv8, slot_lam, part, ticket);
 }
 
 }  // namespace ctpd

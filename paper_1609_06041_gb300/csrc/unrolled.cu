@@ -23,8 +23,8 @@ using namespace ctpd;
 namespace {
 
 struct UL {
-    size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gq, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa, pb,
-        tcorr, tacc, orb, total;
+    size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa,
+        tcorr, tacc, orb, ticket, total;
     size_t ck_stride;   // floats per checkpoint
 };
 
@@ -47,7 +47,6 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.gz = o;    o += a256(F * S * J);
     L.gp = o;    o += a256(F * S * 2 * J);
     L.gp2 = o;   o += a256(F * S * 2 * J);
-    L.gq = o;    o += a256(F * S * 2 * J);
     L.gm = o;    o += a256(F * S * I);
     L.gmb = o;   o += a256(F * S * I);
     L.gmu = o;   o += a256(F * S * I);
@@ -57,8 +56,8 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.vv = o;    o += a256(F * S * I);
     L.traj = o;  o += a256(F * (size_t)(ntv + 1) * S * 2 * J);
     L.pa = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
-    L.pb = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
-    L.tcorr = o; o += a256(sizeof(double) * tapcorr_partials(S * g->n_views, half));
+    L.ticket = o; o += a256(sizeof(unsigned));
+    L.tcorr = o; o += a256(tapcorr_partial_bytes(S * g->n_views, g->n_bins, half));
     L.tacc = o;  o += a256(sizeof(double) * (2 * (size_t)half - 1));
     L.orb = o;   o += a256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, S) : 1));
     L.total = o;
@@ -112,6 +111,16 @@ void set_scalars(double *scal, double *scal2, double tau, double sigma, double b
     launch_scalars(scal2, SC_SET, -1.0, 0, 0, S_TAU, st);       // backprojection that adds
 }
 
+// The prox steps of one iteration run as one register-resident launch
+// (launch_tv) when there are 1 .. tv_max_steps() of them and lambda > 0
+// (otherwise as whole-image single steps); both give the same iterates.
+constexpr int TV_UNROLL_ROWS = 48;   // interior rows per tile: the batch fills the GPU
+bool tv_fused(double tau, double beta, int mode, int ntv)
+{
+    const double lam = mode == CT_LOWDOSE ? tau * beta : tau;
+    return ntv >= 1 && ntv <= tv_max_steps() && lam > 0.0;
+}
+
 void backproject(const Geometry *g, const float *y, float *out, int mode, const float *xin, const double *scal,
                  int S, char *ws, const UL &L, cudaStream_t st)
 {
@@ -161,9 +170,16 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
     cudaMemsetAsync(c0.mu, 0, sizeof(float) * S * I, st);
     cudaMemsetAsync(c0.p, 0, sizeof(float) * S * 2 * J, st);
     launch_filter_fft(g, hhat, b, c0.mubar, nullptr, nullptr, 1, scal, S, st);      // mubar_0 = -sigma D b
+    const bool fused = tv_fused(tau, beta, mode, tv_iters);
     for (int k = 0; k < iters; ++k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
         backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);                       // z = x - tau A^T mubar
+        if (fused) {
+            launch_tv(z, c.p, n.p, n.x, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 1, scal, st, false, S);
+            launch_project_bands(g, n.x, band, S, st);
+            launch_dual_fft_batched(g, hhat, band, b, c.mu, n.mu, n.mubar, winv, lowdose, scal, S, st);
+            continue;
+        }
         if (tv_iters == 0) {
             cudaMemcpyAsync(n.p, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
         } else {
@@ -210,16 +226,18 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     const float *winv = (const float *)(ws + L.winv);
     float *z = (float *)(ws + L.z), *band = (float *)(ws + L.band);
     float *gx = (float *)(ws + L.gx), *gz = (float *)(ws + L.gz);
-    float *gp = (float *)(ws + L.gp), *gp2 = (float *)(ws + L.gp2), *gq = (float *)(ws + L.gq);
+    float *gp = (float *)(ws + L.gp), *gp2 = (float *)(ws + L.gp2);
     float *gm = (float *)(ws + L.gm), *gmb = (float *)(ws + L.gmb), *gmu = (float *)(ws + L.gmu);
     float *gr = (float *)(ws + L.gr), *gm1 = (float *)(ws + L.gm1), *rr = (float *)(ws + L.rr),
           *vv = (float *)(ws + L.vv);
     float *traj = (float *)(ws + L.traj);
-    double *pa = (double *)(ws + L.pa), *pb = (double *)(ws + L.pb);
-    double *tcorr = (double *)(ws + L.tcorr), *tacc = (double *)(ws + L.tacc);
-    const size_t npx = tv_px_blocks(N, S);
+    double *pa = (double *)(ws + L.pa);
+    unsigned *ticket = (unsigned *)(ws + L.ticket);
+    float *tcorr = (float *)(ws + L.tcorr);
+    double *tacc = (double *)(ws + L.tacc);
     const int nl = 2 * half_len - 1;
     const double lam = lowdose ? tau * beta : tau;
+    const bool fused = tv_fused(tau, beta, mode, tv_iters);
 
     // the scalars of the forward pass are still in the workspace; reset the accumulators
     set_scalars(scal, scal2, tau, sigma, beta, mode, st);
@@ -227,30 +245,33 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     cudaMemsetAsync(gmb, 0, sizeof(float) * S * I, st);
     cudaMemsetAsync(gp, 0, sizeof(float) * S * 2 * J, st);
     cudaMemsetAsync(tacc, 0, sizeof(double) * nl, st);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
     cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
         // recompute z_k and the prox trajectory p_k = traj[0] .. traj[n_tv]
         backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);
         cudaMemcpyAsync(traj, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
-        for (int l = 0; l < tv_iters; ++l)
-            launch_tv_step(z, traj + (size_t)l * S * 2 * J, traj + (size_t)(l + 1) * S * 2 * J, N, S, scal, st);
+        if (fused)
+            launch_tv(z, traj, traj + (size_t)tv_iters * S * 2 * J, nullptr, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 0,
+                      scal, st, false, S, traj + (size_t)S * 2 * J);
+        else
+            for (int l = 0; l < tv_iters; ++l)
+                launch_tv_step(z, traj + (size_t)l * S * 2 * J, traj + (size_t)(l + 1) * S * 2 * J, N, S, scal, st);
         // adjoint of the dual step (needs A x_{k+1} for the residual)
         launch_project_bands(g, n.x, band, S, st);
         launch_dual_bwd_fft(g, hhat, band, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv, lowdose, scal, S, st);
-        launch_tapcorr_acc(gm1, rr, S * V, g->n_bins, half_len, sigma, tcorr, tacc, st);
-        if (lowdose) launch_tapcorr_acc(gmb, vv, S * V, g->n_bins, half_len, -sigma, tcorr, tacc, st);
+        launch_tapcorr_acc(gm1, rr, sigma, lowdose ? gmb : nullptr, vv, -sigma, S * V, g->n_bins, half_len, tcorr,
+                           tacc, st);
         // dL/dx_{k+1} += A^T dL/dr  (into gz, then swapped)
         backproject(g, gr, gz, 1, gx, scal2, S, ws, L, st);
         std::swap(gx, gz);
         // adjoint of the prox: final step, then the n_tv steps in reverse
         const float *trn = traj + (size_t)tv_iters * S * 2 * J;
-        launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, pb, st);
-        launch_sum_partials(pb, npx, scal, U_LAMACC, 1.0, st);
+        launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, U_LAMACC, pa, ticket, st);
         for (int l = tv_iters - 1; l >= 0; --l) {
-            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gq, gz, gp, N, S, scal, pa, pb, st);
-            launch_sum_partials(pa, npx, scal, U_INV8ACC, 1.0, st);
-            launch_sum_partials(pb, npx, scal, U_LAMACC, 1.0, st);
+            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gz, gp, N, S, scal, U_INV8ACC, U_LAMACC, pa,
+                               ticket, st);
             std::swap(gp, gp2);
         }
         std::swap(gp, gp2);   // gp: dL/dp_k
@@ -261,7 +282,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
         std::swap(gm, gmu);   // dL/dmu_k
     }
     // mubar_0 = -sigma D b
-    launch_tapcorr_acc(gmb, b, S * V, g->n_bins, half_len, -sigma, tcorr, tacc, st);
+    launch_tapcorr_acc(gmb, b, -sigma, nullptr, nullptr, 0.0, S * V, g->n_bins, half_len, tcorr, tacc, st);
     // dL/dbeta = dL/dlambda dlambda/dbeta, dL/dlambda = lamacc + inv8acc d(1/(8 lam))/dlam
     if (lam > 0.0) launch_scalars(scal, SC_AXPY_SLOT, -1.0 / (8.0 * lam * lam), (double)U_INV8ACC, 0, U_LAMACC, st);
     launch_grad_out(tacc, nl, scal, U_LAMACC, lowdose ? tau : 0.0, grad, st);
