@@ -219,15 +219,17 @@ size_t tv_px_blocks(int n, int batch);
 void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int batch, const double *scal,
                     cudaStream_t st);
 void launch_tv_final(const float *z, const float *p, float *x, int n, int batch, const double *scal, cudaStream_t st);
-// The adjoints add their lambda (and inv8) derivative terms into scal[slot_*]
-// through the block partials part[tv_px_blocks] (doubles) and a zeroed ticket counter,
-// which the last block resets.
+// The adjoints write their block sums of the inv8 and lambda derivative
+// terms as pairs into part[tv_px_blocks] (doubles; the final step's inv8
+// terms are 0); launch_pair_sums adds the pairs of many launches into two
+// scalar slots, deterministically (scratch: pair_sums_scratch_doubles()).
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, double *scal, int slot_lam, double *part, unsigned *ticket,
-                         cudaStream_t st);
+                         float *gp, int n, int batch, const double *scal, double *part, cudaStream_t st);
 void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
-                        int batch, double *scal, int slot_inv8, int slot_lam, double *part, unsigned *ticket,
-                        cudaStream_t st);
+                        int batch, const double *scal, double *part, cudaStream_t st);
+size_t pair_sums_scratch_doubles();
+void launch_pair_sums(const double *part, size_t npairs, double *scratch, double *scal, int slot_a, int slot_b,
+                      cudaStream_t st);
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started
 // dual field p = (px, py)), temporally blocked tiles held in registers.

@@ -316,20 +316,15 @@ __device__ __forceinline__ float2 proj_adj(float2 q, float2 g)
     return make_float2((g.x - hx * d) * inv, (g.y - hy * d) * inv);
 }
 
-// Adds the per-thread float terms va (vb) of the whole grid into
-// scal[slot_a] (scal[slot_b]), in double, deterministically: a fixed
-// shuffle tree per warp (float), the block's warp sums in order (double)
-// into part[2 block], part[2 block + 1]; the last block to finish (ticket
-// counter) adds the partials in block order, adds the totals to the slots
-// and resets the counter.  FP64 arithmetic is slow on this GPU, so only the
-// per-warp sums and the final pass are double.  slot_b < 0: one value.
-// Blocks of 256 threads.
-__device__ __forceinline__ void grid_sum2_to(float va, float vb, double *part, unsigned *ticket, double *scal,
-                                             int slot_a, int slot_b)
+// Block sums of the per-thread float terms va, vb: a fixed shuffle tree per
+// warp (float), then the block's warp sums in order (double) into
+// part[2 block], part[2 block + 1].  FP64 arithmetic is slow on this GPU,
+// so only the per-warp sums are double; launch_pair_sums adds the partials
+// of many launches at the end.  Blocks of 256 threads.
+__device__ __forceinline__ void block_pair_to(float va, float vb, double *part)
 {
     __shared__ double wa[8], wb[8];
-    __shared__ bool last;
-    const int t = threadIdx.y * blockDim.x + threadIdx.x, nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -350,50 +345,6 @@ __device__ __forceinline__ void grid_sum2_to(float va, float vb, double *part, u
         }
         part[2 * blk] = sa;
         part[2 * blk + 1] = sb;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == (unsigned)nblk - 1u;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // four independent runs per thread, so the loads overlap
-    double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
-    int i = t;
-    for (; i + 3 * 256 < nblk; i += 4 * 256) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + i + u * 256);
-            a[u] += v.x;
-            b[u] += v.y;
-        }
-    }
-    for (; i < nblk; i += 256) {
-        const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + i);
-        a[0] += v.x;
-        b[0] += v.y;
-    }
-    double sa = (a[0] + a[1]) + (a[2] + a[3]), sb = (b[0] + b[1]) + (b[2] + b[3]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_down_sync(0xffffffffu, sa, o);
-        sb += __shfl_down_sync(0xffffffffu, sb, o);
-    }
-    __syncthreads();
-    if ((t & 31) == 0) {
-        wa[t >> 5] = sa;
-        wb[t >> 5] = sb;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double ta = 0.0, tb = 0.0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            ta += wa[k];
-            tb += wb[k];
-        }
-        scal[slot_a] += ta;
-        if (slot_b >= 0) scal[slot_b] += tb;
-        *ticket = 0u;
     }
 }
 
@@ -436,7 +387,7 @@ k_tv_final(const float *__restrict__ z, const float *__restrict__ p, float *__re
 __global__ void __launch_bounds__(256)
 k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gx,
                const float *__restrict__ gp_next, float *__restrict__ gz, float *__restrict__ gp, int N,
-               double *scal, int slot_lam, double *__restrict__ part, unsigned *ticket)
+               const double *__restrict__ scal, double *__restrict__ part)
 {
     const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
     float contrib = 0.0f;
@@ -458,7 +409,7 @@ k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const f
         oy[j] = gny[j] - lam * (r < N - 1 ? gsd - gs0 : 0.0f);
         contrib = gs0 * tv_div(px, py, r, c, N);
     }
-    grid_sum2_to(contrib, 0.0f, part, ticket, scal, slot_lam, -1);
+    block_pair_to(0.0f, contrib, part);
 }
 
 // Adjoint of one step p' = Pi(q), q = p + inv8 grad x, x = max(0, s),
@@ -469,21 +420,21 @@ k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const f
 // lam).  One block per BT_W x BT_H tile: p is staged with a halo of two,
 // s with a halo of one (one more column and row on the far side), gq with
 // a halo of one and gs one column and row past the tile, each phase
-// reading only shared memory and the phase before.
-constexpr int BT_W = 32, BT_H = 16;
-constexpr int BP_W = BT_W + 4, BP_H = BT_H + 4;   // p: origin (r0 - 2, c0 - 2)
-constexpr int BS_W = BT_W + 3, BS_H = BT_H + 3;   // s: origin (r0 - 1, c0 - 1)
-constexpr int BQ_W = BT_W + 2, BQ_H = BT_H + 2;   // gq: origin (r0 - 1, c0 - 1)
-constexpr int BG_W = BT_W + 1, BG_H = BT_H + 1;   // gs: origin (r0, c0)
+// reading only shared memory and the phase before.  The tile is 28 columns
+// wide so that every staged row fits one warp: lane = column, warp = row.
+constexpr int BT_W = 28, BT_H = 16;
+constexpr int BP_H = BT_H + 4;   // p: origin (r0 - 2, c0 - 2), 32 columns
+constexpr int BS_H = BT_H + 3;   // s: origin (r0 - 1, c0 - 1), 31 columns
+constexpr int BQ_H = BT_H + 2;   // gq: origin (r0 - 1, c0 - 1), 30 columns
+constexpr int BG_H = BT_H + 1;   // gs: origin (r0, c0), 29 columns
 
 __global__ void __launch_bounds__(256)
 k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
-              float *__restrict__ gz, float *__restrict__ gp, int N, double *scal, int slot_inv8, int slot_lam,
-              double *__restrict__ part, unsigned *ticket)
+              float *__restrict__ gz, float *__restrict__ gp, int N, const double *__restrict__ scal,
+              double *__restrict__ part)
 {
-    __shared__ float PX[BP_H][BP_W], PY[BP_H][BP_W], SS[BS_H][BS_W], QX[BQ_H][BQ_W], QY[BQ_H][BQ_W],
-        GS[BG_H][BG_W];
-    const int t = threadIdx.y * 32 + threadIdx.x;
+    __shared__ float PX[BP_H][32], PY[BP_H][32], SS[BS_H][32], QX[BQ_H][32], QY[BQ_H][32], GS[BG_H][32];
+    const int lx = threadIdx.x, ly = threadIdx.y;
     const int r0 = blockIdx.y * BT_H, c0 = blockIdx.x * BT_W;
     const size_t NN = (size_t)N * N;
     z += blockIdx.z * NN;
@@ -492,78 +443,103 @@ k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const fl
     const float *gnx = gp_next + blockIdx.z * 2 * NN, *gny = gnx + NN;
     float *ox = gp + blockIdx.z * 2 * NN, *oy = ox + NN;
     const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
-    auto inside = [&](int a, int b) { return (unsigned)a < (unsigned)N && (unsigned)b < (unsigned)N; };
-    // div p at image cell (a, b) from the staged p (zero outside the image)
-    auto div_p = [&](int a, int b) {
-        const int i = a - r0 + 2, j = b - c0 + 2;
+    // image column of this lane in each region, and whether it is inside
+    const int bp = c0 - 2 + lx, bs = c0 - 1 + lx, bg = c0 + lx;
+    const bool inp = (unsigned)bp < (unsigned)N, ins = lx < 31 && (unsigned)bs < (unsigned)N;
+    const bool inq = lx < 30 && (unsigned)bs < (unsigned)N, ing = lx < 29 && (unsigned)bg < (unsigned)N;
+    // div p at image cell (a, b) = region p cell (i, j) (zero outside the image)
+    auto div_p = [&](int i, int j, int a, int b) {
         return ((b < N - 1 ? PX[i][j] : 0.0f) - (b > 0 ? PX[i][j - 1] : 0.0f)) +
                ((a < N - 1 ? PY[i][j] : 0.0f) - (a > 0 ? PY[i - 1][j] : 0.0f));
     };
 
-    for (int k = t; k < BP_H * BP_W; k += 256) {
-        const int i = k / BP_W, j = k - i * BP_W, a = r0 - 2 + i, b = c0 - 2 + j;
-        const bool in = inside(a, b);
-        const size_t gi = (size_t)a * N + b;
-        PX[i][j] = in ? px[gi] : 0.0f;
-        PY[i][j] = in ? py[gi] : 0.0f;
+    for (int i = ly; i < BP_H; i += 8) {
+        const int a = r0 - 2 + i;
+        const bool in = inp && (unsigned)a < (unsigned)N;
+        const size_t gi = (size_t)a * N + bp;
+        PX[i][lx] = in ? px[gi] : 0.0f;
+        PY[i][lx] = in ? py[gi] : 0.0f;
     }
-    for (int k = t; k < BS_H * BS_W; k += 256) {
-        const int i = k / BS_W, j = k - i * BS_W, a = r0 - 1 + i, b = c0 - 1 + j;
-        SS[i][j] = inside(a, b) ? z[(size_t)a * N + b] : 0.0f;
+    // every global load of the block goes out before the first barrier
+    float zr[3], gnr[3][2], gzr[2];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const int i = ly + 8 * m, a = r0 - 1 + i;
+        const bool in = ins && (unsigned)a < (unsigned)N;
+        const size_t gi = (size_t)a * N + bs;
+        zr[m] = (i < BS_H && in) ? z[gi] : 0.0f;
+        gnr[m][0] = (i < BQ_H && lx < 30 && in) ? gnx[gi] : 0.0f;
+        gnr[m][1] = (i < BQ_H && lx < 30 && in) ? gny[gi] : 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int a = r0 + ly + 8 * m;
+        gzr[m] = (lx < BT_W && bg < N && a < N) ? gz[(size_t)a * N + bg] : 0.0f;
     }
     __syncthreads();
-    for (int k = t; k < BS_H * BS_W; k += 256) {   // s = z + lam div p
-        const int i = k / BS_W, j = k - i * BS_W, a = r0 - 1 + i, b = c0 - 1 + j;
-        if (inside(a, b)) SS[i][j] = fmaf(lam, div_p(a, b), SS[i][j]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {   // s = z + lam div p
+        const int i = ly + 8 * m, a = r0 - 1 + i;
+        if (i < BS_H && lx < 31)
+            SS[i][lx] = (ins && (unsigned)a < (unsigned)N) ? fmaf(lam, div_p(i + 1, lx + 1, a, bs), zr[m]) : 0.0f;
     }
     __syncthreads();
     float c_inv8 = 0.0f, c_lam = 0.0f;
-    for (int k = t; k < BQ_H * BQ_W; k += 256) {   // gq = J_Pi(q)^T gp_next
-        const int i = k / BQ_W, j = k - i * BQ_W, a = r0 - 1 + i, b = c0 - 1 + j;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {   // gq = J_Pi(q)^T gp_next
+        const int i = ly + 8 * m, a = r0 - 1 + i;
+        if (i >= BQ_H) break;
         float2 g = make_float2(0.0f, 0.0f);
-        if (inside(a, b)) {
-            const float x0 = fmaxf(0.0f, SS[i][j]);
-            const float gxv = b < N - 1 ? fmaxf(0.0f, SS[i][j + 1]) - x0 : 0.0f;
-            const float gyv = a < N - 1 ? fmaxf(0.0f, SS[i + 1][j]) - x0 : 0.0f;
-            const float2 q = make_float2(PX[i + 1][j + 1] + gxv * inv8, PY[i + 1][j + 1] + gyv * inv8);
-            const size_t gi = (size_t)a * N + b;
-            g = proj_adj(q, make_float2(gnx[gi], gny[gi]));
-            if (i >= 1 && i <= BT_H && j >= 1 && j <= BT_W) c_inv8 = fmaf(g.x, gxv, fmaf(g.y, gyv, c_inv8));
+        if (inq && (unsigned)a < (unsigned)N) {
+            const float x0 = fmaxf(0.0f, SS[i][lx]);
+            const float gxv = bs < N - 1 ? fmaxf(0.0f, SS[i][lx + 1]) - x0 : 0.0f;
+            const float gyv = a < N - 1 ? fmaxf(0.0f, SS[i + 1][lx]) - x0 : 0.0f;
+            const float2 q = make_float2(PX[i + 1][lx + 1] + gxv * inv8, PY[i + 1][lx + 1] + gyv * inv8);
+            g = proj_adj(q, make_float2(gnr[m][0], gnr[m][1]));
+            if (i >= 1 && i <= BT_H && lx >= 1 && lx <= BT_W) c_inv8 = fmaf(g.x, gxv, fmaf(g.y, gyv, c_inv8));
         }
-        QX[i][j] = g.x;
-        QY[i][j] = g.y;
+        if (lx < 30) {
+            QX[i][lx] = g.x;
+            QY[i][lx] = g.y;
+        }
     }
     __syncthreads();
-    for (int k = t; k < BG_H * BG_W; k += 256) {   // gs = [s > 0] (-inv8 div gq)
-        const int i = k / BG_W, j = k - i * BG_W, a = r0 + i, b = c0 + j;
+    for (int i = ly; i < BG_H; i += 8) {   // gs = [s > 0] (-inv8 div gq)
+        const int a = r0 + i;
         float v = 0.0f;
-        if (inside(a, b) && SS[i + 1][j + 1] > 0.0f) {
-            const float d = ((b < N - 1 ? QX[i + 1][j + 1] : 0.0f) - (b > 0 ? QX[i + 1][j] : 0.0f)) +
-                            ((a < N - 1 ? QY[i + 1][j + 1] : 0.0f) - (a > 0 ? QY[i][j + 1] : 0.0f));
+        if (ing && (unsigned)a < (unsigned)N && SS[i + 1][lx + 1] > 0.0f) {
+            const float d = ((bg < N - 1 ? QX[i + 1][lx + 1] : 0.0f) - (bg > 0 ? QX[i + 1][lx] : 0.0f)) +
+                            ((a < N - 1 ? QY[i + 1][lx + 1] : 0.0f) - (a > 0 ? QY[i][lx + 1] : 0.0f));
             v = -inv8 * d;
         }
-        GS[i][j] = v;
+        if (lx < 29) GS[i][lx] = v;
     }
     __syncthreads();
-    for (int k = t; k < BT_H * BT_W; k += 256) {
-        const int i = k / BT_W, j = k - i * BT_W, a = r0 + i, b = c0 + j;
-        if (!inside(a, b)) continue;
-        const size_t gi = (size_t)a * N + b;
-        const float gs0 = GS[i][j];
-        gz[gi] += gs0;
-        ox[gi] = QX[i + 1][j + 1] - lam * (b < N - 1 ? GS[i][j + 1] - gs0 : 0.0f);
-        oy[gi] = QY[i + 1][j + 1] - lam * (a < N - 1 ? GS[i + 1][j] - gs0 : 0.0f);
-        c_lam = fmaf(gs0, div_p(a, b), c_lam);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int i = ly + 8 * m, a = r0 + i;
+        if (lx < BT_W && bg < N && a < N) {
+            const size_t gi = (size_t)a * N + bg;
+            const float gs0 = GS[i][lx];
+            gz[gi] = gzr[m] + gs0;
+            ox[gi] = QX[i + 1][lx + 1] - lam * (bg < N - 1 ? GS[i][lx + 1] - gs0 : 0.0f);
+            oy[gi] = QY[i + 1][lx + 1] - lam * (a < N - 1 ? GS[i + 1][lx] - gs0 : 0.0f);
+            c_lam = fmaf(gs0, div_p(i + 2, lx + 2, a, bg), c_lam);
+        }
     }
-    grid_sum2_to(c_inv8, c_lam, part, ticket, scal, slot_inv8, slot_lam);
+    block_pair_to(c_inv8, c_lam, part);
 }
 
 namespace {
 dim3 tv_px_grid(int n, int batch) { return dim3((n + 31) / 32, (n + 7) / 8, batch); }
 }
 
-// partials (two doubles per block) of the adjoint kernels
-size_t tv_px_blocks(int n, int batch) { return 2 * (size_t)((n + 31) / 32) * ((n + 7) / 8) * batch; }
+// partials (two doubles per block) of the adjoint kernels: the larger grid
+size_t tv_px_blocks(int n, int batch)
+{
+    const size_t px = (size_t)((n + 31) / 32) * ((n + 7) / 8), tl = (size_t)((n + BT_W - 1) / BT_W) * ((n + BT_H - 1) / BT_H);
+    return 2 * std::max(px, tl) * batch;
+}
 
 void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int batch, const double *scal,
                     cudaStream_t st)
@@ -579,21 +555,71 @@ void launch_tv_final(const float *z, const float *p, float *x, int n, int batch,
 }
 
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, double *scal, int slot_lam, double *part, unsigned *ticket,
-                         cudaStream_t st)
+                         float *gp, int n, int batch, const double *scal, double *part, cudaStream_t st)
 {
     counted();
-    k_tv_final_bwd<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gx, gp_next, gz, gp, n, scal, slot_lam,
-                                                                  part, ticket);
+    k_tv_final_bwd<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gx, gp_next, gz, gp, n, scal, part);
 }
 
 void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
-                        int batch, double *scal, int slot_inv8, int slot_lam, double *part, unsigned *ticket,
-                        cudaStream_t st)
+                        int batch, const double *scal, double *part, cudaStream_t st)
 {
     counted();
     k_tv_step_bwd<<<dim3((n + BT_W - 1) / BT_W, (n + BT_H - 1) / BT_H, batch), dim3(32, 8), 0, st>>>(
-        z, p, gp_next, gz, gp, n, scal, slot_inv8, slot_lam, part, ticket);
+        z, p, gp_next, gz, gp, n, scal, part);
+}
+
+// scal[slot_a] += sum of part[2 i], scal[slot_b] += sum of part[2 i + 1],
+// i < npairs, in a fixed order: PS_BLOCKS blocks add contiguous runs
+// (double), one block adds their results in order.
+constexpr int PS_BLOCKS = 152;
+
+__global__ void __launch_bounds__(256) k_pair_sums(const double *__restrict__ part, size_t npairs, double *out)
+{
+    const size_t per = (npairs + gridDim.x - 1) / gridDim.x, lo = blockIdx.x * per;
+    const size_t hi = lo + per < npairs ? lo + per : npairs;
+    double a = 0.0, b = 0.0;
+    for (size_t i = lo + threadIdx.x; i < hi; i += 256) {
+        const double2 v = reinterpret_cast<const double2 *>(part)[i];
+        a += v.x;
+        b += v.y;
+    }
+    __shared__ double ra[256], rb[256];
+    ra[threadIdx.x] = a;
+    rb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ra[threadIdx.x] += ra[threadIdx.x + o];
+            rb[threadIdx.x] += rb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = ra[0];
+        out[2 * blockIdx.x + 1] = rb[0];
+    }
+}
+
+__global__ void k_pair_final(const double *__restrict__ r, int nb, double *scal, int slot_a, int slot_b)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        a += r[2 * i];
+        b += r[2 * i + 1];
+    }
+    scal[slot_a] += a;
+    scal[slot_b] += b;
+}
+
+size_t pair_sums_scratch_doubles() { return 2 * PS_BLOCKS; }
+
+void launch_pair_sums(const double *part, size_t npairs, double *scratch, double *scal, int slot_a, int slot_b,
+                      cudaStream_t st)
+{
+    counted(2);
+    k_pair_sums<<<PS_BLOCKS, 256, 0, st>>>(part, npairs, scratch);
+    k_pair_final<<<1, 1, 0, st>>>(scratch, PS_BLOCKS, scal, slot_a, slot_b);
 }
 
 }  // namespace ctpd

@@ -24,7 +24,7 @@ namespace {
 
 struct UL {
     size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa,
-        tcorr, tacc, orb, ticket, total;
+        tcorr, tacc, orb, psum, total;
     size_t ck_stride;   // floats per checkpoint
 };
 
@@ -55,8 +55,9 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.rr = o;    o += a256(F * S * I);
     L.vv = o;    o += a256(F * S * I);
     L.traj = o;  o += a256(F * (size_t)(ntv + 1) * S * 2 * J);
-    L.pa = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S));
-    L.ticket = o; o += a256(sizeof(unsigned));
+    // block pairs of every prox adjoint launch of the backward pass
+    L.pa = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S) * (size_t)iters * (ntv + 1));
+    L.psum = o;  o += a256(sizeof(double) * pair_sums_scratch_doubles());
     L.tcorr = o; o += a256(tapcorr_partial_bytes(S * g->n_views, g->n_bins, half));
     L.tacc = o;  o += a256(sizeof(double) * (2 * (size_t)half - 1));
     L.orb = o;   o += a256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, S) : 1));
@@ -231,8 +232,8 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     float *gr = (float *)(ws + L.gr), *gm1 = (float *)(ws + L.gm1), *rr = (float *)(ws + L.rr),
           *vv = (float *)(ws + L.vv);
     float *traj = (float *)(ws + L.traj);
-    double *pa = (double *)(ws + L.pa);
-    unsigned *ticket = (unsigned *)(ws + L.ticket);
+    double *pa = (double *)(ws + L.pa), *psum = (double *)(ws + L.psum);
+    const size_t npx = tv_px_blocks(N, S), ncall = (size_t)iters * (tv_iters + 1);
     float *tcorr = (float *)(ws + L.tcorr);
     double *tacc = (double *)(ws + L.tacc);
     const int nl = 2 * half_len - 1;
@@ -245,7 +246,8 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     cudaMemsetAsync(gmb, 0, sizeof(float) * S * I, st);
     cudaMemsetAsync(gp, 0, sizeof(float) * S * 2 * J, st);
     cudaMemsetAsync(tacc, 0, sizeof(double) * nl, st);
-    cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(pa, 0, sizeof(double) * npx * ncall, st);
+    double *part = pa;   // the next launch's block pairs
     cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
@@ -268,10 +270,11 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
         std::swap(gx, gz);
         // adjoint of the prox: final step, then the n_tv steps in reverse
         const float *trn = traj + (size_t)tv_iters * S * 2 * J;
-        launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, U_LAMACC, pa, ticket, st);
+        launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, part, st);
+        part += npx;
         for (int l = tv_iters - 1; l >= 0; --l) {
-            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gz, gp, N, S, scal, U_INV8ACC, U_LAMACC, pa,
-                               ticket, st);
+            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gz, gp, N, S, scal, part, st);
+            part += npx;
             std::swap(gp, gp2);
         }
         std::swap(gp, gp2);   // gp: dL/dp_k
@@ -283,6 +286,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     }
     // mubar_0 = -sigma D b
     launch_tapcorr_acc(gmb, b, -sigma, nullptr, nullptr, 0.0, S * V, g->n_bins, half_len, tcorr, tacc, st);
+    launch_pair_sums(pa, npx * ncall / 2, psum, scal, U_INV8ACC, U_LAMACC, st);
     // dL/dbeta = dL/dlambda dlambda/dbeta, dL/dlambda = lamacc + inv8acc d(1/(8 lam))/dlam
     if (lam > 0.0) launch_scalars(scal, SC_AXPY_SLOT, -1.0 / (8.0 * lam * lam), (double)U_INV8ACC, 0, U_LAMACC, st);
     launch_grad_out(tacc, nl, scal, U_LAMACC, lowdose ? tau : 0.0, grad, st);

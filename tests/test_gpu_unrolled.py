@@ -85,6 +85,54 @@ def test_unrolled_gradients_match_fp64_finite_differences():
         assert got == pytest.approx(fd, rel=3e-3)
 
 
+@pytest.mark.parametrize("case", [
+    # 150 taps: 299 lags, two passes of the correlation's lag loop
+    dict(mode=0, N=20, V=24, B=170, S=2, K=3, ntv=4, half=150),
+    # Algorithm 2: one correlation pair per iteration, lambda = tau
+    dict(mode=1, N=24, V=12, B=35, S=2, K=4, ntv=5, half=8),
+    # no prox steps: the whole-image single-step path instead of the tiled one
+    dict(mode=0, N=24, V=30, B=35, S=1, K=4, ntv=0, half=8),
+], ids=["lowdose_299_lags", "fewview", "no_tv_steps"])
+def test_unrolled_gradients_more_cases(case):
+    P = need_gpu()
+    import torch
+    c = case
+    N, V, B, S, K, ntv, half, mode = c["N"], c["V"], c["B"], c["S"], c["K"], c["ntv"], c["half"], c["mode"]
+    xt, bs, ws = make_batch(N, V, B, S, 11)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    if mode == 1:   # noiseless data of the phantoms, no weights
+        bs = np.stack([f32(O.project(xt[s], V, B)) for s in range(S)])
+    sigma, beta = 0.5, 0.05
+    g = P.Geometry(N, V, B)
+    t = to_gpu(taps).requires_grad_(True)
+    bt = torch.tensor(beta, device="cuda", requires_grad=True)
+    wg = to_gpu(ws) if mode == 0 else None
+    x = P.UnrolledPDTV.apply(t, bt, g, to_gpu(bs), wg, tau, sigma, mode, K, ntv)
+    loss = ((x - to_gpu(xt)) ** 2).sum() / (S * N * N)
+    loss.backward()
+    gt = to_np(t.grad)
+
+    def oloss(tp, be):
+        L = 0.0
+        for s in range(S):
+            st, _ = O.pdtv(bs[s], ws[s] if mode == 0 else None, tp, mode, be, tau, sigma, ntv, K, N)
+            L += float(((st.x - xt[s]) ** 2).sum())
+        return L / (S * N * N)
+
+    L0 = oloss(taps, beta)
+    assert abs(float(loss.detach()) - L0) <= 1e-4 * L0
+    if mode == 0 and ntv > 0:
+        hb = 1e-3 * beta
+        fd_b = (oloss(taps, beta + hb) - oloss(taps, beta - hb)) / (2 * hb)
+        assert float(bt.grad) == pytest.approx(fd_b, rel=1e-4)
+    rng = np.random.default_rng(1)
+    for d in [rng.standard_normal(taps.size), np.eye(taps.size)[half - 1], np.eye(taps.size)[0],
+              np.eye(taps.size)[-1]]:
+        eps = 1e-4 * np.abs(taps).max() / np.abs(d).max()
+        fd = (oloss(taps + eps * d, beta) - oloss(taps - eps * d, beta)) / (2 * eps)
+        assert float(gt @ d) == pytest.approx(fd, rel=3e-3, abs=1e-4 * np.abs(gt).max())
+
+
 def test_project_backproject_autograd_are_adjoint():
     P = need_gpu()
     import torch
