@@ -633,10 +633,21 @@ def run_ncu_case(args):
     return 0
 
 
+def run_form(args):
+    """One of the forms' measurements alone, as one JSON line."""
+    import __graft_entry__ as entry
+    entry.build()
+    import paper_1609_06041_gb300 as P
+    fn = {"batched": measure_batched, "differentiable": measure_unrolled,
+          "convergence": measure_convergence}[args.form]
+    print(json.dumps({"form": args.form, **fn(P)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -645,7 +656,11 @@ def main():
                     help="run the short fixed launch sequence used for ncu captures")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
+    ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "convergence"],
+                    help="run only this form's measurement")
     args = ap.parse_args()
+    if args.form:
+        return run_form(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.impl == "reference":

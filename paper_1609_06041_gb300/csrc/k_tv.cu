@@ -571,7 +571,7 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
 
 // scal[slot_a] += sum of part[2 i], scal[slot_b] += sum of part[2 i + 1],
 // i < npairs, in a fixed order: PS_BLOCKS blocks add contiguous runs
-// (double), one block adds their results in order.
+// (double), one warp adds their results.
 constexpr int PS_BLOCKS = 152;
 
 __global__ void __launch_bounds__(256) k_pair_sums(const double *__restrict__ part, size_t npairs, double *out)
@@ -601,15 +601,23 @@ __global__ void __launch_bounds__(256) k_pair_sums(const double *__restrict__ pa
     }
 }
 
+// one warp: strided lanes, then a fixed shuffle tree
 __global__ void k_pair_final(const double *__restrict__ r, int nb, double *scal, int slot_a, int slot_b)
 {
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) {
+    for (int i = threadIdx.x; i < nb; i += 32) {
         a += r[2 * i];
         b += r[2 * i + 1];
     }
-    scal[slot_a] += a;
-    scal[slot_b] += b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        scal[slot_a] += a;
+        scal[slot_b] += b;
+    }
 }
 
 size_t pair_sums_scratch_doubles() { return 2 * PS_BLOCKS; }
@@ -619,7 +627,7 @@ void launch_pair_sums(const double *part, size_t npairs, double *scratch, double
 {
     counted(2);
     k_pair_sums<<<PS_BLOCKS, 256, 0, st>>>(part, npairs, scratch);
-    k_pair_final<<<1, 1, 0, st>>>(scratch, PS_BLOCKS, scal, slot_a, slot_b);
+    k_pair_final<<<1, 32, 0, st>>>(scratch, PS_BLOCKS, scal, slot_a, slot_b);
 }
 
 }  // namespace ctpd

@@ -8,9 +8,11 @@
 //   z_k      = x_k - tau A^T mubar_k
 //   x_{k+1}  = prox(z_k), n_tv projected-gradient steps from p_k -> p_{k+1}
 //   mu_{k+1}, mubar_{k+1} = dual step (Step 3 and the next Step 1)
-// The checkpoint of iteration k is (x_k, mu_k, mubar_k, p_k).
-// Backward, from dL/dx_K, for k = K-1 .. 0: recompute z_k and the prox
-// trajectory from the checkpoint, apply the adjoint of the dual step
+// The checkpoint of iteration k is (x_k, mu_k, mubar_k, p_k), plus z_k and
+// the band partial sums of A x_{k+1}, which the forward computes anyway: the
+// backward then needs no A^T for z_k and no A for the dual step's residual.
+// Backward, from dL/dx_K, for k = K-1 .. 0: recompute the prox trajectory
+// from the checkpoint, apply the adjoint of the dual step
 // (k_dual_bwd_fft), of A (A^T), of the prox (k_tv_*_bwd) and of A^T (A),
 // accumulating dL/dt (tap correlations) and dL/dlambda.  sigma and tau are
 // constants of the unroll (not differentiated).
@@ -23,7 +25,7 @@ using namespace ctpd;
 namespace {
 
 struct UL {
-    size_t scal, scal2, hhat, winv, ck, z, band, gx, gz, gp, gp2, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa,
+    size_t scal, scal2, hhat, winv, ck, zk, bk, band, gx, gz, gp, gp2, gm, gmb, gmu, gr, gm1, rr, vv, traj, pa,
         tcorr, tacc, orb, psum, total;
     size_t ck_stride;   // floats per checkpoint
 };
@@ -41,7 +43,8 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.hhat = o;  o += a256(sizeof(float2) * g->n_fft);
     L.winv = o;  o += a256(F * S * I);
     L.ck = o;    o += a256(F * L.ck_stride * (iters + 1));
-    L.z = o;     o += a256(F * S * J);
+    L.zk = o;    o += a256(F * S * J * (size_t)std::max(iters, 1));                       // z_k
+    L.bk = o;    o += a256(F * S * I * proj_bands(g->n) * (size_t)std::max(iters, 1));    // A x_{k+1}
     L.band = o;  o += a256(F * S * I * proj_bands(g->n));
     L.gx = o;    o += a256(F * S * J);
     L.gz = o;    o += a256(F * S * J);
@@ -158,8 +161,9 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
     char *ws = static_cast<char *>(workspace);
     double *scal = (double *)(ws + L.scal), *scal2 = (double *)(ws + L.scal2);
     float2 *hhat = (float2 *)(ws + L.hhat);
-    float *winv = (float *)(ws + L.winv), *z = (float *)(ws + L.z), *band = (float *)(ws + L.band);
+    float *winv = (float *)(ws + L.winv), *zk = (float *)(ws + L.zk), *bk = (float *)(ws + L.bk);
     float *tmpa = (float *)(ws + L.gp), *tmpb = (float *)(ws + L.gp2);
+    const size_t bstride = (size_t)S * I * proj_bands(N);
 
     cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
     cudaMemsetAsync(scal2, 0, sizeof(double) * S_COUNT, st);
@@ -174,6 +178,7 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
     const bool fused = tv_fused(tau, beta, mode, tv_iters);
     for (int k = 0; k < iters; ++k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
+        float *z = zk + (size_t)k * S * J, *band = bk + (size_t)k * bstride;
         backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);                       // z = x - tau A^T mubar
         if (fused) {
             launch_tv(z, c.p, n.p, n.x, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 1, scal, st, false, S);
@@ -225,7 +230,9 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     double *scal = (double *)(ws + L.scal), *scal2 = (double *)(ws + L.scal2);
     const float2 *hhat = (const float2 *)(ws + L.hhat);
     const float *winv = (const float *)(ws + L.winv);
-    float *z = (float *)(ws + L.z), *band = (float *)(ws + L.band);
+    const float *zk = (const float *)(ws + L.zk), *bk = (const float *)(ws + L.bk);
+    float *band = (float *)(ws + L.band);
+    const size_t bstride = (size_t)S * I * proj_bands(N);
     float *gx = (float *)(ws + L.gx), *gz = (float *)(ws + L.gz);
     float *gp = (float *)(ws + L.gp), *gp2 = (float *)(ws + L.gp2);
     float *gm = (float *)(ws + L.gm), *gmb = (float *)(ws + L.gmb), *gmu = (float *)(ws + L.gmu);
@@ -251,29 +258,28 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
-        // recompute z_k and the prox trajectory p_k = traj[0] .. traj[n_tv]
-        backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);
-        cudaMemcpyAsync(traj, c.p, sizeof(float) * S * 2 * J, cudaMemcpyDeviceToDevice, st);
+        const float *z = zk + (size_t)k * S * J;
+        // recompute the prox trajectory p_k = tp(0) .. tp(n_tv) = p_{k+1}
+        auto tp = [&](int l) { return l == 0 ? c.p : traj + (size_t)l * S * 2 * J; };
         if (fused)
-            launch_tv(z, traj, traj + (size_t)tv_iters * S * 2 * J, nullptr, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 0,
-                      scal, st, false, S, traj + (size_t)S * 2 * J);
+            launch_tv(z, c.p, tp(tv_iters), nullptr, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 0, scal, st, false, S,
+                      traj + (size_t)S * 2 * J);
         else
-            for (int l = 0; l < tv_iters; ++l)
-                launch_tv_step(z, traj + (size_t)l * S * 2 * J, traj + (size_t)(l + 1) * S * 2 * J, N, S, scal, st);
-        // adjoint of the dual step (needs A x_{k+1} for the residual)
-        launch_project_bands(g, n.x, band, S, st);
-        launch_dual_bwd_fft(g, hhat, band, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv, lowdose, scal, S, st);
+            for (int l = 0; l < tv_iters; ++l) launch_tv_step(z, tp(l), tp(l + 1), N, S, scal, st);
+        // adjoint of the dual step (A x_{k+1} from the checkpoint's band sums)
+        launch_dual_bwd_fft(g, hhat, bk + (size_t)k * bstride, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv,
+                            lowdose, scal, S, st);
         launch_tapcorr_acc(gm1, rr, sigma, lowdose ? gmb : nullptr, vv, -sigma, S * V, g->n_bins, half_len, tcorr,
                            tacc, st);
         // dL/dx_{k+1} += A^T dL/dr  (into gz, then swapped)
         backproject(g, gr, gz, 1, gx, scal2, S, ws, L, st);
         std::swap(gx, gz);
         // adjoint of the prox: final step, then the n_tv steps in reverse
-        const float *trn = traj + (size_t)tv_iters * S * 2 * J;
+        const float *trn = tp(tv_iters);
         launch_tv_final_bwd(z, trn, gx, gp, gz, gp2, N, S, scal, part, st);
         part += npx;
         for (int l = tv_iters - 1; l >= 0; --l) {
-            launch_tv_step_bwd(z, traj + (size_t)l * S * 2 * J, gp2, gz, gp, N, S, scal, part, st);
+            launch_tv_step_bwd(z, tp(l), gp2, gz, gp, N, S, scal, part, st);
             part += npx;
             std::swap(gp, gp2);
         }
