@@ -73,10 +73,11 @@ def _load():
                 "orc_cost": [_i, _i, _i, _p, _p, _p, _d, _p],
                 "orc_residual": [_i, _i, _i, _p, _p, _p],
                 "orc_apply_d": [_i, _i, _p, _p, _i, _p, _p, _p],
-                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i, _i,
+                "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i, _i, _d,
                              _i, _i, _p, _p, _p, _p, _p, _p],
+                "orc_eps_prox": [_i, _i, _p, _i, _d, _p, _p],
                 "orc_power_norm": [_i, _i, _i, _i, _p, _p, _p, _p, _i, _p, _i],
-                "orc_cp_reference": [_i, _i, _i, _p, _p, _p, _i, _d, _d, _d, _i, _p],
+                "orc_cp_reference": [_i, _i, _i, _p, _p, _p, _i, _d, _d, _d, _d, _i, _p],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -235,12 +236,13 @@ class PDState:
 
 
 def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
-         state=None, trace=False, taps_hi=None, s=None, fgp=False):
+         state=None, trace=False, taps_hi=None, s=None, fgp=False, eps=0.0):
     """Run `iters` iterations of Algorithm 1 (mode 0) / 2 (mode 1) from
     `state` (fresh zero state if None).  With taps_hi (and s) the
     preconditioner is the shift-variant D = T_lo + S T_hi S (apply_d); with
-    fgp the prox runs the fast gradient projection.  Returns (state, trace
-    or None)."""
+    fgp the prox runs the fast gradient projection; with eps > 0 (mode 1)
+    the epsilon-constrained form, whose dual steps take eps_prox.  Returns
+    (state, trace or None)."""
     b = _f64(b)
     V, B = b.shape
     w = None if w is None else _f64(w)
@@ -251,7 +253,7 @@ def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
     st = PDState(n, V, B) if state is None else state
     tr = np.empty(iters) if trace else None
     _load().orc_pdtv(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), _ptr(taps), _ptr(th), _ptr(sv), half,
-                     int(mode), float(beta), float(tau), float(sigma), int(n_tv), int(bool(fgp)),
+                     int(mode), float(beta), float(tau), float(sigma), int(n_tv), int(bool(fgp)), float(eps),
                      int(st.k), int(iters), _ptr(st.x), _ptr(st.mu), _ptr(st.mu_prev),
                      _ptr(st.px), _ptr(st.py), _ptr(tr))
     st.k += iters
@@ -269,15 +271,29 @@ def power_norm(which, n, n_views, n_bins, taps=None, w=None, iters=50, angles=No
                                         _ptr(taps), _ptr(th), _ptr(sv), half, _ptr(w), int(iters)))
 
 
-def cp_reference(b, w, mode, beta, s, t, iters, n, angles=None):
-    """Chambolle-Pock on K = [A; grad] (independent limit reference)."""
+def cp_reference(b, w, mode, beta, s, t, iters, n, angles=None, eps=0.0):
+    """Chambolle-Pock on K = [A; grad] (independent limit reference); mode 1
+    with eps > 0: TV subject to ||Ax - b|| <= eps, x >= 0."""
     b = _f64(b)
     V, B = b.shape
     w = None if w is None else _f64(w)
     x = np.empty((n, n))
     _load().orc_cp_reference(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), int(mode),
-                             float(beta), float(s), float(t), int(iters), _ptr(x))
+                             float(beta), float(eps), float(s), float(t), int(iters), _ptr(x))
     return x
+
+
+def eps_prox(q, taps, se):
+    """The epsilon-constrained form's dual step (reading 19): argmin_nu
+    se |nu| + 1/2 (nu - q)^T D^-1 (nu - q), D the per-view Toeplitz matrix of
+    the taps, by bisection on c in (I + c D) nu = q, c = se / |nu|."""
+    q = _f64(q)
+    V, B = q.shape
+    taps = _f64(taps)
+    half = (taps.size + 1) // 2
+    out = np.empty((V, B))
+    _load().orc_eps_prox(V, B, _ptr(taps), half, float(se), _ptr(q), _ptr(out))
+    return out
 
 
 def fewview_ell(n, n_views, n_bins, angles=None):

@@ -429,14 +429,118 @@ double orc_residual(int N, int V, int B, const double *angles,
     return sqrt(acc);
 }
 
+/* ------------------------------------------------------------------ */
+/* The dual step of the epsilon-constrained few-view form               */
+/*   min TV(x)  s.t.  ||Ax - b|| <= eps,  x >= 0    (Sec. 5)             */
+/* (reading 19): with the ball's support function in h, the dual step   */
+/* in the metric of sigma D is the proximal map                         */
+/*   nu = argmin_nu  se |nu| + 1/2 (nu - q)^T D^-1 (nu - q),  se = s eps, */
+/* where q is the equality form's update mu + sigma D (A x - b) and D   */
+/* is block diagonal over views with the B x B Toeplitz matrix T of the */
+/* taps.  Optimality: (I + c T) nu = q with c = se / |nu|, or nu = 0    */
+/* when |T^-1 q| <= se.  c |nu(c)| grows with c, so c is found by       */
+/* bisection, each trial one dense Cholesky solve of I + c T for all    */
+/* views (norms over the whole sinogram).                               */
+/* ------------------------------------------------------------------ */
+
+/* lower Cholesky factor of the n x n SPD matrix a (row-major, in place);
+ * returns 0 if a pivot is not positive */
+static int chol(double *a, int n)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = a[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= a[(size_t)j * n + k] * a[(size_t)j * n + k];
+        if (!(d > 0.0)) return 0;
+        d = sqrt(d);
+        a[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = a[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= a[(size_t)i * n + k] * a[(size_t)j * n + k];
+            a[(size_t)i * n + j] = v / d;
+        }
+    }
+    return 1;
+}
+
+/* x = (L L^T)^-1 r */
+static void chol_solve(const double *l, int n, const double *r, double *x)
+{
+    for (int i = 0; i < n; ++i) {
+        double v = r[i];
+        for (int k = 0; k < i; ++k) v -= l[(size_t)i * n + k] * x[k];
+        x[i] = v / l[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = x[i];
+        for (int k = i + 1; k < n; ++k) v -= l[(size_t)k * n + i] * x[k];
+        x[i] = v / l[(size_t)i * n + i];
+    }
+}
+
+/* out = (I + c T)^-1 q for every view (c < 0: T^-1 q); returns |out| over
+ * the whole sinogram, or -1 if the matrix is not positive definite */
+static double eps_solve(int V, int B, const double *taps, int half, double c, const double *q, double *out,
+                        double *m)
+{
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            int k = i - j;
+            double t = (k > -half && k < half) ? taps[half - 1 + k] : 0.0;
+            m[(size_t)i * B + j] = c < 0.0 ? t : (i == j ? 1.0 : 0.0) + c * t;
+        }
+    if (!chol(m, B)) return -1.0;
+    double n2 = 0.0;
+    for (int v = 0; v < V; ++v) {
+        chol_solve(m, B, q + (size_t)v * B, out + (size_t)v * B);
+        for (int d = 0; d < B; ++d) n2 += out[(size_t)v * B + d] * out[(size_t)v * B + d];
+    }
+    return sqrt(n2);
+}
+
+void orc_eps_prox(int V, int B, const double *taps, int half, double se, const double *q, double *nu)
+{
+    size_t I = (size_t)V * B;
+    if (!(se > 0.0)) {
+        memcpy(nu, q, sizeof(double) * I);
+        return;
+    }
+    double *m = malloc(sizeof(double) * (size_t)B * B);
+    double qn = 0.0;
+    for (size_t i = 0; i < I; ++i) qn += q[i] * q[i];
+    qn = sqrt(qn);
+    /* nu = 0 when |T^-1 q| <= se (T singular: the bound is infinite) */
+    double tn = eps_solve(V, B, taps, half, -1.0, q, nu, m);
+    if (qn == 0.0 || (tn >= 0.0 && tn <= se)) {
+        memset(nu, 0, sizeof(double) * I);
+        free(m);
+        return;
+    }
+    /* |nu(c)| <= |q|, so c |nu(c)| <= se at c = se / |q| */
+    double lo = se / qn, hi = 2.0 * lo;
+    for (int it = 0; it < 400 && hi * eps_solve(V, B, taps, half, hi, q, nu, m) < se; ++it) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        double c = 0.5 * (lo + hi);
+        if (c * eps_solve(V, B, taps, half, c, q, nu, m) < se) lo = c;
+        else hi = c;
+    }
+    eps_solve(V, B, taps, half, 0.5 * (lo + hi), q, nu, m);
+    free(m);
+}
+
 void orc_pdtv(int N, int V, int B, const double *angles,
               const double *b, const double *w,
               const double *taps, const double *taps_hi, const double *sv, int half, int mode,
-              double beta, double tau, double sigma, int n_tv, int fgp,
+              double beta, double tau, double sigma, int n_tv, int fgp, double eps,
               int k0, int iters,
               double *x, double *mu, double *mu_prev, double *px, double *py,
               double *trace)
 {
+    /* eps > 0 (mode 1, taps_hi NULL): the epsilon-constrained form; Step 3
+     * and Step 1 at k = 0 take the proximal map of orc_eps_prox */
+    int epsf = mode == 1 && eps > 0.0;
     size_t I = (size_t)V * B, J = (size_t)N * N;
     double *mubar = malloc(sizeof(double) * I);
     double *t1 = malloc(sizeof(double) * I), *t2 = malloc(sizeof(double) * I);
@@ -455,6 +559,10 @@ void orc_pdtv(int N, int V, int B, const double *angles,
         if (k == 0) {
             apply_d(V, B, taps, taps_hi, half, sv, b, t1, dtmp);
             for (size_t i = 0; i < I; ++i) mubar[i] = -sigma * t1[i];
+            if (epsf) {
+                memcpy(t2, mubar, sizeof(double) * I);
+                orc_eps_prox(V, B, taps, half, sigma * eps, t2, mubar);
+            }
         } else if (mode == 0) {
             for (size_t i = 0; i < I; ++i) t2[i] = (mu[i] - mu_prev[i]) / w[i];
             apply_d(V, B, taps, taps_hi, half, sv, t2, t1, dtmp);
@@ -478,6 +586,10 @@ void orc_pdtv(int N, int V, int B, const double *angles,
         for (size_t i = 0; i < I; ++i) {
             mu_prev[i] = mu[i];
             mu[i] = mu[i] + sigma * t1[i];
+        }
+        if (epsf) {
+            memcpy(t2, mu, sizeof(double) * I);
+            orc_eps_prox(V, B, taps, half, sigma * eps, t2, mu);
         }
         if (trace) {
             trace[k - k0] = (mode == 0)
@@ -541,6 +653,7 @@ double orc_power_norm(int which, int N, int V, int B, const double *angles,
 /* K = [A; grad] with no inner loop, for                               */
 /*   mode 0: min_{x>=0} beta TV(x) + 1/2 ||Ax - b||_W^2   (Eq. 1)       */
 /*   mode 1: min_{x>=0} TV(x)  s.t.  Ax = b               (Eq. 25)      */
+/*           (eps > 0: s.t. ||Ax - b|| <= eps, Sec. 5)                  */
 /* Dual variables q (sinogram) and (gx, gy) (image pair):              */
 /*   q  <- prox_{s F1*}(q + s A xb),  F1* = conj. of the fidelity      */
 /*   g  <- project onto |g_j| <= beta of (g + s grad xb)               */
@@ -550,7 +663,7 @@ double orc_power_norm(int which, int N, int V, int B, const double *angles,
 
 void orc_cp_reference(int N, int V, int B, const double *angles,
                       const double *b, const double *w, int mode,
-                      double beta, double s, double t, int iters, double *x)
+                      double beta, double eps, double s, double t, int iters, double *x)
 {
     size_t I = (size_t)V * B, J = (size_t)N * N;
     double *q = calloc(I, sizeof(double)), *ax = malloc(sizeof(double) * I);
@@ -562,10 +675,25 @@ void orc_cp_reference(int N, int V, int B, const double *angles,
     memset(x, 0, sizeof(double) * J);
     for (int it = 0; it < iters; ++it) {
         orc_project(N, V, B, angles, xb, ax);
-        for (size_t i = 0; i < I; ++i) {
-            double y = q[i] + s * ax[i];
-            if (mode == 0) q[i] = (y - s * b[i]) / (1.0 + s / w[i]);
-            else q[i] = y - s * b[i];
+        if (mode == 1 && eps > 0.0) {
+            /* Moreau: prox_{sF*}(y) = y - s P(y / s), P the projection onto
+             * the ball of radius eps about b */
+            double n2 = 0.0;
+            for (size_t i = 0; i < I; ++i) {
+                double u = (q[i] + s * ax[i]) / s - b[i];
+                n2 += u * u;
+            }
+            double f = sqrt(n2) > eps ? eps / sqrt(n2) : 1.0;
+            for (size_t i = 0; i < I; ++i) {
+                double y = q[i] + s * ax[i];
+                q[i] = y - s * (b[i] + f * (y / s - b[i]));
+            }
+        } else {
+            for (size_t i = 0; i < I; ++i) {
+                double y = q[i] + s * ax[i];
+                if (mode == 0) q[i] = (y - s * b[i]) / (1.0 + s / w[i]);
+                else q[i] = y - s * b[i];
+            }
         }
         orc_grad(N, xb, gx, gy);
         for (size_t j = 0; j < J; ++j) {
