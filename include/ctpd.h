@@ -204,6 +204,20 @@ ct_status ct_ramp_filter_split(const ct_geometry *geom, const float *taps_lo, co
 ct_status ct_ramp_filter_noalloc(const ct_geometry *geom, const float *taps, int half_len,
                                  const float *in, float *out, int batch, void *stream);
 
+/*
+ * Eigendecomposition of the n x n symmetric Toeplitz matrix T[i][j] =
+ * t[|i - j|] (host memory, FP64, no GPU work): q (n x n, row-major) gets
+ * the unit eigenvectors as columns, lambda[j] the eigenvalue of column j,
+ * in no particular order.  The matrix of the per-view convolution D with
+ * taps of half length h is t[k] = taps[h - 1 + k] for k < h, 0 beyond.
+ * Used by the error-tolerant few-view form (ct_pdtv_params.eps); exported
+ * for checking.  Householder tridiagonalisation and implicit QR steps on
+ * the two half-size problems of T's symmetric and antisymmetric
+ * eigenvectors.  CT_ERR_ARG for NULL pointers or n < 1; CT_ERR_NONFINITE
+ * if the QR steps do not converge.
+ */
+ct_status ct_sym_toeplitz_eig(const double *t, int n, double *q, double *lambda);
+
 /* Parameters of ct_pdtv_solve (zero-initialise, then set what you need). */
 typedef struct {
     int mode;         /* CT_LOWDOSE: Algorithm 1 (beta > 0) / 1' (beta = 0);
@@ -234,6 +248,21 @@ typedef struct {
                          field; 1 its fast form (Beck-Teboulle FGP: Nesterov
                          momentum, restarted every outer iteration;
                          tv_iters <= 16)                                      */
+    double eps;       /* CT_FEWVIEW only: > 0 solves the error-tolerant form of
+                         Sec. 5, min TV(x) s.t. ||Ax - b|| <= eps, x >= 0:
+                         Step 3 (and Step 1 at k = 0) take the proximal map
+                         nu = argmin sigma eps |nu| + 1/2 |nu - q|^2_{D^-1} of
+                         Algorithm 2's update q, i.e. (I + c D) nu = q with
+                         c = sigma eps / |nu|, or nu = 0 when
+                         |D^-1 q| <= sigma eps.  precond 0, 1 or 3 and
+                         n_bins <= 4096.  With precond 1 or 3 the map runs in
+                         the eigenbasis of D's B x B Toeplitz matrix: the first
+                         solve for a geometry, precond and tau copies the taps
+                         to the host, synchronises the stream once, computes
+                         the FP64 eigendecomposition (cached in the geometry;
+                         that solve cannot be captured in a CUDA graph, later
+                         ones with the same precond and tau can).  0: the
+                         equality form (Eq. 25).                              */
 } ct_pdtv_params;
 
 /* Scalars of a solve, copied to the host at the end when requested. */

@@ -27,6 +27,7 @@ from .ctpd import (  # noqa: F401
     ct_project,
     ct_ramp_filter,
     ct_ramp_filter_noalloc,
+    ct_sym_toeplitz_eig,
     ct_ramp_filter_split,
     ct_ramp_taps,
     ct_version,

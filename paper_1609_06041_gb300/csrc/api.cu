@@ -74,10 +74,11 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
-    size_t scal, partials, taps, hhat, taps2, hhat2, sv, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, total;
+    size_t scal, partials, taps, hhat, taps2, hhat2, sv, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, eps,
+        total;
 };
 
-Layout layout(const Geometry *g)
+Layout layout(const Geometry *g, const ct_pdtv_params *prm)
 {
     Layout L;
     const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
@@ -102,6 +103,9 @@ Layout layout(const Geometry *g)
     L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
     L.orb = o;      o += align256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, 1) : 1));
     L.aux = o;      o += align256(sizeof(float) * 2 * I);   // the sinogram-side Lanczos, run beside the image side
+    // error-tolerant form: s, w2 and the split-K partial sums of its maps
+    L.eps = o;
+    if (prm && prm->eps > 0.0) o += align256(sizeof(float) * (2 * (size_t)g->n_bins + eps_partial_floats(g)));
     L.total = o;
     return L;
 }
@@ -305,6 +309,7 @@ void ct_geometry_destroy(ct_geometry *g)
     if (g->d_tw) cudaFree(g->d_tw);
     if (g->d_row_items) cudaFree(g->d_row_items);
     if (g->d_col_items) cudaFree(g->d_col_items);
+    eps_cache_free(g);
     delete[] g->h_angles;
     delete g;
 }
@@ -414,9 +419,8 @@ ct_status ct_ramp_filter(const ct_geometry *g, const float *taps, int half_len, 
 
 size_t ct_pdtv_workspace_bytes(const ct_geometry *g, const ct_pdtv_params *p)
 {
-    (void)p;
     if (!g) return 0;
-    return layout(g).total;
+    return layout(g, p).total;
 }
 
 ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
@@ -447,6 +451,12 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         return fail(CT_ERR_ARG, "ct_pdtv_solve: tv_accel must be 0 or 1 (1 needs tv_iters <= %d)", tv_max_steps());
     if (prm->precond == 2 && (mode != CT_LOWDOSE || !fft_supported(g)))
         return fail(CT_ERR_ARG, "ct_pdtv_solve: the shift-variant preconditioner needs CT_LOWDOSE and n_bins <= 4096");
+    if (!(prm->eps >= 0.0) || !std::isfinite(prm->eps))
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: eps must be finite and >= 0");
+    const bool epsf = prm->eps > 0.0;
+    if (epsf && (mode != CT_FEWVIEW || prm->precond == 2 || !fft_supported(g)))
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: the error-tolerant form (eps > 0) needs CT_FEWVIEW, precond 0, 1 or 3 "
+                                "and n_bins <= 4096");
     if (!aligned16(b) || !aligned16(x_out) || (w && !aligned16(w)) || (workspace && !aligned16(workspace)))
         return fail(CT_ERR_ARG, "ct_pdtv_solve: pointers must be 16-byte aligned");
     const double rho = prm->rho > 0.0 ? prm->rho : 0.95;
@@ -454,7 +464,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const int ntv = prm->tv_iters > 0 ? prm->tv_iters : 10;
     const int nlz = std::min(prm->norm_iters > 0 ? prm->norm_iters : 12, (int)LANCZOS_MAX);
     cudaStream_t st = S(stream);
-    const Layout L = layout(g);
+    const Layout L = layout(g, prm);
     const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
 
     char *ws = static_cast<char *>(workspace);
@@ -590,6 +600,13 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         filter(b, mubar, nullptr, nullptr, 1, st);
     }
     ct_status cs = cuda_check("ct_pdtv_solve setup");
+    // error-tolerant form: D's eigenbasis (precond 1, 3; none for D = I),
+    // and Step 1 at k = 0 through the same proximal map
+    const float *eQ = nullptr, *eLam = nullptr;
+    float *es = (float *)(ws + L.eps), *ew2 = es + g->n_bins, *epart = ew2 + g->n_bins;
+    if (cs == CT_OK && epsf && prm->precond != 0) cs = eps_basis(g, prm->precond, prm->tau, taps, st, &eQ, &eLam);
+    if (cs == CT_OK && epsf && !prm->resume)
+        launch_eps_step(g, mubar, mubar, nullptr, nullptr, eQ, eLam, prm->eps, scal, aux, es, ew2, epart, st);
     if (cs != CT_OK) {
         if (owned) cudaFreeAsync(ws, st);
         return cs;
@@ -615,9 +632,14 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
         // performs Step 1 of the next iteration
         launch_project_bands(g, x_out, band, 1, st);
+        if (epsf) cudaMemcpyAsync(r, mu, sizeof(float) * I, cudaMemcpyDeviceToDevice, st);   // mu^k
         if (sv_d) launch_dual_sv(g, hhat, hhat2, sv, band, b, mu, mubar, winv, scal, st);
         else if (use_fft) launch_dual_fft(g, hhat, band, b, mu, mubar, winv, lowdose, scal, st);
         else launch_dual_update(g, taps, half, band, b, mu, mubar, winv, lowdose, scal, st);
+        // error-tolerant form: mu^{k+1} = the proximal map of Algorithm 2's
+        // update, mu_bar = 2 mu^{k+1} - mu^k
+        if (epsf)
+            launch_eps_step(g, mu, mu, mubar, r, eQ, eLam, prm->eps, scal, aux, es, ew2, epart, st);
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
     cs = cuda_check("ct_pdtv_solve");

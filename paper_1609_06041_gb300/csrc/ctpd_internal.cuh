@@ -51,6 +51,7 @@ struct Geometry {
     int tune_orb;         // A^T orbit base-view slices (1..8)
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     double *h_angles;     // host copy
+    void *eps_cache;      // eigenbases of D for the error-tolerant form (eps.cu)
 };
 
 // Records a printf-style message as the calling thread's last error.
@@ -105,6 +106,7 @@ enum {
     S_RED0 = 16,   // reduction results
     S_LN0 = 24,    // norm of the first Lanczos vector (image side)
     S_LN0B = 25,   // and of the sinogram side
+    S_EPSC = 26,   // u = 1 / c of the last proximal map of the error-tolerant form
     S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1 (image side)
     S_LZ2 = 32 + 2 * 64,   // the same for the sinogram side
     S_COUNT = 32 + 4 * 64
@@ -244,6 +246,22 @@ void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                int n, int n_sm, int min_rows, int steps, int final, const double *scal, cudaStream_t st,
                bool fgp = false, int batch = 1, float *traj = nullptr);
 int tv_max_steps();
+
+// The error-tolerant few-view form (eps.cu).  toeplitz_eig: FP64 host
+// eigendecomposition of T[i][j] = t[|i - j|].  eps_basis: D's eigenbasis
+// (Q as B x B row-major floats, lambda) for a geometry, precond and tau,
+// computed from the device taps (2B - 1 values) on first use and cached.
+// launch_eps_step: out = the proximal map of q (see eps.cu), out2 (may be
+// NULL) = 2 out - mu0; Q = NULL means D = I.  wbuf: V x B floats, s and w2:
+// B floats each, part: eps_partial_floats(g) floats.
+bool toeplitz_eig(const double *t, int n, double *q, double *lambda);
+ct_status eps_basis(const Geometry *g, int precond, double tau_key, const float *taps, cudaStream_t st,
+                    const float **q, const float **lambda);
+void eps_cache_free(Geometry *g);
+size_t eps_partial_floats(const Geometry *g);
+void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2, const float *mu0, const float *Q,
+                     const float *lambda, double eps, double *scal, float *wbuf, float *s, float *w2, float *part,
+                     cudaStream_t st);
 
 // Small helpers
 void launch_fill(float *p, float v, size_t n, cudaStream_t st);

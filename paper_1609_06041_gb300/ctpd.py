@@ -34,7 +34,7 @@ CT_TAPS_LOW_BAND, CT_TAPS_HIGH_BAND = 2, 3   # ct_ramp_taps: bands of the shift-
 class ct_pdtv_params(ctypes.Structure):
     _fields_ = [("mode", _i), ("iters", _i), ("tv_iters", _i), ("precond", _i),
                 ("norm_iters", _i), ("resume", _i), ("beta", _d), ("tau", _d),
-                ("sigma", _d), ("rho", _d), ("tv_accel", _i)]
+                ("sigma", _d), ("rho", _d), ("tv_accel", _i), ("eps", _d)]
 
 
 class ct_pdtv_report(ctypes.Structure):
@@ -63,6 +63,7 @@ EXPORTS = {
     "ct_ramp_filter": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
     "ct_ramp_filter_split": ([_vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_filter_noalloc": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
+    "ct_sym_toeplitz_eig": ([_vp, _i, _vp, _vp], _i),
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
                        ctypes.POINTER(ct_pdtv_report), _vp], _i),
@@ -269,6 +270,18 @@ def ct_ramp_filter_noalloc(g: Geometry, taps: torch.Tensor, sino: torch.Tensor, 
     return out
 
 
+def ct_sym_toeplitz_eig(t):
+    """Eigendecomposition of the symmetric Toeplitz matrix T[i][j] = t[|i-j|]
+    (host, FP64): returns (q, lambda), q's columns the unit eigenvectors."""
+    import numpy as np
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    n = t.size
+    q = np.empty((n, n))
+    lam = np.empty(n)
+    _check(_lib.ct_sym_toeplitz_eig(t.ctypes.data_as(_vp), n, q.ctypes.data_as(_vp), lam.ctypes.data_as(_vp)))
+    return q, lam
+
+
 @dataclass
 class PDTVParams:
     mode: int = CT_LOWDOSE
@@ -282,11 +295,13 @@ class PDTVParams:
     sigma: float = 0.0
     rho: float = 0.95
     tv_accel: int = 0
+    eps: float = 0.0             # CT_FEWVIEW: > 0 solves min TV s.t. ||Ax - b|| <= eps
 
     def to_c(self):
         return ct_pdtv_params(int(self.mode), int(self.iters), int(self.tv_iters), int(self.precond),
                               int(self.norm_iters), int(self.resume), float(self.beta),
-                              float(self.tau), float(self.sigma), float(self.rho), int(self.tv_accel))
+                              float(self.tau), float(self.sigma), float(self.rho), int(self.tv_accel),
+                              float(self.eps))
 
 
 def ct_pdtv_workspace_bytes(g: Geometry, params: PDTVParams) -> int:
