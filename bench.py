@@ -311,13 +311,13 @@ def measure_unrolled(P, steps=3):
 CHECKPOINTS = (1, 3, 10, 30, 100, 300, 1000)
 
 
-def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0):
+def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0, eps=0.0):
     """Iterates of one solve at CHECKPOINTS (resumed solves continue the
     same iteration exactly): RMSE of x / scale against the phantom v_true
     and the relative data residual |A x - b| / |b|."""
     import torch
     prm = P.PDTVParams(mode=mode, iters=CHECKPOINTS[0], tv_iters=10, precond=precond, beta=beta,
-                       norm_iters=WORK["norm_iters"], tv_accel=tv_accel)
+                       norm_iters=WORK["norm_iters"], tv_accel=tv_accel, eps=eps)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     xs, rmse, resid = {}, {}, {}
@@ -333,11 +333,11 @@ def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0):
     return xs, rmse, resid
 
 
-def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3, tv_accel=0):
+def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3, tv_accel=0, eps=0.0):
     """iterations/s of a whole solve (setup included), CUDA events."""
     import torch
     prm = P.PDTVParams(mode=mode, iters=iters, tv_iters=10, precond=precond, beta=beta, norm_iters=WORK["norm_iters"],
-                       tv_accel=tv_accel)
+                       tv_accel=tv_accel, eps=eps)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     for _ in range(2):
@@ -365,8 +365,11 @@ def measure_convergence(P):
     the same slice with beta 500 (a TV weight that shapes the image),
     few-view (512^2, 32 views, 736 bins, noiseless b = A v, Alg. 2), and the
     paper's shapes (256^2 with 1200 views low-dose at beta 500, and with 32
-    views few-view; 369 bins); plus whole-solve rates (iterations/s, setup
-    included, 30 iterations low-dose, 100 few-view)."""
+    views few-view; 369 bins), and the error-tolerant few-view form (Sec. 5)
+    on the 512^2 / 32-view slice with Gaussian noise of 1 % of the mean line
+    integral and eps = |noise| (x*: the smoothed ramp's 1000-iteration
+    iterate); plus whole-solve rates (iterations/s, setup included, 30
+    iterations low-dose, 100 few-view)."""
     import torch
     out = {}
     # (name, N, views, bins, mode, beta, attenuation factor); the last two are
@@ -376,8 +379,10 @@ def measure_convergence(P):
              ("lowdose_tv", WORK["n"], WORK["views"], WORK["bins"], 0, 500.0, 1.0),
              ("fewview", WORK["n"], 32, WORK["bins"], 1, 0.0, 1.0),
              ("paper_lowdose_256_v1200", 256, 1200, 369, 0, 500.0, 1.0),
-             ("paper_fewview_256_v32", 256, 32, 369, 1, 0.0, 1.0)]
+             ("paper_fewview_256_v32", 256, 32, 369, 1, 0.0, 1.0),
+             ("fewview_eps", WORK["n"], 32, WORK["bins"], 1, 0.0, 1.0)]
     for name, N, V, B, mode, beta, dense in cases:
+        epsf = name == "fewview_eps"
         g = P.Geometry(N, V, B)
         g.autotune()
         v_true = synth.ellipse_phantom(N, WORK["ellipses"], 0)
@@ -389,16 +394,29 @@ def measure_convergence(P):
             w = torch.from_numpy(ww.astype(np.float32)).cuda()
         else:
             b, w = p, None
+        eps = 0.0
+        if epsf:
+            gen = torch.Generator(device="cpu").manual_seed(7)
+            noise = (0.01 * float(p.abs().mean()) * torch.randn(p.shape, generator=gen)).cuda()
+            b = p + noise
+            eps = float(torch.linalg.norm(noise))
         vt = torch.from_numpy(v_true).cuda()
-        arms = [("preconditioned", 1, 0), ("preconditioned_fgp", 1, 1), ("plain_cp", 0, 0)]
-        arms.insert(2, ("shift_variant", 2, 0) if mode == 0 else ("smoothed_ramp", 3, 0))
-        runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale, acc) for label, pc, acc in arms}
-        xstar = runs["preconditioned"][0][CHECKPOINTS[-1]]
+        if epsf:
+            arms = [("preconditioned", 1, 0), ("smoothed_ramp", 3, 0), ("plain_cp", 0, 0)]
+        else:
+            arms = [("preconditioned", 1, 0), ("preconditioned_fgp", 1, 1), ("plain_cp", 0, 0)]
+            arms.insert(2, ("shift_variant", 2, 0) if mode == 0 else ("smoothed_ramp", 3, 0))
+        runs = {label: _trajectory(P, g, b, w, mode, pc, beta, vt, scale, acc, eps) for label, pc, acc in arms}
+        xstar = runs["smoothed_ramp" if epsf else "preconditioned"][0][CHECKPOINTS[-1]]
         xn = float(torch.linalg.norm(xstar))
         entry = {"workload": f"{N}^2, {V} views, {B} bins, " +
                              (f"Poisson I0 5e3, attenuation x{dense}, beta {beta}, Alg. 1" if mode == 0
+                              else "b = A v + Gaussian noise (1 % of the mean line integral), "
+                                   "min TV s.t. |Ax - b| <= eps = |noise| (Sec. 5)" if epsf
                               else "noiseless b = A v, Alg. 2"),
                  "checkpoints": list(CHECKPOINTS)}
+        if epsf:
+            entry["eps_over_norm_b"] = eps / float(torch.linalg.norm(b))
         if mode == 0:
             entry["weight_range"] = [float(w.min()), float(w.max())]
         for label, (xs, rmse, resid) in runs.items():
@@ -407,7 +425,8 @@ def measure_convergence(P):
                             "rel_dist_to_xstar": [float(torch.linalg.norm(xs[k] - xstar)) / xn
                                                   for k in CHECKPOINTS]}
         iters = 100 if mode == 1 else WORK["iters"]
-        entry[f"iterations_per_s_{iters}"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, iters, tv_accel=acc)
+        entry[f"iterations_per_s_{iters}"] = {label: _solve_rate(P, g, b, w, mode, pc, beta, iters, tv_accel=acc,
+                                                                 eps=eps)
                                               for label, pc, acc in arms}
         out[name] = entry
     return out

@@ -117,6 +117,25 @@ constexpr int LANCZOS_MAX = 64;
 // kernels convert nothing on the slow FP64 pipe.
 constexpr int S_F32 = 20;
 enum { F_TAU = 0, F_SIGMA, F_LAMBDA, F_INV8LAM };
+
+// Neumaier-compensated FP32 sum: the running sum s and the rounding errors
+// it dropped, c (value s + c).  The data-parallel reductions of the
+// adjoint use it instead of FP64, which is slow on this GPU; with a fixed
+// order of additions the result is deterministic.
+struct FSum {
+    float s, c;
+};
+__device__ __forceinline__ void fsum_add(FSum &a, float x)
+{
+    const float t = a.s + x;
+    a.c += fabsf(a.s) >= fabsf(x) ? (a.s - t) + x : (x - t) + a.s;
+    a.s = t;
+}
+__device__ __forceinline__ void fsum_merge(FSum &a, const FSum &b)
+{
+    fsum_add(a, b.s);
+    a.c += b.c;
+}
 __device__ __forceinline__ float fscal(const double *scal, int k) { return reinterpret_cast<const float *>(scal + S_F32)[k]; }
 
 // Number of kernels this library has enqueued (all threads), for callers
@@ -205,12 +224,13 @@ void launch_dual_bwd_fft(const Geometry *g, const float2 *hhat, const float *par
 
 // Reductions of the adjoint (k_grad.cu).
 // acc[half - 1 + k] += c0 <g0, T_k s0> + c1 <g1, T_k s1> over nviews rows of B
-// bins (T_k: shift by k, |k| < half); g1 = NULL drops the second pair.
+// bins (T_k: shift by k, |k| < half); g1 = NULL drops the second pair.  acc
+// holds compensated sums (value x + y, see FSum).
 size_t tapcorr_partial_bytes(int nviews, int B, int half);
 void launch_tapcorr_acc(const float *g0, const float *s0, double c0, const float *g1, const float *s1, double c1,
-                        int nviews, int B, int half, float *partial, double *acc, cudaStream_t st);
+                        int nviews, int B, int half, float *partial, float2 *acc, cudaStream_t st);
 void kernel_attrs_grad();
-void launch_grad_out(const double *acc, int nl, const double *scal, int slot, double fac, float *grad,
+void launch_grad_out(const float2 *acc, int nl, const double *scal, int slot, double fac, float *grad,
                      cudaStream_t st);
 // out = fac[0] * scale_v * sum_b partial[b]
 void launch_band_reduce_scaled(const Geometry *g, const float *partial, float *out, const double *fac, int batch,
@@ -222,15 +242,15 @@ void launch_tv_step(const float *z, const float *p_in, float *p_out, int n, int 
                     cudaStream_t st);
 void launch_tv_final(const float *z, const float *p, float *x, int n, int batch, const double *scal, cudaStream_t st);
 // The adjoints write their block sums of the inv8 and lambda derivative
-// terms as pairs into part[tv_px_blocks] (doubles; the final step's inv8
+// terms as pairs into part[tv_px_blocks] (floats; the final step's inv8
 // terms are 0); launch_pair_sums adds the pairs of many launches into two
-// scalar slots, deterministically (scratch: pair_sums_scratch_doubles()).
+// scalar slots, deterministically (scratch: pair_sums_scratch_floats()).
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, const double *scal, double *part, cudaStream_t st);
+                         float *gp, int n, int batch, const double *scal, float *part, cudaStream_t st);
 void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
-                        int batch, const double *scal, double *part, cudaStream_t st);
-size_t pair_sums_scratch_doubles();
-void launch_pair_sums(const double *part, size_t npairs, double *scratch, double *scal, int slot_a, int slot_b,
+                        int batch, const double *scal, float *part, cudaStream_t st);
+size_t pair_sums_scratch_floats();
+void launch_pair_sums(const float *part, size_t npairs, float *scratch, double *scal, int slot_a, int slot_b,
                       cudaStream_t st);
 
 // TV prox of Eq. 17 with x >= 0 (projected-gradient dual steps, warm-started

@@ -318,21 +318,20 @@ __global__ void k_eps_w2(const float *__restrict__ W, int V, int B, float *__res
 }
 
 // One block; warp 0 solves.  se = sigma eps.  With u = 1 / c the condition
-// c |nu(c)| = se
-// reads f(u) = sum_j W2_j / (u + l_j)^2 = se^2 (l_j = max(lambda_j, 0);
-// lambda = NULL: 1), the secular equation of a trust-region step: f falls
-// from f(0) (infinite when some l_j = 0 carries energy) to 0.  If f(0) <=
-// se^2, nu = 0.  Otherwise u solves psi(u) = 1 / sqrt(f(u)) - 1 / se = 0;
-// psi is concave and increasing, so Newton steps from a point where
-// psi < 0 climb to the root without overshooting (Hebden; More and
-// Sorensen).  The start is the last step's u (scal[S_EPSC]) when psi < 0
-// there, else u = 0 (or the smallest l_j > 0 / 1e6 when f(0) is infinite,
-// halved until psi < 0).  Stops at |sqrt(f) - se| <= 1e-7 se (the map is
-// applied in FP32).  Terms in FP32, lane sums in FP64 by a fixed butterfly
-// (FP64 arithmetic is slow on this GPU).  Writes s_j = u / (u + l_j) =
-// 1 / (1 + c l_j), or 0, and u to scal[S_EPSC].
+// c |nu(c)| = se reads f(u) = sum_j W2_j / (u + l_j)^2 = se^2 (l_j =
+// max(lambda_j, 0); lambda = NULL: 1), the secular equation of a
+// trust-region step: f falls from f(0) (infinite when some l_j = 0 carries
+// energy) to 0.  If f(0) <= se^2, nu = 0.  Otherwise u solves
+// psi(u) = 1 / sqrt(f(u)) - 1 / se = 0; psi is concave and increasing, so
+// Newton steps from a point where psi < 0 climb to the root without
+// overshooting (Hebden; More and Sorensen).  The start is the last step's
+// u when psi < 0 there, else u = 0 (or the smallest l_j > 0 / 1e6 when
+// f(0) is infinite, halved until psi < 0).  Stops at |sqrt(f) - se| <=
+// 2e-6 se, the FP32 map's own accuracy.  All FP32 (lane sums by a fixed
+// butterfly).  Writes s_j = u / (u + l_j) = 1 / (1 + c l_j), or 0; u is
+// kept as a float in the double slot scal[S_EPSC].
 __global__ void k_eps_root(const float *__restrict__ w2g, const float *__restrict__ lambda, int B, double *scal,
-                           double eps, float *__restrict__ s)
+                           float eps, float *__restrict__ s)
 {
     // W2 and l staged once by the whole block (n_bins <= 4096), then warp 0
     // alone solves, every evaluation reading shared memory
@@ -344,18 +343,18 @@ __global__ void k_eps_root(const float *__restrict__ w2g, const float *__restric
     __syncthreads();
     if (threadIdx.x >= 32) return;
     const int l = threadIdx.x;
-    const double se = scal[S_SIGMA] * eps;
-    auto wsum = [](double v) {
+    float *uslot = reinterpret_cast<float *>(scal + S_EPSC);
+    const float se = fscal(scal, F_SIGMA) * eps, se2 = se * se;
+    auto wsum = [](float v) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
     // f(u) and g(u) = sum_j W2_j / (u + l_j)^3
-    auto eval = [&](double u, double &f, double &g) {
-        const float uf = (float)u;
+    auto eval = [&](float u, float &f, float &g) {
         float a = 0.0f, b = 0.0f;
         for (int j = l; j < B; j += 32) {
-            const float inv = __fdividef(1.0f, uf + ls[j]), t = w2[j] * inv * inv;
+            const float inv = __fdividef(1.0f, u + ls[j]), t = w2[j] * inv * inv;
             a += t;
             b = fmaf(t, inv, b);
         }
@@ -373,43 +372,41 @@ __global__ void k_eps_root(const float *__restrict__ w2g, const float *__restric
             unb = 1;
         }
     }
-    const double f0d = wsum(f0);
+    f0 = wsum(f0);
     unb = __any_sync(0xffffffffu, unb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-    double u = 0.0;
+    float u = 0.0f;
     bool zero = false, all = false;
-    if (!(se > 0.0)) {
+    if (!(se > 0.0f)) {
         all = true;   // c = 0: s = 1
-    } else if (!unb && f0d <= se * se) {
+    } else if (!unb && f0 <= se2) {
         zero = true;
     } else {
-        double f, g;
-        const double up = scal[S_EPSC];
-        u = 0.0;
-        if (up > 0.0) {
+        float f, g;
+        const float up = *uslot;
+        if (up > 0.0f) {
             eval(up, f, g);
-            if (f > se * se) u = up;
+            if (f > se2) u = up;
         }
-        if (u == 0.0 && unb) {
-            u = (lmin < 3.0e38f ? (double)lmin : 1.0) * 1e-6;
-            for (int k = 0; k < 200; ++k, u *= 0.5) {
+        if (u == 0.0f && unb) {
+            u = (lmin < 3.0e38f ? lmin : 1.0f) * 1e-6f;
+            for (int k = 0; k < 120 && u > 0.0f; ++k, u *= 0.5f) {
                 eval(u, f, g);
-                if (f > se * se) break;
+                if (f > se2) break;
             }
         }
-        for (int k = 0; k < 60; ++k) {
+        for (int k = 0; k < 40; ++k) {
             eval(u, f, g);
-            const double nrm = sqrt(f);
-            if (fabs(nrm - se) <= 1e-7 * se || !(g > 0.0)) break;
+            const float nrm = sqrtf(f);
+            if (fabsf(nrm - se) <= 2e-6f * se || !(g > 0.0f)) break;
             // psi = 1/nrm - 1/se, psi' = g / nrm^3
-            const double un = u - (1.0 / nrm - 1.0 / se) * nrm * nrm * nrm / g;
-            u = un > 0.0 ? un : 0.5 * u;
+            const float un = u - (1.0f / nrm - 1.0f / se) * nrm * nrm * nrm / g;
+            u = un > 0.0f ? un : 0.5f * u;
         }
     }
-    const float uf = (float)u;
-    for (int j = l; j < B; j += 32) s[j] = all ? 1.0f : zero ? 0.0f : __fdividef(uf, uf + ls[j]);
-    if (l == 0) scal[S_EPSC] = (zero || all) ? 0.0 : u;
+    for (int j = l; j < B; j += 32) s[j] = all ? 1.0f : zero ? 0.0f : __fdividef(u, u + ls[j]);
+    if (l == 0) *uslot = (zero || all) ? 0.0f : u;
 }
 
 void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2, const float *mu0, const float *Q,
@@ -425,13 +422,13 @@ void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2,
         counted(5);
         k_eps_gemm<false><<<grid, tb, 0, st>>>(q, Q, nullptr, part, V, B, kchunk);
         k_eps_sum_w2<<<(B + 31) / 32, dim3(32, 8), 0, st>>>(part, ks, V, B, wbuf, w2);
-        k_eps_root<<<1, 512, 0, st>>>(w2, lambda, B, scal, eps, s);
+        k_eps_root<<<1, 512, 0, st>>>(w2, lambda, B, scal, (float)eps, s);
         k_eps_gemm<true><<<grid, tb, 0, st>>>(wbuf, Q, s, part, V, B, kchunk);
         k_eps_sum_out<<<eblocks, 256, 0, st>>>(part, ks, n, out, out2, mu0);
     } else {
         counted(3);
         k_eps_w2<<<(B + 127) / 128, 128, 0, st>>>(q, V, B, w2);
-        k_eps_root<<<1, 512, 0, st>>>(w2, nullptr, B, scal, eps, s);
+        k_eps_root<<<1, 512, 0, st>>>(w2, nullptr, B, scal, (float)eps, s);
         k_eps_scale<<<eblocks, 256, 0, st>>>(q, s, out, out2, mu0, V, B);
     }
 }

@@ -16,7 +16,7 @@ namespace ctpd {
 // l / 4 bins ahead of lane 0, which puts the 32 lanes' s loads in 32
 // different banks and their g loads in eight consecutive words.  A block
 // adds its warps' results in order into partial[lag][block] (float);
-// k_tapcorr_sum adds the blocks in order in double.
+// k_tapcorr_sum adds the blocks in order (compensated FP32).
 constexpr int TC_PASS = 256;                  // lags per pass: 32 lanes x 8
 constexpr int TC_MAXW = 8;                    // warps per block
 constexpr int TC_SMEM = 112 * 1024;           // dynamic shared memory bound per block
@@ -92,18 +92,26 @@ k_tapcorr(const float *__restrict__ g0, const float *__restrict__ s0, float c0, 
     }
 }
 
-// acc[lag] += sum over blocks of partial[lag][block]: one warp per lag, lanes
-// over strided blocks in double, then a fixed shuffle tree.
-__global__ void k_tapcorr_sum(const float *__restrict__ partial, int nblocks, int nl, double *__restrict__ acc)
+// acc[lag] += sum over blocks of partial[lag][block]: one warp per lag,
+// lanes over strided blocks, then a fixed shuffle tree, all in compensated
+// FP32 (acc holds value x + y)
+__global__ void k_tapcorr_sum(const float *__restrict__ partial, int nblocks, int nl, float2 *__restrict__ acc)
 {
     const int lag = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), l = threadIdx.x & 31;
     if (lag >= nl) return;
     const float *p = partial + (size_t)lag * nblocks;
-    double t = 0.0;
-    for (int b = l; b < nblocks; b += 32) t += (double)p[b];
+    FSum t{0.0f, 0.0f};
+    for (int b = l; b < nblocks; b += 32) fsum_add(t, p[b]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (l == 0) acc[lag] += t;
+    for (int o = 16; o > 0; o >>= 1) {
+        const FSum u{__shfl_down_sync(0xffffffffu, t.s, o), __shfl_down_sync(0xffffffffu, t.c, o)};
+        fsum_merge(t, u);
+    }
+    if (l == 0) {
+        FSum a{acc[lag].x, acc[lag].y};
+        fsum_merge(a, t);
+        acc[lag] = make_float2(a.s, a.c);
+    }
 }
 
 size_t tapcorr_partial_bytes(int nviews, int B, int half)
@@ -114,7 +122,7 @@ size_t tapcorr_partial_bytes(int nviews, int B, int half)
 }
 
 void launch_tapcorr_acc(const float *g0, const float *s0, double c0, const float *g1, const float *s1, double c1,
-                        int nviews, int B, int half, float *partial, double *acc, cudaStream_t st)
+                        int nviews, int B, int half, float *partial, float2 *acc, cudaStream_t st)
 {
     const TcPlan pl = tc_plan(B, half);
     const int npairs = g1 ? 2 : 1;
@@ -127,16 +135,17 @@ void launch_tapcorr_acc(const float *g0, const float *s0, double c0, const float
 
 void kernel_attrs_grad() { cudaFuncSetAttribute(k_tapcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM); }
 
-// grad[0 .. nl) = (float) tap accumulators; grad[nl] = (float) scal[slot] * fac
-__global__ void k_grad_out(const double *__restrict__ acc, int nl, const double *__restrict__ scal, int slot,
+// grad[0 .. nl) = the compensated tap accumulators; grad[nl] = scal[slot] * fac
+// (one thread's scalar arithmetic)
+__global__ void k_grad_out(const float2 *__restrict__ acc, int nl, const double *__restrict__ scal, int slot,
                            double fac, float *__restrict__ grad)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nl) grad[i] = (float)acc[i];
+    if (i < nl) grad[i] = acc[i].x + acc[i].y;
     if (i == nl) grad[nl] = (float)(scal[slot] * fac);
 }
 
-void launch_grad_out(const double *acc, int nl, const double *scal, int slot, double fac, float *grad,
+void launch_grad_out(const float2 *acc, int nl, const double *scal, int slot, double fac, float *grad,
                      cudaStream_t st)
 {
     counted();

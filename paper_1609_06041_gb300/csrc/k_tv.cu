@@ -317,13 +317,12 @@ __device__ __forceinline__ float2 proj_adj(float2 q, float2 g)
 }
 
 // Block sums of the per-thread float terms va, vb: a fixed shuffle tree per
-// warp (float), then the block's warp sums in order (double) into
-// part[2 block], part[2 block + 1].  FP64 arithmetic is slow on this GPU,
-// so only the per-warp sums are double; launch_pair_sums adds the partials
-// of many launches at the end.  Blocks of 256 threads.
-__device__ __forceinline__ void block_pair_to(float va, float vb, double *part)
+// warp, then the block's warp sums in order (compensated FP32, FSum) into
+// part[2 block], part[2 block + 1].  launch_pair_sums adds the partials of
+// many launches at the end.  Blocks of 256 threads.
+__device__ __forceinline__ void block_pair_to(float va, float vb, float *part)
 {
-    __shared__ double wa[8], wb[8];
+    __shared__ float wa[8], wb[8];
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 #pragma unroll
@@ -332,19 +331,19 @@ __device__ __forceinline__ void block_pair_to(float va, float vb, double *part)
         vb += __shfl_down_sync(0xffffffffu, vb, o);
     }
     if ((t & 31) == 0) {
-        wa[t >> 5] = (double)va;
-        wb[t >> 5] = (double)vb;
+        wa[t >> 5] = va;
+        wb[t >> 5] = vb;
     }
     __syncthreads();
     if (t == 0) {
-        double sa = 0.0, sb = 0.0;
+        FSum sa{0.0f, 0.0f}, sb{0.0f, 0.0f};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            sa += wa[k];
-            sb += wb[k];
+            fsum_add(sa, wa[k]);
+            fsum_add(sb, wb[k]);
         }
-        part[2 * blk] = sa;
-        part[2 * blk + 1] = sb;
+        part[2 * blk] = sa.s + sa.c;
+        part[2 * blk + 1] = sb.s + sb.c;
     }
 }
 
@@ -387,7 +386,7 @@ k_tv_final(const float *__restrict__ z, const float *__restrict__ p, float *__re
 __global__ void __launch_bounds__(256)
 k_tv_final_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gx,
                const float *__restrict__ gp_next, float *__restrict__ gz, float *__restrict__ gp, int N,
-               const double *__restrict__ scal, double *__restrict__ part)
+               const double *__restrict__ scal, float *__restrict__ part)
 {
     const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
     float contrib = 0.0f;
@@ -431,7 +430,7 @@ constexpr int BG_H = BT_H + 1;   // gs: origin (r0, c0), 29 columns
 __global__ void __launch_bounds__(256)
 k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
               float *__restrict__ gz, float *__restrict__ gp, int N, const double *__restrict__ scal,
-              double *__restrict__ part)
+              float *__restrict__ part)
 {
     __shared__ float PX[BP_H][32], PY[BP_H][32], SS[BS_H][32], QX[BQ_H][32], QY[BQ_H][32], GS[BG_H][32];
     const int lx = threadIdx.x, ly = threadIdx.y;
@@ -534,7 +533,7 @@ namespace {
 dim3 tv_px_grid(int n, int batch) { return dim3((n + 31) / 32, (n + 7) / 8, batch); }
 }
 
-// partials (two doubles per block) of the adjoint kernels: the larger grid
+// partials (two floats per block) of the adjoint kernels: the larger grid
 size_t tv_px_blocks(int n, int batch)
 {
     const size_t px = (size_t)((n + 31) / 32) * ((n + 7) / 8), tl = (size_t)((n + BT_W - 1) / BT_W) * ((n + BT_H - 1) / BT_H);
@@ -555,14 +554,14 @@ void launch_tv_final(const float *z, const float *p, float *x, int n, int batch,
 }
 
 void launch_tv_final_bwd(const float *z, const float *p, const float *gx, const float *gp_next, float *gz,
-                         float *gp, int n, int batch, const double *scal, double *part, cudaStream_t st)
+                         float *gp, int n, int batch, const double *scal, float *part, cudaStream_t st)
 {
     counted();
     k_tv_final_bwd<<<tv_px_grid(n, batch), dim3(32, 8), 0, st>>>(z, p, gx, gp_next, gz, gp, n, scal, part);
 }
 
 void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, float *gz, float *gp, int n,
-                        int batch, const double *scal, double *part, cudaStream_t st)
+                        int batch, const double *scal, float *part, cudaStream_t st)
 {
     counted();
     k_tv_step_bwd<<<dim3((n + BT_W - 1) / BT_W, (n + BT_H - 1) / BT_H, batch), dim3(32, 8), 0, st>>>(
@@ -570,59 +569,62 @@ void launch_tv_step_bwd(const float *z, const float *p, const float *gp_next, fl
 }
 
 // scal[slot_a] += sum of part[2 i], scal[slot_b] += sum of part[2 i + 1],
-// i < npairs, in a fixed order: PS_BLOCKS blocks add contiguous runs
-// (double), one warp adds their results.
+// i < npairs, in a fixed order and compensated FP32: PS_BLOCKS blocks add
+// contiguous runs, one warp adds their results; the one thread then adds
+// the two totals to the double slots.
 constexpr int PS_BLOCKS = 152;
 
-__global__ void __launch_bounds__(256) k_pair_sums(const double *__restrict__ part, size_t npairs, double *out)
+__global__ void __launch_bounds__(256) k_pair_sums(const float *__restrict__ part, size_t npairs, float *out)
 {
     const size_t per = (npairs + gridDim.x - 1) / gridDim.x, lo = blockIdx.x * per;
     const size_t hi = lo + per < npairs ? lo + per : npairs;
-    double a = 0.0, b = 0.0;
+    FSum a{0.0f, 0.0f}, b{0.0f, 0.0f};
     for (size_t i = lo + threadIdx.x; i < hi; i += 256) {
-        const double2 v = reinterpret_cast<const double2 *>(part)[i];
-        a += v.x;
-        b += v.y;
+        const float2 v = reinterpret_cast<const float2 *>(part)[i];
+        fsum_add(a, v.x);
+        fsum_add(b, v.y);
     }
-    __shared__ double ra[256], rb[256];
+    __shared__ FSum ra[256], rb[256];
     ra[threadIdx.x] = a;
     rb[threadIdx.x] = b;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
-            ra[threadIdx.x] += ra[threadIdx.x + o];
-            rb[threadIdx.x] += rb[threadIdx.x + o];
+            fsum_merge(ra[threadIdx.x], ra[threadIdx.x + o]);
+            fsum_merge(rb[threadIdx.x], rb[threadIdx.x + o]);
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[2 * blockIdx.x] = ra[0];
-        out[2 * blockIdx.x + 1] = rb[0];
+        out[4 * blockIdx.x] = ra[0].s;
+        out[4 * blockIdx.x + 1] = ra[0].c;
+        out[4 * blockIdx.x + 2] = rb[0].s;
+        out[4 * blockIdx.x + 3] = rb[0].c;
     }
 }
 
 // one warp: strided lanes, then a fixed shuffle tree
-__global__ void k_pair_final(const double *__restrict__ r, int nb, double *scal, int slot_a, int slot_b)
+__global__ void k_pair_final(const float *__restrict__ r, int nb, double *scal, int slot_a, int slot_b)
 {
-    double a = 0.0, b = 0.0;
+    FSum a{0.0f, 0.0f}, b{0.0f, 0.0f};
     for (int i = threadIdx.x; i < nb; i += 32) {
-        a += r[2 * i];
-        b += r[2 * i + 1];
+        fsum_merge(a, FSum{r[4 * i], r[4 * i + 1]});
+        fsum_merge(b, FSum{r[4 * i + 2], r[4 * i + 3]});
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
+        fsum_merge(a, FSum{__shfl_down_sync(0xffffffffu, a.s, o), __shfl_down_sync(0xffffffffu, a.c, o)});
+        fsum_merge(b, FSum{__shfl_down_sync(0xffffffffu, b.s, o), __shfl_down_sync(0xffffffffu, b.c, o)});
     }
     if (threadIdx.x == 0) {
-        scal[slot_a] += a;
-        scal[slot_b] += b;
+        scal[slot_a] += (double)a.s + (double)a.c;
+        scal[slot_b] += (double)b.s + (double)b.c;
     }
 }
 
-size_t pair_sums_scratch_doubles() { return 2 * PS_BLOCKS; }
+size_t pair_sums_scratch_floats() { return 4 * PS_BLOCKS; }
 
-void launch_pair_sums(const double *part, size_t npairs, double *scratch, double *scal, int slot_a, int slot_b,
+void launch_pair_sums(const float *part, size_t npairs, float *scratch, double *scal, int slot_a, int slot_b,
                       cudaStream_t st)
 {
     counted(2);

@@ -59,10 +59,10 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.vv = o;    o += a256(F * S * I);
     L.traj = o;  o += a256(F * (size_t)(ntv + 1) * S * 2 * J);
     // block pairs of every prox adjoint launch of the backward pass
-    L.pa = o;    o += a256(sizeof(double) * tv_px_blocks(g->n, S) * (size_t)iters * (ntv + 1));
-    L.psum = o;  o += a256(sizeof(double) * pair_sums_scratch_doubles());
+    L.pa = o;    o += a256(sizeof(float) * tv_px_blocks(g->n, S) * (size_t)iters * (ntv + 1));
+    L.psum = o;  o += a256(sizeof(float) * pair_sums_scratch_floats());
     L.tcorr = o; o += a256(tapcorr_partial_bytes(S * g->n_views, g->n_bins, half));
-    L.tacc = o;  o += a256(sizeof(double) * (2 * (size_t)half - 1));
+    L.tacc = o;  o += a256(sizeof(float2) * (2 * (size_t)half - 1));
     L.orb = o;   o += a256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, S) : 1));
     L.total = o;
     return L;
@@ -239,10 +239,10 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     float *gr = (float *)(ws + L.gr), *gm1 = (float *)(ws + L.gm1), *rr = (float *)(ws + L.rr),
           *vv = (float *)(ws + L.vv);
     float *traj = (float *)(ws + L.traj);
-    double *pa = (double *)(ws + L.pa), *psum = (double *)(ws + L.psum);
+    float *pa = (float *)(ws + L.pa), *psum = (float *)(ws + L.psum);
     const size_t npx = tv_px_blocks(N, S), ncall = (size_t)iters * (tv_iters + 1);
     float *tcorr = (float *)(ws + L.tcorr);
-    double *tacc = (double *)(ws + L.tacc);
+    float2 *tacc = (float2 *)(ws + L.tacc);
     const int nl = 2 * half_len - 1;
     const double lam = lowdose ? tau * beta : tau;
     const bool fused = tv_fused(tau, beta, mode, tv_iters);
@@ -252,9 +252,9 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     cudaMemsetAsync(gm, 0, sizeof(float) * S * I, st);
     cudaMemsetAsync(gmb, 0, sizeof(float) * S * I, st);
     cudaMemsetAsync(gp, 0, sizeof(float) * S * 2 * J, st);
-    cudaMemsetAsync(tacc, 0, sizeof(double) * nl, st);
-    cudaMemsetAsync(pa, 0, sizeof(double) * npx * ncall, st);
-    double *part = pa;   // the next launch's block pairs
+    cudaMemsetAsync(tacc, 0, sizeof(float2) * nl, st);
+    cudaMemsetAsync(pa, 0, sizeof(float) * npx * ncall, st);
+    float *part = pa;   // the next launch's block pairs
     cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
