@@ -121,3 +121,62 @@ def test_eps_form_argument_checks():
                     (P.PDTVParams(mode=P.CT_FEWVIEW, iters=1, eps=1.0, precond=2), None)]:
         with pytest.raises(P.CTError):
             P.ct_pdtv_solve(g, b, ww, prm)
+
+
+def test_eps_form_in_batched_solve_and_graph():
+    # an error-tolerant slice beside an equality slice in one batched call:
+    # each equals its own single solve bit for bit; once its eigenbasis is
+    # cached, the call replays from a CUDA graph
+    P = need_gpu()
+    import torch
+    N, V, B = 32, 16, 47
+    x1, b1, nn1 = noisy_fewview(N, V, B, 5)
+    x2, b2, _ = noisy_fewview(N, V, B, 6)
+    g1, g2 = P.Geometry(N, V, B), P.Geometry(N, V, B)
+    tau = O.default_tau(1, V, 0.0)
+    p1 = P.PDTVParams(mode=P.CT_FEWVIEW, iters=10, precond=3, tau=tau, eps=nn1)
+    p2 = P.PDTVParams(mode=P.CT_FEWVIEW, iters=10, precond=3, tau=tau)
+    s1, _ = P.ct_pdtv_solve(g1, to_gpu(b1), None, p1)
+    s2, _ = P.ct_pdtv_solve(g2, to_gpu(b2), None, p2)
+    bs = P.BatchedSolve([(g1, to_gpu(b1), None, p1), (g2, to_gpu(b2), None, p2)])
+    xs, _ = bs.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(xs[0]), to_np(s1)) and np.array_equal(to_np(xs[1]), to_np(s2))
+    for x in bs.x:
+        x.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bs.run()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(bs.x[0]), to_np(s1)) and np.array_equal(to_np(bs.x[1]), to_np(s2))
+
+
+def test_eps_form_first_solve_refuses_capture():
+    # the first solve for a (geometry, precond, tau) reads the taps back to the
+    # host for the eigendecomposition: inside stream capture it returns an
+    # error instead
+    P = need_gpu()
+    import torch
+    N, V, B = 24, 12, 35
+    _, b, nn = noisy_fewview(N, V, B, 8)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=P.CT_FEWVIEW, iters=2, precond=1, tau=0.0123, eps=nn)
+    ws = P.workspace_for(g, prm)
+    bg = to_gpu(b)
+    x = torch.empty(N, N, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with pytest.raises(P.CTError):
+        with torch.cuda.graph(graph):
+            P.ct_pdtv_solve(g, bg, None, prm, x_out=x, workspace=ws, report=False)
+    torch.cuda.synchronize()
+    # uncaptured it runs, and then capture works
+    P.ct_pdtv_solve(g, bg, None, prm, x_out=x, workspace=ws, report=False)
+    torch.cuda.synchronize()
+    ref = to_np(x).copy()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        P.ct_pdtv_solve(g, bg, None, prm, x_out=x, workspace=ws, report=False)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(x), ref)
