@@ -168,3 +168,48 @@ def test_unrolled_module_at_scale():
     assert torch.isfinite(loss)
     assert torch.isfinite(m.taps_half.grad).all() and torch.isfinite(m.log_beta.grad)
     assert float(m.taps_half.grad.abs().max()) > 0
+
+
+def test_unrolled_full_size_sampled_slices_match_oracle():
+    # the differentiable configuration as the bench runs it (16 x 256^2,
+    # 180 views, 368 bins, K = 10, n_tv = 10, 128 one-sided taps): slices
+    # 0 and 11 of the batch against the oracle
+    P = need_gpu()
+    N, V, B, S, K, ntv, half = 256, 180, 368, 16, 10, 10, 128
+    xt, bs, ws = make_batch(N, V, B, S, 21)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.01
+    g = P.Geometry(N, V, B)
+    import torch
+    x = P.UnrolledPDTV.apply(to_gpu(taps), torch.tensor(beta, device="cuda"), g, to_gpu(bs), to_gpu(ws), tau,
+                             sigma, 0, K, ntv)
+    for s in (0, 11):
+        st, _ = O.pdtv(bs[s], ws[s], taps, 0, beta, tau, sigma, ntv, K, N)
+        assert rel_l2(to_np(x[s]), st.x) <= 1e-3
+
+
+def test_unrolled_full_size_gradients_match_fp64_finite_differences():
+    # one full-size slice (256^2, 180 views, 368 bins, K = 10, 128 taps):
+    # dL/dbeta and one random tap direction against central differences of
+    # the oracle's loss
+    P = need_gpu()
+    import torch
+    N, V, B, S, K, ntv, half = 256, 180, 368, 1, 10, 10, 128
+    xt, bs, ws = make_batch(N, V, B, S, 31)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.01
+    g = P.Geometry(N, V, B)
+    t = to_gpu(taps).requires_grad_(True)
+    bt = torch.tensor(beta, device="cuda", requires_grad=True)
+    x = P.UnrolledPDTV.apply(t, bt, g, to_gpu(bs), to_gpu(ws), tau, sigma, 0, K, ntv)
+    loss = ((x - to_gpu(xt)) ** 2).sum() / (S * N * N)
+    loss.backward()
+    hb = 1e-3 * beta
+    fd_b = (oracle_loss(bs, ws, xt, taps, beta + hb, tau, sigma, K, ntv, N) -
+            oracle_loss(bs, ws, xt, taps, beta - hb, tau, sigma, K, ntv, N)) / (2 * hb)
+    assert float(bt.grad) == pytest.approx(fd_b, rel=1e-3)
+    d = np.random.default_rng(2).standard_normal(taps.size)
+    eps = 1e-4 * np.abs(taps).max() / np.abs(d).max()
+    fd = (oracle_loss(bs, ws, xt, taps + eps * d, beta, tau, sigma, K, ntv, N) -
+          oracle_loss(bs, ws, xt, taps - eps * d, beta, tau, sigma, K, ntv, N)) / (2 * eps)
+    assert float(to_np(t.grad) @ d) == pytest.approx(fd, rel=3e-3)
