@@ -3,12 +3,15 @@ workload at scale (512 x 512 image of 20 random ellipses, 720 parallel views
 over 180 degrees, 736 bins, transmission Poisson I0 = 5e3 with statistical
 weights, beta = 0.005, 30 iterations of Algorithm 1 per solve).
 
-One step = one ct_pdtv_solve call: setup (kappa, tau, taps, power-method
-step sizes) and 30 iterations, all on the GPU.  value = iterations/sec over
-all ranks (each rank solves its own slice: independent replicas, weak
-scaling, no collective on the data path).
+One step = one ct_pdtv_solve call: setup (kappa, tau, taps, Lanczos step
+sizes) and 30 iterations, all on the GPU; repeated calls replay the
+library's CUDA graph of the solve (--eager: CTPD_SOLVE_GRAPHS=0, every call
+launches its kernels).  value = iterations/sec over all ranks (each rank
+solves its own slice: independent replicas, weak scaling, no collective on
+the data path).  e2e: the same calls with the inputs copied from pinned
+host memory and x copied back, every step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--eager]
 
 --impl reference times the FP64 CPU oracle (the reference implementation
 of this project) on the same workload and metric, one PD iteration per step.
@@ -480,26 +483,34 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         solve()
     torch.cuda.synchronize()
+    # repeated calls replay the library's CUDA graph of this solve (captured
+    # by the first call after the warm-up ones above); its kernels count as
+    # launched on every replay
+    step = solve
+
+    def timed_steps(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in ev)
 
     # ---- timed region: K solves, L2 flushed between them (untimed) ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     launches0 = P.ct_kernel_launches()
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with sampler:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            solve()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+        t_local = timed_steps(step, args.steps)
     launches = P.ct_kernel_launches() - launches0
     if world > 1:
         dist.barrier()
-    t_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), device="cuda")
+    t_ms = max_over_ranks(t_local, device="cuda")
     value = job_value(WORK["iters"] * args.steps, world, t_ms)
 
     # ---- breakdown: setup vs iterations (resume runs iterations only) ----
@@ -589,9 +600,13 @@ def run_ours(args):
                        "beta": WORK["beta"], "i0": WORK["i0"], "iters_per_step": WORK["iters"],
                        "tv_iters": WORK["tv_iters"], "norm_iters": WORK["norm_iters"],
                        "l2": "flushed between steps (512 MB write, untimed)",
+                       "launch": ("ct_pdtv_solve calls, each replaying the library's CUDA graph of the solve"
+                                  if not args.eager else "ct_pdtv_solve calls launching their kernels (no graph)"),
                        "parallelism": f"replicas x{world}", "tuning": tuning},
-            "breakdown_ms": {"solve": step_ms, "iterations_only": loop_ms,
-                             "setup": step_ms - loop_ms, "per_iteration": loop_ms / WORK["iters"],
+            # iterations_only_eager: resumed solves, which read their iteration
+            # count back to the host and so launch their kernels one by one
+            "breakdown_ms": {"solve": step_ms, "iterations_only_eager": loop_ms,
+                             "per_iteration_eager": loop_ms / WORK["iters"],
                              "A_launch": a_ms, "AT_launch": at_ms},
             "loop_iterations_per_s": WORK["iters"] / (loop_ms / 1e3) * world,
             # effective operator bandwidth: (4 N^2 + 4 V B) bytes per pass
@@ -673,11 +688,15 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, differentiable and convergence measurements")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
+    ap.add_argument("--eager", action="store_true",
+                    help="time eager ct_pdtv_solve calls instead of replaying one captured CUDA graph of the solve")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
     ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "convergence"],
                     help="run only this form's measurement")
     args = ap.parse_args()
+    if args.eager:
+        os.environ["CTPD_SOLVE_GRAPHS"] = "0"   # read when the library first solves
     if args.form:
         return run_form(args)
     if args.ncu_case:

@@ -4,17 +4,20 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "ctpd_internal.cuh"
 
 using namespace ctpd;
 
 std::atomic<unsigned long long> ctpd::g_launches{0};
+thread_local unsigned long long ctpd::t_launches = 0;
 
 namespace {
 
@@ -171,6 +174,159 @@ Fork *fork_for(int dev)
     return &f;
 }
 
+
+// ---------------------------------------------------------------------
+// Solve graphs.  A call of ct_pdtv_solve with a caller-owned workspace, no
+// report, no resume and eps = 0 enqueues only device work, so the whole
+// solve (setup and iterations) can be captured once as a CUDA graph and
+// replayed by later calls with the same geometry, pointers, stream and
+// parameters: one graph launch instead of some 280 kernel launches.  The
+// graph reads the buffers when it runs, so new data in the same buffers is
+// solved as usual.  Per geometry the most recent GRAPH_CACHE_MAX graphs are
+// kept (until ct_geometry_destroy).  The capture uses a fork stream of its
+// own for the setup's second branch.  Environment CTPD_SOLVE_GRAPHS=0 turns
+// this off (every call then launches its kernels).
+// ---------------------------------------------------------------------
+constexpr size_t GRAPH_CACHE_MAX = 16;
+
+struct SolveKey {
+    const void *b, *w, *x, *ws;
+    cudaStream_t st;
+    int dev;
+    ct_pdtv_params p;
+};
+
+bool same_params(const ct_pdtv_params &a, const ct_pdtv_params &b)
+{
+    return a.mode == b.mode && a.iters == b.iters && a.tv_iters == b.tv_iters && a.precond == b.precond &&
+           a.norm_iters == b.norm_iters && a.resume == b.resume && a.beta == b.beta && a.tau == b.tau &&
+           a.sigma == b.sigma && a.rho == b.rho && a.tv_accel == b.tv_accel && a.eps == b.eps;
+}
+
+bool same_key(const SolveKey &a, const SolveKey &b)
+{
+    return a.b == b.b && a.w == b.w && a.x == b.x && a.ws == b.ws && a.st == b.st && a.dev == b.dev &&
+           same_params(a.p, b.p);
+}
+
+struct SolveGraph {
+    SolveKey key;
+    cudaGraphExec_t exec;
+    unsigned long long launches;   // kernels in the graph
+};
+
+struct GraphCache {
+    std::mutex mu;
+    std::vector<SolveGraph> entries;   // least recently used first
+    cudaStream_t cap = nullptr;        // captures run here (the caller's stream may be the
+                                       // legacy default stream, which cannot be captured)
+    Fork fork;                         // the captures' own fork stream
+};
+
+bool solve_graphs_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("CTPD_SOLVE_GRAPHS");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+ct_status solve_graph(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
+                      float *x_out, void *workspace, void *stream)
+{
+    cudaStream_t st = S(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    int dev = -1;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone ||
+        cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();   // inside a caller's capture (or unknown): enqueue the kernels
+        return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, nullptr, stream, true);
+    }
+    Geometry *gm = const_cast<ct_geometry *>(g);
+    {
+        static std::mutex create_mu;
+        std::lock_guard<std::mutex> lock(create_mu);
+        if (!gm->graph_cache) gm->graph_cache = new GraphCache();
+    }
+    GraphCache *c = static_cast<GraphCache *>(gm->graph_cache);
+    std::lock_guard<std::mutex> lock(c->mu);
+    const SolveKey key{b, w, x_out, workspace, st, dev, *prm};
+    for (size_t i = 0; i < c->entries.size(); ++i)
+        if (same_key(c->entries[i].key, key)) {
+            SolveGraph e = c->entries[i];
+            c->entries.erase(c->entries.begin() + i);
+            c->entries.push_back(e);
+            g_err[0] = 0;
+            if (cudaGraphLaunch(e.exec, st) != cudaSuccess) return cuda_check("ct_pdtv_solve (graph)");
+            counted((unsigned)e.launches);
+            return CT_OK;
+        }
+    if (!c->fork.ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->fork.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, nullptr, stream, true);
+        }
+        c->fork.ready = true;
+    }
+    // capture this call on the cache's stream (nothing runs), instantiate,
+    // then launch the graph on the caller's stream
+    const unsigned long long t0 = t_launches;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, nullptr, stream, true);
+    }
+    const ct_status r = ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, nullptr, c->cap, true, &c->fork);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+    const unsigned long long n = t_launches - t0;
+    g_launches.fetch_sub(n, std::memory_order_relaxed);   // captured, not run
+    t_launches -= n;
+    if (r != CT_OK) {   // an argument error: nothing was enqueued
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return r;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = ec;
+    if (ei == cudaSuccess) ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {   // not capturable after all: run the call directly
+        cudaGetLastError();
+        return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, nullptr, stream, true);
+    }
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return cuda_check("ct_pdtv_solve (graph)");
+    }
+    counted((unsigned)n);
+    if (c->entries.size() >= GRAPH_CACHE_MAX) {
+        cudaGraphExecDestroy(c->entries.front().exec);
+        c->entries.erase(c->entries.begin());
+    }
+    c->entries.push_back(SolveGraph{key, exec, n});
+    g_err[0] = 0;
+    return CT_OK;
+}
+
+void graph_cache_free(Geometry *g)
+{
+    GraphCache *c = static_cast<GraphCache *>(g->graph_cache);
+    if (!c) return;
+    for (const SolveGraph &e : c->entries) cudaGraphExecDestroy(e.exec);
+    if (c->fork.ready) {
+        cudaStreamDestroy(c->cap);
+        cudaStreamDestroy(c->fork.s);
+        cudaEventDestroy(c->fork.fork);
+        cudaEventDestroy(c->fork.join);
+    }
+    delete c;
+    g->graph_cache = nullptr;
+}
 }  // namespace
 
 extern "C" {
@@ -310,6 +466,7 @@ void ct_geometry_destroy(ct_geometry *g)
     if (g->d_row_items) cudaFree(g->d_row_items);
     if (g->d_col_items) cudaFree(g->d_col_items);
     eps_cache_free(g);
+    graph_cache_free(g);
     delete[] g->h_angles;
     delete g;
 }
@@ -427,13 +584,17 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                         const ct_pdtv_params *prm, float *x_out, void *workspace,
                         ct_pdtv_report *report, void *stream)
 {
+    // a repeat of an earlier call replays that call's CUDA graph
+    if (g && prm && workspace && !report && !prm->resume && !(prm->eps > 0.0) && solve_graphs_enabled())
+        return solve_graph(g, b, w, prm, x_out, workspace, stream);
     return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, report, stream, true);
 }
 
 }  // extern "C"
 
 ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
-                           float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork)
+                           float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork,
+                           void *fork)
 {
     g_err[0] = 0;
     if (!g || !b || !prm || !x_out) return fail(CT_ERR_ARG, "ct_pdtv_solve: NULL argument");
@@ -557,7 +718,8 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             Fork *fk = nullptr;
             if (allow_fork && lowdose && use_fft) {
                 int dev = -1;
-                if (cudaGetDevice(&dev) == cudaSuccess) fk = fork_for(dev);
+                if (fork) fk = static_cast<Fork *>(fork);
+                else if (cudaGetDevice(&dev) == cudaSuccess) fk = fork_for(dev);
             }
             if (lowdose) {
                 cudaStream_t s2 = st;

@@ -52,6 +52,7 @@ struct Geometry {
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     double *h_angles;     // host copy
     void *eps_cache;      // eigenbases of D for the error-tolerant form (eps.cu)
+    void *graph_cache;    // instantiated CUDA graphs of repeated solves (api.cu)
 };
 
 // Records a printf-style message as the calling thread's last error.
@@ -67,8 +68,11 @@ struct ct_geometry : public ctpd::Geometry {};
 namespace ctpd {
 // ct_pdtv_solve; allow_fork lets one solve run independent setup work on a
 // second stream of the device (off for solves already run side by side).
+// fork (optional): the stream and events to fork the setup's second branch
+// onto instead of the device's shared ones.
 ct_status pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
-                     float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork);
+                     float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork,
+                     void *fork = nullptr);
 }  // namespace ctpd
 
 namespace ctpd {
@@ -141,7 +145,12 @@ __device__ __forceinline__ float fscal(const double *scal, int k) { return reint
 // Number of kernels this library has enqueued (all threads), for callers
 // that account for launches.
 extern std::atomic<unsigned long long> g_launches;
-inline void counted(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern thread_local unsigned long long t_launches;   // this thread's share of g_launches
+inline void counted(unsigned n = 1)
+{
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 
 // ---- kernels (defined in the k_*.cu files) ----
 // Forward projection in two parts: band partial sums (one image band of

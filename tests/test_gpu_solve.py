@@ -209,3 +209,46 @@ def test_fewview_smoothed_ramp_parity():
     assert rep["sigma"] == pytest.approx(0.95 / (tau * rep["norm_ADA"]), rel=1e-6)
     with pytest.raises(P.CTError):
         P.ct_pdtv_solve(g, to_gpu(b), to_gpu(np.ones((V, B))), P.PDTVParams(mode=0, iters=1, precond=3))
+
+
+def test_repeated_solves_replay_a_graph():
+    # a call with a workspace and no report is captured as a CUDA graph the
+    # first time and replayed by the same call later: the results equal the
+    # eager solve (report requested: kernels launched one by one), new data in
+    # the same buffers is solved, each replay counts its kernels, and other
+    # parameters get their own graph
+    P = need_gpu()
+    import torch
+    N, V, B = 64, 90, 95
+    _, b1, w1 = lowdose_case(N, V, B, 0)
+    _, b2, w2 = lowdose_case(N, V, B, 1)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=0, iters=10, beta=0.01)
+    ws = P.workspace_for(g, prm)
+    bd, wd = to_gpu(b1), to_gpu(w1)
+    x = torch.empty(N, N, device="cuda")
+    ref1, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
+    n0 = P.ct_kernel_launches()
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
+    n1 = P.ct_kernel_launches()
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
+    n2 = P.ct_kernel_launches()
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref1)
+    assert n1 - n0 > 100 and n2 - n1 == n1 - n0
+    bd.copy_(to_gpu(b2))
+    wd.copy_(to_gpu(w2))
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
+    ref2, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref2) and not torch.equal(ref1, ref2)
+    prm3 = P.PDTVParams(mode=0, iters=7, beta=0.02)
+    for _ in range(2):
+        P.ct_pdtv_solve(g, bd, wd, prm3, x_out=x, workspace=ws, report=False)
+    ref3, _ = P.ct_pdtv_solve(g, bd, wd, prm3, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref3)
+    # and the first parameters still replay their own graph
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref2)
