@@ -313,6 +313,20 @@ ct_status solve_graph(const ct_geometry *g, const float *b, const float *w, cons
     return CT_OK;
 }
 
+}  // namespace
+
+// drop the cached graphs (their launch shapes are out of date); the streams stay
+void ctpd::graph_cache_clear(Geometry *g)
+{
+    GraphCache *c = static_cast<GraphCache *>(g->graph_cache);
+    if (!c) return;
+    std::lock_guard<std::mutex> lock(c->mu);
+    for (const SolveGraph &e : c->entries) cudaGraphExecDestroy(e.exec);
+    c->entries.clear();
+}
+
+namespace {
+
 void graph_cache_free(Geometry *g)
 {
     GraphCache *c = static_cast<GraphCache *>(g->graph_cache);

@@ -96,6 +96,7 @@ extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block,
     g->tune_qrows = proj_rows;
     g->tune_orb = orbit_slices;
     g->tune_tv = tv_rows;
+    graph_cache_clear(g);
     return CT_OK;
 }
 
@@ -195,6 +196,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    graph_cache_clear(g);
     if (result != CT_OK) {
         g->tune_pg = old_pg;
         g->tune_qrows = old_rows;

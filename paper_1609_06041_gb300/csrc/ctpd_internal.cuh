@@ -68,6 +68,9 @@ struct ct_geometry : public ctpd::Geometry {};
 namespace ctpd {
 // ct_pdtv_solve; allow_fork lets one solve run independent setup work on a
 // second stream of the device (off for solves already run side by side).
+// Drops the geometry's cached solve graphs (api.cu); the tuning calls use it,
+// as the graphs hold the old launch shapes.
+void graph_cache_clear(Geometry *g);
 // fork (optional): the stream and events to fork the setup's second branch
 // onto instead of the device's shared ones.
 ct_status pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,

@@ -252,3 +252,9 @@ def test_repeated_solves_replay_a_graph():
     P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
     torch.cuda.synchronize()
     assert torch.equal(x, ref2)
+    # new launch shapes drop the cached graphs: the next call is captured anew
+    g.set_tuning(orbit_slices=2, tv_rows=8)
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=x, workspace=ws, report=False)
+    ref4, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref4)
