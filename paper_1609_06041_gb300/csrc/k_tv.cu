@@ -427,34 +427,43 @@ constexpr int BS_H = BT_H + 3;   // s: origin (r0 - 1, c0 - 1), 31 columns
 constexpr int BQ_H = BT_H + 2;   // gq: origin (r0 - 1, c0 - 1), 30 columns
 constexpr int BG_H = BT_H + 1;   // gs: origin (r0, c0), 29 columns
 
-__global__ void __launch_bounds__(256)
-k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
-              float *__restrict__ gz, float *__restrict__ gp, int N, const double *__restrict__ scal,
-              float *__restrict__ part)
+// INT: the tile and its halos lie inside the image, one cell away from the
+// last row and column (r0 >= 2, c0 >= 2, r0 + BT_H + 3 <= N, c0 + 31 <= N),
+// so every bounds and boundary test below is true and is left out.
+struct BwdTile {   // the staged regions (one per block, shared by both paths)
+    float PX[BP_H][32], PY[BP_H][32], SS[BS_H][32], QX[BQ_H][32], QY[BQ_H][32], GS[BG_H][32];
+};
+
+template <bool INT>
+__device__ __forceinline__ void tv_step_bwd_tile(BwdTile &t, const float *__restrict__ z, const float *__restrict__ px,
+                                                 const float *__restrict__ py, const float *__restrict__ gnx,
+                                                 const float *__restrict__ gny, float *__restrict__ gz,
+                                                 float *__restrict__ ox, float *__restrict__ oy, int N, int r0,
+                                                 int c0, float lam, float inv8, float &c_inv8, float &c_lam)
 {
-    __shared__ float PX[BP_H][32], PY[BP_H][32], SS[BS_H][32], QX[BQ_H][32], QY[BQ_H][32], GS[BG_H][32];
+    auto &PX = t.PX;
+    auto &PY = t.PY;
+    auto &SS = t.SS;
+    auto &QX = t.QX;
+    auto &QY = t.QY;
+    auto &GS = t.GS;
     const int lx = threadIdx.x, ly = threadIdx.y;
-    const int r0 = blockIdx.y * BT_H, c0 = blockIdx.x * BT_W;
-    const size_t NN = (size_t)N * N;
-    z += blockIdx.z * NN;
-    gz += blockIdx.z * NN;
-    const float *px = p + blockIdx.z * 2 * NN, *py = px + NN;
-    const float *gnx = gp_next + blockIdx.z * 2 * NN, *gny = gnx + NN;
-    float *ox = gp + blockIdx.z * 2 * NN, *oy = ox + NN;
-    const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
+    auto in_img = [&](int v) { return INT || (unsigned)v < (unsigned)N; };
+    auto below_last = [&](int v) { return INT || v < N - 1; };   // a forward difference exists
+    auto above_first = [&](int v) { return INT || v > 0; };
     // image column of this lane in each region, and whether it is inside
     const int bp = c0 - 2 + lx, bs = c0 - 1 + lx, bg = c0 + lx;
-    const bool inp = (unsigned)bp < (unsigned)N, ins = lx < 31 && (unsigned)bs < (unsigned)N;
-    const bool inq = lx < 30 && (unsigned)bs < (unsigned)N, ing = lx < 29 && (unsigned)bg < (unsigned)N;
+    const bool inp = in_img(bp), ins = lx < 31 && in_img(bs);
+    const bool inq = lx < 30 && in_img(bs), ing = lx < 29 && in_img(bg);
     // div p at image cell (a, b) = region p cell (i, j) (zero outside the image)
     auto div_p = [&](int i, int j, int a, int b) {
-        return ((b < N - 1 ? PX[i][j] : 0.0f) - (b > 0 ? PX[i][j - 1] : 0.0f)) +
-               ((a < N - 1 ? PY[i][j] : 0.0f) - (a > 0 ? PY[i - 1][j] : 0.0f));
+        return ((below_last(b) ? PX[i][j] : 0.0f) - (above_first(b) ? PX[i][j - 1] : 0.0f)) +
+               ((below_last(a) ? PY[i][j] : 0.0f) - (above_first(a) ? PY[i - 1][j] : 0.0f));
     };
 
     for (int i = ly; i < BP_H; i += 8) {
         const int a = r0 - 2 + i;
-        const bool in = inp && (unsigned)a < (unsigned)N;
+        const bool in = inp && in_img(a);
         const size_t gi = (size_t)a * N + bp;
         PX[i][lx] = in ? px[gi] : 0.0f;
         PY[i][lx] = in ? py[gi] : 0.0f;
@@ -464,7 +473,7 @@ k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const fl
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         const int i = ly + 8 * m, a = r0 - 1 + i;
-        const bool in = ins && (unsigned)a < (unsigned)N;
+        const bool in = ins && in_img(a);
         const size_t gi = (size_t)a * N + bs;
         zr[m] = (i < BS_H && in) ? z[gi] : 0.0f;
         gnr[m][0] = (i < BQ_H && lx < 30 && in) ? gnx[gi] : 0.0f;
@@ -473,26 +482,25 @@ k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const fl
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
         const int a = r0 + ly + 8 * m;
-        gzr[m] = (lx < BT_W && bg < N && a < N) ? gz[(size_t)a * N + bg] : 0.0f;
+        gzr[m] = (lx < BT_W && (INT || (bg < N && a < N))) ? gz[(size_t)a * N + bg] : 0.0f;
     }
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 3; ++m) {   // s = z + lam div p
         const int i = ly + 8 * m, a = r0 - 1 + i;
         if (i < BS_H && lx < 31)
-            SS[i][lx] = (ins && (unsigned)a < (unsigned)N) ? fmaf(lam, div_p(i + 1, lx + 1, a, bs), zr[m]) : 0.0f;
+            SS[i][lx] = (ins && in_img(a)) ? fmaf(lam, div_p(i + 1, lx + 1, a, bs), zr[m]) : 0.0f;
     }
     __syncthreads();
-    float c_inv8 = 0.0f, c_lam = 0.0f;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {   // gq = J_Pi(q)^T gp_next
         const int i = ly + 8 * m, a = r0 - 1 + i;
         if (i >= BQ_H) break;
         float2 g = make_float2(0.0f, 0.0f);
-        if (inq && (unsigned)a < (unsigned)N) {
+        if (inq && in_img(a)) {
             const float x0 = fmaxf(0.0f, SS[i][lx]);
-            const float gxv = bs < N - 1 ? fmaxf(0.0f, SS[i][lx + 1]) - x0 : 0.0f;
-            const float gyv = a < N - 1 ? fmaxf(0.0f, SS[i + 1][lx]) - x0 : 0.0f;
+            const float gxv = below_last(bs) ? fmaxf(0.0f, SS[i][lx + 1]) - x0 : 0.0f;
+            const float gyv = below_last(a) ? fmaxf(0.0f, SS[i + 1][lx]) - x0 : 0.0f;
             const float2 q = make_float2(PX[i + 1][lx + 1] + gxv * inv8, PY[i + 1][lx + 1] + gyv * inv8);
             g = proj_adj(q, make_float2(gnr[m][0], gnr[m][1]));
             if (i >= 1 && i <= BT_H && lx >= 1 && lx <= BT_W) c_inv8 = fmaf(g.x, gxv, fmaf(g.y, gyv, c_inv8));
@@ -506,9 +514,9 @@ k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const fl
     for (int i = ly; i < BG_H; i += 8) {   // gs = [s > 0] (-inv8 div gq)
         const int a = r0 + i;
         float v = 0.0f;
-        if (ing && (unsigned)a < (unsigned)N && SS[i + 1][lx + 1] > 0.0f) {
-            const float d = ((bg < N - 1 ? QX[i + 1][lx + 1] : 0.0f) - (bg > 0 ? QX[i + 1][lx] : 0.0f)) +
-                            ((a < N - 1 ? QY[i + 1][lx + 1] : 0.0f) - (a > 0 ? QY[i][lx + 1] : 0.0f));
+        if (ing && in_img(a) && SS[i + 1][lx + 1] > 0.0f) {
+            const float d = ((below_last(bg) ? QX[i + 1][lx + 1] : 0.0f) - (above_first(bg) ? QX[i + 1][lx] : 0.0f)) +
+                            ((below_last(a) ? QY[i + 1][lx + 1] : 0.0f) - (above_first(a) ? QY[i][lx + 1] : 0.0f));
             v = -inv8 * d;
         }
         if (lx < 29) GS[i][lx] = v;
@@ -517,15 +525,36 @@ k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const fl
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
         const int i = ly + 8 * m, a = r0 + i;
-        if (lx < BT_W && bg < N && a < N) {
+        if (lx < BT_W && (INT || (bg < N && a < N))) {
             const size_t gi = (size_t)a * N + bg;
             const float gs0 = GS[i][lx];
             gz[gi] = gzr[m] + gs0;
-            ox[gi] = QX[i + 1][lx + 1] - lam * (bg < N - 1 ? GS[i][lx + 1] - gs0 : 0.0f);
-            oy[gi] = QY[i + 1][lx + 1] - lam * (a < N - 1 ? GS[i + 1][lx] - gs0 : 0.0f);
+            ox[gi] = QX[i + 1][lx + 1] - lam * (below_last(bg) ? GS[i][lx + 1] - gs0 : 0.0f);
+            oy[gi] = QY[i + 1][lx + 1] - lam * (below_last(a) ? GS[i + 1][lx] - gs0 : 0.0f);
             c_lam = fmaf(gs0, div_p(i + 2, lx + 2, a, bg), c_lam);
         }
     }
+}
+
+__global__ void __launch_bounds__(256, 6)
+k_tv_step_bwd(const float *__restrict__ z, const float *__restrict__ p, const float *__restrict__ gp_next,
+              float *__restrict__ gz, float *__restrict__ gp, int N, const double *__restrict__ scal,
+              float *__restrict__ part)
+{
+    const int r0 = blockIdx.y * BT_H, c0 = blockIdx.x * BT_W;
+    const size_t NN = (size_t)N * N;
+    const float *px = p + blockIdx.z * 2 * NN;
+    const float *gnx = gp_next + blockIdx.z * 2 * NN;
+    float *ox = gp + blockIdx.z * 2 * NN;
+    const float lam = fscal(scal, F_LAMBDA), inv8 = fscal(scal, F_INV8LAM);
+    __shared__ BwdTile tile;
+    float c_inv8 = 0.0f, c_lam = 0.0f;
+    if (r0 >= 2 && c0 >= 2 && r0 + BT_H + 3 <= N && c0 + 31 <= N)
+        tv_step_bwd_tile<true>(tile, z + blockIdx.z * NN, px, px + NN, gnx, gnx + NN, gz + blockIdx.z * NN, ox, ox + NN,
+                               N, r0, c0, lam, inv8, c_inv8, c_lam);
+    else
+        tv_step_bwd_tile<false>(tile, z + blockIdx.z * NN, px, px + NN, gnx, gnx + NN, gz + blockIdx.z * NN, ox, ox + NN,
+                                N, r0, c0, lam, inv8, c_inv8, c_lam);
     block_pair_to(c_inv8, c_lam, part);
 }
 

@@ -92,7 +92,9 @@ def test_unrolled_gradients_match_fp64_finite_differences():
     dict(mode=1, N=24, V=12, B=35, S=2, K=4, ntv=5, half=8),
     # no prox steps: the whole-image single-step path instead of the tiled one
     dict(mode=0, N=24, V=30, B=35, S=1, K=4, ntv=0, half=8),
-], ids=["lowdose_299_lags", "fewview", "no_tv_steps"])
+    # 64^2: prox-adjoint tiles inside the image (the path without bounds tests) and at its edges
+    dict(mode=0, N=64, V=24, B=95, S=1, K=3, ntv=4, half=8),
+], ids=["lowdose_299_lags", "fewview", "no_tv_steps", "interior_tiles_64"])
 def test_unrolled_gradients_more_cases(case):
     P = need_gpu()
     import torch
