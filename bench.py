@@ -667,13 +667,47 @@ def run_ncu_case(args):
     return 0
 
 
+def measure_eps(P, steps=5):
+    """The error-tolerant few-view form (Sec. 5) against the equality form on
+    the few-view slice (512^2, 32 views, 736 bins, the few-view smoothed
+    ramp, 100 iterations per solve): Gaussian noise of 1 % of the mean line
+    integral, eps = |noise|; whole-solve iterations/s (setup included) and
+    the final relative residual over eps."""
+    import torch
+    N, V, B = WORK["n"], 32, WORK["bins"]
+    g = P.Geometry(N, V, B)
+    p = P.ct_project(g, torch.from_numpy(synth.ellipse_phantom(N, WORK["ellipses"], 0).astype(np.float32)).cuda())
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    noise = (0.01 * float(p.abs().mean()) * torch.randn(p.shape, generator=gen)).cuda()
+    b = p + noise
+    eps = float(torch.linalg.norm(noise))
+    out = {"workload": f"{N}^2, {V} views, {B} bins, b = A v + 1 % Gaussian noise, eps = |noise|, "
+                       "few-view smoothed ramp, 100 iterations"}
+    for name, e in (("equality", 0.0), ("eps", eps)):
+        prm = P.PDTVParams(mode=P.CT_FEWVIEW, iters=100, precond=3, eps=e)
+        ws = P.workspace_for(g, prm)
+        x = torch.empty(N, N, device="cuda")
+        for _ in range(2):
+            P.ct_pdtv_solve(g, b, None, prm, x_out=x, workspace=ws, report=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            P.ct_pdtv_solve(g, b, None, prm, x_out=x, workspace=ws, report=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"iterations_per_s": 100 * steps / (e0.elapsed_time(e1) / 1e3),
+                     "residual_over_eps": float(torch.linalg.norm(P.ct_project(g, x) - b)) / eps}
+    return out
+
+
 def run_form(args):
     """One of the forms' measurements alone, as one JSON line."""
     import __graft_entry__ as entry
     entry.build()
     import paper_1609_06041_gb300 as P
     fn = {"batched": measure_batched, "differentiable": measure_unrolled,
-          "convergence": measure_convergence}[args.form]
+          "convergence": measure_convergence, "eps": measure_eps}[args.form]
     print(json.dumps({"form": args.form, **fn(P)}), flush=True)
     return 0
 
@@ -692,7 +726,7 @@ def main():
                     help="time eager ct_pdtv_solve calls instead of replaying one captured CUDA graph of the solve")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
-    ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "convergence"],
+    ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "convergence", "eps"],
                     help="run only this form's measurement")
     args = ap.parse_args()
     if args.eager:

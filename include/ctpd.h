@@ -296,8 +296,9 @@ size_t ct_pdtv_workspace_bytes(const ct_geometry *geom, const ct_pdtv_params *pa
  * (the only synchronising path of this call).
  * The call enqueues only device work (no host round trip), so it can be
  * captured into a CUDA graph when workspace and report are non-NULL / NULL.
- * Such a call (workspace given, report NULL, resume 0, eps 0) is also
- * captured by the library itself: the first call with a geometry, b, w,
+ * Such a call (workspace given, report NULL, resume 0; with eps > 0 once an
+ * earlier solve has computed D's eigenbasis) is also captured by the
+ * library itself: the first call with a geometry, b, w,
  * x_out, workspace, stream and parameters records the whole solve as a CUDA
  * graph and launches it; later identical calls launch that graph (one
  * launch instead of some 280).  The graph reads the buffers when it runs,

@@ -598,8 +598,11 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                         const ct_pdtv_params *prm, float *x_out, void *workspace,
                         ct_pdtv_report *report, void *stream)
 {
-    // a repeat of an earlier call replays that call's CUDA graph
-    if (g && prm && workspace && !report && !prm->resume && !(prm->eps > 0.0) && solve_graphs_enabled())
+    // a repeat of an earlier call replays that call's CUDA graph (the
+    // error-tolerant form once D's eigenbasis is cached: its first solve
+    // computes it on the host)
+    if (g && prm && workspace && !report && !prm->resume && solve_graphs_enabled() &&
+        (!(prm->eps > 0.0) || eps_basis_ready(g, prm->precond, prm->tau)))
         return solve_graph(g, b, w, prm, x_out, workspace, stream);
     return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, report, stream, true);
 }

@@ -290,6 +290,8 @@ bool toeplitz_eig(const double *t, int n, double *q, double *lambda);
 ct_status eps_basis(const Geometry *g, int precond, double tau_key, const float *taps, cudaStream_t st,
                     const float **q, const float **lambda);
 void eps_cache_free(Geometry *g);
+// whether eps_basis has the basis already (so a solve needs no host step)
+bool eps_basis_ready(const Geometry *g, int precond, double tau_key);
 size_t eps_partial_floats(const Geometry *g);
 void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2, const float *mu0, const float *Q,
                      const float *lambda, double eps, double *scal, float *wbuf, float *s, float *w2, float *part,

@@ -512,6 +512,17 @@ ct_status eps_basis(const Geometry *g, int precond, double tau_key, const float 
     return CT_OK;
 }
 
+bool eps_basis_ready(const Geometry *g, int precond, double tau_key)
+{
+    if (precond == 0) return true;   // D = I: no basis
+    EpsCache *c = static_cast<EpsCache *>(g->eps_cache);
+    if (!c) return false;
+    std::lock_guard<std::mutex> lock(c->mu);
+    for (const EpsEntry &e : c->entries)
+        if (e.precond == precond && e.tau == tau_key) return true;
+    return false;
+}
+
 void eps_cache_free(Geometry *g)
 {
     EpsCache *c = static_cast<EpsCache *>(g->eps_cache);

@@ -180,3 +180,26 @@ def test_eps_form_first_solve_refuses_capture():
     graph.replay()
     torch.cuda.synchronize()
     assert np.array_equal(to_np(x), ref)
+
+
+@pytest.mark.parametrize("precond", [3, 0])
+def test_eps_form_replayed_solves_equal_eager(precond):
+    # once the eigenbasis is cached, a call with a workspace and no report is
+    # captured and replayed by the library; the results equal the eager solve
+    P = need_gpu()
+    import torch
+    N, V, B = 32, 16, 47
+    _, b, nn = noisy_fewview(N, V, B, 9)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=P.CT_FEWVIEW, iters=12, precond=precond, tau=O.default_tau(1, V, 0.0), eps=nn)
+    ws = P.workspace_for(g, prm)
+    bg = to_gpu(b)
+    ref, _ = P.ct_pdtv_solve(g, bg, None, prm, workspace=ws)       # eager (report): caches the basis
+    x = torch.empty(N, N, device="cuda")
+    n0 = P.ct_kernel_launches()
+    for _ in range(3):
+        P.ct_pdtv_solve(g, bg, None, prm, x_out=x, workspace=ws, report=False)
+    n1 = P.ct_kernel_launches()
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref)
+    assert (n1 - n0) % 3 == 0 and n1 > n0
