@@ -203,3 +203,23 @@ def test_eps_form_replayed_solves_equal_eager(precond):
     torch.cuda.synchronize()
     assert torch.equal(x, ref)
     assert (n1 - n0) % 3 == 0 and n1 > n0
+
+
+def test_eps_form_custom_angles():
+    P = need_gpu()
+    N, V, B = 32, 14, 47
+    rng = np.random.default_rng(14)
+    ang = np.sort(rng.uniform(0.0, np.pi, V))
+    x = synth.ellipse_phantom(N, 8, 10)
+    clean = O.project(x, V, B, angles=ang)
+    noise = 0.02 * np.abs(clean).mean() * np.random.default_rng(15).standard_normal((V, B))
+    b = f32(clean + noise)
+    nn = float(np.linalg.norm(b - clean))
+    tau = O.default_tau(1, V, 0.0)
+    taps = O.ramp_taps(1, V, B, tau)
+    sigma, _, _ = O.step_sizes(1, N, V, B, taps, None, tau, angles=ang)
+    g = P.Geometry(N, V, B, angles=ang)
+    prm = P.PDTVParams(mode=P.CT_FEWVIEW, iters=15, precond=1, tau=tau, sigma=sigma, eps=nn)
+    xg, _ = P.ct_pdtv_solve(g, to_gpu(b), None, prm)
+    st, _ = O.pdtv(b, None, taps, 1, 0.0, tau, sigma, 10, 15, N, angles=ang, eps=nn)
+    assert rel_l2(to_np(xg), st.x) <= TOL

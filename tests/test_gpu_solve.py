@@ -258,3 +258,45 @@ def test_repeated_solves_replay_a_graph():
     ref4, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
     torch.cuda.synchronize()
     assert torch.equal(x, ref4)
+
+
+def test_custom_angles_solve_parity():
+    # irregular angles: the projector and backprojector without symmetry
+    # sharing (k_project_mirror, k_backproject_tiles) inside the whole solve
+    P = need_gpu()
+    N, V, B = 48, 40, 71
+    rng = np.random.default_rng(12)
+    ang = np.sort(rng.uniform(0.0, np.pi, V))
+    x = synth.ellipse_phantom(N, 6, 2) * (2.0 / N)
+    b, w = synth.poisson_data(O.project(x, V, B, angles=ang), 1e4, 3)
+    b, w = f32(b), f32(w)
+    tau = O.default_tau(0, V, float(np.mean(1.0 / w)))
+    g = P.Geometry(N, V, B, angles=ang)
+    prm = P.PDTVParams(mode=0, iters=15, beta=0.01, tau=tau, sigma=0.5)
+    xg, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    taps = O.ramp_taps(0, V, B, tau, float(np.mean(1.0 / w)))
+    st, _ = O.pdtv(b, w, taps, 0, 0.01, tau, 0.5, 10, 15, N, angles=ang)
+    assert rel_l2(to_np(xg), st.x) <= TOL
+
+
+@pytest.mark.parametrize("case", [dict(mode=0, precond=0), dict(mode=0, precond=2), dict(mode=1, precond=3),
+                                  dict(mode=0, precond=1, tv_accel=1)],
+                         ids=["plain_cp", "shift_variant", "fewview_smoothed", "fgp"])
+def test_graph_replay_equals_eager_for_every_form(case):
+    P = need_gpu()
+    import torch
+    N, V, B = 48, 60, 70
+    x, b, w = lowdose_case(N, V, B, 4)
+    if case["mode"] == 1:
+        b, w = f32(O.project(synth.ellipse_phantom(N, 6, 4), V, B)), None
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(iters=9, beta=0.01, **case)
+    ws = P.workspace_for(g, prm)
+    bd = to_gpu(b)
+    wd = None if w is None else to_gpu(w)
+    ref, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
+    xo = torch.empty(N, N, device="cuda")
+    for _ in range(3):
+        P.ct_pdtv_solve(g, bd, wd, prm, x_out=xo, workspace=ws, report=False)
+    torch.cuda.synchronize()
+    assert torch.equal(xo, ref)
