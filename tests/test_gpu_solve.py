@@ -300,3 +300,27 @@ def test_graph_replay_equals_eager_for_every_form(case):
         P.ct_pdtv_solve(g, bd, wd, prm, x_out=xo, workspace=ws, report=False)
     torch.cuda.synchronize()
     assert torch.equal(xo, ref)
+
+
+def test_solve_inside_a_callers_graph_capture():
+    # inside the caller's own stream capture the library enqueues the kernels
+    # (no graph of its own); replaying the caller's graph gives the eager result
+    P = need_gpu()
+    import torch
+    N, V, B = 48, 60, 70
+    x, b, w = lowdose_case(N, V, B, 5)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=0, iters=6, beta=0.01)
+    ws = P.workspace_for(g, prm)
+    bd, wd = to_gpu(b), to_gpu(w)
+    ref, _ = P.ct_pdtv_solve(g, bd, wd, prm, workspace=ws)
+    xo = torch.zeros(N, N, device="cuda")
+    P.ct_pdtv_solve(g, bd, wd, prm, x_out=xo, workspace=ws, report=False)   # warm (creates the fork stream)
+    torch.cuda.synchronize()
+    xo.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        P.ct_pdtv_solve(g, bd, wd, prm, x_out=xo, workspace=ws, report=False)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(xo, ref)
