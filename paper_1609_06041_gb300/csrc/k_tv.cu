@@ -5,7 +5,7 @@
 // across the last row/column), div = -grad^T.  lam = 0 gives max(0, z).
 //
 // Temporal blocking: one block owns a tile of tc x tr pixels and holds it
-// with a halo of H = steps + 1 pixels on every side.  Each step spoils one
+// with a halo of H >= steps + 1 pixels on every side.  Each step spoils one
 // more ring of the halo (its outermost cells see zeros instead of their
 // neighbours), so after `steps` steps the tile holds exactly what a
 // whole-image iteration would give, with no grid-wide synchronisation and
@@ -43,9 +43,14 @@ struct TvTiles {
 // Column tiles are as wide as the region allows; rows are split so that the
 // tiles of one image about fill the GPU once (one block per SM), but no
 // narrower than TV_MIN_TR rows and no taller than the region.
-static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr)
+// Halo: steps + 1; the trajectory variant rounds it up to even, so that tile
+// origins (and every lane's column pair) fall on even columns: with N even
+// each pair of its many stores is one aligned 8-byte store.
+__host__ __device__ __forceinline__ int tv_halo(int steps, bool even) { return even ? (steps + 2) & ~1 : steps + 1; }
+
+static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr, bool even = false)
 {
-    const int H = steps + 1;
+    const int H = tv_halo(steps, even);
     TvTiles t;
     t.tc = 64 - 2 * H;
     t.ncb = (N + t.tc - 1) / t.tc;
@@ -79,7 +84,8 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
     __shared__ float2 pub_y[(TV_ROWS + 2) * 32];
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int H = steps + 1, Sr = tr + 2 * H;
+    const int H = tv_halo(steps, TRAJ), Sr = tr + 2 * H;
+    const bool vec2 = TRAJ && (N & 1) == 0;   // column pairs 8-byte aligned
     const int R0 = blockIdx.y * tr - H, C0 = blockIdx.x * tc - H;
     const int c0 = C0 + 2 * lane;   // image columns c0, c0 + 1 of this lane
     const size_t NN = (size_t)N * N, img = blockIdx.z;
@@ -205,13 +211,22 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                 for (int j = 0; j < TV_J; ++j) {
                     const int li = w + TV_WARPS * j, rr = R0 + li;
                     if (li >= H && li < H + tr && rr < N) {
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int lj = 2 * lane + e, cc = C0 + lj;
+                        if (vec2) {   // H, tc even: both columns of the pair are interior, or neither
+                            const int lj = 2 * lane, cc = C0 + lj;
                             if (lj >= H && lj < H + tc && cc < N) {
                                 const size_t gi = (size_t)rr * N + cc;
-                                tp[gi] = pxr[j][e];
-                                tp[NN + gi] = pyr[j][e];
+                                *reinterpret_cast<float2 *>(tp + gi) = make_float2(pxr[j][0], pxr[j][1]);
+                                *reinterpret_cast<float2 *>(tp + NN + gi) = make_float2(pyr[j][0], pyr[j][1]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const int lj = 2 * lane + e, cc = C0 + lj;
+                                if (lj >= H && lj < H + tc && cc < N) {
+                                    const size_t gi = (size_t)rr * N + cc;
+                                    tp[gi] = pxr[j][e];
+                                    tp[NN + gi] = pyr[j][e];
+                                }
                             }
                         }
                     }
@@ -257,7 +272,8 @@ void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
 {
     // a batch fills the GPU with its images: the tiles of one image only
     // need to cover n_sm / batch SMs
-    const TvTiles t = tv_tiles(n, steps, std::max(1, n_sm / std::max(1, batch)), min_rows > 0 ? min_rows : TV_MIN_TR);
+    const TvTiles t = tv_tiles(n, steps, std::max(1, n_sm / std::max(1, batch)), min_rows > 0 ? min_rows : TV_MIN_TR,
+                               traj != nullptr);
     const dim3 grid(t.ncb, t.nrb, std::max(1, batch));
     counted();
     if (traj)
