@@ -345,13 +345,13 @@ ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const fl
  * previous iteration's dual field.
  *
  * ct_unrolled_forward writes x_K (batch x N x N) and keeps one checkpoint
- * per iteration (x, mu, mubar, TV dual field, and z = x - tau A^T mubar and
- * the band partial sums of A x_{k+1}, which it computes anyway) in
- * `workspace` (ct_unrolled_workspace_bytes, device; about 0.9 GB for 16
- * slices of 256^2, 180 views, 10 iterations, 10 prox steps).
+ * per iteration (x, mu, mubar, TV dual field, and z = x - tau A^T mubar,
+ * the band partial sums of A x_{k+1} and the dual fields after each inner
+ * prox step, which it computes anyway) in `workspace`
+ * (ct_unrolled_workspace_bytes, device; about 1.6 GB for 16 slices of
+ * 256^2, 180 views, 10 iterations, 10 prox steps).
  * ct_unrolled_backward, given grad_x = dL/dx_K (batch x N x N, device) and
- * the workspace of the forward call with the same arguments, recomputes
- * each iteration's prox trajectory from its checkpoint and applies the
+ * the workspace of the forward call with the same arguments, applies the
  * adjoint of every step in reverse order (A^T for A, A for A^T, D^T for D,
  * the adjoints of the projected-gradient steps); it writes grad (device, 2*half_len floats): grad[0 .. 2*half_len-2]
  * = dL/dtaps, grad[2*half_len-1] = dL/dbeta (0 for CT_FEWVIEW).  tau and

@@ -8,14 +8,14 @@
 //   z_k      = x_k - tau A^T mubar_k
 //   x_{k+1}  = prox(z_k), n_tv projected-gradient steps from p_k -> p_{k+1}
 //   mu_{k+1}, mubar_{k+1} = dual step (Step 3 and the next Step 1)
-// The checkpoint of iteration k is (x_k, mu_k, mubar_k, p_k), plus z_k and
-// the band partial sums of A x_{k+1}, which the forward computes anyway: the
-// backward then needs no A^T for z_k and no A for the dual step's residual.
-// Backward, from dL/dx_K, for k = K-1 .. 0: recompute the prox trajectory
-// from the checkpoint, apply the adjoint of the dual step
-// (k_dual_bwd_fft), of A (A^T), of the prox (k_tv_*_bwd) and of A^T (A),
-// accumulating dL/dt (tap correlations) and dL/dlambda.  sigma and tau are
-// constants of the unroll (not differentiated).
+// The checkpoint of iteration k is (x_k, mu_k, mubar_k, p_k), plus z_k, the
+// band partial sums of A x_{k+1} and the prox's intermediate dual fields,
+// which the forward computes anyway: the backward then needs no A^T for z_k,
+// no A for the dual step's residual and no second run of the prox.
+// Backward, from dL/dx_K, for k = K-1 .. 0: apply the adjoint of the dual
+// step (k_dual_bwd_fft), of A (A^T), of the prox (k_tv_*_bwd) and of A^T
+// (A), accumulating dL/dt (tap correlations) and dL/dlambda.  sigma and tau
+// are constants of the unroll (not differentiated).
 #include <algorithm>
 
 #include "ctpd_internal.cuh"
@@ -57,7 +57,8 @@ UL layout(const Geometry *g, int S, int half, int iters, int ntv)
     L.gm1 = o;   o += a256(F * S * I);
     L.rr = o;    o += a256(F * S * I);
     L.vv = o;    o += a256(F * S * I);
-    L.traj = o;  o += a256(F * (size_t)(ntv + 1) * S * 2 * J);
+    // the prox's dual fields after steps 1 .. n_tv - 1 of every iteration
+    L.traj = o;  o += a256(F * (size_t)std::max(ntv - 1, 0) * iters * S * 2 * J);
     // block pairs of every prox adjoint launch of the backward pass
     L.pa = o;    o += a256(sizeof(float) * tv_px_blocks(g->n, S) * (size_t)iters * (ntv + 1));
     L.psum = o;  o += a256(sizeof(float) * pair_sums_scratch_floats());
@@ -82,6 +83,13 @@ CK ck_at(char *ws, const UL &L, const Geometry *g, int S, int k)
     c.mubar = c.mu + S * I;
     c.p = c.mubar + S * I;
     return c;
+}
+
+// the dual field of iteration k's prox after inner step l (1 <= l < n_tv)
+float *traj_at(char *ws, const UL &L, const Geometry *g, int S, int ntv, int k, int l)
+{
+    const size_t f = (size_t)S * 2 * g->n * g->n;
+    return (float *)(ws + L.traj) + ((size_t)k * (ntv - 1) + (l - 1)) * f;
 }
 
 enum { U_LAMACC = S_RED0 + 1, U_INV8ACC = S_RED0 + 2 };
@@ -162,7 +170,6 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
     double *scal = (double *)(ws + L.scal), *scal2 = (double *)(ws + L.scal2);
     float2 *hhat = (float2 *)(ws + L.hhat);
     float *winv = (float *)(ws + L.winv), *zk = (float *)(ws + L.zk), *bk = (float *)(ws + L.bk);
-    float *tmpa = (float *)(ws + L.gp), *tmpb = (float *)(ws + L.gp2);
     const size_t bstride = (size_t)S * I * proj_bands(N);
 
     cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
@@ -181,7 +188,9 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
         float *z = zk + (size_t)k * S * J, *band = bk + (size_t)k * bstride;
         backproject(g, c.mubar, z, 1, c.x, scal, S, ws, L, st);                       // z = x - tau A^T mubar
         if (fused) {
-            launch_tv(z, c.p, n.p, n.x, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 1, scal, st, false, S);
+            // the prox, writing its intermediate dual fields for the backward pass
+            launch_tv(z, c.p, n.p, n.x, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 1, scal, st, false, S,
+                      tv_iters > 1 ? traj_at(ws, L, g, S, tv_iters, k, 1) : nullptr);
             launch_project_bands(g, n.x, band, S, st);
             launch_dual_fft_batched(g, hhat, band, b, c.mu, n.mu, n.mubar, winv, lowdose, scal, S, st);
             continue;
@@ -191,7 +200,7 @@ extern "C" ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b
         } else {
             const float *src = c.p;
             for (int l = 0; l < tv_iters; ++l) {
-                float *dst = (l == tv_iters - 1) ? n.p : ((l & 1) ? tmpb : tmpa);
+                float *dst = (l == tv_iters - 1) ? n.p : traj_at(ws, L, g, S, tv_iters, k, l + 1);
                 launch_tv_step(z, src, dst, N, S, scal, st);
                 src = dst;
             }
@@ -238,14 +247,12 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     float *gm = (float *)(ws + L.gm), *gmb = (float *)(ws + L.gmb), *gmu = (float *)(ws + L.gmu);
     float *gr = (float *)(ws + L.gr), *gm1 = (float *)(ws + L.gm1), *rr = (float *)(ws + L.rr),
           *vv = (float *)(ws + L.vv);
-    float *traj = (float *)(ws + L.traj);
     float *pa = (float *)(ws + L.pa), *psum = (float *)(ws + L.psum);
     const size_t npx = tv_px_blocks(N, S), ncall = (size_t)iters * (tv_iters + 1);
     float *tcorr = (float *)(ws + L.tcorr);
     float2 *tacc = (float2 *)(ws + L.tacc);
     const int nl = 2 * half_len - 1;
     const double lam = lowdose ? tau * beta : tau;
-    const bool fused = tv_fused(tau, beta, mode, tv_iters);
 
     // the scalars of the forward pass are still in the workspace; reset the accumulators
     set_scalars(scal, scal2, tau, sigma, beta, mode, st);
@@ -259,13 +266,10 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
         const float *z = zk + (size_t)k * S * J;
-        // recompute the prox trajectory p_k = tp(0) .. tp(n_tv) = p_{k+1}
-        auto tp = [&](int l) { return l == 0 ? c.p : traj + (size_t)l * S * 2 * J; };
-        if (fused)
-            launch_tv(z, c.p, tp(tv_iters), nullptr, N, g->n_sm, TV_UNROLL_ROWS, tv_iters, 0, scal, st, false, S,
-                      traj + (size_t)S * 2 * J);
-        else
-            for (int l = 0; l < tv_iters; ++l) launch_tv_step(z, tp(l), tp(l + 1), N, S, scal, st);
+        // the prox trajectory p_k = tp(0) .. tp(n_tv) = p_{k+1}, kept by the forward pass
+        auto tp = [&](int l) -> const float * {
+            return l == 0 ? c.p : (l == tv_iters ? n.p : traj_at(ws, L, g, S, tv_iters, k, l));
+        };
         // adjoint of the dual step (A x_{k+1} from the checkpoint's band sums)
         launch_dual_bwd_fft(g, hhat, bk + (size_t)k * bstride, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv,
                             lowdose, scal, S, st);
