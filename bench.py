@@ -267,6 +267,9 @@ def measure_unrolled(P, steps=3):
     import torch
     N, V, B, S = 256, 180, 368, 16
     g = P.Geometry(N, V, B)
+    g.autotune(batch=S)   # launch shapes for the batch of the unrolled form (untimed)
+    g1 = P.Geometry(N, V, B)
+    g1.autotune()         # and for the single-slice solve it is compared with
     xt = torch.from_numpy(np.stack([synth.ellipse_phantom(N, 10, s) * (2.0 / N) for s in range(S)])
                           .astype(np.float32)).cuda()
     p = P.ct_project(g, xt).cpu().numpy()
@@ -294,21 +297,22 @@ def measure_unrolled(P, steps=3):
     torch.cuda.synchronize()
     t_fb = e0.elapsed_time(e1) / steps
     prm = P.PDTVParams(mode=0, iters=10, beta=0.01)
-    wsp = P.workspace_for(g, prm)
+    wsp = P.workspace_for(g1, prm)
     x1 = torch.empty(N, N, device="cuda")
     for _ in range(2):
-        P.ct_pdtv_solve(g, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
+        P.ct_pdtv_solve(g1, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps * 4):
-        P.ct_pdtv_solve(g, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
+        P.ct_pdtv_solve(g1, b[0], w[0], prm, x_out=x1, workspace=wsp, report=False)
     e1.record(stream)
     torch.cuda.synchronize()
     t_one = e0.elapsed_time(e1) / (steps * 4)
     return {"workload": "16 slices of 256^2, 180 views, 368 bins, I0 1e4, 10 unrolled iterations, "
                         "learnable log beta + 128 taps, MSE loss, forward + backward",
             "fwd_bwd_slices_per_s": S / (t_fb / 1e3), "fwd_bwd_ms": t_fb,
-            "plain_solve_slices_per_s": 1.0 / (t_one / 1e3), "plain_solve_ms": t_one}
+            "plain_solve_slices_per_s": 1.0 / (t_one / 1e3), "plain_solve_ms": t_one,
+            "tuning": g.tuning, "plain_solve_tuning": g1.tuning}
 
 
 CHECKPOINTS = (1, 3, 10, 30, 100, 300, 1000)

@@ -357,6 +357,12 @@ ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const fl
  * = dL/dtaps, grad[2*half_len-1] = dL/dbeta (0 for CT_FEWVIEW).  tau and
  * sigma are constants of the unroll.  b, w: batch x V x B; w > 0, required
  * for CT_LOWDOSE.  Needs n_bins <= 4096.  Both calls only enqueue work.
+ * ct_unrolled_backward runs the tap correlations on a side stream of the
+ * device (created on first use, kept until exit; make the first call
+ * outside stream capture), forked from `stream` and joined back into it
+ * with events, so later work on `stream` sees grad and the call can be
+ * captured into a CUDA graph; concurrent calls from several host threads
+ * share that side stream.
  */
 size_t ct_unrolled_workspace_bytes(const ct_geometry *geom, int batch, int half_len, int iters, int tv_iters);
 ct_status ct_unrolled_forward(const ct_geometry *geom, const float *b, const float *w, int batch,

@@ -62,6 +62,29 @@ ct_status ctpd::read_report(const void *workspace, ct_pdtv_report *report)
 }
 
 namespace {
+std::mutex g_fork_mu;
+Fork g_forks[64];
+}  // namespace
+
+Fork *ctpd::fork_for(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_fork_mu);
+    Fork &f = g_forks[dev];
+    if (!f.ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        f.ready = true;
+    }
+    return &f;
+}
+
+namespace {
 
 ct_status cuda_check(const char *where)
 {
@@ -146,33 +169,6 @@ void lanczos_norm(Op op, float *t, float *tp, float *w, size_t n, int k, double 
     launch_lanczos_max(scal, base, k, slot, st);
 }
 
-// A second stream and two events per device for forking work inside one
-// solve (created on first use, kept until exit).
-struct Fork {
-    bool ready = false;
-    cudaStream_t s;
-    cudaEvent_t fork, join;
-};
-std::mutex g_fork_mu;
-Fork g_forks[64];
-
-Fork *fork_for(int dev)
-{
-    if (dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lock(g_fork_mu);
-    Fork &f = g_forks[dev];
-    if (!f.ready) {
-        cudaError_t e = cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        f.ready = true;
-    }
-    return &f;
-}
 
 
 // ---------------------------------------------------------------------
@@ -740,11 +736,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             }
             if (lowdose) {
                 cudaStream_t s2 = st;
-                if (fk) {
-                    cudaEventRecord(fk->fork, st);
-                    cudaStreamWaitEvent(fk->s, fk->fork, 0);
-                    s2 = fk->s;
-                }
+                if (fk) s2 = fork_begin(fk, st);
                 float *sw = aux;
                 launch_sqrt(winv, sw, I, s2);
                 auto op_wdw = [&](const float *v, float *out) { filter(v, out, sw, sw, 0, s2); };
@@ -764,10 +756,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 backproject(mubar, out, 0, nullptr);
             };
             lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, S_LZ, S_LN0, partials, ticket, S_NADA, st);
-            if (fk) {
-                cudaEventRecord(fk->join, fk->s);
-                cudaStreamWaitEvent(st, fk->join, 0);
-            }
+            if (fk) fork_end(fk, st);
         }
         launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);
         launch_scalars(scal, SC_LAMBDA, lowdose ? prm->beta : 0.0, 0, 0, mode, st);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "../../include/ctpd.h"
 
@@ -66,16 +67,45 @@ ct_status read_report(const void *workspace, ct_pdtv_report *report);
 struct ct_geometry : public ctpd::Geometry {};
 
 namespace ctpd {
-// ct_pdtv_solve; allow_fork lets one solve run independent setup work on a
-// second stream of the device (off for solves already run side by side).
 // Drops the geometry's cached solve graphs (api.cu); the tuning calls use it,
 // as the graphs hold the old launch shapes.
 void graph_cache_clear(Geometry *g);
-// fork (optional): the stream and events to fork the setup's second branch
-// onto instead of the device's shared ones.
+// ct_pdtv_solve; allow_fork lets one solve run independent setup work on a
+// second stream of the device (off for solves already run side by side).
+// fork (optional): the Fork to put the setup's second branch on instead of
+// the device's shared one.
 ct_status pdtv_solve(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
                      float *x_out, void *workspace, ct_pdtv_report *report, void *stream, bool allow_fork,
                      void *fork = nullptr);
+
+// A side stream and two events for running independent work beside a
+// caller's stream: fork_begin makes the side stream wait for the work
+// enqueued so far on `st` and returns it; fork_end makes `st` wait for
+// everything enqueued on the side stream.  Each record-and-wait pair runs
+// under the Fork's lock, so calls from several host threads each wait on
+// their own record.  Both are stream-ordered and can be captured.
+struct Fork {
+    bool ready = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    std::mutex mu;
+};
+inline cudaStream_t fork_begin(Fork *f, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(f->mu);
+    cudaEventRecord(f->fork, st);
+    cudaStreamWaitEvent(f->s, f->fork, 0);
+    return f->s;
+}
+inline void fork_end(Fork *f, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(f->mu);
+    cudaEventRecord(f->join, f->s);
+    cudaStreamWaitEvent(st, f->join, 0);
+}
+// The device's shared Fork (created on first use, kept until exit; NULL if
+// that fails or dev is outside [0, 64)).
+Fork *fork_for(int dev);
 }  // namespace ctpd
 
 namespace ctpd {

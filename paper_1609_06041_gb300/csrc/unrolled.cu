@@ -262,6 +262,10 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
     cudaMemsetAsync(tacc, 0, sizeof(float2) * nl, st);
     cudaMemsetAsync(pa, 0, sizeof(float) * npx * ncall, st);
     float *part = pa;   // the next launch's block pairs
+    // the tap correlations of a step read only its dual adjoints, so they
+    // run on the device's side stream beside the adjoints of A^T and the prox
+    int dev = -1;
+    Fork *fk = cudaGetDevice(&dev) == cudaSuccess ? fork_for(dev) : nullptr;
     cudaMemcpyAsync(gx, grad_x, sizeof(float) * S * J, cudaMemcpyDeviceToDevice, st);
     for (int k = iters - 1; k >= 0; --k) {
         CK c = ck_at(ws, L, g, S, k), n = ck_at(ws, L, g, S, k + 1);
@@ -274,7 +278,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
         launch_dual_bwd_fft(g, hhat, bk + (size_t)k * bstride, b, winv, c.mu, n.mu, gm, gmb, gmu, gr, gm1, rr, vv,
                             lowdose, scal, S, st);
         launch_tapcorr_acc(gm1, rr, sigma, lowdose ? gmb : nullptr, vv, -sigma, S * V, g->n_bins, half_len, tcorr,
-                           tacc, st);
+                           tacc, fk ? fork_begin(fk, st) : st);
         // dL/dx_{k+1} += A^T dL/dr  (into gz, then swapped)
         backproject(g, gr, gz, 1, gx, scal2, S, ws, L, st);
         std::swap(gx, gz);
@@ -291,6 +295,7 @@ extern "C" ct_status ct_unrolled_backward(const ct_geometry *geom, const float *
         // x_k enters through z_k only: dL/dx_k = dL/dz_k; dL/dmubar_k = -tau A dL/dz_k
         std::swap(gx, gz);
         launch_project_bands(g, gx, band, S, st);
+        if (fk) fork_end(fk, st);   // the correlations are done with gmb, gm1, rr and vv
         launch_band_reduce_scaled(g, band, gmb, scal + S_RED0, S, st);
         std::swap(gm, gmu);   // dL/dmu_k
     }
