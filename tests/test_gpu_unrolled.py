@@ -258,3 +258,49 @@ def test_unrolled_custom_angles_gradients():
     eps = 1e-4 * np.abs(taps).max() / np.abs(d).max()
     fd = (oloss(taps + eps * d, beta) - oloss(taps - eps * d, beta)) / (2 * eps)
     assert float(to_np(t.grad) @ d) == pytest.approx(fd, rel=3e-3)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_unrolled_backward_is_deterministic_and_capturable(mode):
+    # the tap correlations run on a side stream beside the other adjoints:
+    # repeated calls give the same gradients bit for bit, on another caller
+    # stream too, and forward + backward captured in a CUDA graph replay to
+    # the eager results
+    P = need_gpu()
+    import torch
+    N, V, B, S, K, ntv, half = 64, 90, 95, 4, 3, 5, 16
+    xt, bs, ws = make_batch(N, V, B, S, 21)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.02
+    g = P.Geometry(N, V, B)
+    bd, td = to_gpu(bs), to_gpu(taps)
+    wd = to_gpu(ws) if mode == 0 else None
+    wsp = torch.empty(P.ct_unrolled_workspace_bytes(g, S, half, K, ntv), dtype=torch.uint8, device="cuda")
+    gx = to_gpu(np.random.default_rng(5).standard_normal((S, N, N)))
+
+    def run():
+        x = P.ct_unrolled_forward(g, bd, wd, td, tau, sigma, beta, mode, K, ntv, wsp)
+        return x, P.ct_unrolled_backward(g, bd, wd, td, tau, sigma, beta, mode, K, ntv, gx, wsp)
+
+    x0, g0 = run()
+    x1, g1 = run()
+    torch.cuda.synchronize()
+    assert torch.equal(x0, x1) and torch.equal(g0, g1)
+    assert float(g0[:2 * half - 1].abs().max()) > 0
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        x2, g2 = run()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    assert torch.equal(x0, x2) and torch.equal(g0, g2)
+    xo = torch.zeros(S, N, N, device="cuda")
+    go = torch.zeros(2 * half, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        xc, gc = run()
+        xo.copy_(xc)
+        go.copy_(gc)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(xo, x0) and torch.equal(go, g0)
