@@ -394,7 +394,10 @@ __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP
 
 // ROWS = 2: up to 16 items (1024 threads, 64 registers); ROWS = 4: more
 // loads in flight per thread, up to 12 items (768 threads, 85 registers).
-template <int ROWS>
+// DEEP: the staging issues the loads of four pairs per thread before it
+// stores them, for grids of few blocks whose threads each stage many pairs
+// (few views); otherwise one pair at a time (fewer registers).
+template <int ROWS, bool DEEP>
 __global__ void __launch_bounds__(ROWS == 2 ? 1024 : 768)
 k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                const int2 *__restrict__ row_items, int n_row, const int2 *__restrict__ col_items, int n_col,
@@ -426,36 +429,94 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
     // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
     // the line N-1-s0-t read backwards (image value at N-1-i); one thread
     // forms both bands' pairs of (t, i) and stores them as one float4
-    {
-        const int lx = tid & 31, nw = nth >> 5;
-        if (rows) {
-            // warps take 32-pair chunks of the 16 steps, lanes neighbouring pairs
-            const int nch = (CW + 31) >> 5;
-            for (int c = tid >> 5; c < MR * nch; c += nw) {
-                const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
-                if (ii < CW) {
-                    const int i = ii - 2;
-                    const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
-                    const float a0 = (i >= 0 && i < N) ? ra[i] : 0.0f;
-                    const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
-                    const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
-                    const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
-                    Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+    if constexpr (DEEP) {
+        // the same pairs, each thread issuing the loads of SU of them before
+        // it stores any, so that SU L2 round trips overlap
+        {
+            constexpr int SU = 4;
+            const int lx = tid & 31, nw = nth >> 5;
+            float a0[SU], a1[SU], b0[SU], b1[SU];
+            if (rows) {
+                const int nch = (CW + 31) >> 5, nc = MR * nch;
+                for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
+    #pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int c = c0 + u * nw;
+                        const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
+                        const bool ok = c < nc && ii < CW;
+                        const int i = ii - 2;
+                        const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
+                        a0[u] = (ok && i >= 0 && i < N) ? ra[i] : 0.0f;
+                        a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
+                        b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
+                        b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
+                    }
+    #pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int c = c0 + u * nw;
+                        const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
+                        if (c < nc && ii < CW)
+                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), a1[u] - a0[u], 0.5f * (b0[u] + b1[u]),
+                                                         b1[u] - b0[u]);
+                    }
+                }
+            } else {
+                const int t = lx & 15;
+                const float *ia = img + (s0 + t), *ib = img + (N - 1 - s0 - t);   // columns of bands A, B
+                const int nc = (CW + 1) >> 1;
+                for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
+    #pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int ii = 2 * (c0 + u * nw) + (lx >> 4);
+                        const bool ok = c0 + u * nw < nc && ii < CW;
+                        const int i = ii - 2;   // rows i, i + 1 (band A), N-1-i, N-2-i (band B); N N < 2^31
+                        a0[u] = (ok && i >= 0 && i < N) ? ia[i * N] : 0.0f;
+                        a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ia[(i + 1) * N] : 0.0f;
+                        b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? ib[(N - 1 - i) * N] : 0.0f;
+                        b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? ib[(N - 2 - i) * N] : 0.0f;
+                    }
+    #pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int ii = 2 * (c0 + u * nw) + (lx >> 4);
+                        if (c0 + u * nw < nc && ii < CW)
+                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), a1[u] - a0[u], 0.5f * (b0[u] + b1[u]),
+                                                         b1[u] - b0[u]);
+                    }
                 }
             }
-        } else {
-            // lanes take the 16 steps (columns) of two neighbouring pairs:
-            // 64-byte row segments in, conflict-free float4 stores (odd SP)
-            const int t = lx & 15, ca = s0 + t, cb = N - 1 - s0 - t;
-            for (int c = tid >> 5; 2 * c < CW; c += nw) {
-                const int ii = 2 * c + (lx >> 4);
-                if (ii < CW) {
-                    const int i = ii - 2;
-                    const float a0 = (i >= 0 && i < N) ? img[(size_t)i * N + ca] : 0.0f;
-                    const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
-                    const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
-                    const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
-                    Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+        }
+    } else {
+        {
+            const int lx = tid & 31, nw = nth >> 5;
+            if (rows) {
+                // warps take 32-pair chunks of the 16 steps, lanes neighbouring pairs
+                const int nch = (CW + 31) >> 5;
+                for (int c = tid >> 5; c < MR * nch; c += nw) {
+                    const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
+                    if (ii < CW) {
+                        const int i = ii - 2;
+                        const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
+                        const float a0 = (i >= 0 && i < N) ? ra[i] : 0.0f;
+                        const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
+                        const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
+                        const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
+                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+                    }
+                }
+            } else {
+                // lanes take the 16 steps (columns) of two neighbouring pairs:
+                // 64-byte row segments in, conflict-free float4 stores (odd SP)
+                const int t = lx & 15, ca = s0 + t, cb = N - 1 - s0 - t;
+                for (int c = tid >> 5; 2 * c < CW; c += nw) {
+                    const int ii = 2 * c + (lx >> 4);
+                    if (ii < CW) {
+                        const int i = ii - 2;
+                        const float a0 = (i >= 0 && i < N) ? img[(size_t)i * N + ca] : 0.0f;
+                        const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
+                        const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
+                        const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
+                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+                    }
                 }
             }
         }
@@ -541,14 +602,12 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
         const int groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
         const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
         const dim3 grd2(N / (2 * MR), groups, batch);
-        if (rows4)
-            k_project_quad<4><<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items,
-                                                            g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
-                                                            pg, partial);
-        else
-            k_project_quad<2><<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items,
-                                                            g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins,
-                                                            pg, partial);
+        // few blocks (few views): each thread stages many pairs, so issue their loads four at a time
+        const bool deep = (long)grd2.x * grd2.y * grd2.z < 2L * g->n_sm;
+        auto kern = rows4 ? (deep ? k_project_quad<4, true> : k_project_quad<4, false>)
+                          : (deep ? k_project_quad<2, true> : k_project_quad<2, false>);
+        kern<<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items,
+                                           g->n_col_items, N, g->n_views, g->n_bins, pg, partial);
     } else if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // two mirrored 16-step bands per block: N/32 partial slots, as below
         dim3 grd2(N / (2 * MR), grd.y, batch);
@@ -967,8 +1026,10 @@ void kernel_attrs_joseph()
     cudaFuncSetAttribute(k_backproject_orbit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_backproject_orbit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
-    cudaFuncSetAttribute(k_project_quad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
-    cudaFuncSetAttribute(k_project_quad<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_quad<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }
