@@ -680,13 +680,14 @@ def measure_eps(P, steps=5):
     import torch
     N, V, B = WORK["n"], 32, WORK["bins"]
     g = P.Geometry(N, V, B)
+    g.autotune()   # launch shapes for this geometry (untimed)
     p = P.ct_project(g, torch.from_numpy(synth.ellipse_phantom(N, WORK["ellipses"], 0).astype(np.float32)).cuda())
     gen = torch.Generator(device="cpu").manual_seed(7)
     noise = (0.01 * float(p.abs().mean()) * torch.randn(p.shape, generator=gen)).cuda()
     b = p + noise
     eps = float(torch.linalg.norm(noise))
     out = {"workload": f"{N}^2, {V} views, {B} bins, b = A v + 1 % Gaussian noise, eps = |noise|, "
-                       "few-view smoothed ramp, 100 iterations"}
+                       "few-view smoothed ramp, 100 iterations", "tuning": g.tuning}
     for name, e in (("equality", 0.0), ("eps", eps)):
         prm = P.PDTVParams(mode=P.CT_FEWVIEW, iters=100, precond=3, eps=e)
         ws = P.workspace_for(g, prm)

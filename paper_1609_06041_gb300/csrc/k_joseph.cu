@@ -832,7 +832,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <bool AL>
 __global__ void __launch_bounds__(ORB_TH, 8)
 k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, const float4 *__restrict__ trig,
-                    int N, int V, int B, int nsl)
+                    int N, int V, int B, int nsl, int fin, float *out, const float *xin,
+                    const double *__restrict__ scal)
 {
     // raw[buffer][view][row (v, v+V/2)][window (e, mirror e, e90, mirror e90)][value]
     extern __shared__ __align__(16) unsigned char osm[];
@@ -948,15 +949,22 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
         }
         __syncthreads();   // the buffer is refilled two chunks later
     }
-    float *pp = partial + ((size_t)img * nsl + slice) * N * N;
+    // fin 0: the slice's partial image; with a single slice the sums are
+    // complete and the block writes k_orbit_reduce's result itself: fin 1
+    // out = sum, fin 2 out = xin - tau sum
+    float *pp = (fin ? out : partial) + ((size_t)img * (fin ? 1 : nsl) + slice) * N * N;
+    const float *xq0 = fin == 2 ? xin + (size_t)img * N * N : nullptr;
+    const float tau = fin == 2 ? fscal(scal, F_TAU) : 0.0f;
 #pragma unroll
     for (int j = 0; j < ORB_PX; ++j) {
         const int rj = r + j * ORB_TY;
         if (rj < half && c < N) {
-            pp[(size_t)rj * N + c] = acc[j][0];
-            pp[(size_t)c * N + (N - 1 - rj)] = acc[j][1];              // R90 (r, c) = (c, N-1-r)
-            pp[(size_t)(N - 1 - rj) * N + (N - 1 - c)] = acc[j][2];    // R180 (r, c) = (N-1-r, N-1-c)
-            pp[(size_t)(N - 1 - c) * N + rj] = acc[j][3];              // R270 (r, c) = (N-1-c, r)
+            const size_t o[4] = {(size_t)rj * N + c,                    // P
+                                 (size_t)c * N + (N - 1 - rj),          // R90 (r, c) = (c, N-1-r)
+                                 (size_t)(N - 1 - rj) * N + (N - 1 - c), // R180 (r, c) = (N-1-r, N-1-c)
+                                 (size_t)(N - 1 - c) * N + rj};         // R270 (r, c) = (N-1-c, r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pp[o[k]] = fin == 2 ? xq0[o[k]] - tau * acc[j][k] : acc[j][k];
         }
     }
 }
@@ -997,13 +1005,17 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     const int q = g->n / 2;
     const int nsl = orbit_slices(g);
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, nsl * batch);
-    counted(2);
+    // one slice: the orbit kernel writes the result (the same arithmetic as
+    // k_orbit_reduce with one slice), and no reduction pass runs
+    const int fin = nsl == 1 ? 1 + (mode != 0) : 0;
+    counted(fin ? 1 : 2);
     if (g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0)
-        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
-                                                                                g->n_views, g->n_bins, nsl);
+        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(
+            y, partial, g->d_trig, g->n, g->n_views, g->n_bins, nsl, fin, out, xin, scal);
     else
-        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(y, partial, g->d_trig, g->n,
-                                                                                 g->n_views, g->n_bins, nsl);
+        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(
+            y, partial, g->d_trig, g->n, g->n_views, g->n_bins, nsl, fin, out, xin, scal);
+    if (fin) return;
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
     if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN, nsl);

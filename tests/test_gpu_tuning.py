@@ -92,3 +92,36 @@ def test_orbit_slices_limit_large_view_count():
         g.set_tuning(orbit_slices=2)
     g.set_tuning(orbit_slices=4)
     assert g.tuning["orbit_slices"] == 4
+
+
+def test_single_orbit_slice_writes_the_result():
+    # with one base-view slice the orbit backprojector writes A^T y (and, in
+    # the solve, z = x - tau A^T mubar) itself, with no reduction pass:
+    # batched A^T and the low-dose solve against the oracle
+    P = need_gpu()
+    import torch
+    N, V, B = 64, 90, 95
+    g = P.Geometry(N, V, B)
+    g.set_tuning(orbit_slices=1)
+    ys = np.stack([f32(synth.random_sinogram(V, B, 20 + s)) for s in range(3)])
+    out = to_np(P.ct_backproject(g, to_gpu(ys)))
+    for s in range(3):
+        assert rel_l2(out[s], O.backproject(ys[s], N)) <= TOL
+    x_true = synth.ellipse_phantom(N, 10, 1) * (2.0 / N)
+    b, w = synth.poisson_data(O.project(x_true, V, B), 1e4, 101)
+    b, w = f32(b), f32(w)
+    kappa = float(np.mean(1.0 / w))
+    tau = O.default_tau(0, V, kappa)
+    taps = O.ramp_taps(0, V, B, tau, kappa)
+    prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=20, tv_iters=10, precond=1, beta=0.01, tau=tau, sigma=0.5)
+    n0 = P.ct_kernel_launches()
+    x, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    torch.cuda.synchronize()
+    st, _ = O.pdtv(b, w, taps, 0, 0.01, tau, 0.5, 10, 20, N)
+    assert rel_l2(to_np(x), st.x) <= 1e-3
+    g.set_tuning(orbit_slices=2)
+    n1 = P.ct_kernel_launches()
+    P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    torch.cuda.synchronize()
+    # two slices: one reduction pass more per iteration (20) and per A^T of the setup
+    assert (P.ct_kernel_launches() - n1) - (n1 - n0) >= 20
