@@ -43,8 +43,9 @@ L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory bytes per clock x max clock
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
-# workload, from the full ncu capture in profiles/kernels_lowdose_512_v720_b736.md
-# (update together with the kernels; None when no capture of the current kernel exists)
+# workload, from one ncu capture of the kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); update together with the kernels, None when no
+# capture of the current kernel exists
 TRAFFIC_BYTES = {"A": 1.098240e6, "AT": 2.022912e6}
 
 

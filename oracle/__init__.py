@@ -74,7 +74,7 @@ def _load():
                 "orc_residual": [_i, _i, _i, _p, _p, _p],
                 "orc_apply_d": [_i, _i, _p, _p, _i, _p, _p, _p],
                 "orc_pdtv": [_i, _i, _i, _p, _p, _p, _p, _p, _p, _i, _i, _d, _d, _d, _i, _i, _d,
-                             _i, _i, _p, _p, _p, _p, _p, _p],
+                             _i, _i, _p, _p, _p, _p, _p, _p, _p],
                 "orc_eps_prox": [_i, _i, _p, _i, _d, _p, _p],
                 "orc_power_norm": [_i, _i, _i, _i, _p, _p, _p, _p, _i, _p, _i],
                 "orc_cp_reference": [_i, _i, _i, _p, _p, _p, _i, _d, _d, _d, _d, _i, _p],
@@ -236,13 +236,14 @@ class PDState:
 
 
 def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
-         state=None, trace=False, taps_hi=None, s=None, fgp=False, eps=0.0):
+         state=None, trace=False, taps_hi=None, s=None, fgp=False, eps=0.0, mubar=None):
     """Run `iters` iterations of Algorithm 1 (mode 0) / 2 (mode 1) from
     `state` (fresh zero state if None).  With taps_hi (and s) the
     preconditioner is the shift-variant D = T_lo + S T_hi S (apply_d); with
     fgp the prox runs the fast gradient projection; with eps > 0 (mode 1)
-    the epsilon-constrained form, whose dual steps take eps_prox.  Returns
-    (state, trace or None)."""
+    the epsilon-constrained form, whose dual steps take eps_prox.  mubar (a
+    V x B float64 array, optional) receives the mu_bar of the last
+    iteration's Step 1.  Returns (state, trace or None)."""
     b = _f64(b)
     V, B = b.shape
     w = None if w is None else _f64(w)
@@ -255,7 +256,7 @@ def pdtv(b, w, taps, mode, beta, tau, sigma, n_tv, iters, n, angles=None,
     _load().orc_pdtv(n, V, B, _ptr(_angles(angles)), _ptr(b), _ptr(w), _ptr(taps), _ptr(th), _ptr(sv), half,
                      int(mode), float(beta), float(tau), float(sigma), int(n_tv), int(bool(fgp)), float(eps),
                      int(st.k), int(iters), _ptr(st.x), _ptr(st.mu), _ptr(st.mu_prev),
-                     _ptr(st.px), _ptr(st.py), _ptr(tr))
+                     _ptr(st.px), _ptr(st.py), _ptr(tr), _ptr(mubar))
     st.k += iters
     return st, tr
 
@@ -284,7 +285,9 @@ def cp_reference(b, w, mode, beta, s, t, iters, n, angles=None, eps=0.0):
 
 
 def eps_prox(q, taps, se):
-    """The epsilon-constrained form's dual step (reading 19): argmin_nu
+    """The epsilon-constrained form's dual step (Sec. 5 names the form
+    without its steps; with the eps-ball's support function in h the dual
+    step becomes a proximal map): argmin_nu
     se |nu| + 1/2 (nu - q)^T D^-1 (nu - q), D the per-view Toeplitz matrix of
     the taps, by bisection on c in (I + c D) nu = q, c = se / |nu|."""
     q = _f64(q)

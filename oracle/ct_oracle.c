@@ -399,7 +399,8 @@ void orc_tv_prox_fgp(int N, const double *z, double lam, int n_tv,
 /* the state (x, mu, mu_prev, px, py); k0 = 0 starts from x = mu = p = 0. */
 /* fgp: the prox by orc_tv_prox_fgp instead of orc_tv_prox.            */
 /* trace[i] (optional) receives f(x) (Eq. 1) for mode 0 or ||Ax-b||    */
-/* for mode 1 after iteration i.                                       */
+/* for mode 1 after iteration i.  mubar_out (optional, V*B) receives   */
+/* the mu_bar that Step 1 of the last iteration formed.                */
 /* ------------------------------------------------------------------ */
 
 double orc_cost(int N, int V, int B, const double *angles, const double *b,
@@ -432,7 +433,9 @@ double orc_residual(int N, int V, int B, const double *angles,
 /* ------------------------------------------------------------------ */
 /* The dual step of the epsilon-constrained few-view form               */
 /*   min TV(x)  s.t.  ||Ax - b|| <= eps,  x >= 0    (Sec. 5)             */
-/* (reading 19): with the ball's support function in h, the dual step   */
+/* (Sec. 5 names the form without its steps; here the indicator of the */
+/* eps-ball replaces the equality constraint): with the ball's support  */
+/* function in h, the dual step                                         */
 /* in the metric of sigma D is the proximal map                         */
 /*   nu = argmin_nu  se |nu| + 1/2 (nu - q)^T D^-1 (nu - q),  se = s eps, */
 /* where q is the equality form's update mu + sigma D (A x - b) and D   */
@@ -536,7 +539,7 @@ void orc_pdtv(int N, int V, int B, const double *angles,
               double beta, double tau, double sigma, int n_tv, int fgp, double eps,
               int k0, int iters,
               double *x, double *mu, double *mu_prev, double *px, double *py,
-              double *trace)
+              double *trace, double *mubar_out)
 {
     /* eps > 0 (mode 1, taps_hi NULL): the epsilon-constrained form; Step 3
      * and Step 1 at k = 0 take the proximal map of orc_eps_prox */
@@ -571,6 +574,7 @@ void orc_pdtv(int N, int V, int B, const double *angles,
         } else {
             for (size_t i = 0; i < I; ++i) mubar[i] = 2.0 * mu[i] - mu_prev[i];
         }
+        if (mubar_out && k == k0 + iters - 1) memcpy(mubar_out, mubar, sizeof(double) * I);
         /* Step 2: primal update through the prox of tau*g */
         orc_backproject(N, V, B, angles, mubar, z);
         for (size_t j = 0; j < J; ++j) z[j] = x[j] - tau * z[j];

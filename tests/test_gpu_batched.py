@@ -11,7 +11,10 @@ from gpu_util import need_gpu, rel_l2, to_gpu, to_np, f32
 pytestmark = pytest.mark.gpu
 
 
-def make_slices(P, shapes, iters, oracle_data=True):
+def make_slices(P, shapes, iters, oracle_data=True, explicit_steps=False):
+    """Slices of the given shapes; with explicit_steps, tau and sigma are set
+    from the oracle (default tau, sigma by the oracle's power method), so an
+    oracle run with the same values needs nothing from the GPU."""
     out = []
     for n, v, b, mode, sd in shapes:
         g = P.Geometry(n, v, b)
@@ -23,6 +26,12 @@ def make_slices(P, shapes, iters, oracle_data=True):
             bb = O.project(synth.ellipse_phantom(n, 6, sd), v, b)
             w = None
         prm = P.PDTVParams(mode=mode, iters=iters, beta=0.01)
+        if explicit_steps:
+            wh = None if w is None else to_np(w)
+            kappa = float(np.mean(1.0 / wh)) if mode == 0 else 0.0
+            prm.tau = O.default_tau(mode, v, kappa)
+            taps = O.ramp_taps(mode, v, b, prm.tau, kappa)
+            prm.sigma, _, _ = O.step_sizes(mode, n, v, b, taps, wh, prm.tau)
         out.append((g, to_gpu(f32(bb)), w, prm))
     return out
 
@@ -42,14 +51,14 @@ def test_batched_equals_single_slice_solves():
 def test_batched_matches_oracle():
     P = need_gpu()
     shapes = [(32, 45, 47, 0, 11), (40, 10, 58, 1, 12), (24, 36, 35, 0, 13)]
-    slices = make_slices(P, shapes, 8)
+    slices = make_slices(P, shapes, 8, explicit_steps=True)
     xs, reps = P.ct_pdtv_solve_batched(slices)
     for (g, b, w, prm), xb, rep, (n, v, nb, mode, sd) in zip(slices, xs, reps, shapes):
         bh = to_np(b)
         wh = None if w is None else to_np(w)
         kappa = float(np.mean(1.0 / wh)) if mode == 0 else 0.0
-        taps = O.ramp_taps(mode, v, nb, rep["tau"], kappa)
-        st, _ = O.pdtv(bh, wh, taps, mode, 0.01, rep["tau"], rep["sigma"], 10, 8, n)
+        taps = O.ramp_taps(mode, v, nb, prm.tau, kappa)
+        st, _ = O.pdtv(bh, wh, taps, mode, 0.01, prm.tau, prm.sigma, 10, 8, n)
         assert rel_l2(to_np(xb), st.x) <= 1e-3
 
 

@@ -1,5 +1,6 @@
 """GPU parity of the error-tolerant few-view form (min TV(x) s.t.
-||Ax - b|| <= eps, x >= 0; Sec. 5, reading 19) against the FP64 oracle, whose
+||Ax - b|| <= eps, x >= 0; Sec. 5 names it without its steps: the dual step
+is the proximal map of the eps-ball's support function) against the FP64 oracle, whose
 dual step is computed independently (bisection with dense Cholesky solves
 instead of the eigenbasis): relative L2 <= 1e-3 on the image after the
 stated iterations, for the paper's ramp, the few-view smoothed ramp and
@@ -104,8 +105,8 @@ def test_eps_form_paper_fewview_shape():
     x, b, nn = noisy_fewview(N, V, B, 4, rel_noise=0.01)
     tau = O.default_tau(1, V, 0.0)
     g = P.Geometry(N, V, B)
-    _, rep = P.ct_pdtv_solve(g, to_gpu(b), None, P.PDTVParams(mode=P.CT_FEWVIEW, iters=0, precond=3, tau=tau))
-    xg, st, _, _, _ = solve_both(P, N, V, B, b, nn, 3, 3, tau, rep["sigma"], g=g)
+    sigma, _, _ = O.step_sizes(1, N, V, B, oracle_taps(3, N, V, B, tau), None, tau)
+    xg, st, _, _, _ = solve_both(P, N, V, B, b, nn, 3, 3, tau, sigma, g=g)
     assert rel_l2(xg, st.x) <= TOL
 
 

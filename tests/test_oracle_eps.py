@@ -1,5 +1,7 @@
 """Pins of the oracle's epsilon-constrained few-view form (min TV(x) subject
-to ||Ax - b|| <= eps, x >= 0; Sec. 5, reading 19).  Its dual step is checked
+to ||Ax - b|| <= eps, x >= 0; Sec. 5 names it without giving its steps:
+the eps-ball's support function takes h's place, so the dual step is a
+proximal map).  Its dual step is checked
 against a brute-force minimisation of its variational definition and its
 closed forms; its limit against the independent Chambolle-Pock run on
 K = [A; grad] with the Euclidean ball projection, the constraint being

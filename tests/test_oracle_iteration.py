@@ -212,3 +212,70 @@ def test_fewview_smoothed_ramp_converges_faster_than_eq32():
     d32 = np.linalg.norm(O.pdtv(b, None, t32, 1, 0.0, tau, s32, 10, 30, N)[0].x - xs)
     dsm = np.linalg.norm(O.pdtv(b, None, tsm, 1, 0.0, tau, ssm, 10, 30, N)[0].x - xs)
     assert dsm < 0.5 * d32
+
+
+def test_extrapolation_agrees_with_the_first_form_of_eq18_and_eq29():
+    # Eq. 18 states Step 1 of Algorithm 1 in two forms,
+    #   mu^k + sigma D (A x^k - b - W^-1 mu^k)                    (APP's own step)
+    #   2 mu^k - mu^{k-1} - sigma D W^-1 (mu^k - mu^{k-1})        (the box form),
+    # equal because mu^k - mu^{k-1} is the previous dual update; Eq. 29 is the
+    # same without W^-1 (Algorithm 2).  The oracle runs the box form; here
+    # the first form is formed from its state at k = 0 .. 5 with the oracle's
+    # A, D and W, so a dropped term, a wrong sign or a stale mu^{k-1} in the
+    # box form shows up as a mismatch.
+    N, V, B = 12, 18, 17
+    xt, b, w = lowdose_problem(N, V, B, seed=7, noise=0.05)
+    for mode in (0, 1):
+        ww = w if mode == 0 else None
+        kappa = float(np.mean(1 / w)) if mode == 0 else 0.0
+        tau = O.default_tau(mode, V, kappa)
+        taps = O.ramp_taps(mode, V, B, tau, kappa)
+        sigma, _, _ = O.step_sizes(mode, N, V, B, taps, ww, tau)
+        st = None
+        for k in range(6):
+            x_k = np.zeros((N, N)) if st is None else st.x.copy()
+            mu_k = np.zeros((V, B)) if st is None else st.mu.copy()
+            r = O.project(x_k, V, B) - b
+            if mode == 0:
+                r = r - mu_k / w
+            first = mu_k + sigma * O.filt(r, taps)
+            mb = np.empty((V, B))
+            st, _ = O.pdtv(b, ww, taps, mode, 0.05, tau, sigma, 5, 1, N, state=st, mubar=mb)
+            assert np.linalg.norm(mb - first) <= 1e-12 * np.linalg.norm(first)
+        # the low-dose correction term is not negligible here: dropping it
+        # (Algorithm 2's Step 1 on Algorithm 1's state) misses the first form
+        if mode == 0:
+            st2, _ = O.pdtv(b, ww, taps, mode, 0.05, tau, sigma, 5, 3, N)
+            mu_prev = st2.mu_prev.copy()
+            mu_k = st2.mu.copy()
+            first = mu_k + sigma * O.filt(O.project(st2.x, V, B) - b - mu_k / w, taps)
+            no_corr = 2 * mu_k - mu_prev
+            assert np.linalg.norm(no_corr - first) > 1e-3 * np.linalg.norm(first)
+
+
+def test_cost_of_eq1_has_the_half():
+    # Eq. 1: f(x) = beta psi(x) + 1/2 ||Ax - b||_W^2.  At the unconstrained
+    # beta = 0 minimiser x* (normal equations, numpy solve) the gradient
+    # vanishes, so f(x* + e d) - f(x*) = 1/2 e^2 ||A d||_W^2 exactly, with A
+    # the explicit matrix; a missing 1/2 doubles it.
+    N, V, B = 8, 16, 13
+    xt, b, w = lowdose_problem(N, V, B, seed=3)
+    A = explicit_A(N, V, B)
+    wv = w.ravel()
+    xs = np.linalg.solve(A.T @ (wv[:, None] * A), A.T @ (wv * b.ravel())).reshape(N, N)
+    d = np.random.default_rng(11).standard_normal((N, N))
+    Ad = A @ d.ravel()
+    for eps in (0.1, 0.5):
+        df = O.cost(xs + eps * d, b, w, 0.0) - O.cost(xs, b, w, 0.0)
+        assert df == pytest.approx(0.5 * eps ** 2 * float(Ad @ (wv * Ad)), rel=1e-8)
+    # and the penalty term: b = A x gives zero fidelity, so f = beta psi(x);
+    # a vertical step of height h across all N rows has psi = N h (Eq. 2
+    # with forward differences)
+    h, beta = 0.7, 0.3
+    x = np.zeros((N, N))
+    x[:, N // 2:] = h
+    assert O.cost(x, O.project(x, V, B), w, beta) == pytest.approx(beta * N * h, rel=1e-12)
+    # unit weights (W = I, the few-view residual's norm): f = 1/2 ||Ax - b||^2
+    bb = b + 0.1
+    r = O.residual(x, bb)
+    assert O.cost(x, bb, None, 0.0) == pytest.approx(0.5 * r * r, rel=1e-12)
