@@ -40,7 +40,7 @@ WORK = dict(name="lowdose_512x512_v720_b736", n=512, views=720, bins=736, ellips
 METRIC = "PD-TV iterations/sec (512^2, 720 views, 736 bins, low-dose Alg. 1)"
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock (context)
 SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory bytes per clock x max clock
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from one ncu capture of the kernel (dram__bytes_read.sum +
@@ -161,18 +161,52 @@ def oracle_inputs(seed=0):
 
 
 def oracle_iterations(b, w, tau, taps, k, state=None):
+    # the oracle as it stands: OpenMP over every core
     import oracle as O
     return O.pdtv(b, w, taps, 0, WORK["beta"], tau, 0.5, WORK["tv_iters"], k, WORK["n"], state=state)[0]
 
 
-def cpu_baseline(iters=2):
-    b, w, tau, taps = oracle_inputs()
+def _oracle_rate(name, iters, threads):
+    """iterations/s of the oracle's Algorithm 1 / 2 on a workload of
+    synth.CONFIGS (oracle-projected data, sigma 0.5 / 0.9: timing only)."""
+    import oracle as O
+    cfg = synth.CONFIGS[name]
+    N, V, B = cfg["n"], cfg["views"], cfg["bins"]
+    x = synth.ellipse_phantom(N, cfg["ellipses"], 0) * cfg["scale"]
+    if cfg["mode"] == "lowdose":
+        b, w = synth.poisson_data(O.project(x, V, B), cfg["i0"], 100)
+        kappa = float(np.mean(1.0 / w))
+        mode, sigma = 0, 0.5
+    else:
+        b, w, kappa, mode, sigma = O.project(x, V, B), None, 0.0, 1, 0.9
+    tau = O.default_tau(mode, V, kappa)
+    taps = O.ramp_taps(mode, V, B, tau, kappa)
+    O.set_threads(threads)
     t0 = time.perf_counter()
-    oracle_iterations(b, w, tau, taps, iters)
+    O.pdtv(b, w, taps, mode, cfg["beta"], tau, sigma, 10, iters, N)
     dt = time.perf_counter() - t0
-    return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} iterations of Algorithm 1 at 512^2/720 views/736 bins, "
-                      f"FP64 C oracle, single thread, setup excluded ({dt:.1f} s)"}
+    O.set_threads(0)
+    return iters / dt, dt
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands on this host's cores: the three
+    single-slice workloads, a bounded number of iterations each, on one
+    thread and on every core (OpenMP over views / image rows; the results
+    do not depend on the thread count).  value: the bench workload on every
+    core."""
+    nproc = os.cpu_count() or 1
+    runs = {}
+    for name, iters in (("lowdose_64", 20), ("fewview_512", 5), ("lowdose_512", 2)):
+        for threads in (1, nproc):
+            rate, dt = _oracle_rate(name, iters, threads)
+            runs[f"{name}_threads{threads}"] = {"iterations_per_s": rate, "iterations": iters, "seconds": dt}
+    value = runs[f"lowdose_512_threads{nproc}"]["iterations_per_s"]
+    return {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"2 iterations of Algorithm 1 at 512^2/720 views/736 bins on {nproc} threads "
+                      f"(FP64 C oracle, setup excluded); runs: 20 iterations at 64^2/90/95, 5 of the "
+                      f"100 at 512^2/32/736, 2 of the 30 at 512^2/720/736, each on 1 and {nproc} threads",
+            "runs": runs}
 
 
 def run_reference(args):
@@ -197,9 +231,9 @@ def run_reference(args):
             "config": {"workload": WORK["name"], "n": WORK["n"], "views": WORK["views"],
                        "bins": WORK["bins"], "beta": WORK["beta"], "i0": WORK["i0"],
                        "iters_per_step": 1, "l2": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                              "sample": "one Algorithm-1 iteration per step, FP64 C oracle, "
-                                       "single thread, setup excluded"},
+                                       "OpenMP over every core, setup excluded"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -319,19 +353,19 @@ def measure_unrolled(P, steps=3):
 CHECKPOINTS = (1, 3, 10, 30, 100, 300, 1000)
 
 
-def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0, eps=0.0):
+def _trajectory(P, g, b, w, mode, precond, beta, v_true, scale, tv_accel=0, eps=0.0, checkpoints=CHECKPOINTS):
     """Iterates of one solve at CHECKPOINTS (resumed solves continue the
     same iteration exactly): RMSE of x / scale against the phantom v_true
     and the relative data residual |A x - b| / |b|."""
     import torch
-    prm = P.PDTVParams(mode=mode, iters=CHECKPOINTS[0], tv_iters=10, precond=precond, beta=beta,
+    prm = P.PDTVParams(mode=mode, iters=checkpoints[0], tv_iters=10, precond=precond, beta=beta,
                        norm_iters=WORK["norm_iters"], tv_accel=tv_accel, eps=eps)
     ws = P.workspace_for(g, prm)
     x = torch.empty(g.n, g.n, device="cuda")
     xs, rmse, resid = {}, {}, {}
     done = 0
     bn = float(torch.linalg.norm(b))
-    for k in CHECKPOINTS:
+    for k in checkpoints:
         q = P.PDTVParams(**{**prm.__dict__, "iters": k - done, "resume": 1 if done else 0})
         P.ct_pdtv_solve(g, b, w, q, x_out=x, workspace=ws, report=False)
         done = k
@@ -358,6 +392,29 @@ def _solve_rate(P, g, b, w, mode, precond, beta, iters, steps=3, tv_accel=0, eps
     e1.record()
     torch.cuda.synchronize()
     return iters * steps / (e0.elapsed_time(e1) / 1e3)
+
+
+def measure_fewview_vs_cp(P):
+    """The few-view workload (512^2, 32 views, 736 bins, noiseless b = A v,
+    100 iterations of Algorithm 2): the ramp preconditioner of Eq. 32 and the
+    few-view smoothed ramp against plain Chambolle-Pock (D = I) on the same
+    GPU kernels: whole-solve iterations/s and, after 3 / 10 / 30 / 100
+    iterations, the RMSE to the phantom and |A x - b| / |b|."""
+    import torch
+    N, V, B = WORK["n"], 32, WORK["bins"]
+    g = P.Geometry(N, V, B)
+    g.autotune()
+    v_true = synth.ellipse_phantom(N, WORK["ellipses"], 0)
+    b = P.ct_project(g, torch.from_numpy(v_true.astype(np.float32)).cuda())
+    vt = torch.from_numpy(v_true).cuda()
+    cps = (3, 10, 30, 100)
+    out = {"workload": f"{N}^2, {V} views, {B} bins, noiseless b = A v, Alg. 2, 100 iterations per solve",
+           "checkpoints": list(cps), "tuning": g.tuning}
+    for label, pc in (("preconditioned_eq32", 1), ("smoothed_ramp", 3), ("plain_cp", 0)):
+        _, rmse, resid = _trajectory(P, g, b, None, 1, pc, 0.0, vt, 1.0, checkpoints=cps)
+        out[label] = {"rmse": [rmse[k] for k in cps], "rel_residual": [resid[k] for k in cps],
+                      "iterations_per_s": _solve_rate(P, g, b, None, 1, pc, 0.0, 100)}
+    return out
 
 
 def measure_convergence(P):
@@ -554,6 +611,11 @@ def run_ours(args):
     a_ms = fw0.elapsed_time(fw1) / nrep
     nnz = joseph_nnz(N, V, B)
     flops = 2.0 * nnz
+    # measured FP32 FMA peak (scalar and packed f32x2 FMA chains), clocks sampled
+    with ClockSampler(local) as peak_clock:
+        fma_scalar = P.ct_probe_fp32_fma(False)
+        fma_packed = P.ct_probe_fp32_fma(True)
+    fp32_peak = max(fma_scalar, fma_packed)
     # dominant operator: the slower of A (ct_project: band kernel + reduction)
     # and A^T (ct_backproject: orbit kernel + slice reduction); both carry
     # 2 nnz(A) algorithmic flops
@@ -590,7 +652,7 @@ def run_ours(args):
     forms = None
     if not args.no_forms and world == 1:
         forms = {"batched": measure_batched(P), "differentiable": measure_unrolled(P),
-                 "convergence": measure_convergence(P)}
+                 "fewview_vs_plain_cp": measure_fewview_vs_cp(P)}
 
     clocks = sampler.summary()
     if rank == 0:
@@ -619,10 +681,14 @@ def run_ours(args):
                               "AT": (4.0 * N * N + 4.0 * V * B) / (at_ms / 1e3) / 1e9},
             "report": {k: rep[k] for k in ("tau", "sigma", "kappa", "norm_ADA", "norm_WDW")},
             "roofline": {"kernel": dom_name, "bound": "alu", "achieved": achieved,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": TRAFFIC_BYTES.get(dom_key), "traffic_unit": "bytes/launch",
                          "algorithmic_flops": flops, "nnz": nnz, "launch_ms": dom_ms,
-                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+                         "peak_source": "measured: ct_probe_fp32_fma, the faster of scalar and packed "
+                                        "(f32x2) FMA chains, CUDA events, same process",
+                         "peak_probe": {"scalar_tflops": fma_scalar, "packed_f32x2_tflops": fma_packed,
+                                        "clocks": peak_clock.summary(),
+                                        "nominal_tflops": FP32_NOMINAL_TFLOPS}},
             # the projector's binding resource: every Joseph sample reads one
             # interpolation pair (8 bytes) from shared memory; samples = nnz / 2
             "roofline_shared_memory": {"kernel": "ct_project (A)", "achieved": 8.0 * (nnz / 2) / (a_ms / 1e3) / 1e12,
@@ -712,7 +778,7 @@ def run_form(args):
     import __graft_entry__ as entry
     entry.build()
     import paper_1609_06041_gb300 as P
-    fn = {"batched": measure_batched, "differentiable": measure_unrolled,
+    fn = {"batched": measure_batched, "differentiable": measure_unrolled, "fewview_cp": measure_fewview_vs_cp,
           "convergence": measure_convergence, "eps": measure_eps}[args.form]
     print(json.dumps({"form": args.form, **fn(P)}), flush=True)
     return 0
@@ -732,7 +798,7 @@ def main():
                     help="time eager ct_pdtv_solve calls instead of replaying one captured CUDA graph of the solve")
     ap.add_argument("--tuning", default="",
                     help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
-    ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "convergence", "eps"],
+    ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "fewview_cp", "convergence", "eps"],
                     help="run only this form's measurement")
     args = ap.parse_args()
     if args.eager:

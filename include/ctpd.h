@@ -76,6 +76,17 @@ const char *ct_last_error(void);
 unsigned long long ct_kernel_launches(void);
 
 /*
+ * Measured FP32 FMA throughput of the current device in TFLOP/s (*tflops,
+ * host), the denominator of the roofline fraction of the FMA-carrying
+ * operators.  No counterpart in the paper: a fixed kernel of independent
+ * FMA chains (packed = 0: fma.rn.f32; 1: the packed fma.rn.f32x2, two FMAs
+ * per instruction) over 8 blocks of 256 threads per SM, timed with CUDA
+ * events on `stream` (best of three after one warm-up launch).
+ * Synchronises the stream; allocates a small stream-ordered buffer.
+ */
+ct_status ct_probe_fp32_fma(int packed, double *tflops, void *stream);
+
+/*
  * Create a 2-D parallel-beam geometry (Sec. 2.1): N x N image, V views,
  * B bins.  angles (host, V doubles, radians) may be NULL for t_v = v*pi/V.
  * 1 <= N, V, B <= 8192.  On success *out receives a handle; destroy it with
@@ -199,7 +210,8 @@ ct_status ct_ramp_filter_split(const ct_geometry *geom, const float *taps_lo, co
  * capture.  All calls share the array and each call overwrites all of its
  * contents, so calls whose work may overlap on the GPU (other streams,
  * other threads) race with each other: serialise them.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * cudaMalloc, cudaFree or other allocating routine.  The geometry's device
+ * must be the current device (CT_ERR_ARG otherwise).
  */
 ct_status ct_ramp_filter_noalloc(const ct_geometry *geom, const float *taps, int half_len,
                                  const float *in, float *out, int batch, void *stream);
@@ -265,12 +277,22 @@ typedef struct {
                          equality form (Eq. 25).                              */
 } ct_pdtv_params;
 
-/* Scalars of a solve, copied to the host at the end when requested. */
+/* Scalars of a solve, copied to the host at the end when requested.  The
+ * caller sets `trace` before the call (zero-initialise the struct first);
+ * the solve fills the other fields. */
 typedef struct {
     double tau, sigma, kappa, lambda;  /* lambda = tau*beta (Alg. 1), tau (Alg. 2) */
     double norm_ADA;   /* ||A^T D A|| = ||D^1/2 A A^T D^T/2||                    */
     double norm_WDW;   /* ||W^-1/2 D W^-1/2|| = ||D^1/2 W^-1 D^T/2|| (low-dose)   */
     int k;             /* iterations done in total (including resumed ones)      */
+    double *trace;     /* host, params->iters doubles, or NULL (no trace).  After
+                          iteration i of this call: CT_LOWDOSE the cost of Eq. 1,
+                          f(x) = beta TV(x) + 1/2 ||Ax - b||_W^2 (with its 1/2),
+                          CT_FEWVIEW the residual ||Ax - b|| of the constraint of
+                          Eq. 25, both at x = x^{k+1} (one device reduction per
+                          iteration over the projector's partial sums; a stream-
+                          ordered buffer of iters + 608 doubles is allocated for
+                          the call)                                             */
 } ct_pdtv_report;
 
 /* Device workspace (bytes) a solve with these parameters needs. */
@@ -288,6 +310,14 @@ size_t ct_pdtv_workspace_bytes(const ct_geometry *geom, const ct_pdtv_params *pa
  * b: V x B line integrals.  w: V x B statistical weights W = diag(w), w > 0
  * (CT_LOWDOSE; NULL for CT_FEWVIEW).  x_out: N x N, receives x^K (with
  * params->resume it must hold the x of the resumed state).
+ * Input checks: b and w live on the device, so a device pass checks them
+ * (w > 0 and finite, b finite) and the image x^K (finite) and records what
+ * it finds in the workspace.  The result comes back at the next
+ * synchronisation the caller asks for: with a report this call returns
+ * CT_ERR_ARG (some w_i <= 0) or CT_ERR_NONFINITE (NaN or infinity in b, w
+ * or x^K) after filling the report; without one, ct_pdtv_status(workspace,
+ * stream) returns the same codes.  The solve itself still runs (its image
+ * is then not meaningful).
  * workspace: device memory of ct_pdtv_workspace_bytes(); it holds the whole
  * iteration state (mu, mu_bar, TV dual field, scalars), so a later call
  * with resume = 1 continues exactly.  workspace == NULL: the library
@@ -312,6 +342,16 @@ ct_status ct_pdtv_solve(const ct_geometry *geom, const float *b, const float *w,
                         void *workspace, ct_pdtv_report *report, void *stream);
 
 /*
+ * Result of the input and result checks of the last solve that used this
+ * workspace (caller-owned, device): synchronises `stream` and returns
+ * CT_OK, CT_ERR_ARG (a weight w_i <= 0: W of Eq. 1 is not positive
+ * definite), or CT_ERR_NONFINITE (NaN or infinity in b, w or the image),
+ * with a message in ct_last_error().  CT_ERR_CUDA if the synchronisation
+ * or the read fails.
+ */
+ct_status ct_pdtv_status(const void *workspace, void *stream);
+
+/*
  * Many independent slices in one call (the batched form of the solve):
  * slice i is ct_pdtv_solve(geoms[i], b[i], w[i], &params[i], x_out[i],
  * workspaces[i]) with no report, for n slices of any mix of geometries
@@ -325,9 +365,15 @@ ct_status ct_pdtv_solve(const ct_geometry *geom, const float *b, const float *w,
  * call outside stream capture); the work is forked from `stream` and
  * joined back into it, so later work on `stream` sees every x_out, and the
  * whole call can be captured into a CUDA graph.  reports (host, n entries,
- * may be NULL) are filled after synchronising `stream`.  Calls from
- * several host threads at once share the pool; do not capture two of them
- * at the same time.
+ * may be NULL) are filled after synchronising `stream` (their trace is not
+ * used); the call then returns the first slice's check failure, if any
+ * (see ct_pdtv_solve), naming the slice.  Calls from several host threads
+ * at once share the pool: each call holds the pool's lock while it
+ * enqueues, so its slices wait on its own fork and its stream on its own
+ * joins, and the calls' slices run one call after the other on the pool.
+ * Do not capture two calls at the same time, and do not run an uncaptured
+ * call while another thread captures one (the pool streams would join the
+ * capture).
  */
 ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const float *const *b,
                                 const float *const *w, const ct_pdtv_params *params,

@@ -45,11 +45,13 @@ _p = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
-    """Compile ct_oracle.c into libct_oracle.so (gcc, -O2, portable flags)."""
+    """Compile ct_oracle.c into libct_oracle.so (gcc, -O2, portable flags,
+    OpenMP when the compiler has it; results do not depend on it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +62,8 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             sig = {
+                "orc_set_threads": [_i],
+                "orc_get_threads": [],
                 "orc_project": [_i, _i, _i, _p, _p, _p],
                 "orc_backproject": [_i, _i, _i, _p, _p, _p],
                 "orc_fft_len": [_i],
@@ -84,12 +88,23 @@ def _load():
                 fn.argtypes = args
                 fn.restype = None
             lib.orc_fft_len.restype = _i
+            lib.orc_get_threads.restype = _i
             lib.orc_tv.restype = _d
             lib.orc_cost.restype = _d
             lib.orc_residual.restype = _d
             lib.orc_power_norm.restype = _d
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the projector, backprojector and filter (<= 0: every
+    core).  Results are the same for any count."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _f64(a):

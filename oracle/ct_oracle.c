@@ -9,8 +9,13 @@
  * load it through oracle/__init__.py to check and time the CUDA path.  It
  * shares no code, header or table with the CUDA sources.
  *
- * Every routine is written in the most direct form, single-threaded, with
- * no blocking, fusion or reordering beyond what the definition states.
+ * Every routine is written in the most direct form, with no blocking,
+ * fusion or reordering beyond what the definition states.  Built with
+ * OpenMP, the projector and the filter run their independent rays / views
+ * on several threads and the backprojector gives each thread a band of
+ * image rows; every output element is still formed by the same operations
+ * in the same order as with one thread, so results do not depend on the
+ * thread count (orc_set_threads).
  *
  * Conventions (the paper leaves the discretisation open; these are the
  * readings this project fixes):
@@ -22,6 +27,28 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the projector, backprojector and filter (<= 0: all). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -73,6 +100,7 @@ void orc_project(int N, int V, int B, const double *angles,
                  const double *x, double *sino)
 {
     const double h = 0.5 * (N - 1), hb = 0.5 * (B - 1);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int v = 0; v < V; ++v) {
         view_t g = view_of(v, V, angles);
         for (int d = 0; d < B; ++d) {
@@ -106,40 +134,66 @@ void orc_project(int N, int V, int B, const double *angles,
 /* A^T).                                                               */
 /* ------------------------------------------------------------------ */
 
-static void add_pix(double *x, int N, int r, int c, double val)
+/* adds val to pixel (r, c) if it lies in the image and in rows [r0, r1) */
+static void add_pix(double *x, int N, int r, int c, double val, int r0, int r1)
 {
-    if (r < 0 || r >= N || c < 0 || c >= N) return;
+    if (r < r0 || r >= r1 || c < 0 || c >= N) return;
     x[(size_t)r * N + c] += val;
 }
 
+/* Each thread owns the image rows [r0, r1) and visits the rays in the
+ * serial order (view, then ray d, then step), so every pixel receives its
+ * contributions in the same order as with one thread.  A row-stepping view
+ * touches row r only at step r; a column-stepping view reaches rows near
+ * u(d) = (s_d - x_c cos t) / sin t + h, which is linear in d, so at column c
+ * only a short range of rays needs visiting (taken with a margin; the
+ * per-ray arithmetic is unchanged and the row test decides). */
 void orc_backproject(int N, int V, int B, const double *angles,
                      const double *sino, double *x)
 {
     const double h = 0.5 * (N - 1), hb = 0.5 * (B - 1);
     memset(x, 0, sizeof(double) * (size_t)N * N);
-    for (int v = 0; v < V; ++v) {
-        view_t g = view_of(v, V, angles);
-        for (int d = 0; d < B; ++d) {
-            double s = d - hb;
+#pragma omp parallel
+    {
+        int T = 1, t = 0;
+#ifdef _OPENMP
+        T = omp_get_num_threads();
+        t = omp_get_thread_num();
+#endif
+        const int r0 = (int)((long long)N * t / T), r1 = (int)((long long)N * (t + 1) / T);
+        for (int v = 0; v < V && r0 < r1; ++v) {
+            view_t g = view_of(v, V, angles);
             if (g.rows) {
-                double val = sino[(size_t)v * B + d] / fabs(g.c);
-                for (int r = 0; r < N; ++r) {
-                    double y = r - h;
-                    double u = (s - y * g.s) / g.c + h;
-                    double fl = floor(u), f = u - fl;
-                    int i0 = (int)fl;
-                    add_pix(x, N, r, i0, (1.0 - f) * val);
-                    add_pix(x, N, r, i0 + 1, f * val);
+                for (int d = 0; d < B; ++d) {
+                    double s = d - hb;
+                    double val = sino[(size_t)v * B + d] / fabs(g.c);
+                    for (int r = r0; r < r1; ++r) {
+                        double y = r - h;
+                        double u = (s - y * g.s) / g.c + h;
+                        double fl = floor(u), f = u - fl;
+                        int i0 = (int)fl;
+                        add_pix(x, N, r, i0, (1.0 - f) * val, r0, r1);
+                        add_pix(x, N, r, i0 + 1, f * val, r0, r1);
+                    }
                 }
             } else {
-                double val = sino[(size_t)v * B + d] / fabs(g.s);
                 for (int c = 0; c < N; ++c) {
                     double xc = c - h;
-                    double u = (s - xc * g.c) / g.s + h;
-                    double fl = floor(u), f = u - fl;
-                    int i0 = (int)fl;
-                    add_pix(x, N, i0, c, (1.0 - f) * val);
-                    add_pix(x, N, i0 + 1, c, f * val);
+                    /* rays whose row coordinate u lies in [r0 - 2, r1 + 1] */
+                    double da = (r0 - 2 - h) * g.s + hb + xc * g.c;
+                    double db = (r1 + 1 - h) * g.s + hb + xc * g.c;
+                    double dlo = floor(da < db ? da : db) - 1.0, dhi = ceil(da < db ? db : da) + 1.0;
+                    int d0 = dlo < 0.0 ? 0 : (dlo > B ? B : (int)dlo);
+                    int d1 = dhi < 0.0 ? -1 : (dhi > B - 1 ? B - 1 : (int)dhi);
+                    for (int d = d0; d <= d1; ++d) {
+                        double s = d - hb;
+                        double val = sino[(size_t)v * B + d] / fabs(g.s);
+                        double u = (s - xc * g.c) / g.s + h;
+                        double fl = floor(u), f = u - fl;
+                        int i0 = (int)fl;
+                        add_pix(x, N, i0, c, (1.0 - f) * val, r0, r1);
+                        add_pix(x, N, i0 + 1, c, f * val, r0, r1);
+                    }
                 }
             }
         }
@@ -200,6 +254,7 @@ void orc_ramp_taps(int mode, int m, int P, double tau, double kappa,
 void orc_filter(int V, int B, const double *taps, int half,
                 const double *in, double *out)
 {
+#pragma omp parallel for schedule(dynamic, 1)
     for (int v = 0; v < V; ++v) {
         const double *a = in + (size_t)v * B;
         double *o = out + (size_t)v * B;

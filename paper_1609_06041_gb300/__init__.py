@@ -22,8 +22,10 @@ from .ctpd import (  # noqa: F401
     ct_kernel_launches,
     ct_last_error,
     ct_pdtv_solve,
+    ct_pdtv_status,
     ct_pdtv_solve_batched,
     ct_pdtv_workspace_bytes,
+    ct_probe_fp32_fma,
     ct_project,
     ct_ramp_filter,
     ct_ramp_filter_noalloc,

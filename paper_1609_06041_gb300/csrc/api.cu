@@ -58,6 +58,25 @@ ct_status ctpd::read_report(const void *workspace, ct_pdtv_report *report)
     report->norm_ADA = h[S_NADA];
     report->norm_WDW = h[S_NWDW];
     report->k = (int)h[S_K];
+    unsigned flags = 0;
+    memcpy(&flags, &h[S_FLAGS], sizeof(flags));
+    return status_from_flags(flags, "ct_pdtv_solve");
+}
+
+ct_status ctpd::status_from_flags(unsigned flags, const char *who)
+{
+    if (flags & CHK_WEIGHT_NOT_POSITIVE) {
+        set_error("%s: a weight w_i is zero or negative (W of Eq. 1 must be positive definite)", who);
+        return CT_ERR_ARG;
+    }
+    if (flags & CHK_NONFINITE_INPUT) {
+        set_error("%s: b or w holds NaN or infinity", who);
+        return CT_ERR_NONFINITE;
+    }
+    if (flags & CHK_NONFINITE_RESULT) {
+        set_error("%s: the image holds NaN or infinity (step sizes too large?)", who);
+        return CT_ERR_NONFINITE;
+    }
     return CT_OK;
 }
 
@@ -584,6 +603,19 @@ ct_status ct_ramp_filter(const ct_geometry *g, const float *taps, int half_len, 
     return cuda_check("ct_ramp_filter");
 }
 
+ct_status ct_pdtv_status(const void *workspace, void *stream)
+{
+    g_err[0] = 0;
+    if (!workspace) return fail(CT_ERR_ARG, "ct_pdtv_status: NULL workspace");
+    cudaError_t e = cudaStreamSynchronize(S(stream));
+    unsigned flags = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&flags, static_cast<const char *>(workspace) + sizeof(double) * S_FLAGS, sizeof(flags),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(CT_ERR_CUDA, "ct_pdtv_status: %s", cudaGetErrorString(e));
+    return status_from_flags(flags, "ct_pdtv_status");
+}
+
 size_t ct_pdtv_workspace_bytes(const ct_geometry *g, const ct_pdtv_params *p)
 {
     if (!g) return 0;
@@ -683,6 +715,21 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};
     const int half = prm->precond ? g->n_bins : 1;
     const int lowdose = mode == CT_LOWDOSE;
+    // per-iteration trace (report->trace, host): device values, copied at the report's sync
+    double *trace_h = report ? report->trace : nullptr;
+    double *trace_d = nullptr;
+    if (trace_h && prm->iters > 0) {
+        if (cudaMallocAsync((void **)&trace_d, sizeof(double) * (prm->iters + trace_scratch_doubles()), st) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            if (owned) cudaFreeAsync(ws, st);
+            return fail(CT_ERR_OOM, "ct_pdtv_solve: trace buffer allocation failed");
+        }
+    }
+    // the input checks: w > 0 and finite (low-dose), b finite; bits in the flag word
+    unsigned *flags = flags_of(scal);
+    cudaMemsetAsync(flags, 0, sizeof(unsigned), st);
+    launch_check_inputs(b, lowdose ? w : nullptr, I, flags, st);
 
     long long k0 = 0;
     if (prm->resume) {
@@ -776,6 +823,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     if (cs == CT_OK && epsf && !prm->resume)
         launch_eps_step(g, mubar, mubar, nullptr, nullptr, eQ, eLam, prm->eps, scal, aux, es, ew2, epart, st);
     if (cs != CT_OK) {
+        if (trace_d) cudaFreeAsync(trace_d, st);
         if (owned) cudaFreeAsync(ws, st);
         return cs;
     }
@@ -800,6 +848,9 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         // residual A x^{k+1} - b [- W^-1 mu^k] from them, applies D and also
         // performs Step 1 of the next iteration
         launch_project_bands(g, x_out, band, 1, st);
+        if (trace_d)
+            launch_trace(g, band, b, w, x_out, lowdose ? prm->beta : 0.0, lowdose, trace_d + prm->iters,
+                         trace_d + k, st);
         if (epsf) cudaMemcpyAsync(r, mu, sizeof(float) * I, cudaMemcpyDeviceToDevice, st);   // mu^k
         if (sv_d) launch_dual_sv(g, hhat, hhat2, sv, band, b, mu, mubar, winv, scal, st);
         else if (use_fft) launch_dual_fft(g, hhat, band, b, mu, mubar, winv, lowdose, scal, st);
@@ -810,12 +861,21 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             launch_eps_step(g, mu, mu, mubar, r, eQ, eLam, prm->eps, scal, aux, es, ew2, epart, st);
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
+    launch_check_finite(x_out, J, flags, CHK_NONFINITE_RESULT, st);
     cs = cuda_check("ct_pdtv_solve");
     if (report && cs == CT_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) cs = fail(CT_ERR_CUDA, "ct_pdtv_solve: %s", cudaGetErrorString(e));
-        else cs = ctpd::read_report(ws, report);
+        else {
+            if (trace_d) {
+                e = cudaMemcpy(trace_h, trace_d, sizeof(double) * prm->iters, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) cs = fail(CT_ERR_CUDA, "ct_pdtv_solve: trace: %s", cudaGetErrorString(e));
+            }
+            const ct_status rs = ctpd::read_report(ws, report);
+            if (cs == CT_OK) cs = rs;
+        }
     }
+    if (trace_d) cudaFreeAsync(trace_d, st);
     if (owned) cudaFreeAsync(ws, st);
     return cs;
 }

@@ -24,6 +24,10 @@ struct Pool {
     cudaStream_t s[POOL_STREAMS];
     cudaEvent_t fork;
     cudaEvent_t join[POOL_STREAMS];
+    // held from the fork record to the last join wait: a call's pool
+    // streams then wait on its own fork record, and its stream on its own
+    // join records, when several host threads call at once
+    std::mutex mu;
 };
 
 std::mutex g_pool_mu;
@@ -82,6 +86,7 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int used = n < POOL_STREAMS ? n : POOL_STREAMS;
+    std::unique_lock<std::mutex> lock(pool->mu);
     cudaEventRecord(pool->fork, st);
     for (int i = 0; i < used; ++i) cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
     ct_status result = CT_OK;
@@ -99,6 +104,7 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
         cudaEventRecord(pool->join[i], pool->s[i]);
         cudaStreamWaitEvent(st, pool->join[i], 0);
     }
+    lock.unlock();
     if (result != CT_OK) return result;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -112,9 +118,18 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
             ctpd::set_error("ct_pdtv_solve_batched: %s", cudaGetErrorString(e));
             return CT_ERR_CUDA;
         }
+        ct_status first = CT_OK;
+        char msg[400] = "";
         for (int i = 0; i < n; ++i) {
             result = ctpd::read_report(workspaces[i], &reports[i]);
-            if (result != CT_OK) return result;
+            if (result != CT_OK && first == CT_OK) {
+                first = result;
+                snprintf(msg, sizeof(msg), "slice %d: %s", i, ct_last_error());
+            }
+        }
+        if (first != CT_OK) {
+            ctpd::set_error("ct_pdtv_solve_batched: %s", msg);
+            return first;
         }
     }
     return CT_OK;

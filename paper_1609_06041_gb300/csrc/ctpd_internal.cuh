@@ -144,11 +144,22 @@ enum {
     S_LN0 = 24,    // norm of the first Lanczos vector (image side)
     S_LN0B = 25,   // and of the sinogram side
     S_EPSC = 26,   // u = 1 / c of the last proximal map of the error-tolerant form
+    S_FLAGS = 27,  // input / result check bits (CHK_*), an unsigned in the slot's first 4 bytes
     S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1 (image side)
     S_LZ2 = 32 + 2 * 64,   // the same for the sinogram side
     S_COUNT = 32 + 4 * 64
 };
 constexpr int LANCZOS_MAX = 64;
+// Bits of the S_FLAGS word (k_check.cu).
+enum : unsigned {
+    CHK_WEIGHT_NOT_POSITIVE = 1u,   // some w_i <= 0 (W of Eq. 1 must be positive definite)
+    CHK_NONFINITE_INPUT = 2u,       // NaN or infinity in b or w
+    CHK_NONFINITE_RESULT = 4u       // NaN or infinity in the returned image
+};
+inline unsigned *flags_of(double *scal) { return reinterpret_cast<unsigned *>(scal + S_FLAGS); }
+// Status of a finished solve from its flag word (CT_OK if none is set; the
+// message names the first problem).
+ct_status status_from_flags(unsigned flags, const char *who);
 // Float copies of the scalars the per-iteration kernels read (doubles 20-21
 // hold four floats; every scalar-program launch refreshes them), so those
 // kernels convert nothing on the slow FP64 pipe.
@@ -186,6 +197,15 @@ inline void counted(unsigned n = 1)
 }
 
 // ---- kernels (defined in the k_*.cu files) ----
+// Input and result checks, and the per-iteration trace (k_check.cu).
+void launch_check_inputs(const float *b, const float *w, size_t n, unsigned *flags, cudaStream_t st);
+void launch_check_finite(const float *x, size_t n, unsigned *flags, unsigned bit, cudaStream_t st);
+size_t trace_scratch_doubles();
+// *out = beta psi(x) + 1/2 sum w (A x - b)^2 (lowdose) or ||A x - b|| (A x
+// given as the projector's band partial sums of one slice); part holds
+// trace_scratch_doubles() doubles
+void launch_trace(const Geometry *g, const float *partial, const float *b, const float *w, const float *x,
+                  double beta, int lowdose, double *part, double *out, cudaStream_t st);
 // Forward projection in two parts: band partial sums (one image band of
 // PROJ_R rows / columns per block, deterministic) and their reduction.
 // partial holds n_bands(N) x V x B floats per image.

@@ -66,6 +66,19 @@ extern "C" ct_status ct_ramp_filter_noalloc(const ct_geometry *geom, const float
         ctpd::set_error("ct_ramp_filter_noalloc: bad pointer");
         return CT_ERR_ARG;
     }
+    // the scratch array's address and the geometry's twiddle table must
+    // belong to the same GPU: the geometry's
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        ctpd::set_error("ct_ramp_filter_noalloc: cudaGetDevice failed");
+        return CT_ERR_CUDA;
+    }
+    if (dev != g->device) {
+        ctpd::set_error("ct_ramp_filter_noalloc: the current device is %d but the geometry lives on device %d",
+                        dev, g->device);
+        return CT_ERR_ARG;
+    }
     float2 *hhat = nullptr;
     if (scratch_address(&hhat) != CT_OK) {
         ctpd::set_error("ct_ramp_filter_noalloc: cudaGetSymbolAddress of the scratch array failed");

@@ -39,7 +39,7 @@ class ct_pdtv_params(ctypes.Structure):
 
 class ct_pdtv_report(ctypes.Structure):
     _fields_ = [("tau", _d), ("sigma", _d), ("kappa", _d), ("lambda_", _d),
-                ("norm_ADA", _d), ("norm_WDW", _d), ("k", _i)]
+                ("norm_ADA", _d), ("norm_WDW", _d), ("k", _i), ("trace", ctypes.POINTER(_d))]
 
     def as_dict(self):
         return {"tau": self.tau, "sigma": self.sigma, "kappa": self.kappa,
@@ -51,6 +51,7 @@ EXPORTS = {
     "ct_version": ([], ctypes.c_char_p),
     "ct_last_error": ([], ctypes.c_char_p),
     "ct_kernel_launches": ([], ctypes.c_ulonglong),
+    "ct_probe_fp32_fma": ([_i, ctypes.POINTER(_d), _vp], _i),
     "ct_geometry_create": ([_i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
     "ct_geometry_destroy": ([_vp], None),
     "ct_geometry_autotune": ([_vp, _i, _vp], _i),
@@ -67,6 +68,7 @@ EXPORTS = {
     "ct_pdtv_workspace_bytes": ([_vp, ctypes.POINTER(ct_pdtv_params)], ctypes.c_size_t),
     "ct_pdtv_solve": ([_vp, _vp, _vp, ctypes.POINTER(ct_pdtv_params), _vp, _vp,
                        ctypes.POINTER(ct_pdtv_report), _vp], _i),
+    "ct_pdtv_status": ([_vp, _vp], _i),
     "ct_unrolled_workspace_bytes": ([_vp, _i, _i, _i, _i], ctypes.c_size_t),
     "ct_unrolled_forward": ([_vp, _vp, _vp, _i, _vp, _i, _d, _d, _d, _i, _i, _i, _vp, _vp, _vp], _i),
     "ct_unrolled_backward": ([_vp, _vp, _vp, _i, _vp, _i, _d, _d, _d, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
@@ -124,6 +126,13 @@ def ct_last_error() -> str:
 
 def ct_kernel_launches() -> int:
     return int(_lib.ct_kernel_launches())
+
+
+def ct_probe_fp32_fma(packed: bool = False) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    v = _d(0.0)
+    _check(_lib.ct_probe_fp32_fma(int(bool(packed)), ctypes.byref(v), _stream()))
+    return float(v.value)
 
 
 class Geometry:
@@ -311,10 +320,12 @@ def ct_pdtv_workspace_bytes(g: Geometry, params: PDTVParams) -> int:
 
 def ct_pdtv_solve(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, params: PDTVParams,
                   x_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-                  report: bool = True):
+                  report: bool = True, trace: bool = False):
     """Algorithm 1 / 1' / 2.  Returns (x, report dict or None).
     `workspace` (uint8 CUDA tensor of ct_pdtv_workspace_bytes) holds the
-    iteration state for params.resume."""
+    iteration state for params.resume.  trace (needs report): the report's
+    "trace" lists the cost of Eq. 1 (low-dose) or ||Ax - b|| (few-view)
+    after each iteration."""
     pb = _dev(b, "b", (g.n_views, g.n_bins))
     pw = None if w is None else _dev(w, "w", (g.n_views, g.n_bins))
     if x_out is None:
@@ -326,10 +337,22 @@ def ct_pdtv_solve(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, params: 
             raise ValueError("workspace too small")
         pws = ctypes.c_void_p(workspace.data_ptr())
     p = params.to_c()
-    rep = ct_pdtv_report() if report else None
+    rep = ct_pdtv_report() if report or trace else None
+    tr = (_d * max(int(params.iters), 1))() if trace else None
+    if tr is not None:
+        rep.trace = ctypes.cast(tr, ctypes.POINTER(_d))
     _check(_lib.ct_pdtv_solve(g.handle, pb, pw, ctypes.byref(p), px, pws,
                               ctypes.byref(rep) if rep is not None else None, _stream()))
-    return x_out, (rep.as_dict() if rep is not None else None)
+    out = rep.as_dict() if rep is not None else None
+    if tr is not None:
+        out["trace"] = [tr[i] for i in range(int(params.iters))]
+    return x_out, out
+
+
+def ct_pdtv_status(workspace: torch.Tensor) -> None:
+    """Raise CTError if the last solve with this workspace found a weight
+    w_i <= 0 or NaN / infinity in b, w or the image (synchronises)."""
+    _check(_lib.ct_pdtv_status(ctypes.c_void_p(workspace.data_ptr()), _stream()))
 
 
 def workspace_for(g: Geometry, params: PDTVParams, device="cuda") -> torch.Tensor:
