@@ -311,11 +311,11 @@ size_t ct_pdtv_workspace_bytes(const ct_geometry *geom, const ct_pdtv_params *pa
  * (CT_LOWDOSE; NULL for CT_FEWVIEW).  x_out: N x N, receives x^K (with
  * params->resume it must hold the x of the resumed state).
  * Input checks: b and w live on the device, so a device pass checks them
- * (w > 0 and finite, b finite) and the image x^K (finite) and records what
+ * (w > 0 and finite, b finite) and the result (x^K and mu^K finite) and records what
  * it finds in the workspace.  The result comes back at the next
  * synchronisation the caller asks for: with a report this call returns
- * CT_ERR_ARG (some w_i <= 0) or CT_ERR_NONFINITE (NaN or infinity in b, w
- * or x^K) after filling the report; without one, ct_pdtv_status(workspace,
+ * CT_ERR_ARG (some w_i <= 0) or CT_ERR_NONFINITE (NaN or infinity in b, w,
+ * x^K or mu^K) after filling the report; without one, ct_pdtv_status(workspace,
  * stream) returns the same codes.  The solve itself still runs (its image
  * is then not meaningful).
  * workspace: device memory of ct_pdtv_workspace_bytes(); it holds the whole
@@ -345,7 +345,7 @@ ct_status ct_pdtv_solve(const ct_geometry *geom, const float *b, const float *w,
  * Result of the input and result checks of the last solve that used this
  * workspace (caller-owned, device): synchronises `stream` and returns
  * CT_OK, CT_ERR_ARG (a weight w_i <= 0: W of Eq. 1 is not positive
- * definite), or CT_ERR_NONFINITE (NaN or infinity in b, w or the image),
+ * definite), or CT_ERR_NONFINITE (NaN or infinity in b, w, the image or the dual variable),
  * with a message in ct_last_error().  CT_ERR_CUDA if the synchronisation
  * or the read fails.
  */

@@ -74,7 +74,7 @@ ct_status ctpd::status_from_flags(unsigned flags, const char *who)
         return CT_ERR_NONFINITE;
     }
     if (flags & CHK_NONFINITE_RESULT) {
-        set_error("%s: the image holds NaN or infinity (step sizes too large?)", who);
+        set_error("%s: the image or the dual variable holds NaN or infinity (step sizes too large?)", who);
         return CT_ERR_NONFINITE;
     }
     return CT_OK;
@@ -726,10 +726,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
             return fail(CT_ERR_OOM, "ct_pdtv_solve: trace buffer allocation failed");
         }
     }
-    // the input checks: w > 0 and finite (low-dose), b finite; bits in the flag word
     unsigned *flags = flags_of(scal);
-    cudaMemsetAsync(flags, 0, sizeof(unsigned), st);
-    launch_check_inputs(b, lowdose ? w : nullptr, I, flags, st);
 
     long long k0 = 0;
     if (prm->resume) {
@@ -740,6 +737,11 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     } else {
         // ---- setup (Alg. 1 / Alg. 2 boxes): kappa, tau, D, sigma ----
         cudaMemsetAsync(scal, 0, sizeof(double) * S_COUNT, st);
+    }
+    // the input checks: w > 0 and finite (low-dose), b finite; bits in the flag word
+    cudaMemsetAsync(flags, 0, sizeof(unsigned), st);
+    launch_check_inputs(b, lowdose ? w : nullptr, I, flags, st);
+    if (!prm->resume) {
         cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
         cudaMemsetAsync(ticket2, 0, sizeof(unsigned), st);
         if (lowdose) {
@@ -862,6 +864,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     }
     launch_scalars(scal, SC_SET, (double)(k0 + prm->iters), 0, 0, S_K, st);
     launch_check_finite(x_out, J, flags, CHK_NONFINITE_RESULT, st);
+    launch_check_finite(mu, I, flags, CHK_NONFINITE_RESULT, st);   // x >= 0 clamps a diverged x, not mu
     cs = cuda_check("ct_pdtv_solve");
     if (report && cs == CT_OK) {
         cudaError_t e = cudaStreamSynchronize(st);

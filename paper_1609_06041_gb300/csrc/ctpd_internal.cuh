@@ -137,6 +137,22 @@ __device__ __forceinline__ void joseph_round(float up, int &i0, float &g)
     g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
 }
 
+// Packed two-wide FP32 arithmetic of sm_100-family GPUs (fma / add / sub
+// .rn.f32x2: two lanes per instruction, each rounded as its scalar form).
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    unsigned long long A, Bv, D;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(Bv) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(Bv));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(D));
+    return d;
+}
+
 // Device scalar block at the start of a solve workspace (doubles).
 enum {
     S_KAPPA = 0, S_TAU, S_SIGMA, S_LAMBDA, S_INV8LAM, S_NADA, S_NWDW, S_K,
@@ -154,7 +170,7 @@ constexpr int LANCZOS_MAX = 64;
 enum : unsigned {
     CHK_WEIGHT_NOT_POSITIVE = 1u,   // some w_i <= 0 (W of Eq. 1 must be positive definite)
     CHK_NONFINITE_INPUT = 2u,       // NaN or infinity in b or w
-    CHK_NONFINITE_RESULT = 4u       // NaN or infinity in the returned image
+    CHK_NONFINITE_RESULT = 4u       // NaN or infinity in the returned image or dual variable
 };
 inline unsigned *flags_of(double *scal) { return reinterpret_cast<unsigned *>(scal + S_FLAGS); }
 // Status of a finished solve from its flag word (CT_OK if none is set; the

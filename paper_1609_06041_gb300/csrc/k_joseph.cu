@@ -331,65 +331,68 @@ k_project_mirror(const float *__restrict__ x, const ViewP *__restrict__ views,
 // Walks one ray through the staged steps lo..hi (ROWS steps per pass, one
 // coordinate evaluation per step) and returns its four sums: band A and
 // band B at the pair i0, and (PAIR) at the reflected pair N-2-i0.  Q holds
-// per step and pair (A mid, A delta, B mid, B delta), so one 16-byte load
-// serves both bands.
+// per step and pair (A mid, B mid, A delta, B delta), so one 16-byte load
+// serves both bands and the two bands' samples are one packed two-wide
+// FMA, mid + g delta, into a pair accumulator (the reflected pair with -g).
+// The coordinates of two steps are evaluated as one packed pair as well.
 template <bool PAIR, int ROWS>
 __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP, float q, float m, int lo, int hi,
                                             int s0, float h, unsigned top)
 {
-    float qk[ROWS];
+    static_assert(ROWS % 2 == 0, "steps are evaluated in pairs");
+    float2 qk[ROWS / 2];   // q + k m for the steps k, k + 1 of a pass
 #pragma unroll
-    for (int k = 0; k < ROWS; ++k) qk[k] = __fmaf_rn((float)k, m, q);
+    for (int k = 0; k < ROWS / 2; ++k) qk[k] = pk(__fmaf_rn((float)(2 * k), m, q), __fmaf_rn((float)(2 * k + 1), m, q));
+    const float2 mm = pk(m, m), bias = pk(JOSEPH_BIAS, JOSEPH_BIAS);
     float spk = (float)lo - h;
     int ridx = (lo - s0) * SP;
-    float a[ROWS], b[ROWS], c[ROWS], e[ROWS];
+    float2 ab[ROWS], ce[ROWS];   // (band A, band B) sums at i0 and at the reflected pair
 #pragma unroll
-    for (int k = 0; k < ROWS; ++k) a[k] = b[k] = c[k] = e[k] = 0.0f;
+    for (int k = 0; k < ROWS; ++k) ab[k] = ce[k] = pk(0.0f, 0.0f);
     int s = lo;
     for (; s + ROWS - 1 <= hi; s += ROWS) {
 #pragma unroll
-        for (int k = 0; k < ROWS; ++k) {
-            const float up = joseph_u(spk, m, qk[k]);
-            const float t = __fadd_rn(up, JOSEPH_BIAS);
-            const unsigned i = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
-            const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
-            const float4 pv = Q[ridx + k * SP + (int)i];
-            a[k] += __fmaf_rn(g, pv.y, pv.x);
-            b[k] += __fmaf_rn(g, pv.w, pv.z);
+        for (int k = 0; k < ROWS / 2; ++k) {
+            const float2 up = pfma(pk(spk, spk), mm, qk[k]);
+            const float2 t = padd(up, bias);
+            const float2 tb = psub(t, bias);
+            const float2 g = psub(up, tb), gn = psub(tb, up);
+            const unsigned i0 = min((unsigned)(__float_as_int(t.x) - (JOSEPH_BIAS_BITS - 2)), top);
+            const unsigned i1 = min((unsigned)(__float_as_int(t.y) - (JOSEPH_BIAS_BITS - 2)), top);
+            const float4 p0 = Q[ridx + (2 * k) * SP + (int)i0];
+            const float4 p1 = Q[ridx + (2 * k + 1) * SP + (int)i1];
+            ab[2 * k] = pfma(pk(g.x, g.x), pk(p0.z, p0.w), padd(ab[2 * k], pk(p0.x, p0.y)));
+            ab[2 * k + 1] = pfma(pk(g.y, g.y), pk(p1.z, p1.w), padd(ab[2 * k + 1], pk(p1.x, p1.y)));
             if (PAIR) {
-                const float4 rv = Q[ridx + k * SP + (int)(top - i)];
-                c[k] += __fmaf_rn(-g, rv.y, rv.x);
-                e[k] += __fmaf_rn(-g, rv.w, rv.z);
+                const float4 r0 = Q[ridx + (2 * k) * SP + (int)(top - i0)];
+                const float4 r1 = Q[ridx + (2 * k + 1) * SP + (int)(top - i1)];
+                ce[2 * k] = pfma(pk(gn.x, gn.x), pk(r0.z, r0.w), padd(ce[2 * k], pk(r0.x, r0.y)));
+                ce[2 * k + 1] = pfma(pk(gn.y, gn.y), pk(r1.z, r1.w), padd(ce[2 * k + 1], pk(r1.x, r1.y)));
             }
         }
         spk = __fadd_rn(spk, (float)ROWS);
         ridx += ROWS * SP;
     }
     for (; s <= hi; ++s) {
-        const float up = joseph_u(spk, m, qk[0]);
+        const float up = joseph_u(spk, m, qk[0].x);
         const float t = __fadd_rn(up, JOSEPH_BIAS);
         const unsigned i = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
         const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
         const float4 pv = Q[ridx + (int)i];
-        a[0] += __fmaf_rn(g, pv.y, pv.x);
-        b[0] += __fmaf_rn(g, pv.w, pv.z);
+        ab[0] = pfma(pk(g, g), pk(pv.z, pv.w), padd(ab[0], pk(pv.x, pv.y)));
         if (PAIR) {
             const float4 rv = Q[ridx + (int)(top - i)];
-            c[0] += __fmaf_rn(-g, rv.y, rv.x);
-            e[0] += __fmaf_rn(-g, rv.w, rv.z);
+            ce[0] = pfma(pk(-g, -g), pk(rv.z, rv.w), padd(ce[0], pk(rv.x, rv.y)));
         }
         spk = __fadd_rn(spk, 1.0f);
         ridx += SP;
     }
-    float4 r = make_float4(a[0], b[0], c[0], e[0]);
 #pragma unroll
     for (int k = 1; k < ROWS; ++k) {
-        r.x += a[k];
-        r.y += b[k];
-        r.z += c[k];
-        r.w += e[k];
+        ab[0] = padd(ab[0], ab[k]);
+        ce[0] = padd(ce[0], ce[k]);
     }
-    return r;
+    return make_float4(ab[0].x, ab[0].y, ce[0].x, ce[0].y);
 }
 
 // ROWS = 2: up to 16 items (1024 threads, 64 registers); ROWS = 4: more
@@ -456,8 +459,8 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                         const int c = c0 + u * nw;
                         const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
                         if (c < nc && ii < CW)
-                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), a1[u] - a0[u], 0.5f * (b0[u] + b1[u]),
-                                                         b1[u] - b0[u]);
+                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]),
+                                                         a1[u] - a0[u], b1[u] - b0[u]);
                     }
                 }
             } else {
@@ -479,8 +482,8 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                     for (int u = 0; u < SU; ++u) {
                         const int ii = 2 * (c0 + u * nw) + (lx >> 4);
                         if (c0 + u * nw < nc && ii < CW)
-                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), a1[u] - a0[u], 0.5f * (b0[u] + b1[u]),
-                                                         b1[u] - b0[u]);
+                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]),
+                                                         a1[u] - a0[u], b1[u] - b0[u]);
                     }
                 }
             }
@@ -500,7 +503,7 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                         const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
                         const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
                         const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
-                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
                     }
                 }
             } else {
@@ -515,7 +518,7 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                         const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
                         const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
                         const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
-                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), a1 - a0, 0.5f * (b0 + b1), b1 - b0);
+                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
                     }
                 }
             }
