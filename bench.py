@@ -242,9 +242,31 @@ def run_reference(args):
 # ----------------------------------------------------------------------
 # batched form: 64 slices of mixed size, view count and mode
 # ----------------------------------------------------------------------
+def _time_graph(P, bs, steps):
+    """ms per replay of one CUDA graph of bs.run() (after one eager call)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    bs.run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bs.run()
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def measure_batched(P, steps=3, count=64, seed=0):
-    """slices/s of one ct_pdtv_solve_batched call (captured in a CUDA graph)
-    against the same slices solved one after another with ct_pdtv_solve."""
+    """slices/s of one ct_pdtv_solve_batched call (captured in a CUDA graph):
+    the persistent form (setups on the stream pool, every iteration of every
+    slice in one persistent launch) and the stream-pool form, against the
+    same slices solved one after another with ct_pdtv_solve."""
     import torch
     shapes = synth.mixed_slices(count, seed)
     slices, geoms = [], {}
@@ -261,20 +283,14 @@ def measure_batched(P, steps=3, count=64, seed=0):
         slices.append((g, b, w, P.PDTVParams(mode=mode, iters=30, beta=0.005)))
     stream = torch.cuda.current_stream()
     bs = P.BatchedSolve(slices, autotune=True)   # one autotune per distinct geometry, before capture
-    bs.run()
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        bs.run()
-    graph.replay()
-    torch.cuda.synchronize()
+    P.ct_batched_options(P.CT_BATCH_AUTO)
+    t_batched = _time_graph(P, bs, steps)
+    try:
+        P.ct_batched_options(P.CT_BATCH_POOL)
+        t_pool = _time_graph(P, bs, steps)
+    finally:
+        P.ct_batched_options(P.CT_BATCH_AUTO)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_batched = e0.elapsed_time(e1) / steps
     # the same slices one after another through the single-slice solve
     ws = bs.ws
     for i, (g, b, w, prm) in enumerate(slices):
@@ -289,7 +305,9 @@ def measure_batched(P, steps=3, count=64, seed=0):
     t_single = e0.elapsed_time(e1) / steps
     return {"workload": f"{count} slices, N in (256,384,512), views in (32,90,360,720), "
                         f"bins = ceil(1.44 N), low-dose if V*B > N^2 else few-view, 30 iterations",
+            "form": "persistent (setups on the stream pool, then one persistent launch for all iterations)",
             "batched_slices_per_s": count / (t_batched / 1e3), "batched_ms": t_batched,
+            "pool_slices_per_s": count / (t_pool / 1e3), "pool_ms": t_pool,
             "single_slices_per_s": count / (t_single / 1e3), "single_ms": t_single,
             "speedup": t_single / t_batched}
 

@@ -360,25 +360,55 @@ ct_status ct_pdtv_status(const void *workspace, void *stream);
  * per-slice handles, device pointers and parameters; w may be NULL when no
  * slice is low-dose, and w[i] may be NULL for few-view slices.  Every
  * workspace must be ct_pdtv_workspace_bytes(geoms[i], &params[i]) bytes;
- * resume is not accepted here.  The slices run concurrently on a pool of
- * streams the library creates per device on first use (keep that first
- * call outside stream capture); the work is forked from `stream` and
- * joined back into it, so later work on `stream` sees every x_out, and the
- * whole call can be captured into a CUDA graph.  reports (host, n entries,
- * may be NULL) are filled after synchronising `stream` (their trace is not
- * used); the call then returns the first slice's check failure, if any
- * (see ct_pdtv_solve), naming the slice.  Calls from several host threads
- * at once share the pool: each call holds the pool's lock while it
- * enqueues, so its slices wait on its own fork and its stream on its own
- * joins, and the calls' slices run one call after the other on the pool.
- * Do not capture two calls at the same time, and do not run an uncaptured
- * call while another thread captures one (the pool streams would join the
- * capture).
+ * resume is not accepted here.
+ *
+ * Two forms, the same result up to the order of float additions:
+ *   persistent  when every slice qualifies (default angles with N and V
+ *               even, N a multiple of 32 and at most 637, n_bins <= 4096,
+ *               precond 0, 1 or 3, eps = 0, tv_iters <= 16, the same
+ *               iters > 0 for all slices, the geometries on the current
+ *               device) and the form is CT_BATCH_AUTO (ct_batched_options):
+ *               each slice's setup (kappa, tau, D, the Lanczos step sizes,
+ *               Step 1 at k = 0) runs on the stream pool below, and then ONE
+ *               kernel launch on `stream` (one per 96 slices) runs every
+ *               iteration of every slice: one block per SM takes work items
+ *               (slice, phase, tile) from a queue in iteration order, and
+ *               waits for the slice's previous phase with a bounded spin
+ *               (ct_batched_options' limit, 5 s by default).  A wait that
+ *               runs out stops the launch and marks every slice's checks,
+ *               so the reports (or ct_pdtv_status) give CT_ERR_TIMEOUT.
+ *   stream pool otherwise: the slices' ordinary solves run concurrently.
+ * The slices run on a pool of streams the library creates per device on
+ * first use (keep that first call outside stream capture); the work is
+ * forked from `stream` and joined back into it, so later work on `stream`
+ * sees every x_out, and the whole call can be captured into a CUDA graph.
+ * reports (host, n entries, may be NULL) are filled after synchronising
+ * `stream` (their trace is not used); the call then returns the first
+ * slice's check failure, if any (see ct_pdtv_solve), naming the slice.
+ * Calls from several host threads at once share the pool: each call holds
+ * the pool's lock while it enqueues, so its slices wait on its own fork and
+ * its stream on its own joins, and the calls' slices run one call after the
+ * other on the pool.  Do not capture two calls at the same time, and do not
+ * run an uncaptured call while another thread captures one (the pool
+ * streams would join the capture).
  */
 ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geoms, const float *const *b,
                                 const float *const *w, const ct_pdtv_params *params,
                                 float *const *x_out, void *const *workspaces,
                                 ct_pdtv_report *reports, void *stream);
+
+/*
+ * Options of ct_pdtv_solve_batched for this process (no counterpart in the
+ * paper; they choose how the slices are scheduled, never what is
+ * computed).  form: CT_BATCH_AUTO (the default) uses the persistent launch
+ * when every slice qualifies, CT_BATCH_POOL always the stream pool.
+ * wait_seconds: time limit of one wait of the persistent launch for a
+ * slice's previous phase (< 0: the default, 5 s; 0: a wait that is not
+ * satisfied at once fails, which tests use to see the timeout path).
+ * CT_ERR_ARG for an unknown form, NaN or more than 3600 s.
+ */
+enum { CT_BATCH_AUTO = 0, CT_BATCH_POOL = 1 };
+ct_status ct_batched_options(int form, double wait_seconds);
 
 /*
  * The differentiable form: `iters` iterations of Algorithm 1 (mode

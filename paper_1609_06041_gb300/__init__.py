@@ -5,6 +5,8 @@ The compute path is libctpd.so (hand-written CUDA for sm_103a) behind the
 C ABI of include/ctpd.h; ``ctpd`` is its thin Python binding.
 """
 from .ctpd import (  # noqa: F401
+    CT_BATCH_AUTO,
+    CT_BATCH_POOL,
     CT_FEWVIEW,
     CT_LOWDOSE,
     CT_TAPS_HIGH_BAND,
@@ -14,6 +16,7 @@ from .ctpd import (  # noqa: F401
     Geometry,
     PDTVParams,
     ct_backproject,
+    ct_batched_options,
     ct_geometry_autotune,
     ct_geometry_create,
     ct_geometry_destroy,

@@ -65,6 +65,11 @@ ct_status ctpd::read_report(const void *workspace, ct_pdtv_report *report)
 
 ct_status ctpd::status_from_flags(unsigned flags, const char *who)
 {
+    if (flags & CHK_TIMEOUT) {
+        set_error("%s: a wait of the persistent batched solve ran out of its time limit; the slices are "
+                  "incomplete", who);
+        return CT_ERR_TIMEOUT;
+    }
     if (flags & CHK_WEIGHT_NOT_POSITIVE) {
         set_error("%s: a weight w_i is zero or negative (W of Eq. 1 must be positive definite)", who);
         return CT_ERR_ARG;
@@ -329,6 +334,24 @@ ct_status solve_graph(const ct_geometry *g, const float *b, const float *w, cons
 }
 
 }  // namespace
+
+ctpd::SolveBuffers ctpd::solve_buffers(const Geometry *g, const ct_pdtv_params *prm, void *workspace)
+{
+    const Layout L = layout(g, prm);
+    char *ws = static_cast<char *>(workspace);
+    SolveBuffers sb;
+    sb.scal = (double *)(ws + L.scal);
+    sb.winv = (float *)(ws + L.winv);
+    sb.mu = (float *)(ws + L.mu);
+    sb.mubar = (float *)(ws + L.mubar);
+    sb.z = (float *)(ws + L.z);
+    sb.p0 = (float *)(ws + L.p0);
+    sb.p1 = (float *)(ws + L.p1);
+    sb.band = (float *)(ws + L.band);
+    sb.orb = (float *)(ws + L.orb);
+    sb.hhat = (float2 *)(ws + L.hhat);
+    return sb;
+}
 
 // drop the cached graphs (their launch shapes are out of date); the streams stay
 void ctpd::graph_cache_clear(Geometry *g)

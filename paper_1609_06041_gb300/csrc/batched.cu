@@ -1,16 +1,19 @@
 // batched.cu -- ct_pdtv_solve_batched: many independent slices (their own
 // geometry, data, mode and parameters) solved in one call.
 //
-// Each slice's solve is the single-slice ct_pdtv_solve.  The call forks
-// the caller's stream onto a pool of streams (one pool per device, created
-// on first use and kept until exit) with events, enqueues slice i on pool
-// stream i mod S, and joins every pool stream back into the caller's
-// stream.  Small slices that cannot fill the GPU on their own then run
-// side by side.  The fork and join are stream-ordered event waits, so the
-// whole call can be captured into one CUDA graph.
+// The call forks the caller's stream onto a pool of streams (one pool per
+// device, created on first use and kept until exit) with events, enqueues
+// slice i on pool stream i mod S, and joins every pool stream back into
+// the caller's stream.  The fork and join are stream-ordered event waits,
+// so the whole call can be captured into one CUDA graph.  When every slice
+// qualifies for the persistent form, the pool runs only the slices' setups
+// and one persistent launch after the join runs all their iterations
+// (persist.cu); otherwise the pool runs each slice's whole single-slice
+// solve, so small slices that cannot fill the GPU alone run side by side.
 #include <stdio.h>
 
 #include <mutex>
+#include <vector>
 
 #include "ctpd_internal.cuh"
 
@@ -86,13 +89,25 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int used = n < POOL_STREAMS ? n : POOL_STREAMS;
+    // the persistent form: every slice qualifies and shares the iteration count
+    bool persistent = ctpd::batched_form() == CT_BATCH_AUTO;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n && persistent; ++i)
+        persistent = geoms[i]->device == dev && ctpd::persistent_slice_ok(geoms[i], &params[i], params[0].iters);
+    std::vector<ct_pdtv_params> setup;
+    if (persistent) {
+        // the pool runs each slice's setup and Step 1 at k = 0 (no iteration)
+        setup.assign(params, params + n);
+        for (auto &p : setup) p.iters = 0;
+    }
     std::unique_lock<std::mutex> lock(pool->mu);
     cudaEventRecord(pool->fork, st);
     for (int i = 0; i < used; ++i) cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
     ct_status result = CT_OK;
     for (int i = 0; i < n && result == CT_OK; ++i) {
-        result = ctpd::pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, &params[i], x_out[i], workspaces[i],
-                                  nullptr, pool->s[i % POOL_STREAMS], false);
+        result = ctpd::pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, persistent ? &setup[i] : &params[i], x_out[i],
+                                  workspaces[i], nullptr, pool->s[i % POOL_STREAMS], false);
         if (result != CT_OK) {
             char msg[400];
             snprintf(msg, sizeof(msg), "%s", ct_last_error());
@@ -106,6 +121,11 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
     }
     lock.unlock();
     if (result != CT_OK) return result;
+    // the iterations of every slice: one persistent launch on the caller's stream
+    if (persistent) {
+        result = ctpd::launch_persistent(n, geoms, b, params, x_out, workspaces, st);
+        if (result != CT_OK) return result;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         ctpd::set_error("ct_pdtv_solve_batched: %s", cudaGetErrorString(e));

@@ -137,6 +137,30 @@ __device__ __forceinline__ void joseph_round(float up, int &i0, float &g)
     g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
 }
 
+// The threads that run one kernel body: a whole one-dimensional thread
+// block (a normal launch; sync = __syncthreads), or one fixed group of a
+// persistent block (GroupCtx: its own named barrier `bar` (1..15) over nth
+// threads).  Bodies are templates on the context type, so a normal launch
+// pays nothing for the choice.
+struct BlockCtx {
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ int nth() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct GroupCtx {
+    int t, n, bar;
+    __device__ __forceinline__ int tid() const { return t; }
+    __device__ __forceinline__ int nth() const { return n; }
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory"); }
+};
+__device__ __forceinline__ BlockCtx whole_block() { return BlockCtx{}; }
+// A whole two-dimensional block, threads numbered row by row.
+struct Block2D {
+    __device__ __forceinline__ int tid() const { return threadIdx.y * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int nth() const { return blockDim.x * blockDim.y; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
 // Packed two-wide FP32 arithmetic of sm_100-family GPUs (fma / add / sub
 // .rn.f32x2: two lanes per instruction, each rounded as its scalar form).
 __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
@@ -161,6 +185,9 @@ enum {
     S_LN0B = 25,   // and of the sinogram side
     S_EPSC = 26,   // u = 1 / c of the last proximal map of the error-tolerant form
     S_FLAGS = 27,  // input / result check bits (CHK_*), an unsigned in the slot's first 4 bytes
+    S_PDONE = 28,  // persistent batched kernel: items of this slice completed (unsigned)
+    S_PQUEUE = 29, // persistent batched kernel, first slice only: next work item (unsigned)
+    S_PERR = 30,   // persistent batched kernel, first slice only: a wait ran out (unsigned)
     S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1 (image side)
     S_LZ2 = 32 + 2 * 64,   // the same for the sinogram side
     S_COUNT = 32 + 4 * 64
@@ -170,9 +197,10 @@ constexpr int LANCZOS_MAX = 64;
 enum : unsigned {
     CHK_WEIGHT_NOT_POSITIVE = 1u,   // some w_i <= 0 (W of Eq. 1 must be positive definite)
     CHK_NONFINITE_INPUT = 2u,       // NaN or infinity in b or w
-    CHK_NONFINITE_RESULT = 4u       // NaN or infinity in the returned image or dual variable
+    CHK_NONFINITE_RESULT = 4u,      // NaN or infinity in the returned image or dual variable
+    CHK_TIMEOUT = 8u                // a wait of the persistent batched kernel ran out
 };
-inline unsigned *flags_of(double *scal) { return reinterpret_cast<unsigned *>(scal + S_FLAGS); }
+__host__ __device__ inline unsigned *flags_of(double *scal) { return reinterpret_cast<unsigned *>(scal + S_FLAGS); }
 // Status of a finished solve from its flag word (CT_OK if none is set; the
 // message names the first problem).
 ct_status status_from_flags(unsigned flags, const char *who);
@@ -213,6 +241,31 @@ inline void counted(unsigned n = 1)
 }
 
 // ---- kernels (defined in the k_*.cu files) ----
+// The persistent batched solve (persist.cu).  persistent_slice_ok: the slice
+// qualifies (default angles with N, V even, N a multiple of 32 and at most
+// 637, n_bins <= 4096, precond 0, 1 or 3, no eps, at most 16 prox steps,
+// iters == iters0 > 0, no resume).  launch_persistent enqueues on st one
+// persistent launch per 96 slices that runs all iterations of the slices,
+// whose setup (and Step 1 at k = 0) must already be enqueued before it.
+int batched_form();
+bool persistent_slice_ok(const Geometry *g, const ct_pdtv_params *p, int iters0);
+ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float *const *b,
+                            const ct_pdtv_params *params, float *const *x_out, void *const *workspaces,
+                            cudaStream_t st);
+// Launch shapes shared with the persistent batched kernel (persist.cu).
+int orbit_slices(const Geometry *g);            // base-view slices of the orbit backprojector
+size_t orbit_smem_bytes();                      // shared memory of one orbit block
+bool quad_ok(const Geometry *g);                // the view-pair projector serves this geometry
+// TV prox tiles of one image spread over n_sm blocks (k_tv.cu's rule)
+void tv_tile_shape(int n, int steps, int n_sm, int min_rows, int *tc, int *tr, int *ncb, int *nrb);
+size_t dual_fft_smem(const Geometry *g);
+// Device pointers into a solve workspace (api.cu's layout).
+struct SolveBuffers {
+    double *scal;
+    float *winv, *mu, *mubar, *z, *p0, *p1, *band, *orb;
+    float2 *hhat;
+};
+SolveBuffers solve_buffers(const Geometry *g, const ct_pdtv_params *prm, void *workspace);
 // Input and result checks, and the per-iteration trace (k_check.cu).
 void launch_check_inputs(const float *b, const float *w, size_t n, unsigned *flags, cudaStream_t st);
 void launch_check_finite(const float *x, size_t n, unsigned *flags, unsigned bit, cudaStream_t st);

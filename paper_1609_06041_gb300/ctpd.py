@@ -29,6 +29,7 @@ _d = ctypes.c_double
 CT_OK, CT_ERR_ARG, CT_ERR_CUDA, CT_ERR_OOM, CT_ERR_TIMEOUT, CT_ERR_NONFINITE = range(6)
 CT_LOWDOSE, CT_FEWVIEW = 0, 1
 CT_TAPS_LOW_BAND, CT_TAPS_HIGH_BAND = 2, 3   # ct_ramp_taps: bands of the shift-variant D
+CT_BATCH_AUTO, CT_BATCH_POOL = 0, 1           # ct_batched_options: persistent launch when possible / stream pool
 
 
 class ct_pdtv_params(ctypes.Structure):
@@ -52,6 +53,7 @@ EXPORTS = {
     "ct_last_error": ([], ctypes.c_char_p),
     "ct_kernel_launches": ([], ctypes.c_ulonglong),
     "ct_probe_fp32_fma": ([_i, ctypes.POINTER(_d), _vp], _i),
+    "ct_batched_options": ([_i, _d], _i),
     "ct_geometry_create": ([_i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
     "ct_geometry_destroy": ([_vp], None),
     "ct_geometry_autotune": ([_vp, _i, _vp], _i),
@@ -126,6 +128,13 @@ def ct_last_error() -> str:
 
 def ct_kernel_launches() -> int:
     return int(_lib.ct_kernel_launches())
+
+
+def ct_batched_options(form: int = CT_BATCH_AUTO, wait_seconds: float = -1.0) -> None:
+    """How ct_pdtv_solve_batched schedules the slices (this process):
+    CT_BATCH_AUTO (persistent launch when every slice qualifies) or
+    CT_BATCH_POOL; wait_seconds < 0 restores the 5 s wait limit."""
+    _check(_lib.ct_batched_options(int(form), float(wait_seconds)))
 
 
 def ct_probe_fp32_fma(packed: bool = False) -> float:
