@@ -282,14 +282,16 @@ def measure_batched(P, steps=3, count=64, seed=0):
             b, w = p, None
         slices.append((g, b, w, P.PDTVParams(mode=mode, iters=30, beta=0.005)))
     stream = torch.cuda.current_stream()
-    bs = P.BatchedSolve(slices, autotune=True)   # one autotune per distinct geometry, before capture
-    P.ct_batched_options(P.CT_BATCH_AUTO)
-    t_batched = _time_graph(P, bs, steps)
-    try:
-        P.ct_batched_options(P.CT_BATCH_POOL)
-        t_pool = _time_graph(P, bs, steps)
-    finally:
-        P.ct_batched_options(P.CT_BATCH_AUTO)
+    # launch shapes per distinct geometry and the faster form, both tuned before capture
+    bs = P.BatchedSolve(slices, autotune=True)
+    chosen = bs.form
+    t_form = {}
+    for form in (P.CT_BATCH_AUTO, P.CT_BATCH_POOL):
+        bs.form = form
+        t_form[form] = _time_graph(P, bs, steps)
+    bs.form = chosen
+    t_batched = t_form[chosen]
+    t_persistent, t_pool = t_form[P.CT_BATCH_AUTO], t_form[P.CT_BATCH_POOL]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # the same slices one after another through the single-slice solve
     ws = bs.ws
@@ -305,8 +307,10 @@ def measure_batched(P, steps=3, count=64, seed=0):
     t_single = e0.elapsed_time(e1) / steps
     return {"workload": f"{count} slices, N in (256,384,512), views in (32,90,360,720), "
                         f"bins = ceil(1.44 N), low-dose if V*B > N^2 else few-view, 30 iterations",
-            "form": "persistent (setups on the stream pool, then one persistent launch for all iterations)",
+            "form": "persistent" if chosen == P.CT_BATCH_AUTO else "stream pool",
+            "form_choice": "the faster of the two forms in one untimed trial each (BatchedSolve autotune)",
             "batched_slices_per_s": count / (t_batched / 1e3), "batched_ms": t_batched,
+            "persistent_slices_per_s": count / (t_persistent / 1e3), "persistent_ms": t_persistent,
             "pool_slices_per_s": count / (t_pool / 1e3), "pool_ms": t_pool,
             "single_slices_per_s": count / (t_single / 1e3), "single_ms": t_single,
             "speedup": t_single / t_batched}

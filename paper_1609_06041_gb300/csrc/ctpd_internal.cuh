@@ -185,9 +185,10 @@ enum {
     S_LN0B = 25,   // and of the sinogram side
     S_EPSC = 26,   // u = 1 / c of the last proximal map of the error-tolerant form
     S_FLAGS = 27,  // input / result check bits (CHK_*), an unsigned in the slot's first 4 bytes
-    S_PDONE = 28,  // persistent batched kernel: items of this slice completed (unsigned)
-    S_PQUEUE = 29, // persistent batched kernel, first slice only: next work item (unsigned)
+    S_PDONE = 28,  // persistent batched kernel: items of the slice's current task completed (unsigned)
+    S_PQUEUE = 29, // persistent batched kernel, first slice only: slices finished (unsigned)
     S_PERR = 30,   // persistent batched kernel, first slice only: a wait ran out (unsigned)
+    S_PSTATE = 31, // persistent batched kernel: current task << 32 | items handed out (64-bit)
     S_LZ = 32,     // Lanczos coefficients: alpha_j at S_LZ + 2j, beta_j at S_LZ + 2j + 1 (image side)
     S_LZ2 = 32 + 2 * 64,   // the same for the sinogram side
     S_COUNT = 32 + 4 * 64

@@ -24,10 +24,13 @@
 // make the slice's finished writes visible to the block's loads.
 //
 // The item bodies are those of the single-slice kernels (body_*.cuh), run
-// by the whole 512-thread block (TV prox, projector with 8 view-pair items)
-// or by groups with their own named barriers (four 128-thread orbit tiles,
-// two 256-thread view pairs of the dual update).  All counters live in the
-// slices' scalar blocks, which each slice's setup clears.
+// by the whole 1024-thread block (the projector with 16 view-pair items) or
+// by groups with their own named barriers (eight 128-thread orbit tiles,
+// four 256-thread view pairs of the dual update, two 512-thread TV tiles),
+// so A, A^T and the dual update keep the 32 warps per SM of their own
+// kernels; the block's 64 registers per thread are fewer than the TV
+// prox's own kernel uses.  All counters live in the slices' scalar blocks,
+// which each slice's setup clears.
 #include <stdio.h>
 
 #include <algorithm>
@@ -43,14 +46,16 @@ namespace ctpd {
 
 namespace {
 
-constexpr int PS_THREADS = 512;
+constexpr int PS_THREADS = 1024;
 constexpr int PS_MAX = 96;                         // slices per launch (kernel parameter space)
 enum { PH_ORBIT = 0, PH_OREDUCE, PH_TV, PH_QUAD, PH_DUAL, PH_N };
 constexpr int ORB_GROUPS = PS_THREADS / ORB_TH;    // orbit tiles per item
 constexpr int DUAL_GROUPS = PS_THREADS / FFT_T;    // view pairs per item
 constexpr int RED_PIX = PS_THREADS * 8;            // pixels per slice-reduction item
 constexpr int QUAD_PG = PS_THREADS / 64;           // projector view-pair items per block
-static_assert(TV_THREADS == PS_THREADS, "a TV tile takes the whole block");
+constexpr int TV_GROUPS = PS_THREADS / TV_THREADS; // TV tiles per item
+static_assert(TV_GROUPS * TV_THREADS == PS_THREADS && QUAD_PG == PG, "whole groups");
+static_assert(1 + ORB_GROUPS + DUAL_GROUPS + TV_GROUPS <= 16, "named barriers 1..15");
 static_assert(ORB_GROUPS * ORB_TH == PS_THREADS && DUAL_GROUPS * FFT_T == PS_THREADS, "whole groups");
 
 struct PSlice {
@@ -123,24 +128,26 @@ __device__ __forceinline__ void run_item(const PSlice &S, int p, int k, int i, u
             S.z[q] = S.x[q] - tau * t;
         }
     } else if (p == PH_TV) {
-        // x^{k+1} = prox(z): one tile, the dual field read from p[k & 1] and written to p[(k + 1) & 1]
-        float2 *pub_x = reinterpret_cast<float2 *>(psm), *pub_y = pub_x + (TV_ROWS + 2) * 32;
-        const int bx = i % S.tv_ncb, by = i / S.tv_ncb;
-        if (S.fgp)
-            tv_body<true, false>(BlockCtx{}, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x, S.N,
-                                 S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
-        else
-            tv_body<false, false>(BlockCtx{}, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x,
-                                  S.N, S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
+        // x^{k+1} = prox(z): one tile per group, the dual field read from
+        // p[k & 1] and written to p[(k + 1) & 1]
+        const int g = tid / TV_THREADS, j = i * TV_GROUPS + g;
+        if (j < S.tv_ncb * S.tv_nrb) {
+            float2 *pub_x = reinterpret_cast<float2 *>(psm) + (size_t)g * 2 * (TV_ROWS + 2) * 32;
+            float2 *pub_y = pub_x + (TV_ROWS + 2) * 32;
+            const int bx = j % S.tv_ncb, by = j / S.tv_ncb;
+            const GroupCtx c{tid % TV_THREADS, TV_THREADS, 1 + ORB_GROUPS + DUAL_GROUPS + g};
+            if (S.fgp)
+                tv_body<true, false>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x, S.N,
+                                     S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
+            else
+                tv_body<false, false>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x, S.N,
+                                      S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
+        }
     } else if (p == PH_QUAD) {
         // band partial sums of A x^{k+1}
         const int nbp = S.N / (2 * MR), bx = i % nbp, by = i / nbp;
-        if (S.qrows4)
-            quad_body<4, false>(BlockCtx{}, bx, by, 0, nbp, psm, S.x, S.views, S.row_items, S.n_row_items,
-                                S.col_items, S.n_col_items, S.N, S.V, S.B, QUAD_PG, S.band);
-        else
-            quad_body<2, false>(BlockCtx{}, bx, by, 0, nbp, psm, S.x, S.views, S.row_items, S.n_row_items,
-                                S.col_items, S.n_col_items, S.N, S.V, S.B, QUAD_PG, S.band);
+        quad_body<2, false>(BlockCtx{}, bx, by, 0, nbp, psm, S.x, S.views, S.row_items, S.n_row_items, S.col_items,
+                            S.n_col_items, S.N, S.V, S.B, QUAD_PG, S.band);
     } else if (p == PH_DUAL) {
         // residual, Step 3 and the next Step 1 for one view pair per group
         const int g = tid / FFT_T, vp = i * DUAL_GROUPS + g;
@@ -279,17 +286,20 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.n_row_items = g->n_row_items;
             S.n_col_items = g->n_col_items;
             S.qgroups = (g->n_row_items + QUAD_PG - 1) / QUAD_PG + (g->n_col_items + QUAD_PG - 1) / QUAD_PG;
-            S.qrows4 = g->tune_qrows == 4;
+            S.qrows4 = 0;   // 1024 threads: two steps per pass
             S.nsl = orbit_slices(g);
             S.q16 = (g->n / 2 + ORB_T - 1) / ORB_T;
             S.orb_smem = (int)a16(orbit_smem_bytes());
             S.dual_smem = (int)a16(dual_fft_smem(g));
             S.ntv = prm.tv_iters > 0 ? prm.tv_iters : 10;
             S.fgp = prm.tv_accel == 1;
-            tv_tile_shape(g->n, S.ntv, g->n_sm, g->tune_tv, &S.tv_tc, &S.tv_tr, &S.tv_ncb, &S.tv_nrb);
+            // TV tiles: the batch's tiles together fill the GPU about twice
+            // (tiling does not change the prox's values)
+            tv_tile_shape(g->n, S.ntv, std::max(1, 2 * g->n_sm / m), g->tune_tv, &S.tv_tc, &S.tv_tr, &S.tv_ncb,
+                          &S.tv_nrb);
             S.n_items[PH_ORBIT] = (S.q16 * S.q16 * S.nsl + ORB_GROUPS - 1) / ORB_GROUPS;
             S.n_items[PH_OREDUCE] = S.nsl > 1 ? (int)(((size_t)g->n * g->n + RED_PIX - 1) / RED_PIX) : 0;
-            S.n_items[PH_TV] = S.tv_ncb * S.tv_nrb;
+            S.n_items[PH_TV] = (S.tv_ncb * S.tv_nrb + TV_GROUPS - 1) / TV_GROUPS;
             S.n_items[PH_QUAD] = (g->n / (2 * MR)) * S.qgroups;
             S.n_items[PH_DUAL] = ((g->n_views + 1) / 2 + DUAL_GROUPS - 1) / DUAL_GROUPS;
             S.per_iter = 0;
@@ -314,7 +324,7 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.band = sb.band;
             S.orb = sb.orb;
             S.scal = sb.scal;
-            const size_t tv_smem = sizeof(float2) * 2 * (TV_ROWS + 2) * 32;
+            const size_t tv_smem = sizeof(float2) * 2 * (TV_ROWS + 2) * 32 * TV_GROUPS;
             smem = std::max({smem, (size_t)ORB_GROUPS * S.orb_smem, tv_smem, quad_smem(g->n),
                              (size_t)DUAL_GROUPS * S.dual_smem});
             n_sm = std::max(n_sm, g->n_sm);

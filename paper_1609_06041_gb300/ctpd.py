@@ -376,8 +376,10 @@ class BatchedSolve:
 
     def __init__(self, slices, autotune=False):
         # slices: list of (Geometry, b, w or None, PDTVParams).  autotune:
-        # run ct_geometry_autotune once per distinct geometry first (not
-        # capturable; do it here, before any graph capture of run()).
+        # run ct_geometry_autotune once per distinct geometry first, then
+        # time the batched call's two forms (persistent launch, stream
+        # pool) once each and keep the faster for run() (not capturable; do
+        # it here, before any graph capture of run()).
         self.slices = list(slices)
         n = len(self.slices)
         if autotune:
@@ -400,11 +402,41 @@ class BatchedSolve:
         self._x = V(*[t.data_ptr() for t in self.x])
         self._ws = V(*[t.data_ptr() for t in self.ws])
         self.n = n
+        self.form = None          # None: the process-wide choice (ct_batched_options)
+        self.form_ms = {}
+        if autotune:
+            self._pick_form()
+
+    def _enqueue(self, rep=None):
+        _check(_lib.ct_pdtv_solve_batched(self.n, self._g, self._b, self._w, self._p, self._x, self._ws,
+                                          rep, _stream()))
+
+    def _pick_form(self):
+        """Time each form once after one warm-up call (CUDA events) and keep the faster."""
+        try:
+            for form in (CT_BATCH_AUTO, CT_BATCH_POOL):
+                ct_batched_options(form)
+                self._enqueue()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                self._enqueue()
+                e1.record()
+                torch.cuda.synchronize()
+                self.form_ms[form] = e0.elapsed_time(e1)
+        finally:
+            ct_batched_options(CT_BATCH_AUTO)
+        self.form = min(self.form_ms, key=self.form_ms.get)
 
     def run(self, reports=False):
         rep = (ct_pdtv_report * self.n)() if reports else None
-        _check(_lib.ct_pdtv_solve_batched(self.n, self._g, self._b, self._w, self._p, self._x, self._ws,
-                                          rep, _stream()))
+        if self.form is None:
+            self._enqueue(rep)
+        else:
+            try:
+                ct_batched_options(self.form)
+                self._enqueue(rep)
+            finally:
+                ct_batched_options(CT_BATCH_AUTO)
         return self.x, ([r.as_dict() for r in rep] if reports else None)
 
 

@@ -304,3 +304,40 @@ def test_unrolled_backward_is_deterministic_and_capturable(mode):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(xo, x0) and torch.equal(go, g0)
+
+
+def test_unrolled_with_one_and_two_orbit_slices():
+    # the orbit backprojector writes A^T y (forward: z = x - tau A^T mubar;
+    # backward: gz = gx - tau A^T gr) itself when the base views form one
+    # slice, and through the slice reduction with two: both give the same
+    # x_K and gradients to rounding, and the single-slice gradients match
+    # FP64 central differences of the oracle's loss
+    P = need_gpu()
+    import torch
+    N, V, B, S, K, ntv, half = 32, 40, 47, 2, 4, 5, 8
+    xt, bs, ws = make_batch(N, V, B, S, 13)
+    tau, taps = steps_for(V, B, bs, ws, half)
+    sigma, beta = 0.5, 0.03
+    g = P.Geometry(N, V, B)
+    out = {}
+    for nsl in (1, 2):
+        g.set_tuning(orbit_slices=nsl)
+        t = to_gpu(taps).requires_grad_(True)
+        bt = torch.tensor(beta, device="cuda", requires_grad=True)
+        x = P.UnrolledPDTV.apply(t, bt, g, to_gpu(bs), to_gpu(ws), tau, sigma, 0, K, ntv)
+        loss = ((x - to_gpu(xt)) ** 2).sum() / (S * N * N)
+        loss.backward()
+        out[nsl] = (to_np(x), to_np(t.grad), float(bt.grad))
+    x1, gt1, gb1 = out[1]
+    x2, gt2, gb2 = out[2]
+    assert rel_l2(x1, x2) <= 1e-5
+    assert rel_l2(gt1, gt2) <= 1e-4 and gb1 == pytest.approx(gb2, rel=1e-4)
+    hb = 1e-3 * beta
+    fd_b = (oracle_loss(bs, ws, xt, taps, beta + hb, tau, sigma, K, ntv, N) -
+            oracle_loss(bs, ws, xt, taps, beta - hb, tau, sigma, K, ntv, N)) / (2 * hb)
+    assert gb1 == pytest.approx(fd_b, rel=1e-4)
+    d = np.random.default_rng(5).standard_normal(taps.size)
+    eps = 1e-4 * np.abs(taps).max() / np.abs(d).max()
+    fd = (oracle_loss(bs, ws, xt, taps + eps * d, beta, tau, sigma, K, ntv, N) -
+          oracle_loss(bs, ws, xt, taps - eps * d, beta, tau, sigma, K, ntv, N)) / (2 * eps)
+    assert float(gt1 @ d) == pytest.approx(fd, rel=3e-3)
