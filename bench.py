@@ -760,6 +760,34 @@ def run_ncu_case(args):
     return 0
 
 
+def run_ncu_batched(args):
+    """A short fixed sequence for ncu captures of the persistent batched
+    launch: 8 slices (256^2 and 384^2, 32 and 90 views, both modes), 5
+    iterations each, one ct_pdtv_solve_batched call in the persistent form."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    import paper_1609_06041_gb300 as P
+    slices = []
+    for i, (n, v) in enumerate([(256, 32), (256, 90), (384, 32), (384, 90)] * 2):
+        g = P.Geometry(n, v, synth.bins_for(n))
+        x = synth.ellipse_phantom(n, 10, i)
+        mode = i % 2
+        p = P.ct_project(g, torch.from_numpy((x * ((2.0 / n) if mode == 0 else 1.0)).astype(np.float32)).cuda())
+        if mode == 0:
+            bb, ww = synth.poisson_data(p.cpu().numpy(), 1e4, i)
+            b = torch.from_numpy(bb.astype(np.float32)).cuda()
+            w = torch.from_numpy(ww.astype(np.float32)).cuda()
+        else:
+            b, w = p, None
+        slices.append((g, b, w, P.PDTVParams(mode=mode, iters=5, beta=0.005)))
+    P.ct_batched_options(P.CT_BATCH_AUTO)
+    xs, reps = P.ct_pdtv_solve_batched(slices)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "batched", "slices": len(slices), "k": [r["k"] for r in reps]}))
+    return 0
+
+
 def measure_eps(P, steps=5):
     """The error-tolerant few-view form (Sec. 5) against the equality form on
     the few-view slice (512^2, 32 views, 736 bins, the few-view smoothed
@@ -814,8 +842,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, differentiable and convergence measurements")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="run the short fixed launch sequence used for ncu captures")
+    ap.add_argument("--ncu-case", nargs="?", const="solve", default="", choices=["solve", "batched"],
+                    help="run a short fixed launch sequence for ncu captures: one solve of the bench workload "
+                         "(solve) or one persistent batched call of 8 small slices (batched)")
     ap.add_argument("--eager", action="store_true",
                     help="time eager ct_pdtv_solve calls instead of replaying one captured CUDA graph of the solve")
     ap.add_argument("--tuning", default="",
@@ -827,6 +856,8 @@ def main():
         os.environ["CTPD_SOLVE_GRAPHS"] = "0"   # read when the library first solves
     if args.form:
         return run_form(args)
+    if args.ncu_case == "batched":
+        return run_ncu_batched(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.impl == "reference":

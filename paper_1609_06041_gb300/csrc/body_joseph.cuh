@@ -35,10 +35,7 @@ __device__ __forceinline__ void step_range(float q, float m, float inv_m, float 
 }
 
 // Shared memory of the view-pair projector's block at image side N.
-__host__ __device__ __forceinline__ size_t quad_smem(int N)
-{
-    return sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
-}
+__host__ __device__ __forceinline__ size_t quad_smem(int N) { return sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1); }
 
 // ---------------------------------------------------------------------
 // Forward projection with the detector mirror and the view mirror (default
@@ -124,35 +121,33 @@ __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP
 }
 
 // Body of block (bx, by, bz) of a grid of nbp band pairs: smraw holds
-// quad_smem(N) bytes, the block's c.nth() = 64 pg threads.
+// quad_smem(N) bytes, the block's c.nth() = 64 pg threads.  The block
+// stages its band pair once and then walks gpb groups of pg view-pair
+// items of one class (rows or columns) one after the other, so that the
+// staging is spread over gpb groups.
 template <int ROWS, bool DEEP, class Ctx>
 __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, int nbp, unsigned char *smraw,
                                           const float *x, const ViewP *views, const int2 *row_items, int n_row,
-                                          const int2 *col_items, int n_col, int N, int V, int B, int pg,
+                                          const int2 *col_items, int n_col, int N, int V, int B, int pg, int gpb,
                                           float *partial)
 {
     const int CW = N + 3, SP = CW | 1;
     float4 *Q = reinterpret_cast<float4 *>(smraw);   // [step][pair]: band A pair, band B pair
-    ViewP *sv = reinterpret_cast<ViewP *>(Q + (size_t)MR * SP);
-    int2 *sit = reinterpret_cast<int2 *>(sv + PG);
 
     const int bp = bx;
-    const int row_groups = (n_row + pg - 1) / pg;
-    const bool rows = by < row_groups;
-    const int grp = rows ? by : by - row_groups;
+    const int row_groups = (n_row + pg - 1) / pg, col_groups = (n_col + pg - 1) / pg;
+    const int row_blocks = (row_groups + gpb - 1) / gpb;
+    const bool rows = by < row_blocks;
+    const int grp0 = (rows ? by : by - row_blocks) * gpb;
+    const int ngrp = min(gpb, (rows ? row_groups : col_groups) - grp0);
     const int2 *list = rows ? row_items : col_items;
     const int nl = rows ? n_row : n_col;
-    const int nv = min(pg, nl - grp * pg);
     const float *img = x + (size_t)bz * N * N;
     float *out = partial + ((size_t)bz * nbp + bp) * V * B;
     const int s0 = bp * MR;
     const float h = joseph_h(N), hq = joseph_hq(N);
     const int tid = c.tid(), nth = c.nth();
 
-    if (tid < nv) {
-        sit[tid] = list[grp * pg + tid];
-        sv[tid] = views[sit[tid].x];
-    }
     // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
     // the line N-1-s0-t read backwards (image value at N-1-i); one thread
     // forms both bands' pairs of (t, i) and stores them as one float4
@@ -252,9 +247,12 @@ __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, 
     const int npair = (B + 1) / 2;
     const unsigned top = (unsigned)(N + 2);
     const int vi = tid >> 6;
-    if (vi >= nv) return;
-    const int v = sit[vi].x, vp = sit[vi].y;
-    const float a = sv[vi].a, m = sv[vi].m, inv_m = sv[vi].inv_m;
+    for (int gi = 0; gi < ngrp; ++gi) {
+    const int grp = grp0 + gi;
+    if (vi >= min(pg, nl - grp * pg)) break;
+    const int2 it = list[grp * pg + vi];
+    const int v = it.x, vp = it.y;
+    const float a = views[v].a, m = views[v].m, inv_m = views[v].inv_m;
     for (int d = tid & 63; d < npair; d += 64) {
         const int dm = B - 1 - d;
         float ov[2] = {0.0f, 0.0f}, op[2] = {0.0f, 0.0f};   // view v / V-v: [0] ray d, [1] ray dm
@@ -293,6 +291,7 @@ __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, 
                 o2[dm] = op[1];
             }
         }
+    }
     }
 }
 

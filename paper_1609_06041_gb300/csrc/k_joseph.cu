@@ -298,30 +298,34 @@ template <int ROWS, bool DEEP>
 __global__ void __launch_bounds__(ROWS == 2 ? 1024 : 768)
 k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                const int2 *__restrict__ row_items, int n_row, const int2 *__restrict__ col_items, int n_col,
-               int N, int V, int B, int pg, float *__restrict__ partial)
+               int N, int V, int B, int pg, int gpb, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     quad_body<ROWS, DEEP>(whole_block(), blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, smraw, x, views, row_items,
-                          n_row, col_items, n_col, N, V, B, pg, partial);
+                          n_row, col_items, n_col, N, V, B, pg, gpb, partial);
 }
 
-// items per block of k_project_quad: the fewest waves of blocks (one block
-// per SM, shared memory) times the per-block work, staging counted as two items
-static int quad_pg(const Geometry *g, int batch, int max_pg)
+// Launch shape of k_project_quad: items per group (pg, 64 threads each) and
+// groups per block (gpb, walked one after the other on one staged band
+// pair), by the fewest waves of blocks (one block per SM, shared memory)
+// times the per-block work, staging counted as three items.  pg_fixed > 0
+// fixes pg (the tuner's choice) and picks gpb for it.
+static void quad_shape(const Geometry *g, int batch, int max_pg, int pg_fixed, int *pg_out, int *gpb_out)
 {
     const long bands = g->n / (2 * MR);
-    int best = max_pg;
     long best_cost = -1;
-    for (int pg = 4; pg <= max_pg; ++pg) {
-        const long groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
-        const long blocks = bands * groups * batch;
-        const long cost = ((blocks + g->n_sm - 1) / g->n_sm) * (pg + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = pg;
+    for (int pg = pg_fixed > 0 ? pg_fixed : 4; pg <= (pg_fixed > 0 ? pg_fixed : max_pg); ++pg) {
+        const long rg = (g->n_row_items + pg - 1) / pg, cg = (g->n_col_items + pg - 1) / pg;
+        for (int gpb = 1; gpb <= 8; ++gpb) {
+            const long blocks = bands * ((rg + gpb - 1) / gpb + (cg + gpb - 1) / gpb) * batch;
+            const long cost = ((blocks + g->n_sm - 1) / g->n_sm) * ((long)gpb * pg + 3);
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                *pg_out = pg;
+                *gpb_out = gpb;
+            }
         }
     }
-    return best;
 }
 
 void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st)
@@ -334,16 +338,18 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
         // view pairs and two mirrored 16-step bands per block: N/32 partial slots
         const int rows4 = g->tune_qrows == 4;
         const int max_pg = rows4 ? 12 : PG;
-        const int pg = g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : quad_pg(g, batch, max_pg);
-        const int groups = (g->n_row_items + pg - 1) / pg + (g->n_col_items + pg - 1) / pg;
-        const size_t smem2 = sizeof(float2) * (size_t)2 * MR * ((N + 3) | 1) + sizeof(ViewP) * PG + sizeof(int2) * PG;
-        const dim3 grd2(N / (2 * MR), groups, batch);
+        int pg = 0, gpb = 1;
+        quad_shape(g, batch, max_pg, g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : 0, &pg, &gpb);
+        const int rg = (g->n_row_items + pg - 1) / pg, cg = (g->n_col_items + pg - 1) / pg;
+        const int blocks_y = (rg + gpb - 1) / gpb + (cg + gpb - 1) / gpb;
+        const size_t smem2 = quad_smem(N);
+        const dim3 grd2(N / (2 * MR), blocks_y, batch);
         // few blocks (few views): each thread stages many pairs, so issue their loads four at a time
         const bool deep = (long)grd2.x * grd2.y * grd2.z < 2L * g->n_sm;
         auto kern = rows4 ? (deep ? k_project_quad<4, true> : k_project_quad<4, false>)
                           : (deep ? k_project_quad<2, true> : k_project_quad<2, false>);
         kern<<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items,
-                                           g->n_col_items, N, g->n_views, g->n_bins, pg, partial);
+                                           g->n_col_items, N, g->n_views, g->n_bins, pg, gpb, partial);
     } else if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // two mirrored 16-step bands per block: N/32 partial slots, as below
         dim3 grd2(N / (2 * MR), grd.y, batch);

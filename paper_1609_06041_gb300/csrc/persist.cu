@@ -147,7 +147,7 @@ __device__ __forceinline__ void run_item(const PSlice &S, int p, int k, int i, u
         // band partial sums of A x^{k+1}
         const int nbp = S.N / (2 * MR), bx = i % nbp, by = i / nbp;
         quad_body<2, false>(BlockCtx{}, bx, by, 0, nbp, psm, S.x, S.views, S.row_items, S.n_row_items, S.col_items,
-                            S.n_col_items, S.N, S.V, S.B, QUAD_PG, S.band);
+                            S.n_col_items, S.N, S.V, S.B, QUAD_PG, 1, S.band);
     } else if (p == PH_DUAL) {
         // residual, Step 3 and the next Step 1 for one view pair per group
         const int g = tid / FFT_T, vp = i * DUAL_GROUPS + g;
