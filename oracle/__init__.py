@@ -5,8 +5,9 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference leg are the only callers.  The product
 package never imports this module, and this module never imports the
 product.  The arithmetic lives in ``ct_oracle.c`` (plain C, double
-precision, single-threaded); this file compiles it with gcc on first use and
-wraps each routine for numpy arrays.
+precision; OpenMP over views / image rows where gcc has it, with every
+output element formed in the same order as on one thread); this file
+compiles it with gcc on first use and wraps each routine for numpy arrays.
 
 Parity status per routine (what pins it is in tests/test_oracle_*.py):
   project / backproject  -- pinned: hand sums at 0 and 90 degrees, constant
@@ -17,7 +18,11 @@ Parity status per routine (what pins it is in tests/test_oracle_*.py):
   grad / div / tv        -- pinned: adjoint identity, step-image TV.
   tv_prox                -- pinned: closed form on a two-level image,
                             duality-gap certificate, x >= 0 special case.
-  pdtv                   -- pinned: first iterate = FBP + TV prox, beta = 0
+  cost / residual        -- pinned: the 1/2 of Eq. 1 by the quadratic at the
+                            weighted least-squares minimiser (explicit A), the
+                            TV term by a step image, W = I against residual.
+  pdtv                   -- pinned: Step 1 equals the first form of Eq. 18 /
+                            Eq. 29 at k = 0..5, first iterate = FBP + TV prox, beta = 0
                             limit = weighted least squares (numpy solve),
                             injective few-view limit = x_true, limit equal to
                             the independent Chambolle-Pock reference.
