@@ -162,6 +162,44 @@ Layout layout(const Geometry *g, const ct_pdtv_params *prm)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
+// Ray stride of the view-pair projector's quarter warps for a view with
+// |a| = 1 / max(|cos t|, |sin t|).  The eight lanes of a quarter warp read
+// 16-byte entries at slots round(phi + a c j), j = 0..7; entries whose slots
+// agree mod 8 share a bank group and serialise.  The stride c in 1..16
+// with the fewest expected wavefronts over the offsets phi wins (c = 1, the
+// consecutive rays, unless another is better by more than 1 %).
+int quad_lane_stride(double a)
+{
+    auto cost = [a](int c) {
+        double tot = 0.0;
+        for (int t = 0; t < 64; ++t) {
+            const double phi = 8.0 * (t + 0.5) / 64.0;
+            long slot[8];
+            int group[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int j = 0; j < 8; ++j) slot[j] = (long)floor(phi + a * c * j + 0.5);
+            for (int j = 0; j < 8; ++j) {
+                bool dup = false;
+                for (int i = 0; i < j; ++i) dup = dup || slot[i] == slot[j];
+                if (!dup) ++group[slot[j] & 7];
+            }
+            int mx = 0;
+            for (int k = 0; k < 8; ++k) mx = std::max(mx, group[k]);
+            tot += mx;
+        }
+        return tot / 64.0;
+    };
+    int best = 1;
+    double bc = cost(1);
+    for (int c = 2; c <= 16; ++c) {
+        const double k = cost(c);
+        if (k < 0.99 * bc) {
+            bc = k;
+            best = c;
+        }
+    }
+    return best;
+}
+
 // Largest eigenvalue of the symmetric positive semi-definite operator `op`
 // (n-vectors) by k Lanczos steps from the all-ones vector, into scal[slot]:
 //   w = op(q_j) - beta_{j-1} q_{j-1};  alpha_j = <w, q_j>;  w -= alpha_j q_j;
@@ -442,6 +480,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
         P.inv_a = (float)(rows ? c : s);
         P.inv_m = P.m != 0.0f ? 1.0f / P.m : 0.0f;
         P.three = fabs((double)P.inv_a) >= 1.0 - 1.5 * (double)g->win_eps;
+        P.stride = quad_lane_stride(fabs((double)P.a));
         if (rows) rl[g->n_row++] = v;
         else cl[g->n_col++] = v;
         const double sc = 1.0 / fmax(fabs(c), fabs(s));

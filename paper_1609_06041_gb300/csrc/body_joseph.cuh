@@ -253,7 +253,17 @@ __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, 
     const int2 it = list[grp * pg + vi];
     const int v = it.x, vp = it.y;
     const float a = views[v].a, m = views[v].m, inv_m = views[v].inv_m;
-    for (int d = tid & 63; d < npair; d += 64) {
+    const int cs = views[v].stride, blk = 8 * cs;
+    for (int idx = tid & 63; idx < npair; idx += 64) {
+        // position idx -> ray pair d: in whole blocks of 8 cs positions the
+        // eight lanes of a quarter warp take rays cs apart, spreading their
+        // 16-byte loads over the bank groups; the last partial block maps
+        // to itself
+        int d = idx;
+        {
+            const int b = idx / blk, r = idx - b * blk;
+            if ((b + 1) * blk <= npair) d = b * blk + (r & 7) * cs + (r >> 3);
+        }
         const int dm = B - 1 - d;
         float ov[2] = {0.0f, 0.0f}, op[2] = {0.0f, 0.0f};   // view v / V-v: [0] ray d, [1] ray dm
 #pragma unroll

@@ -27,7 +27,7 @@ struct ViewP {
     float inv_m;   // 1/m (0 when m = 0), for the ray->step range
     int rows;      // 1: steps along rows; 0: along columns
     int three;     // 1: a pixel's candidate-ray window can hold three rays
-    int pad;
+    int stride;    // view-pair projector: rays of one quarter warp are `stride` apart (bank spread)
 };
 
 struct Geometry {
