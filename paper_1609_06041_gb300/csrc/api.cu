@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -163,12 +164,17 @@ Layout layout(const Geometry *g, const ct_pdtv_params *prm)
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 // Ray stride of the view-pair projector's quarter warps for a view with
-// |a| = 1 / max(|cos t|, |sin t|).  The eight lanes of a quarter warp read
-// 16-byte entries at slots round(phi + a c j), j = 0..7; entries whose slots
-// agree mod 8 share a bank group and serialise.  The stride c in 1..16
-// with the fewest expected wavefronts over the offsets phi wins (c = 1, the
-// consecutive rays, unless another is better by more than 1 %).
-int quad_lane_stride(double a)
+// |a| = 1 / max(|cos t|, |sin t|) and npair ray pairs.  The eight lanes of
+// a quarter warp read 16-byte entries at slots round(phi + a c j),
+// j = 0..7; entries whose slots agree mod 8 share a bank group and
+// serialise.  Rays are assigned in whole blocks of 8 c positions (the
+// positions past the last whole block keep stride 1), so the expected
+// wavefronts over the offsets phi are weighted by the share of positions
+// in whole blocks; the stride c in 1..16 with the fewest wins (c = 1, the
+// consecutive rays, unless another is better by more than 1 %).  Larger
+// strides simulate better but measured slower (their partial-sum stores
+// spread over more sectors).
+int quad_lane_stride(double a, int npair)
 {
     auto cost = [a](int c) {
         double tot = 0.0;
@@ -188,10 +194,12 @@ int quad_lane_stride(double a)
         }
         return tot / 64.0;
     };
+    const double c1 = cost(1);
     int best = 1;
-    double bc = cost(1);
-    for (int c = 2; c <= 16; ++c) {
-        const double k = cost(c);
+    double bc = c1;
+    for (int c = 2; c <= 16 && 8 * c <= npair; ++c) {
+        const int full = npair / (8 * c) * (8 * c);
+        const double k = ((double)full * cost(c) + (double)(npair - full) * c1) / npair;
         if (k < 0.99 * bc) {
             bc = k;
             best = c;
@@ -455,6 +463,7 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
     g->win_eps = (float)(16.0 * (n + n_bins) * ldexp(1.0, -24) + ldexp(1.0, -13));
     ViewP *hv = new ViewP[n_views];
     float4 *ht = new float4[n_views];
+    std::map<float, int> stride_of;
     int *rl = new int[n_views], *cl = new int[n_views];
     g->n_row = g->n_col = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -480,7 +489,13 @@ ct_status ct_geometry_create(int n, int n_views, int n_bins, const double *angle
         P.inv_a = (float)(rows ? c : s);
         P.inv_m = P.m != 0.0f ? 1.0f / P.m : 0.0f;
         P.three = fabs((double)P.inv_a) >= 1.0 - 1.5 * (double)g->win_eps;
-        P.stride = quad_lane_stride(fabs((double)P.a));
+        {
+            // views v, V - v, V/2 +- v share |a|: one search per value
+            const float key = P.scale;
+            auto it = stride_of.find(key);
+            if (it == stride_of.end()) it = stride_of.emplace(key, quad_lane_stride(key, (n_bins + 1) / 2)).first;
+            P.stride = it->second;
+        }
         if (rows) rl[g->n_row++] = v;
         else cl[g->n_col++] = v;
         const double sc = 1.0 / fmax(fabs(c), fabs(s));
