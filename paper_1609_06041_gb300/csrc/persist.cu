@@ -329,12 +329,6 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
                              (size_t)DUAL_GROUPS * S.dual_smem});
             n_sm = std::max(n_sm, g->n_sm);
         }
-        // within a phase the smallest slices come first: their items are
-        // short, so by the time a block takes a slice's next phase its
-        // previous phase is more likely complete
-        std::stable_sort(pp.sl, pp.sl + m, [](const PSlice &A, const PSlice &C) {
-            return (double)A.V * A.N * A.N < (double)C.V * C.N * C.N;
-        });
         // queue order: iteration, phase, slice, item
         pp.R = 0;
         for (int q = 0; q < PH_N; ++q) {
