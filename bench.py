@@ -45,8 +45,10 @@ SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory by
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from one ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); update together with the kernels, None when no
-# capture of the current kernel exists
-TRAFFIC_BYTES = {"A": 1.098240e6, "AT": 2.022912e6}
+# capture of the current kernel exists.  A: k_project_qbal<2> (the
+# work-balanced projector, 16 items' threads per block); AT:
+# k_backproject_orbit<true>.
+TRAFFIC_BYTES = {"A": 1.179904e6, "AT": 2.022912e6}
 
 
 def dist_info():
@@ -543,8 +545,8 @@ def run_ours(args):
     g = P.Geometry(N, V, B)
     if args.tuning:
         # fixed launch shapes (for profiler runs, whose timing would mislead the tuner)
-        ip, pr, osl, tvr = (int(t) for t in args.tuning.split(","))
-        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr)
+        ip, pr, osl, tvr, *pf = (int(t) for t in args.tuning.split(","))
+        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr, proj_form=pf[0] if pf else 0)
         tuning = {**g.tuning, "source": "fixed"}
     else:
         tuning = {**g.autotune(), "source": "autotune"}   # by measurement, once per geometry, untimed
@@ -641,8 +643,9 @@ def run_ours(args):
     # dominant operator: the slower of A (ct_project: band kernel + reduction)
     # and A^T (ct_backproject: orbit kernel + slice reduction); both carry
     # 2 nnz(A) algorithmic flops
+    a_kernel = "k_project_qbal" if g.tuning.get("proj_form") == 2 else "k_project_quad"
     dom_name, dom_ms, dom_key = ("ct_backproject (A^T, k_backproject_orbit + k_orbit_reduce)", at_ms, "AT") \
-        if at_ms >= a_ms else ("ct_project (A, k_project_quad + k_band_reduce)", a_ms, "A")
+        if at_ms >= a_ms else (f"ct_project (A, {a_kernel} + k_band_reduce)", a_ms, "A")
     achieved = flops / (dom_ms / 1e3) / 1e12
 
     # ---- end to end through the public API with host buffers ----
@@ -743,8 +746,8 @@ def run_ncu_case(args):
     if args.tuning:
         # fixed launch shapes (items_per_block, proj_rows, orbit_slices, tv_rows),
         # so the captured launches are not the tuner's trial launches
-        ip, pr, osl, tvr = (int(t) for t in args.tuning.split(","))
-        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr)
+        ip, pr, osl, tvr, *pf = (int(t) for t in args.tuning.split(","))
+        g.set_tuning(items_per_block=ip, proj_rows=pr, orbit_slices=osl, tv_rows=tvr, proj_form=pf[0] if pf else 0)
     else:
         g.autotune()
     xt = torch.from_numpy(phantom(0).astype(np.float32)).cuda()
@@ -848,7 +851,7 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="time eager ct_pdtv_solve calls instead of replaying one captured CUDA graph of the solve")
     ap.add_argument("--tuning", default="",
-                    help="fixed launch shapes 'items,rows,orbit_slices,tv_rows' instead of the autotuner")
+                    help="fixed launch shapes 'items,rows,orbit_slices,tv_rows[,proj_form]' instead of the autotuner")
     ap.add_argument("--form", default="", choices=["", "batched", "differentiable", "fewview_cp", "convergence", "eps"],
                     help="run only this form's measurement")
     args = ap.parse_args()

@@ -100,7 +100,7 @@ void ct_geometry_destroy(ct_geometry *geom);
 /*
  * Launch-shape tuning (no counterpart in the paper: it picks how the work of
  * A, A^T and the TV prox of Eq. 17 is cut into thread blocks, never what is
- * computed).  Four shapes are held by the geometry:
+ * computed).  Five shapes are held by the geometry:
  *   items_per_block  view pairs (v, V-v) sharing one staged band pair in the
  *                    projector, 64 threads each (4..16; 4..12 when
  *                    proj_rows is 4);
@@ -109,9 +109,19 @@ void ct_geometry_destroy(ct_geometry *geom);
  *   orbit_slices     base-view slices of the rotation-orbit backprojector,
  *                    one partial image each (1..8, at most 1024 base views
  *                    per slice);
- *   tv_rows          fewest interior rows of a TV prox tile (4..64).
+ *   tv_rows          fewest interior rows of a TV prox tile (4..64);
+ *   proj_form        how the projector's work is cut into blocks (1 or 2):
+ *                    1, each block stages one band pair and walks a few
+ *                    groups of items_per_block items on it, the grid sized
+ *                    by a wave-count model; 2, the work is cut into units
+ *                    (band pair, item, 64 rays) and each block, with
+ *                    64 x items_per_block threads, takes an equal range of
+ *                    them, as many blocks as fit on the device at once,
+ *                    its warps taking the units of each staged band pair
+ *                    from a shared counter.  Both give the same sums.
  * 0 selects the built-in rule (a wave-count model for items_per_block, 2
- * steps per pass, 4 slices, 16 rows).  A shape changes the order in which independent
+ * steps per pass, 4 slices, 16 rows; form 2 with 16 items' threads when
+ * form 1 would need two waves of blocks or more, else form 1).  A shape changes the order in which independent
  * partial sums are added, so results can differ in the last float bits
  * between shapes; for one shape they are deterministic.
  *
@@ -127,9 +137,9 @@ void ct_geometry_destroy(ct_geometry *geom);
  */
 ct_status ct_geometry_autotune(ct_geometry *geom, int batch, void *stream);
 ct_status ct_geometry_set_tuning(ct_geometry *geom, int items_per_block, int proj_rows, int orbit_slices,
-                                 int tv_rows);
+                                 int tv_rows, int proj_form);
 ct_status ct_geometry_get_tuning(const ct_geometry *geom, int *items_per_block, int *proj_rows,
-                                 int *orbit_slices, int *tv_rows);
+                                 int *orbit_slices, int *tv_rows, int *proj_form);
 
 /*
  * Forward projection sino = A img (A of Eq. 1; Joseph interpolation).

@@ -1,12 +1,14 @@
 // autotune.cu -- ct_geometry_autotune / ct_geometry_get_tuning /
 // ct_geometry_set_tuning: launch shapes per geometry picked by measurement.
 //
-// Four shapes are tuned, each by timing every candidate on synthetic data
+// Five shapes are tuned, each by timing every candidate on synthetic data
 // of the geometry's size with CUDA events (one warm-up launch, then the mean
 // of three):
 //   - the projector's view items per block (k_project_quad: 64 threads per
 //     view pair, pg pairs share one staged band pair), pg = 4 .. 16, jointly
-//     with its steps per pass of a ray walk (2, or 4 with pg <= 12);
+//     with its steps per pass of a ray walk (2, or 4 with pg <= 12) and its
+//     form (one band pair per block, or the work-balanced k_project_qbal
+//     with 8, 12 or 16 items' threads per block);
 //   - the backprojector's base-view slices (k_backproject_orbit: grid.z,
 //     one partial image per slice), 1, 2, 4 or 8;
 //   - the TV prox's fewest interior rows per tile (k_tv), 4 .. 64, which
@@ -55,7 +57,7 @@ bool quad_path(const Geometry *g) { return g->vpair && g->n % 32 == 0 && g->n + 
 }  // namespace
 
 extern "C" ct_status ct_geometry_get_tuning(const ct_geometry *g, int *items_per_block, int *proj_rows,
-                                            int *orbit_slices, int *tv_rows)
+                                            int *orbit_slices, int *tv_rows, int *proj_form)
 {
     if (!g) {
         set_error("ct_geometry_get_tuning: NULL geometry");
@@ -65,11 +67,12 @@ extern "C" ct_status ct_geometry_get_tuning(const ct_geometry *g, int *items_per
     if (proj_rows) *proj_rows = g->tune_qrows;
     if (orbit_slices) *orbit_slices = g->tune_orb;
     if (tv_rows) *tv_rows = g->tune_tv;
+    if (proj_form) *proj_form = g->tune_qbal;
     return CT_OK;
 }
 
 extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block, int proj_rows, int orbit_slices,
-                                            int tv_rows)
+                                            int tv_rows, int proj_form)
 {
     if (!g) {
         set_error("ct_geometry_set_tuning: NULL geometry");
@@ -92,10 +95,15 @@ extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block,
         set_error("ct_geometry_set_tuning: tv_rows must be 0 or in [4, 64]");
         return CT_ERR_ARG;
     }
+    if (proj_form < 0 || proj_form > 2) {
+        set_error("ct_geometry_set_tuning: proj_form must be 0, 1 or 2");
+        return CT_ERR_ARG;
+    }
     g->tune_pg = items_per_block;
     g->tune_qrows = proj_rows;
     g->tune_orb = orbit_slices;
     g->tune_tv = tv_rows;
+    g->tune_qbal = proj_form;
     graph_cache_clear(g);
     return CT_OK;
 }
@@ -111,6 +119,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     const int N = g->n;
     const size_t J = (size_t)N * N, I = (size_t)g->n_views * g->n_bins;
     const int old_pg = g->tune_pg, old_rows = g->tune_qrows, old_orb = g->tune_orb, old_tv = g->tune_tv;
+    const int old_qbal = g->tune_qbal;
     Buffers buf;
     float *x = nullptr, *sino = nullptr, *band = nullptr, *orb = nullptr, *img = nullptr, *tvb = nullptr;
     float *scalf = nullptr;
@@ -145,22 +154,28 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     float t;
     if (quad_path(g)) {
         float best = -1.0f;
-        int best_pg = 0, best_rows = 0;
-        for (int rows = 2; rows <= 4 && result == CT_OK; rows += 2) {
-            for (int pg = 4; pg <= (rows == 4 ? 12 : 16) && result == CT_OK; ++pg) {
-                g->tune_pg = pg;
-                g->tune_qrows = rows;
-                t = time_launches([&] { launch_project_bands(g, x, band, batch, st); }, st, e0, e1);
-                if (t < 0.0f) result = CT_ERR_CUDA;
-                else if (best < 0.0f || t < best) {
-                    best = t;
-                    best_pg = pg;
-                    best_rows = rows;
+        int best_pg = 0, best_rows = 0, best_form = 1;
+        for (int form = 1; form <= 2 && result == CT_OK; ++form) {
+            for (int rows = 2; rows <= 4 && result == CT_OK; rows += 2) {
+                for (int pg = form == 1 ? 4 : 8; pg <= (rows == 4 ? 12 : 16) && result == CT_OK;
+                     pg += form == 1 ? 1 : 4) {
+                    g->tune_pg = pg;
+                    g->tune_qrows = rows;
+                    g->tune_qbal = form;
+                    t = time_launches([&] { launch_project_bands(g, x, band, batch, st); }, st, e0, e1);
+                    if (t < 0.0f) result = CT_ERR_CUDA;
+                    else if (best < 0.0f || t < best) {
+                        best = t;
+                        best_pg = pg;
+                        best_rows = rows;
+                        best_form = form;
+                    }
                 }
             }
         }
         g->tune_pg = best_pg;
         g->tune_qrows = best_rows;
+        g->tune_qbal = best_form;
     }
     if (result == CT_OK && orbit_ok(g)) {
         float best = -1.0f;
@@ -202,6 +217,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
         g->tune_qrows = old_rows;
         g->tune_orb = old_orb;
         g->tune_tv = old_tv;
+        g->tune_qbal = old_qbal;
         cudaError_t le = cudaGetLastError();
         set_error("ct_geometry_autotune: %s", cudaGetErrorString(le));
         return result;

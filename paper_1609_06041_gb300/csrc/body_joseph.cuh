@@ -25,7 +25,8 @@ __device__ __forceinline__ void step_range(float q, float m, float inv_m, float 
         hi = (q >= ulo && q <= uhi) ? s_hi : s_lo - 1;
         return;
     }
-    float sa = (ulo - q) * inv_m + h, sb = (uhi - q) * inv_m + h;
+    // explicit roundings: every kernel that walks a ray finds the same range
+    float sa = __fmaf_rn(__fsub_rn(ulo, q), inv_m, h), sb = __fmaf_rn(__fsub_rn(uhi, q), inv_m, h);
     float smin = fminf(sa, sb), smax = fmaxf(sa, sb);
     // clamp before converting: far-off rays give huge (or infinite) s
     smin = fminf(fmaxf(smin, (float)s_lo - 2.0f), (float)s_hi + 2.0f);
@@ -120,6 +121,162 @@ __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP
     return make_float4(ab[0].x, ab[0].y, ce[0].x, ce[0].y);
 }
 
+// Stages band pair s0 of image img into Q: pair i (stored at i + 2) of step
+// t holds (A mid, B mid, A delta, B delta), band A the image line s0 + t
+// and band B the line N-1-s0-t read backwards (image value at N-1-i); the
+// lines are image rows (rows) or columns.  Runs on the threads of c and
+// ends without a barrier.
+template <bool DEEP, class Ctx>
+__device__ __forceinline__ void quad_stage(const Ctx &c, float4 *Q, const float *img, int N, int s0, bool rows)
+{
+    static_assert(MR == 16, "column staging: a warp's lanes take the 16 steps of two pairs");
+    const int CW = N + 3, SP = CW | 1;
+    const int tid = c.tid(), nth = c.nth();
+    // one thread forms both bands' pairs of (t, i) and stores them as one float4
+    const int lx = tid & 31, nw = nth >> 5;
+    if constexpr (DEEP) {
+        // each thread issues the loads of SU pairs before it stores any, so
+        // that SU L2 round trips overlap (grids of few blocks, whose threads
+        // each stage many pairs)
+        constexpr int SU = 4;
+        float a0[SU], a1[SU], b0[SU], b1[SU];
+        if (rows) {
+            const int nch = (CW + 31) >> 5, nc = MR * nch;
+            for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int ch = c0 + u * nw;
+                    const int t = ch / nch, ii = ((ch - t * nch) << 5) + lx;
+                    const bool ok = ch < nc && ii < CW;
+                    const int i = ii - 2;
+                    const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
+                    a0[u] = (ok && i >= 0 && i < N) ? ra[i] : 0.0f;
+                    a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
+                    b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
+                    b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int ch = c0 + u * nw;
+                    const int t = ch / nch, ii = ((ch - t * nch) << 5) + lx;
+                    if (ch < nc && ii < CW)
+                        Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]), a1[u] - a0[u],
+                                                     b1[u] - b0[u]);
+                }
+            }
+        } else {
+            const int t = lx & 15;
+            const float *ia = img + (s0 + t), *ib = img + (N - 1 - s0 - t);   // columns of bands A, B
+            const int nc = (CW + 1) >> 1;
+            for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int ii = 2 * (c0 + u * nw) + (lx >> 4);
+                    const bool ok = c0 + u * nw < nc && ii < CW;
+                    const int i = ii - 2;   // rows i, i + 1 (band A), N-1-i, N-2-i (band B); N N < 2^31
+                    a0[u] = (ok && i >= 0 && i < N) ? ia[i * N] : 0.0f;
+                    a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ia[(i + 1) * N] : 0.0f;
+                    b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? ib[(N - 1 - i) * N] : 0.0f;
+                    b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? ib[(N - 2 - i) * N] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int ii = 2 * (c0 + u * nw) + (lx >> 4);
+                    if (c0 + u * nw < nc && ii < CW)
+                        Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]), a1[u] - a0[u],
+                                                     b1[u] - b0[u]);
+                }
+            }
+        }
+    } else if (rows) {
+        // warps take 32-pair chunks of the 16 steps, lanes neighbouring pairs
+        const int nch = (CW + 31) >> 5;
+        for (int ch = tid >> 5; ch < MR * nch; ch += nw) {
+            const int t = ch / nch, ii = ((ch - t * nch) << 5) + lx;
+            if (ii < CW) {
+                const int i = ii - 2;
+                const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
+                const float a0 = (i >= 0 && i < N) ? ra[i] : 0.0f;
+                const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
+                const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
+                const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
+                Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
+            }
+        }
+    } else {
+        // lanes take the 16 steps (columns) of two neighbouring pairs:
+        // 64-byte row segments in, conflict-free float4 stores (odd SP)
+        const int t = lx & 15, ca = s0 + t, cb = N - 1 - s0 - t;
+        for (int ch = tid >> 5; 2 * ch < CW; ch += nw) {
+            const int ii = 2 * ch + (lx >> 4);
+            if (ii < CW) {
+                const int i = ii - 2;
+                const float a0 = (i >= 0 && i < N) ? img[(size_t)i * N + ca] : 0.0f;
+                const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
+                const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
+                const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
+                Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
+            }
+        }
+    }
+}
+
+// Walks ray position idx of view-pair item (v, vp) through the staged band
+// pair (steps s0 .. s0 + MR - 1) and stores its band sums into the partial
+// slot out (V x B): ray d and its detector mirror B-1-d of view v and, for
+// vp >= 0, of view vp.  Positions map to rays in whole blocks of 8 cs
+// positions, where the eight lanes of a quarter warp take rays cs apart,
+// spreading their 16-byte loads over the bank groups; the last partial
+// block maps to itself.
+template <int ROWS>
+__device__ __forceinline__ void quad_position(const float4 *Q, int SP, float a, float m, float inv_m, int cs, int v,
+                                              int vp, bool rows, int idx, int npair, int N, int B, int s0, float h,
+                                              float hq, unsigned top, float *out)
+{
+    int d = idx;
+    {
+        const int blk = 8 * cs, b = idx / blk, r = idx - b * blk;
+        if ((b + 1) * blk <= npair) d = b * blk + (r & 7) * cs + (r >> 3);
+    }
+    const int dm = B - 1 - d;
+    float ov[2] = {0.0f, 0.0f}, op[2] = {0.0f, 0.0f};   // view v / vp: [0] ray d, [1] ray dm
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+        if (which == 1 && dm == d) break;
+        const int dd = which == 0 ? d : dm;
+        const float q = joseph_q(joseph_dp(dd, B), a, hq);
+        int lo, hi;
+        step_range(q, m, inv_m, h, -2.5f, (float)N + 0.5f, s0, s0 + MR - 1, lo, hi);
+        const float4 r = vp >= 0 ? quad_walk<true, ROWS>(Q, SP, q, m, lo, hi, s0, h, top)
+                                 : quad_walk<false, ROWS>(Q, SP, q, m, lo, hi, s0, h, top);
+        ov[which] += r.x;
+        ov[1 - which] += r.y;
+        if (rows) {
+            op[which] += r.z;
+            op[1 - which] += r.w;
+        } else {
+            op[1 - which] += r.z;
+            op[which] += r.w;
+        }
+    }
+    float *o = out + (size_t)v * B;
+    if (dm == d) {
+        o[d] = ov[0] + ov[1];
+    } else {
+        o[d] = ov[0];
+        o[dm] = ov[1];
+    }
+    if (vp >= 0) {
+        float *o2 = out + (size_t)vp * B;
+        if (dm == d) {
+            o2[d] = op[0] + op[1];
+        } else {
+            o2[d] = op[0];
+            o2[dm] = op[1];
+        }
+    }
+}
+
 // Body of block (bx, by, bz) of a grid of nbp band pairs: smraw holds
 // quad_smem(N) bytes, the block's c.nth() = 64 pg threads.  The block
 // stages its band pair once and then walks gpb groups of pg view-pair
@@ -131,7 +288,7 @@ __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, 
                                           const int2 *col_items, int n_col, int N, int V, int B, int pg, int gpb,
                                           float *partial)
 {
-    const int CW = N + 3, SP = CW | 1;
+    const int SP = (N + 3) | 1;
     float4 *Q = reinterpret_cast<float4 *>(smraw);   // [step][pair]: band A pair, band B pair
 
     const int bp = bx;
@@ -142,166 +299,93 @@ __device__ __forceinline__ void quad_body(const Ctx &c, int bx, int by, int bz, 
     const int ngrp = min(gpb, (rows ? row_groups : col_groups) - grp0);
     const int2 *list = rows ? row_items : col_items;
     const int nl = rows ? n_row : n_col;
-    const float *img = x + (size_t)bz * N * N;
     float *out = partial + ((size_t)bz * nbp + bp) * V * B;
     const int s0 = bp * MR;
     const float h = joseph_h(N), hq = joseph_hq(N);
-    const int tid = c.tid(), nth = c.nth();
+    const int tid = c.tid();
 
-    // pair i (stored at i + 2) of step t: band A the image line s0 + t, band B
-    // the line N-1-s0-t read backwards (image value at N-1-i); one thread
-    // forms both bands' pairs of (t, i) and stores them as one float4
-    if constexpr (DEEP) {
-        // the same pairs, each thread issuing the loads of SU of them before
-        // it stores any, so that SU L2 round trips overlap
-        {
-            constexpr int SU = 4;
-            const int lx = tid & 31, nw = nth >> 5;
-            float a0[SU], a1[SU], b0[SU], b1[SU];
-            if (rows) {
-                const int nch = (CW + 31) >> 5, nc = MR * nch;
-                for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
-    #pragma unroll
-                    for (int u = 0; u < SU; ++u) {
-                        const int c = c0 + u * nw;
-                        const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
-                        const bool ok = c < nc && ii < CW;
-                        const int i = ii - 2;
-                        const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
-                        a0[u] = (ok && i >= 0 && i < N) ? ra[i] : 0.0f;
-                        a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
-                        b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
-                        b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
-                    }
-    #pragma unroll
-                    for (int u = 0; u < SU; ++u) {
-                        const int c = c0 + u * nw;
-                        const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
-                        if (c < nc && ii < CW)
-                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]),
-                                                         a1[u] - a0[u], b1[u] - b0[u]);
-                    }
-                }
-            } else {
-                const int t = lx & 15;
-                const float *ia = img + (s0 + t), *ib = img + (N - 1 - s0 - t);   // columns of bands A, B
-                const int nc = (CW + 1) >> 1;
-                for (int c0 = tid >> 5; c0 < nc; c0 += SU * nw) {
-    #pragma unroll
-                    for (int u = 0; u < SU; ++u) {
-                        const int ii = 2 * (c0 + u * nw) + (lx >> 4);
-                        const bool ok = c0 + u * nw < nc && ii < CW;
-                        const int i = ii - 2;   // rows i, i + 1 (band A), N-1-i, N-2-i (band B); N N < 2^31
-                        a0[u] = (ok && i >= 0 && i < N) ? ia[i * N] : 0.0f;
-                        a1[u] = (ok && i + 1 >= 0 && i + 1 < N) ? ia[(i + 1) * N] : 0.0f;
-                        b0[u] = (ok && N - 1 - i >= 0 && N - 1 - i < N) ? ib[(N - 1 - i) * N] : 0.0f;
-                        b1[u] = (ok && N - 2 - i >= 0 && N - 2 - i < N) ? ib[(N - 2 - i) * N] : 0.0f;
-                    }
-    #pragma unroll
-                    for (int u = 0; u < SU; ++u) {
-                        const int ii = 2 * (c0 + u * nw) + (lx >> 4);
-                        if (c0 + u * nw < nc && ii < CW)
-                            Q[t * SP + ii] = make_float4(0.5f * (a0[u] + a1[u]), 0.5f * (b0[u] + b1[u]),
-                                                         a1[u] - a0[u], b1[u] - b0[u]);
-                    }
-                }
-            }
-        }
-    } else {
-        {
-            const int lx = tid & 31, nw = nth >> 5;
-            if (rows) {
-                // warps take 32-pair chunks of the 16 steps, lanes neighbouring pairs
-                const int nch = (CW + 31) >> 5;
-                for (int c = tid >> 5; c < MR * nch; c += nw) {
-                    const int t = c / nch, ii = ((c - t * nch) << 5) + lx;
-                    if (ii < CW) {
-                        const int i = ii - 2;
-                        const float *ra = img + (size_t)(s0 + t) * N, *rb = img + (size_t)(N - 1 - s0 - t) * N;
-                        const float a0 = (i >= 0 && i < N) ? ra[i] : 0.0f;
-                        const float a1 = (i + 1 >= 0 && i + 1 < N) ? ra[i + 1] : 0.0f;
-                        const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? rb[N - 1 - i] : 0.0f;
-                        const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? rb[N - 2 - i] : 0.0f;
-                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
-                    }
-                }
-            } else {
-                // lanes take the 16 steps (columns) of two neighbouring pairs:
-                // 64-byte row segments in, conflict-free float4 stores (odd SP)
-                const int t = lx & 15, ca = s0 + t, cb = N - 1 - s0 - t;
-                for (int c = tid >> 5; 2 * c < CW; c += nw) {
-                    const int ii = 2 * c + (lx >> 4);
-                    if (ii < CW) {
-                        const int i = ii - 2;
-                        const float a0 = (i >= 0 && i < N) ? img[(size_t)i * N + ca] : 0.0f;
-                        const float a1 = (i + 1 >= 0 && i + 1 < N) ? img[(size_t)(i + 1) * N + ca] : 0.0f;
-                        const float b0 = (N - 1 - i >= 0 && N - 1 - i < N) ? img[(size_t)(N - 1 - i) * N + cb] : 0.0f;
-                        const float b1 = (N - 2 - i >= 0 && N - 2 - i < N) ? img[(size_t)(N - 2 - i) * N + cb] : 0.0f;
-                        Q[(size_t)t * SP + ii] = make_float4(0.5f * (a0 + a1), 0.5f * (b0 + b1), a1 - a0, b1 - b0);
-                    }
-                }
-            }
-        }
-    }
+    quad_stage<DEEP>(c, Q, x + (size_t)bz * N * N, N, s0, rows);
     c.sync();
     const int npair = (B + 1) / 2;
     const unsigned top = (unsigned)(N + 2);
     const int vi = tid >> 6;
     for (int gi = 0; gi < ngrp; ++gi) {
-    const int grp = grp0 + gi;
-    if (vi >= min(pg, nl - grp * pg)) break;
-    const int2 it = list[grp * pg + vi];
-    const int v = it.x, vp = it.y;
-    const float a = views[v].a, m = views[v].m, inv_m = views[v].inv_m;
-    const int cs = views[v].stride, blk = 8 * cs;
-    for (int idx = tid & 63; idx < npair; idx += 64) {
-        // position idx -> ray pair d: in whole blocks of 8 cs positions the
-        // eight lanes of a quarter warp take rays cs apart, spreading their
-        // 16-byte loads over the bank groups; the last partial block maps
-        // to itself
-        int d = idx;
-        {
-            const int b = idx / blk, r = idx - b * blk;
-            if ((b + 1) * blk <= npair) d = b * blk + (r & 7) * cs + (r >> 3);
-        }
-        const int dm = B - 1 - d;
-        float ov[2] = {0.0f, 0.0f}, op[2] = {0.0f, 0.0f};   // view v / V-v: [0] ray d, [1] ray dm
-#pragma unroll
-        for (int which = 0; which < 2; ++which) {
-            if (which == 1 && dm == d) break;
-            const int dd = which == 0 ? d : dm;
-            const float q = joseph_q(joseph_dp(dd, B), a, hq);
-            int lo, hi;
-            step_range(q, m, inv_m, h, -2.5f, (float)N + 0.5f, s0, s0 + MR - 1, lo, hi);
-            const float4 r = vp >= 0 ? quad_walk<true, ROWS>(Q, SP, q, m, lo, hi, s0, h, top)
-                                     : quad_walk<false, ROWS>(Q, SP, q, m, lo, hi, s0, h, top);
-            ov[which] += r.x;
-            ov[1 - which] += r.y;
-            if (rows) {
-                op[which] += r.z;
-                op[1 - which] += r.w;
-            } else {
-                op[1 - which] += r.z;
-                op[which] += r.w;
-            }
-        }
-        float *o = out + (size_t)v * B;
-        if (dm == d) {
-            o[d] = ov[0] + ov[1];
-        } else {
-            o[d] = ov[0];
-            o[dm] = ov[1];
-        }
-        if (vp >= 0) {
-            float *o2 = out + (size_t)vp * B;
-            if (dm == d) {
-                o2[d] = op[0] + op[1];
-            } else {
-                o2[d] = op[0];
-                o2[dm] = op[1];
-            }
-        }
+        const int grp = grp0 + gi;
+        if (vi >= min(pg, nl - grp * pg)) break;
+        const int2 it = list[grp * pg + vi];
+        const ViewP &vw = views[it.x];
+        const float a = vw.a, m = vw.m, inv_m = vw.inv_m;
+        const int cs = vw.stride;
+        for (int idx = tid & 63; idx < npair; idx += 64)
+            quad_position<ROWS>(Q, SP, a, m, inv_m, cs, it.x, it.y, rows, idx, npair, N, B, s0, h, hq, top, out);
     }
+}
+
+// Work-balanced form of the same projection.  The work of a batch is cut
+// into units (slice, class, band pair, item, chunk of 64 ray positions),
+// ordered so that the units of one staged band pair (a segment) are
+// consecutive; each block takes the equal range [u0, u1) of units, stages
+// each segment the range touches once, and its warps take the segment's
+// units one at a time from a shared counter.  Blocks thus carry equal work
+// whatever the number of items, and a block holds as many warps as its
+// registers allow.  The sums are those of quad_body, unit for unit.
+struct QuadUnits {
+    int nch;        // 64-position chunks per item
+    int u_rows;     // units of one row-class segment: n_row items x nch
+    int u_cols;     // units of one column-class segment
+    long long u_z;  // units per slice: nbp (u_rows + u_cols)
+};
+
+template <int ROWS, bool DEEP, class Ctx>
+__device__ __forceinline__ void quad_balanced_body(const Ctx &c, long long u0, long long u1, const QuadUnits &U,
+                                                   unsigned char *smraw, int *next, const float *x,
+                                                   const ViewP *views, const int2 *row_items,
+                                                   const int2 *col_items, int N, int V, int B, float *partial)
+{
+    const int SP = (N + 3) | 1, nbp = N / (2 * MR);
+    float4 *Q = reinterpret_cast<float4 *>(smraw);
+    const float h = joseph_h(N), hq = joseph_hq(N);
+    const int npair = (B + 1) / 2;
+    const unsigned top = (unsigned)(N + 2);
+    const int tid = c.tid(), lane = tid & 31;
+    const long long rows_all = (long long)nbp * U.u_rows;
+    long long u = u0;
+    while (u < u1) {
+        // the segment of unit u: slice z, class, band pair bp
+        const long long z = u / U.u_z, r = u - z * U.u_z;
+        const bool rows = r < rows_all;
+        const long long r2 = rows ? r : r - rows_all;
+        const int per = rows ? U.u_rows : U.u_cols;
+        const int bp = (int)(r2 / per);
+        const long long seg0 = u - (r2 - (long long)bp * per);
+        const long long e = min(u1, seg0 + per);
+        const int s0 = bp * MR;
+        quad_stage<DEEP>(c, Q, x + (size_t)z * N * N, N, s0, rows);
+        if (tid == 0) *next = (int)(u - seg0);
+        c.sync();
+        const int2 *list = rows ? row_items : col_items;
+        float *out = partial + ((size_t)z * nbp + bp) * V * B;
+        const int n_units = (int)(e - seg0);
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(next, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (w >= n_units) break;
+            const int item = w / U.nch, chunk = w - item * U.nch;
+            const int2 it = list[item];
+            const ViewP &vw = views[it.x];
+            const float a = vw.a, m = vw.m, inv_m = vw.inv_m;
+            const int cs = vw.stride;
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                const int idx = chunk * 64 + k * 32 + lane;
+                if (idx < npair)
+                    quad_position<ROWS>(Q, SP, a, m, inv_m, cs, it.x, it.y, rows, idx, npair, N, B, s0, h, hq, top,
+                                        out);
+            }
+        }
+        c.sync();
+        u = e;
     }
 }
 

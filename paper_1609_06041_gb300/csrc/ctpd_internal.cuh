@@ -51,6 +51,7 @@ struct Geometry {
     int tune_qrows;       // projector steps per pass of a ray walk (2 or 4)
     int tune_orb;         // A^T orbit base-view slices (1..8)
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
+    int tune_qbal;        // projector form: 1 band pair per block, 2 work-balanced ranges (0: the rule)
     double *h_angles;     // host copy
     void *eps_cache;      // eigenbases of D for the error-tolerant form (eps.cu)
     void *graph_cache;    // instantiated CUDA graphs of repeated solves (api.cu)

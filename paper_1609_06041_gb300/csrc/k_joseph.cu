@@ -305,6 +305,21 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                           n_row, col_items, n_col, N, V, B, pg, gpb, partial);
 }
 
+// The work-balanced form: block b takes units [total b / nb, total (b+1) / nb)
+// (see quad_balanced_body); its unit counter sits after the staged pairs.
+template <int ROWS, bool DEEP>
+__global__ void __launch_bounds__(ROWS == 2 ? 1024 : 768)
+k_project_qbal(const float *__restrict__ x, const ViewP *__restrict__ views, const int2 *__restrict__ row_items,
+               const int2 *__restrict__ col_items, int N, int V, int B, QuadUnits U, long long total,
+               float *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const long long nb = gridDim.x;
+    const long long u0 = total * blockIdx.x / nb, u1 = total * (blockIdx.x + 1) / nb;
+    quad_balanced_body<ROWS, DEEP>(whole_block(), u0, u1, U, smraw, reinterpret_cast<int *>(smraw + quad_smem(N)),
+                                   x, views, row_items, col_items, N, V, B, partial);
+}
+
 // Launch shape of k_project_quad: items per group (pg, 64 threads each) and
 // groups per block (gpb, walked one after the other on one staged band
 // pair), by the fewest waves of blocks (one block per SM, shared memory)
@@ -342,10 +357,35 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
         quad_shape(g, batch, max_pg, g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : 0, &pg, &gpb);
         const int rg = (g->n_row_items + pg - 1) / pg, cg = (g->n_col_items + pg - 1) / pg;
         const int blocks_y = (rg + gpb - 1) / gpb + (cg + gpb - 1) / gpb;
-        const size_t smem2 = quad_smem(N);
         const dim3 grd2(N / (2 * MR), blocks_y, batch);
+        const long static_blocks = (long)grd2.x * grd2.y * grd2.z;
+        // the built-in rule takes the work-balanced form when one band pair
+        // per block would need two waves of blocks or more
+        if (g->tune_qbal == 2 || (g->tune_qbal == 0 && static_blocks >= 2L * g->n_sm)) {
+            // work-balanced: as many blocks as fit on the device at once
+            // (fewer when the work would leave a warp under two units)
+            const int pgb = g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : max_pg, threads = pgb * 64;
+            const int npair = (g->n_bins + 1) / 2, nch = (npair + 63) / 64;
+            QuadUnits U;
+            U.nch = nch;
+            U.u_rows = g->n_row_items * nch;
+            U.u_cols = g->n_col_items * nch;
+            U.u_z = (long long)(N / (2 * MR)) * (U.u_rows + U.u_cols);
+            const long long total = U.u_z * batch;
+            const size_t smem2 = quad_smem(N) + 16;
+            auto kern = rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem2) != cudaSuccess || occ < 1)
+                occ = 1;
+            const long long by_work = (total + 4 * pgb - 1) / (4 * pgb);   // two units per warp
+            const int blocks = (int)std::max(1LL, std::min((long long)g->n_sm * occ, by_work));
+            kern<<<blocks, threads, smem2, st>>>(x, g->d_views, g->d_row_items, g->d_col_items, N, g->n_views,
+                                                 g->n_bins, U, total, partial);
+            return;
+        }
+        const size_t smem2 = quad_smem(N);
         // few blocks (few views): each thread stages many pairs, so issue their loads four at a time
-        const bool deep = (long)grd2.x * grd2.y * grd2.z < 2L * g->n_sm;
+        const bool deep = static_blocks < 2L * g->n_sm;
         auto kern = rows4 ? (deep ? k_project_quad<4, true> : k_project_quad<4, false>)
                           : (deep ? k_project_quad<2, true> : k_project_quad<2, false>);
         kern<<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items,
@@ -611,6 +651,8 @@ void kernel_attrs_joseph()
     cudaFuncSetAttribute(k_project_quad<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_quad<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_quad<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_qbal<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
+    cudaFuncSetAttribute(k_project_qbal<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_bands<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
 }

@@ -57,9 +57,9 @@ EXPORTS = {
     "ct_geometry_create": ([_i, _i, _i, _vp, ctypes.POINTER(_vp)], _i),
     "ct_geometry_destroy": ([_vp], None),
     "ct_geometry_autotune": ([_vp, _i, _vp], _i),
-    "ct_geometry_set_tuning": ([_vp, _i, _i, _i, _i], _i),
+    "ct_geometry_set_tuning": ([_vp, _i, _i, _i, _i, _i], _i),
     "ct_geometry_get_tuning": ([_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
-                                ctypes.POINTER(_i)], _i),
+                                ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "ct_project": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
@@ -178,15 +178,16 @@ class Geometry:
     @property
     def tuning(self) -> dict:
         """Launch shapes held by the geometry (0: built-in rule)."""
-        a, r, b, c = _i(), _i(), _i(), _i()
+        a, r, b, c, f = _i(), _i(), _i(), _i(), _i()
         _check(_lib.ct_geometry_get_tuning(self.handle, ctypes.byref(a), ctypes.byref(r), ctypes.byref(b),
-                                           ctypes.byref(c)))
-        return {"items_per_block": a.value, "proj_rows": r.value, "orbit_slices": b.value, "tv_rows": c.value}
+                                           ctypes.byref(c), ctypes.byref(f)))
+        return {"items_per_block": a.value, "proj_rows": r.value, "orbit_slices": b.value, "tv_rows": c.value,
+                "proj_form": f.value}
 
     def set_tuning(self, items_per_block: int = 0, orbit_slices: int = 0, tv_rows: int = 0,
-                   proj_rows: int = 0) -> None:
+                   proj_rows: int = 0, proj_form: int = 0) -> None:
         _check(_lib.ct_geometry_set_tuning(self.handle, int(items_per_block), int(proj_rows), int(orbit_slices),
-                                           int(tv_rows)))
+                                           int(tv_rows), int(proj_form)))
 
     def __del__(self):
         try:
@@ -208,8 +209,8 @@ def ct_geometry_autotune(g: Geometry, batch: int = 1) -> dict:
 
 
 def ct_geometry_set_tuning(g: Geometry, items_per_block: int = 0, orbit_slices: int = 0, tv_rows: int = 0,
-                           proj_rows: int = 0) -> None:
-    g.set_tuning(items_per_block, orbit_slices, tv_rows, proj_rows)
+                           proj_rows: int = 0, proj_form: int = 0) -> None:
+    g.set_tuning(items_per_block, orbit_slices, tv_rows, proj_rows, proj_form)
 
 
 def ct_geometry_get_tuning(g: Geometry) -> dict:

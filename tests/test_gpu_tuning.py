@@ -15,17 +15,44 @@ TOL = 1e-4
 
 @pytest.mark.parametrize("N,V,B", [(64, 90, 95), (96, 12, 140), (64, 33, 93)])
 @pytest.mark.parametrize("items,rows,slices", [(4, 2, 1), (7, 4, 2), (13, 2, 8), (16, 2, 4), (12, 4, 4)])
-def test_operator_shapes_parity(N, V, B, items, rows, slices):
+@pytest.mark.parametrize("form", [1, 2])
+def test_operator_shapes_parity(N, V, B, items, rows, slices, form):
     P = need_gpu()
     g = P.Geometry(N, V, B)
     if V % 2:
         slices = 0   # odd V: no orbit backprojector
-    g.set_tuning(items_per_block=items, orbit_slices=slices, proj_rows=rows)
-    assert g.tuning == {"items_per_block": items, "proj_rows": rows, "orbit_slices": slices, "tv_rows": 0}
+    g.set_tuning(items_per_block=items, orbit_slices=slices, proj_rows=rows, proj_form=form)
+    assert g.tuning == {"items_per_block": items, "proj_rows": rows, "orbit_slices": slices, "tv_rows": 0,
+                        "proj_form": form}
     x = f32(synth.ellipse_phantom(N, 6, 3))
     assert rel_l2(to_np(P.ct_project(g, to_gpu(x))), O.project(x, V, B)) <= TOL
     y = f32(synth.random_sinogram(V, B, 4))
     assert rel_l2(to_np(P.ct_backproject(g, to_gpu(y))), O.backproject(y, N)) <= TOL
+
+
+@pytest.mark.parametrize("N,V,B,batch", [(64, 90, 95, 1), (96, 12, 140, 3), (64, 33, 93, 2), (128, 360, 185, 2),
+                                         (512, 720, 736, 1), (256, 180, 368, 5)])
+def test_projector_forms_agree_bit_for_bit(N, V, B, batch):
+    # the work-balanced projector forms every band sum exactly as the
+    # band-pair-per-block form does, whatever the items per block or the
+    # batch: for one number of steps per pass (which sets how a ray's samples
+    # are grouped into partial sums) the projections are equal bit for bit
+    P = need_gpu()
+    import torch
+    g = P.Geometry(N, V, B)
+    xs = np.stack([f32(synth.ellipse_phantom(N, 6, 3 + i)) for i in range(batch)])
+    xg = to_gpu(xs)
+    for rows, shapes in [(2, [(8, 1), (16, 2), (8, 2), (13, 1), (12, 2)]), (4, [(10, 1), (12, 2), (8, 2)])]:
+        outs = []
+        for items, form in shapes:
+            g.set_tuning(items_per_block=items, proj_rows=rows, proj_form=form)
+            outs.append(P.ct_project(g, xg).clone())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        # each slice of the batch equals its own single projection
+        for i in range(batch):
+            assert torch.equal(P.ct_project(g, xg[i].contiguous()), outs[0][i])
+        assert rel_l2(to_np(outs[0][0]), O.project(xs[0], V, B)) <= TOL
 
 
 @pytest.mark.parametrize("rows", [4, 16, 64])
@@ -57,6 +84,7 @@ def test_autotune_picks_valid_shapes_and_keeps_parity():
     assert t["proj_rows"] in (2, 4)
     assert t["orbit_slices"] in (1, 2, 4, 8)
     assert t["tv_rows"] in (4, 8, 16, 32, 64)
+    assert t["proj_form"] in (1, 2)
     x = f32(synth.ellipse_phantom(N, 8, 5))
     assert rel_l2(to_np(P.ct_project(g, to_gpu(x))), O.project(x, V, B)) <= TOL
     y = f32(synth.random_sinogram(V, B, 6))
@@ -69,19 +97,19 @@ def test_autotune_without_shared_paths():
     P = need_gpu()
     g = P.Geometry(37, 13, 53, angles=np.linspace(0.0, 3.0, 13))
     t = g.autotune()
-    assert t["items_per_block"] == 0 and t["proj_rows"] == 0 and t["orbit_slices"] == 0
+    assert t["items_per_block"] == 0 and t["proj_rows"] == 0 and t["orbit_slices"] == 0 and t["proj_form"] == 0
     assert t["tv_rows"] in (4, 8, 16, 32, 64)
 
 
 @pytest.mark.parametrize("bad", [dict(items_per_block=3), dict(items_per_block=17), dict(orbit_slices=9),
                                  dict(orbit_slices=-1), dict(tv_rows=2), dict(tv_rows=65), dict(proj_rows=3),
-                                 dict(items_per_block=13, proj_rows=4)])
+                                 dict(items_per_block=13, proj_rows=4), dict(proj_form=3), dict(proj_form=-1)])
 def test_set_tuning_rejects_out_of_range(bad):
     P = need_gpu()
     g = P.Geometry(64, 90, 95)
     with pytest.raises(P.CTError):
         g.set_tuning(**bad)
-    assert g.tuning == {"items_per_block": 0, "proj_rows": 0, "orbit_slices": 0, "tv_rows": 0}
+    assert g.tuning == {"items_per_block": 0, "proj_rows": 0, "orbit_slices": 0, "tv_rows": 0, "proj_form": 0}
 
 
 def test_orbit_slices_limit_large_view_count():
