@@ -19,6 +19,7 @@ using namespace ctpd;
 
 std::atomic<unsigned long long> ctpd::g_launches{0};
 thread_local unsigned long long ctpd::t_launches = 0;
+thread_local int ctpd::t_pdl = 0;
 
 namespace {
 
@@ -911,6 +912,9 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     const int chunk = tv_max_steps();
     const int chunks = ntv == 0 ? 1 : (ntv + chunk - 1) / chunk;
     int cur = (int)((k0 * chunks) & 1);
+    // each kernel of the loop may be scheduled while its predecessor finishes
+    // (programmatic dependent launch; it waits for it before any memory access)
+    PdlScope pdl(true);
     for (int k = 0; k < prm->iters; ++k) {
         // Step 2: z = x^k - tau A^T mu_bar ; x^{k+1} = prox_{tau g}(z)
         backproject(mubar, z, 1, x_out);

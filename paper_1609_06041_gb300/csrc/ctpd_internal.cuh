@@ -242,6 +242,51 @@ inline void counted(unsigned n = 1)
     t_launches += n;
 }
 
+// Programmatic dependent launch.  A kernel launched with the
+// programmatic-serialization attribute is launched as the blocks of its
+// predecessor in the stream exit, before the predecessor's completion is
+// signalled; pdl_wait() blocks until the predecessor has completed and its
+// writes are visible, so it comes before the kernel's first global load or
+// store.  Without the attribute it returns at once.  (The kernels do not
+// signal their successors early: successor blocks scheduled while the last
+// blocks of a kernel still run were measured slower in replayed graphs.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launches made through launch_kernel while a PdlScope is open on the
+// calling thread carry the programmatic-serialization attribute (the solve
+// loop, whose kernels each begin with pdl_wait()); otherwise launch_kernel
+// is an ordinary launch.
+extern thread_local int t_pdl;
+struct PdlScope {
+    int old;
+    explicit PdlScope(bool on) : old(t_pdl) { t_pdl = on ? 1 : 0; }
+    ~PdlScope() { t_pdl = old; }
+};
+template <class T>
+struct same_type {
+    using type = T;
+};
+template <typename... KArgs>
+inline void launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          typename same_type<KArgs>::type... args)
+{
+    if (t_pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, kern, args...);
+    } else {
+        kern<<<grid, block, smem, st>>>(args...);
+    }
+}
+
 // ---- kernels (defined in the k_*.cu files) ----
 // The persistent batched solve (persist.cu).  persistent_slice_ok: the slice
 // qualifies (default angles with N, V even, N a multiple of 32 and at most

@@ -126,6 +126,7 @@ k_dual_fft(const float2 *__restrict__ hhat, const float *__restrict__ partial, i
            const double *__restrict__ scal, int V, int B, int P, const float2 *__restrict__ tw)
 {
     extern __shared__ float2 fsm[];
+    pdl_wait();
     dual_fft_body(whole_block(), blockIdx.x, blockIdx.y, fsm, hhat, partial, nb, b, mu_in, mu, mu_bar, winv, lowdose,
                   views, scal, V, B, P, tw);
 }
@@ -321,9 +322,9 @@ void launch_dual_fft_batched(const Geometry *g, const float2 *hhat, const float 
                              const double *scal, int batch, cudaStream_t st)
 {
     counted();
-    k_dual_fft<<<dim3((g->n_views + 1) / 2, batch), FFT_T, dual_fft_smem(g), st>>>(
-        hhat, partial, proj_bands(g->n), b, mu_in, mu_out, mu_bar, winv, lowdose, g->d_views, scal, g->n_views,
-        g->n_bins, g->n_fft, g->d_tw);
+    launch_kernel(k_dual_fft, dim3((g->n_views + 1) / 2, batch), dim3(FFT_T), dual_fft_smem(g), st, hhat, partial,
+                  proj_bands(g->n), b, mu_in, mu_out, mu_bar, winv, lowdose, g->d_views, scal, g->n_views, g->n_bins,
+                  g->n_fft, g->d_tw);
 }
 
 // Adjoint of one dual step (Step 3 and the next Step 1) for the pair of

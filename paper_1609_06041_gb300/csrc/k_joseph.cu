@@ -301,6 +301,7 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
                int N, int V, int B, int pg, int gpb, float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
     quad_body<ROWS, DEEP>(whole_block(), blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, smraw, x, views, row_items,
                           n_row, col_items, n_col, N, V, B, pg, gpb, partial);
 }
@@ -314,6 +315,7 @@ k_project_qbal(const float *__restrict__ x, const ViewP *__restrict__ views, con
                float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
     const long long nb = gridDim.x;
     const long long u0 = total * blockIdx.x / nb, u1 = total * (blockIdx.x + 1) / nb;
     quad_balanced_body<ROWS, DEEP>(whole_block(), u0, u1, U, smraw, reinterpret_cast<int *>(smraw + quad_smem(N)),
@@ -379,8 +381,8 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
                 occ = 1;
             const long long by_work = (total + 4 * pgb - 1) / (4 * pgb);   // two units per warp
             const int blocks = (int)std::max(1LL, std::min((long long)g->n_sm * occ, by_work));
-            kern<<<blocks, threads, smem2, st>>>(x, g->d_views, g->d_row_items, g->d_col_items, N, g->n_views,
-                                                 g->n_bins, U, total, partial);
+            launch_kernel(kern, dim3(blocks), dim3(threads), smem2, st, x, g->d_views, g->d_row_items,
+                          g->d_col_items, N, g->n_views, g->n_bins, U, total, partial);
             return;
         }
         const size_t smem2 = quad_smem(N);
@@ -388,8 +390,8 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
         const bool deep = static_blocks < 2L * g->n_sm;
         auto kern = rows4 ? (deep ? k_project_quad<4, true> : k_project_quad<4, false>)
                           : (deep ? k_project_quad<2, true> : k_project_quad<2, false>);
-        kern<<<grd2, pg * 64, smem2, st>>>(x, g->d_views, g->d_row_items, g->n_row_items, g->d_col_items,
-                                           g->n_col_items, N, g->n_views, g->n_bins, pg, gpb, partial);
+        launch_kernel(kern, grd2, dim3(pg * 64), smem2, st, x, g->d_views, g->d_row_items, g->n_row_items,
+                      g->d_col_items, g->n_col_items, N, g->n_views, g->n_bins, pg, gpb, partial);
     } else if (N % (2 * MR) == 0 && N + 3 <= PROJ_CW) {
         // two mirrored 16-step bands per block: N/32 partial slots, as below
         dim3 grd2(N / (2 * MR), grd.y, batch);
@@ -572,6 +574,7 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
                     const double *__restrict__ scal)
 {
     extern __shared__ __align__(16) unsigned char osm[];
+    pdl_wait();
     orbit_body<AL>(Block2D{}, blockIdx.x, blockIdx.y, blockIdx.z, osm, y, partial, trig, N, V, B, nsl, fin, out, xin,
                    scal);
 }
@@ -586,6 +589,7 @@ template <int MODE>
 __global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restrict__ out, const float *xin,
                                const double *__restrict__ scal, size_t NN, int nsl)
 {
+    pdl_wait();
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= NN) return;
     const float *pp = partial + (size_t)blockIdx.y * nsl * NN + i;
@@ -618,17 +622,15 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     // k_orbit_reduce with one slice), and no reduction pass runs
     const int fin = nsl == 1 ? 1 + (mode != 0) : 0;
     counted(fin ? 1 : 2);
-    if (g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0)
-        k_backproject_orbit<true><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(
-            y, partial, g->d_trig, g->n, g->n_views, g->n_bins, nsl, fin, out, xin, scal);
-    else
-        k_backproject_orbit<false><<<grd, dim3(ORB_T, ORB_TY), orbit_smem(), st>>>(
-            y, partial, g->d_trig, g->n, g->n_views, g->n_bins, nsl, fin, out, xin, scal);
+    auto kern = g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0 ? k_backproject_orbit<true>
+                                                                               : k_backproject_orbit<false>;
+    launch_kernel(kern, grd, dim3(ORB_T, ORB_TY), orbit_smem(), st, y, partial, g->d_trig, g->n, g->n_views,
+                  g->n_bins, nsl, fin, out, xin, scal);
     if (fin) return;
     const size_t NN = (size_t)g->n * g->n;
     dim3 g2((unsigned)((NN + 255) / 256), batch);
-    if (mode == 0) k_orbit_reduce<0><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN, nsl);
-    else k_orbit_reduce<1><<<g2, 256, 0, st>>>(partial, out, xin, scal, NN, nsl);
+    launch_kernel(mode == 0 ? k_orbit_reduce<0> : k_orbit_reduce<1>, g2, dim3(256), 0, st, partial, out, xin, scal,
+                  NN, nsl);
 }
 
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,

@@ -59,6 +59,7 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
 {
     __shared__ float2 pub_x[(TV_ROWS + 2) * 32];
     __shared__ float2 pub_y[(TV_ROWS + 2) * 32];
+    pdl_wait();
     tv_body<FGP, TRAJ>(whole_block(), blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, pub_x, pub_y, z, p_in, p_out, x,
                        N, steps, final_, tc, tr, scal, traj);
 }
@@ -82,12 +83,8 @@ void launch_tv(const float *z, const float *p_in, float *p_out, float *x,
                                traj != nullptr);
     const dim3 grid(t.ncb, t.nrb, std::max(1, batch));
     counted();
-    if (traj)
-        k_tv<false, true><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
-    else if (fgp)
-        k_tv<true, false><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
-    else
-        k_tv<false, false><<<grid, TV_THREADS, 0, st>>>(z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
+    auto kern = traj ? k_tv<false, true> : fgp ? k_tv<true, false> : k_tv<false, false>;
+    launch_kernel(kern, grid, dim3(TV_THREADS), 0, st, z, p_in, p_out, x, n, steps, final_, t.tc, t.tr, scal, traj);
 }
 
 void kernel_attrs_tv() {}
