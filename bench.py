@@ -45,10 +45,10 @@ SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory by
 # DRAM bytes (read + write) per launch of each operator's main kernel at this
 # workload, from one ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); update together with the kernels, None when no
-# capture of the current kernel exists.  A: k_project_qbal<2> (the
-# work-balanced projector, 16 items' threads per block); AT:
-# k_backproject_orbit<true>.
-TRAFFIC_BYTES = {"A": 1.179904e6, "AT": 2.022912e6}
+# capture of the current kernel exists.  A: k_project_qbal<4> (the
+# work-balanced projector, 12 items' threads per block, 4 steps per pass);
+# AT: k_backproject_orbit<true>.
+TRAFFIC_BYTES = {"A": 1.137152e6, "AT": 2.02496e6}
 
 
 def dist_info():
