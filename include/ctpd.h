@@ -149,6 +149,24 @@ ct_status ct_project(const ct_geometry *geom, const float *img, float *sino,
                      int batch, void *stream);
 
 /*
+ * The forward projection's band partial sums, the form in which the solve
+ * takes Step 3's A x^{k+1} (Eq. 20) before the dual step adds them: the
+ * image lines (rows for views stepping along rows, columns otherwise) are
+ * cut into ct_project_bands_count(geom) bands (32 lines each, paired by
+ * the image's mirror symmetry), and partial[b][v][d] holds the Joseph
+ * samples of ray (v, d) in band b, summed in step order, before the
+ * per-view path length |a_v| = 1 / max(|cos t_v|, |sin t_v|) is applied:
+ *     sino[v][d] = |a_v| sum_b partial[b][v][d]      (ct_project adds the
+ * bands in b order).  img: batch x N x N; partial: batch x n_bands x V x B
+ * floats (device, caller-owned, overwritten; 16-byte aligned).  The launch
+ * is the projector kernel alone, with no scratch allocation.  Errors:
+ * CT_ERR_ARG (NULL or unaligned pointer, batch outside [0, 65535]).
+ */
+int ct_project_bands_count(const ct_geometry *geom);
+ct_status ct_project_bands(const ct_geometry *geom, const float *img, float *partial,
+                           int batch, void *stream);
+
+/*
  * Backprojection img = A^T sino (the A^T of Eq. 19), a pixel-driven gather
  * over the two rays around each pixel's detector coordinate; deterministic
  * and free of atomics.  sino: batch x V x B, img: batch x N x N (overwritten).

@@ -30,6 +30,8 @@ from .ctpd import (  # noqa: F401
     ct_pdtv_workspace_bytes,
     ct_probe_fp32_fma,
     ct_project,
+    ct_project_bands,
+    ct_project_bands_count,
     ct_ramp_filter,
     ct_ramp_filter_noalloc,
     ct_sym_toeplitz_eig,

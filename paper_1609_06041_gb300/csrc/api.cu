@@ -599,6 +599,20 @@ ct_status ct_project(const ct_geometry *g, const float *img, float *sino, int ba
     return cuda_check("ct_project");
 }
 
+int ct_project_bands_count(const ct_geometry *g) { return g ? proj_bands(g->n) : 0; }
+
+ct_status ct_project_bands(const ct_geometry *g, const float *img, float *partial, int batch, void *stream)
+{
+    g_err[0] = 0;
+    if (!g || batch < 0 || batch > 65535) return fail(CT_ERR_ARG, "ct_project_bands: bad argument");
+    if (batch == 0) return CT_OK;
+    if (!img || !partial) return fail(CT_ERR_ARG, "ct_project_bands: NULL pointer");
+    if (!aligned16(img) || !aligned16(partial))
+        return fail(CT_ERR_ARG, "ct_project_bands: pointers must be 16-byte aligned");
+    launch_project_bands(g, img, partial, batch, S(stream));
+    return cuda_check("ct_project_bands");
+}
+
 ct_status ct_backproject(const ct_geometry *g, const float *sino, float *img, int batch, void *stream)
 {
     g_err[0] = 0;

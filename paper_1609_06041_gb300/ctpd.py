@@ -61,6 +61,8 @@ EXPORTS = {
     "ct_geometry_get_tuning": ([_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                 ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
     "ct_project": ([_vp, _vp, _vp, _i, _vp], _i),
+    "ct_project_bands_count": ([_vp], _i),
+    "ct_project_bands": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_backproject": ([_vp, _vp, _vp, _i, _vp], _i),
     "ct_ramp_taps": ([_vp, _i, _d, _d, _vp, _vp], _i),
     "ct_ramp_filter": ([_vp, _vp, _i, _vp, _vp, _i, _vp], _i),
@@ -224,6 +226,21 @@ def ct_project(g: Geometry, img: torch.Tensor, out: torch.Tensor | None = None) 
         out = torch.empty(*img.shape[:-2], g.n_views, g.n_bins, device=img.device, dtype=torch.float32)
     po = _dev(out, "out", (g.n_views, g.n_bins))
     _check(_lib.ct_project(g.handle, pi, po, _batch(img, 2), _stream()))
+    return out
+
+
+def ct_project_bands_count(g: Geometry) -> int:
+    return int(_lib.ct_project_bands_count(g.handle))
+
+
+def ct_project_bands(g: Geometry, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Band partial sums of A img: (..., n_bands, V, B), sino = |a_v| sum over the band axis."""
+    pi = _dev(img, "img", (g.n, g.n))
+    nb = ct_project_bands_count(g)
+    if out is None:
+        out = torch.empty(*img.shape[:-2], nb, g.n_views, g.n_bins, device=img.device, dtype=torch.float32)
+    po = _dev(out, "out", (nb, g.n_views, g.n_bins))
+    _check(_lib.ct_project_bands(g.handle, pi, po, _batch(img, 2), _stream()))
     return out
 
 

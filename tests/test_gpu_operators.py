@@ -154,3 +154,30 @@ def test_bad_arguments_raise():
         P.ct_project(g, torch.zeros(16, 16, device="cuda", dtype=torch.float64))
     with pytest.raises(P.CTError):
         P.ct_ramp_taps(g, 0, -1.0, 0.1)
+
+
+@pytest.mark.parametrize("N,V,B,angles,batch", [(64, 90, 95, None, 1), (96, 30, 140, None, 3),
+                                                (64, 33, 93, "custom", 2), (37, 13, 53, "custom", 1),
+                                                (512, 720, 736, None, 1)])
+def test_project_bands_add_up_to_the_projection(N, V, B, angles, batch):
+    # ct_project_bands: the band partial sums, which scaled by each view's
+    # path length |a_v| and added over the bands give A img (ct_project)
+    P = need_gpu()
+    import torch
+    ang = np.sort(np.random.default_rng(5).uniform(0.0, np.pi, V)) if angles == "custom" else None
+    g = P.Geometry(N, V, B, angles=ang)
+    xs = np.stack([f32(synth.ellipse_phantom(N, 6, 11 + i)) for i in range(batch)])
+    xg = to_gpu(xs)
+    parts = P.ct_project_bands(g, xg)
+    nb = P.ct_project_bands_count(g)
+    assert parts.shape == (batch, nb, V, B) and nb == (N + 31) // 32
+    t = np.arange(V) * np.pi / V if ang is None else ang
+    a = (1.0 / np.maximum(np.abs(np.cos(t)), np.abs(np.sin(t)))).astype(np.float32)
+    sino = to_np(P.ct_project(g, xg))
+    summed = to_np(parts).astype(np.float64).sum(axis=1) * a[None, :, None]
+    assert rel_l2(summed, sino) <= 1e-6
+    assert rel_l2(summed[0], O.project(xs[0], V, B, angles=ang)) <= TOL
+    # an output 4 bytes off a 16-byte boundary is refused
+    unaligned = torch.empty(batch * nb * V * B + 1, device="cuda")[1:].view(batch, nb, V, B)
+    with pytest.raises(P.CTError):
+        P.ct_project_bands(g, xg, out=unaligned)
