@@ -47,8 +47,8 @@ SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory by
 # dram__bytes_write.sum); update together with the kernels, None when no
 # capture of the current kernel exists.  A: k_project_qbal<4> (the
 # work-balanced projector, 12 items' threads per block, 4 steps per pass);
-# AT: k_backproject_orbit<true>.
-TRAFFIC_BYTES = {"A": 1.137152e6, "AT": 2.02496e6}
+# AT: k_backproject_orbit_cl<true> (mu_bar and x read once).
+TRAFFIC_BYTES = {"A": 1.137152e6, "AT": 3.080704e6}
 
 
 def dist_info():
@@ -652,10 +652,11 @@ def run_ours(args):
         fma_packed = P.ct_probe_fp32_fma(True)
     fp32_peak = max(fma_scalar, fma_packed)
     # dominant operator: the slower of A (ct_project_bands: the projector
-    # kernel) and A^T (ct_backproject: orbit kernel + slice reduction); both
-    # carry 2 nnz(A) algorithmic flops
+    # kernel) and A^T (ct_backproject: the orbit kernel, its slices added in
+    # a thread-block cluster); both carry 2 nnz(A) algorithmic flops
     a_kernel = "k_project_qbal" if g.tuning.get("proj_form") == 2 else "k_project_quad"
-    dom_name, dom_ms, dom_key = ("ct_backproject (A^T, k_backproject_orbit + k_orbit_reduce)", at_ms, "AT") \
+    at_kernel = "k_backproject_orbit_cl" if g.tuning.get("orbit_slices", 0) != 1 else "k_backproject_orbit"
+    dom_name, dom_ms, dom_key = (f"ct_backproject (A^T, {at_kernel})", at_ms, "AT") \
         if at_ms >= a_ms else (f"ct_project_bands (A, {a_kernel})", a_ms, "A")
     achieved = flops / (dom_ms / 1e3) / 1e12
 

@@ -620,20 +620,8 @@ ct_status ct_backproject(const ct_geometry *g, const float *sino, float *img, in
     if (batch == 0) return CT_OK;
     if (!img || !sino) return fail(CT_ERR_ARG, "ct_backproject: NULL pointer");
     if (!aligned16(img) || !aligned16(sino)) return fail(CT_ERR_ARG, "ct_backproject: pointers must be 16-byte aligned");
-    if (!orbit_ok(g)) {
-        launch_backproject(g, sino, img, 0, nullptr, nullptr, batch, S(stream));
-        return cuda_check("ct_backproject");
-    }
-    // slice images of the orbit form: stream-ordered scratch, freed after use
-    const size_t bytes = sizeof(float) * orbit_partial_floats(g, batch);
-    float *partial = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&partial, bytes, S(stream));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CT_ERR_OOM, "ct_backproject: scratch allocation failed (%zu bytes)", bytes);
-    }
-    launch_backproject_orbit(g, sino, img, 0, nullptr, nullptr, batch, partial, S(stream));
-    cudaFreeAsync(partial, S(stream));
+    if (!orbit_ok(g)) launch_backproject(g, sino, img, 0, nullptr, nullptr, batch, S(stream));
+    else launch_backproject_orbit(g, sino, img, 0, nullptr, nullptr, batch, nullptr, S(stream));
     return cuda_check("ct_backproject");
 }
 

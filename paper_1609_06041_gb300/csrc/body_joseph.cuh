@@ -403,9 +403,10 @@ __device__ __forceinline__ void quad_balanced_body(const Ctx &c, long long u0, l
 // 16 ORB_TY threads takes the orbits of ORB_PX pixels of one tile column
 // (rows r, r + ORB_TY, ..), so the per-view constants, window bases and
 // loop control are shared by 8 ORB_PX pixel-views.  Base views are split into
-// nsl slices (grid.z; 4 unless tuned, at most ORB_SL_MAX); each slice
-// writes its own partial image and k_orbit_reduce adds the slices in a
-// fixed order.  The weights are the
+// nsl slices (grid.z; 4 unless tuned, at most ORB_SL_MAX), added in slice
+// order: in a thread-block cluster of the slices' blocks
+// (k_backproject_orbit_cl), or from slice images (the persistent batched
+// kernel's reduction phase).  The weights are the
 // pixel-side Joseph weights of k_backproject_tiles, so both kernels compute
 // the same A^T.
 // =====================================================================
@@ -436,8 +437,10 @@ template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
 // Body of block (bx, by, bz) (c.nth() = ORB_TH threads, as ORB_T x ORB_TY);
-// osm holds orbit_smem() bytes.
-template <bool AL, class Ctx>
+// osm holds orbit_smem() bytes.  CL: instead of storing its sums, the
+// block leaves them in osm, entry (k ORB_PX + j) ORB_TH + tid for rotation
+// k of the thread's pixel orbit j, for a cluster reduction over slices.
+template <bool AL, class Ctx, bool CL = false>
 __device__ __forceinline__ void orbit_body(const Ctx &cb, int bx, int by, int bz, unsigned char *osm, const float *y,
                                            float *partial, const float4 *trig, int N, int V, int B, int nsl,
                                            int fin, float *out, const float *xin, const double *scal)
@@ -556,9 +559,17 @@ __device__ __forceinline__ void orbit_body(const Ctx &cb, int bx, int by, int bz
         }
         cb.sync();   // the buffer is refilled two chunks later
     }
+    if constexpr (CL) {
+        float *red = reinterpret_cast<float *>(osm);   // the staging buffers are free again
+#pragma unroll
+        for (int j = 0; j < ORB_PX; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[(k * ORB_PX + j) * ORB_TH + tid] = acc[j][k];
+        return;
+    }
     // fin 0: the slice's partial image; with a single slice the sums are
-    // complete and the block writes k_orbit_reduce's result itself: fin 1
-    // out = sum, fin 2 out = xin - tau sum
+    // complete and the block writes the result itself: fin 1 out = sum,
+    // fin 2 out = xin - tau sum
     float *pp = (fin ? out : partial) + ((size_t)img * (fin ? 1 : nsl) + slice) * N * N;
     const float *xq0 = fin == 2 ? xin + (size_t)img * N * N : nullptr;
     const float tau = fin == 2 ? fscal(scal, F_TAU) : 0.0f;

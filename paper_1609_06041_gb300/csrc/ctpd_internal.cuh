@@ -287,6 +287,28 @@ inline void launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
     }
 }
 
+// launch_kernel for a grid of thread-block clusters of `cluster` blocks
+template <typename... KArgs>
+inline void launch_kernel_cluster(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  dim3 cluster, typename same_type<KArgs>::type... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster.x;
+    at[0].val.clusterDim.y = cluster.y;
+    at[0].val.clusterDim.z = cluster.z;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = t_pdl ? 2 : 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- kernels (defined in the k_*.cu files) ----
 // The persistent batched solve (persist.cu).  persistent_slice_ok: the slice
 // qualifies (default angles with N, V even, N a multiple of 32 and at most
@@ -334,8 +356,10 @@ void launch_band_reduce(const Geometry *g, const float *partial, float *out, int
                         const float *b, const float *winv, const float *mu, int batch,
                         cudaStream_t st);
 // Backprojection; mode 0: out = A^T y; mode 1: out = xin - tau*A^T y with
-// tau = (float)scal[S_TAU].  The orbit form needs orbit_partial_floats()
-// of scratch (ORB_SL partial images per image).
+// tau = (float)scal[S_TAU].  The orbit form adds its base-view slices in a
+// thread-block cluster and needs no scratch (`partial` is unused); the
+// persistent batched kernel's orbit phase writes slice images of
+// orbit_partial_floats() floats instead.
 bool orbit_ok(const Geometry *g);
 size_t orbit_partial_floats(const Geometry *g, int batch);
 bool orbit_slices_ok(const Geometry *g, int nsl);

@@ -3,6 +3,8 @@
 // deterministic (fixed summation orders, no atomics).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "body_joseph.cuh"
 
 namespace ctpd {
@@ -579,25 +581,53 @@ k_backproject_orbit(const float *__restrict__ y, float *__restrict__ partial, co
                    scal);
 }
 
+// The orbit backprojector with its base-view slices added in a thread-block
+// cluster: the nsl blocks of one tile (grid.z = images x slices, cluster
+// (1, 1, nsl)) each leave their partial sums in shared memory; block s then
+// adds, for its share of the tile's 4 ORB_PX ORB_TH sums, the nsl partials
+// in slice order through distributed shared memory and writes the sum
+// (mode 0) or xin - tau sum (mode 1).  No slice images are written, and no
+// reduction pass runs.
+template <bool AL>
+__global__ void __launch_bounds__(ORB_TH, 8)
+k_backproject_orbit_cl(const float *__restrict__ y, const float4 *__restrict__ trig, int N, int V, int B, int nsl,
+                       int mode, float *out, const float *xin, const double *__restrict__ scal)
+{
+    extern __shared__ __align__(16) unsigned char osm[];
+    pdl_wait();
+    orbit_body<AL, Block2D, true>(Block2D{}, blockIdx.x, blockIdx.y, blockIdx.z, osm, y, nullptr, trig, N, V, B, nsl, 0,
+                                  nullptr, nullptr, scal);
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();   // every slice's partial sums are in its shared memory
+    const int slice = blockIdx.z % nsl, img = blockIdx.z / nsl;   // the block's rank in its cluster
+    float *red = reinterpret_cast<float *>(osm);
+    constexpr int E = 4 * ORB_PX * ORB_TH;
+    const int e0 = E * slice / nsl, e1 = E * (slice + 1) / nsl;
+    const int half = N / 2;
+    const float tau = mode ? fscal(scal, F_TAU) : 0.0f;
+    float *o_img = out + (size_t)img * N * N;
+    const float *x_img = mode ? xin + (size_t)img * N * N : nullptr;
+    for (int e = e0 + (int)(threadIdx.y * blockDim.x + threadIdx.x); e < e1; e += ORB_TH) {
+        float t = *cl.map_shared_rank(red + e, 0);
+        for (int s = 1; s < nsl; ++s) t += *cl.map_shared_rank(red + e, s);
+        const int k = e / (ORB_PX * ORB_TH), rem = e - k * (ORB_PX * ORB_TH);
+        const int j = rem / ORB_TH, th = rem - j * ORB_TH;
+        const int rj = blockIdx.y * ORB_T + th / ORB_T + j * ORB_TY, c = half + blockIdx.x * ORB_T + th % ORB_T;
+        if (rj < half && c < N) {
+            const size_t o = k == 0   ? (size_t)rj * N + c
+                             : k == 1 ? (size_t)c * N + (N - 1 - rj)
+                             : k == 2 ? (size_t)(N - 1 - rj) * N + (N - 1 - c)
+                                      : (size_t)(N - 1 - c) * N + rj;
+            o_img[o] = mode ? x_img[o] - tau * t : t;
+        }
+    }
+    cl.sync();   // no block leaves while its partial sums may still be read
+}
+
 static size_t orbit_smem()
 {
     return sizeof(float) * 2 * ORB_VC * 8 * ORB_RW + sizeof(float4) * 2 * ORB_VC + sizeof(int) * 2 * ORB_MAXS;
-}
-
-// out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
-template <int MODE>
-__global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restrict__ out, const float *xin,
-                               const double *__restrict__ scal, size_t NN, int nsl)
-{
-    pdl_wait();
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= NN) return;
-    const float *pp = partial + (size_t)blockIdx.y * nsl * NN + i;
-    float t = pp[0];
-    for (int s = 1; s < nsl; ++s) t += pp[s * NN];
-    const size_t o = (size_t)blockIdx.y * NN + i;
-    if (MODE == 0) out[o] = t;
-    else out[o] = xin[o] - fscal(scal, F_TAU) * t;
 }
 
 bool orbit_ok(const Geometry *g) { return g->orbit; }
@@ -618,19 +648,20 @@ void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int
     const int q = g->n / 2;
     const int nsl = orbit_slices(g);
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, nsl * batch);
-    // one slice: the orbit kernel writes the result (the same arithmetic as
-    // k_orbit_reduce with one slice), and no reduction pass runs
-    const int fin = nsl == 1 ? 1 + (mode != 0) : 0;
-    counted(fin ? 1 : 2);
-    auto kern = g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0 ? k_backproject_orbit<true>
-                                                                               : k_backproject_orbit<false>;
-    launch_kernel(kern, grd, dim3(ORB_T, ORB_TY), orbit_smem(), st, y, partial, g->d_trig, g->n, g->n_views,
-                  g->n_bins, nsl, fin, out, xin, scal);
-    if (fin) return;
-    const size_t NN = (size_t)g->n * g->n;
-    dim3 g2((unsigned)((NN + 255) / 256), batch);
-    launch_kernel(mode == 0 ? k_orbit_reduce<0> : k_orbit_reduce<1>, g2, dim3(256), 0, st, partial, out, xin, scal,
-                  NN, nsl);
+    const bool al = g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
+    counted();
+    if (nsl > 1) {
+        // several slices: their sums are added in a cluster of the slices' blocks
+        launch_kernel_cluster(al ? k_backproject_orbit_cl<true> : k_backproject_orbit_cl<false>, grd,
+                              dim3(ORB_T, ORB_TY), orbit_smem(), st, dim3(1, 1, nsl), y, (const float4 *)g->d_trig,
+                              g->n, g->n_views, g->n_bins, nsl, mode != 0 ? 1 : 0, out, xin, scal);
+        return;
+    }
+    // one slice: the block's sums are complete and it writes the result
+    launch_kernel(al ? k_backproject_orbit<true> : k_backproject_orbit<false>, grd, dim3(ORB_T, ORB_TY), orbit_smem(),
+                  st, y, (float *)nullptr, g->d_trig, g->n, g->n_views, g->n_bins, nsl, 1 + (mode != 0), out, xin,
+                  scal);
+    (void)partial;
 }
 
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
@@ -648,6 +679,8 @@ void kernel_attrs_joseph()
 {
     cudaFuncSetAttribute(k_backproject_orbit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_backproject_orbit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
+    cudaFuncSetAttribute(k_backproject_orbit_cl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
+    cudaFuncSetAttribute(k_backproject_orbit_cl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orbit_smem());
     cudaFuncSetAttribute(k_project_mirror, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_quad<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));
     cudaFuncSetAttribute(k_project_quad<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem(8192));

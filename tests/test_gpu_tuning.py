@@ -149,7 +149,9 @@ def test_single_orbit_slice_writes_the_result():
     assert rel_l2(to_np(x), st.x) <= 1e-3
     g.set_tuning(orbit_slices=2)
     n1 = P.ct_kernel_launches()
-    P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
+    x2, _ = P.ct_pdtv_solve(g, to_gpu(b), to_gpu(w), prm)
     torch.cuda.synchronize()
-    # two slices: one reduction pass more per iteration (20) and per A^T of the setup
-    assert (P.ct_kernel_launches() - n1) - (n1 - n0) >= 20
+    # two slices: their sums are added in a cluster of the slices' blocks,
+    # so no reduction pass runs either
+    assert P.ct_kernel_launches() - n1 == n1 - n0
+    assert rel_l2(to_np(x2), st.x) <= 1e-3
