@@ -106,9 +106,13 @@ void ct_geometry_destroy(ct_geometry *geom);
  *                    proj_rows is 4);
  *   proj_rows        steps a projector thread evaluates per pass of a ray
  *                    walk (2 or 4: more loads in flight, more registers);
- *   orbit_slices     base-view slices of the rotation-orbit backprojector,
- *                    one partial image each (1..8, at most 1024 base views
- *                    per slice);
+ *   orbit_slices     base-view slices of the rotation-orbit backprojector
+ *                    (1..8, at most 1024 base views per slice), added in a
+ *                    thread-block cluster of the slices' blocks, or (solves
+ *                    run side by side in the batched form) through one
+ *                    partial image each; the tuner picks the count for each
+ *                    of the two forms, this call sets both and the getter
+ *                    returns the first;
  *   tv_rows          fewest interior rows of a TV prox tile (4..64);
  *   proj_form        how the projector's work is cut into blocks (1 or 2):
  *                    1, each block stages one band pair and walks a few

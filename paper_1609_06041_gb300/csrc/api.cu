@@ -789,7 +789,7 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
     float *orb = (float *)(ws + L.orb);
     // A^T, by rotation orbits when the geometry allows
     auto backproject = [&](const float *yy, float *out, int md, const float *xin) {
-        if (orbit_ok(g)) launch_backproject_orbit(g, yy, out, md, xin, scal, 1, orb, st);
+        if (orbit_ok(g)) launch_backproject_orbit(g, yy, out, md, xin, scal, 1, orb, st, allow_fork);
         else launch_backproject(g, yy, out, md, xin, scal, 1, st);
     };
     float *pbuf[2] = {(float *)(ws + L.p0), (float *)(ws + L.p1)};

@@ -9,8 +9,11 @@
 //     with its steps per pass of a ray walk (2, or 4 with pg <= 12) and its
 //     form (one band pair per block, or the work-balanced k_project_qbal
 //     with 8, 12 or 16 items' threads per block);
-//   - the backprojector's base-view slices (k_backproject_orbit: grid.z,
-//     one partial image per slice), 1, 2, 4 or 8;
+//   - the backprojector's base-view slices (grid.z), 1, 2, 4 or 8, for its
+//     cluster form (k_backproject_orbit_cl: the slices' blocks add their
+//     sums through distributed shared memory) and for its slice-image form
+//     (one partial image per slice and k_orbit_reduce, taken by solves run
+//     side by side and by the persistent batched kernel);
 //   - the TV prox's fewest interior rows per tile (k_tv), 4 .. 64, which
 //     sets how many tiles one image is cut into.
 // Each choice changes only the launch shape and the order in which
@@ -101,7 +104,7 @@ extern "C" ct_status ct_geometry_set_tuning(ct_geometry *g, int items_per_block,
     }
     g->tune_pg = items_per_block;
     g->tune_qrows = proj_rows;
-    g->tune_orb = orbit_slices;
+    g->tune_orb = g->tune_orb_si = orbit_slices;
     g->tune_tv = tv_rows;
     g->tune_qbal = proj_form;
     graph_cache_clear(g);
@@ -119,6 +122,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
     const int N = g->n;
     const size_t J = (size_t)N * N, I = (size_t)g->n_views * g->n_bins;
     const int old_pg = g->tune_pg, old_rows = g->tune_qrows, old_orb = g->tune_orb, old_tv = g->tune_tv;
+    const int old_orb_si = g->tune_orb_si;
     const int old_qbal = g->tune_qbal;
     Buffers buf;
     float *x = nullptr, *sino = nullptr, *band = nullptr, *orb = nullptr, *img = nullptr, *tvb = nullptr;
@@ -177,21 +181,26 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
         g->tune_qrows = best_rows;
         g->tune_qbal = best_form;
     }
-    if (result == CT_OK && orbit_ok(g)) {
+    // the orbit backprojector's slices, for each of its two forms: slices
+    // added in a thread-block cluster (single solves) and slice images with
+    // a reduction pass (solves run side by side, the persistent kernel)
+    for (int form = 0; form < 2 && result == CT_OK && orbit_ok(g); ++form) {
+        const bool cl = form == 0;
+        int &slot = cl ? g->tune_orb : g->tune_orb_si;
         float best = -1.0f;
         int best_sl = 0;
         for (int nsl = 1; nsl <= 8 && result == CT_OK; nsl *= 2) {
             if (!orbit_slices_ok(g, nsl)) continue;
-            g->tune_orb = nsl;
-            t = time_launches([&] { launch_backproject_orbit(g, sino, img, 0, nullptr, scal, batch, orb, st); }, st,
-                              e0, e1);
+            slot = nsl;
+            t = time_launches([&] { launch_backproject_orbit(g, sino, img, 0, nullptr, scal, batch, orb, st, cl); },
+                              st, e0, e1);
             if (t < 0.0f) result = CT_ERR_CUDA;
             else if (best < 0.0f || t < best) {
                 best = t;
                 best_sl = nsl;
             }
         }
-        g->tune_orb = best_sl;
+        slot = best_sl;
     }
     if (result == CT_OK) {
         float best = -1.0f;
@@ -216,6 +225,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
         g->tune_pg = old_pg;
         g->tune_qrows = old_rows;
         g->tune_orb = old_orb;
+        g->tune_orb_si = old_orb_si;
         g->tune_tv = old_tv;
         g->tune_qbal = old_qbal;
         cudaError_t le = cudaGetLastError();

@@ -582,7 +582,7 @@ __device__ __forceinline__ void orbit_body(const Ctx &cb, int bx, int by, int bz
                                  (size_t)(N - 1 - rj) * N + (N - 1 - c), // R180 (r, c) = (N-1-r, N-1-c)
                                  (size_t)(N - 1 - c) * N + rj};         // R270 (r, c) = (N-1-c, r)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) pp[o[k]] = fin == 2 ? xq0[o[k]] - tau * acc[j][k] : acc[j][k];
+            for (int k = 0; k < 4; ++k) pp[o[k]] = fin == 2 ? __fmaf_rn(-tau, acc[j][k], xq0[o[k]]) : acc[j][k];
         }
     }
 }

@@ -49,7 +49,8 @@ struct Geometry {
     // launch shapes chosen by ct_geometry_autotune (0: the built-in rule)
     int tune_pg;          // projector view items per block (4..16; 4..12 with 4 steps per pass)
     int tune_qrows;       // projector steps per pass of a ray walk (2 or 4)
-    int tune_orb;         // A^T orbit base-view slices (1..8)
+    int tune_orb;         // A^T orbit base-view slices (1..8), slices added in a cluster
+    int tune_orb_si;      // the same for the slice-image form (solves side by side, the persistent kernel)
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     int tune_qbal;        // projector form: 1 band pair per block, 2 work-balanced ranges (0: the rule)
     double *h_angles;     // host copy
@@ -322,7 +323,9 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
                             const ct_pdtv_params *params, float *const *x_out, void *const *workspaces,
                             cudaStream_t st);
 // Launch shapes shared with the persistent batched kernel (persist.cu).
-int orbit_slices(const Geometry *g);            // base-view slices of the orbit backprojector
+// base-view slices of the orbit backprojector: of its cluster form, or
+// (cluster false) of its slice-image form
+int orbit_slices(const Geometry *g, bool cluster = true);
 size_t orbit_smem_bytes();                      // shared memory of one orbit block
 bool quad_ok(const Geometry *g);                // the view-pair projector serves this geometry
 // TV prox tiles of one image spread over n_sm blocks (k_tv.cu's rule)
@@ -357,14 +360,15 @@ void launch_band_reduce(const Geometry *g, const float *partial, float *out, int
                         cudaStream_t st);
 // Backprojection; mode 0: out = A^T y; mode 1: out = xin - tau*A^T y with
 // tau = (float)scal[S_TAU].  The orbit form adds its base-view slices in a
-// thread-block cluster and needs no scratch (`partial` is unused); the
-// persistent batched kernel's orbit phase writes slice images of
-// orbit_partial_floats() floats instead.
+// thread-block cluster (cluster, or partial NULL), or through slice images
+// in `partial` (orbit_partial_floats() floats) and a reduction pass: the
+// form for solves run side by side, whose clusters would wait for a GPC's
+// SMs to free together.
 bool orbit_ok(const Geometry *g);
 size_t orbit_partial_floats(const Geometry *g, int batch);
 bool orbit_slices_ok(const Geometry *g, int nsl);
 void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
-                              const double *scal, int batch, float *partial, cudaStream_t st);
+                              const double *scal, int batch, float *partial, cudaStream_t st, bool cluster = true);
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,
                         const float *xin, const double *scal, int batch, cudaStream_t st);
 

@@ -619,7 +619,7 @@ k_backproject_orbit_cl(const float *__restrict__ y, const float4 *__restrict__ t
                              : k == 1 ? (size_t)c * N + (N - 1 - rj)
                              : k == 2 ? (size_t)(N - 1 - rj) * N + (N - 1 - c)
                                       : (size_t)(N - 1 - c) * N + rj;
-            o_img[o] = mode ? x_img[o] - tau * t : t;
+            o_img[o] = mode ? __fmaf_rn(-tau, t, x_img[o]) : t;
         }
     }
     cl.sync();   // no block leaves while its partial sums may still be read
@@ -630,6 +630,22 @@ static size_t orbit_smem()
     return sizeof(float) * 2 * ORB_VC * 8 * ORB_RW + sizeof(float4) * 2 * ORB_VC + sizeof(int) * 2 * ORB_MAXS;
 }
 
+// out = sum of the slice images (mode 0), or xin - tau * sum (mode 1)
+template <int MODE>
+__global__ void k_orbit_reduce(const float *__restrict__ partial, float *__restrict__ out, const float *xin,
+                               const double *__restrict__ scal, size_t NN, int nsl)
+{
+    pdl_wait();
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= NN) return;
+    const float *pp = partial + (size_t)blockIdx.y * nsl * NN + i;
+    float t = pp[0];
+    for (int s = 1; s < nsl; ++s) t += pp[s * NN];
+    const size_t o = (size_t)blockIdx.y * NN + i;
+    if (MODE == 0) out[o] = t;
+    else out[o] = __fmaf_rn(-fscal(scal, F_TAU), t, xin[o]);   // one rounding, as every form of z
+}
+
 bool orbit_ok(const Geometry *g) { return g->orbit; }
 size_t orbit_partial_floats(const Geometry *g, int batch) { return (size_t)ORB_SL_MAX * g->n * g->n * batch; }
 
@@ -638,30 +654,40 @@ bool orbit_slices_ok(const Geometry *g, int nsl)
 {
     return nsl >= 1 && nsl <= ORB_SL_MAX && (g->n_views / 2 + nsl - 1) / nsl <= ORB_MAXS;
 }
-int orbit_slices(const Geometry *g) { return g->tune_orb > 0 ? g->tune_orb : ORB_SL; }
+int orbit_slices(const Geometry *g, bool cluster)
+{
+    const int t = cluster ? g->tune_orb : g->tune_orb_si;
+    return t > 0 ? t : ORB_SL;
+}
 size_t orbit_smem_bytes() { return orbit_smem(); }
 bool quad_ok(const Geometry *g) { return g->vpair && g->n % (2 * MR) == 0 && g->n + 3 <= PROJ_CW; }
 
 void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
-                              const double *scal, int batch, float *partial, cudaStream_t st)
+                              const double *scal, int batch, float *partial, cudaStream_t st, bool cluster)
 {
     const int q = g->n / 2;
-    const int nsl = orbit_slices(g);
+    const bool cl = cluster || !partial;
+    const int nsl = orbit_slices(g, cl);
     dim3 grd((q + ORB_T - 1) / ORB_T, (q + ORB_T - 1) / ORB_T, nsl * batch);
     const bool al = g->n_bins % 4 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
-    counted();
-    if (nsl > 1) {
+    if (nsl > 1 && cl) {
         // several slices: their sums are added in a cluster of the slices' blocks
+        counted();
         launch_kernel_cluster(al ? k_backproject_orbit_cl<true> : k_backproject_orbit_cl<false>, grd,
                               dim3(ORB_T, ORB_TY), orbit_smem(), st, dim3(1, 1, nsl), y, (const float4 *)g->d_trig,
                               g->n, g->n_views, g->n_bins, nsl, mode != 0 ? 1 : 0, out, xin, scal);
         return;
     }
-    // one slice: the block's sums are complete and it writes the result
+    // one slice: the block's sums are complete and it writes the result;
+    // several slices without a cluster: slice images, then k_orbit_reduce
+    const int fin = nsl == 1 ? 1 + (mode != 0) : 0;
+    counted(fin ? 1 : 2);
     launch_kernel(al ? k_backproject_orbit<true> : k_backproject_orbit<false>, grd, dim3(ORB_T, ORB_TY), orbit_smem(),
-                  st, y, (float *)nullptr, g->d_trig, g->n, g->n_views, g->n_bins, nsl, 1 + (mode != 0), out, xin,
-                  scal);
-    (void)partial;
+                  st, y, partial, g->d_trig, g->n, g->n_views, g->n_bins, nsl, fin, out, xin, scal);
+    if (fin) return;
+    const size_t NN = (size_t)g->n * g->n;
+    launch_kernel(mode == 0 ? k_orbit_reduce<0> : k_orbit_reduce<1>, dim3((unsigned)((NN + 255) / 256), batch),
+                  dim3(256), 0, st, (const float *)partial, out, xin, scal, NN, nsl);
 }
 
 void launch_backproject(const Geometry *g, const float *y, float *out, int mode,

@@ -125,7 +125,7 @@ __device__ __forceinline__ void run_item(const PSlice &S, int p, int k, int i, u
             const float *pp = S.orb + q;
             float t = pp[0];
             for (int s = 1; s < S.nsl; ++s) t += pp[s * NN];
-            S.z[q] = S.x[q] - tau * t;
+            S.z[q] = __fmaf_rn(-tau, t, S.x[q]);
         }
     } else if (p == PH_TV) {
         // x^{k+1} = prox(z): one tile per group, the dual field read from
@@ -251,7 +251,7 @@ int batched_form() { return g_form.load(); }
 bool persistent_slice_ok(const Geometry *g, const ct_pdtv_params *p, int iters0)
 {
     const int ntv = p->tv_iters > 0 ? p->tv_iters : 10;
-    return g->orbit && quad_ok(g) && fft_supported(g) && orbit_slices_ok(g, orbit_slices(g)) &&
+    return g->orbit && quad_ok(g) && fft_supported(g) && orbit_slices_ok(g, orbit_slices(g, false)) &&
            (p->precond == 0 || p->precond == 1 || p->precond == 3) && !(p->eps > 0.0) && ntv <= TV_MAX_STEPS &&
            p->iters == iters0 && p->iters > 0 && !p->resume;
 }
@@ -287,7 +287,7 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.n_col_items = g->n_col_items;
             S.qgroups = (g->n_row_items + QUAD_PG - 1) / QUAD_PG + (g->n_col_items + QUAD_PG - 1) / QUAD_PG;
             S.qrows4 = 0;   // 1024 threads: two steps per pass
-            S.nsl = orbit_slices(g);
+            S.nsl = orbit_slices(g, false);
             S.q16 = (g->n / 2 + ORB_T - 1) / ORB_T;
             S.orb_smem = (int)a16(orbit_smem_bytes());
             S.dual_smem = (int)a16(dual_fft_smem(g));
