@@ -184,6 +184,7 @@ bool toeplitz_eig(const double *t, int n, double *q, double *lambda)
 // ---------------------------------------------------------------------
 constexpr int EG_T = 32;    // output tile (views x columns) and K tile
 constexpr int EG_KS = 8;    // most K chunks of the split GEMM
+constexpr int EG_PF = 4;    // K tiles whose global loads are in flight together
 
 // K chunks: enough blocks for about two per SM (few views give few tiles)
 int eps_ksplit(const Geometry *g)
@@ -207,31 +208,52 @@ k_eps_gemm(const float *__restrict__ X, const float *__restrict__ Q, const float
     const int v0 = blockIdx.y * EG_T, c0 = blockIdx.x * EG_T;
     const int kb = blockIdx.z * kchunk, ke = min(B, kb + kchunk);
     float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    for (int k0 = kb; k0 < ke; k0 += EG_T) {
-        for (int i = ty; i < EG_T; i += 16)
-            for (int j = tx; j < EG_T; j += 16) {
+    // the K tiles of the chunk go through shared memory one at a time, but
+    // the global loads of up to EG_PF of them are issued before the first
+    // is stored, so that their L2 round trips overlap
+    for (int kg = kb; kg < ke; kg += EG_PF * EG_T) {
+        float xr[EG_PF][4], qr[EG_PF][4];
+#pragma unroll
+        for (int t = 0; t < EG_PF; ++t) {
+            const int k0 = kg + t * EG_T;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = ty + 16 * (e >> 1), j = tx + 16 * (e & 1);
                 const int v = v0 + i, k = k0 + j;
-                xs[i][j] = (v < V && k < ke) ? X[(size_t)v * B + k] * (s ? s[k] : 1.0f) : 0.0f;
-                // qs[kk][cc] = Qop[k0 + kk][c0 + cc]
+                xr[t][e] = (k0 < ke && v < V && k < ke) ? X[(size_t)v * B + k] * (s ? s[k] : 1.0f) : 0.0f;
+                // the element qs[.][.] of this (i, j) below: Q[c][kk] read along kk (TRANS), Q[kk][c] along c
                 if (TRANS) {
-                    const int c = c0 + i, kk = k0 + j;   // Q[c][kk], read along kk
-                    qs[j][i] = (c < B && kk < ke) ? Q[(size_t)c * B + kk] : 0.0f;
+                    const int c = c0 + i, kk = k0 + j;
+                    qr[t][e] = (k0 < ke && c < B && kk < ke) ? Q[(size_t)c * B + kk] : 0.0f;
                 } else {
-                    const int kk = k0 + i, c = c0 + j;   // Q[kk][c], read along c
-                    qs[i][j] = (c < B && kk < ke) ? Q[(size_t)kk * B + c] : 0.0f;
+                    const int kk = k0 + i, c = c0 + j;
+                    qr[t][e] = (k0 < ke && c < B && kk < ke) ? Q[(size_t)kk * B + c] : 0.0f;
                 }
             }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < EG_T; ++kk) {
-            const float x0 = xs[ty][kk], x1 = xs[ty + 16][kk];
-            const float q0 = qs[kk][tx], q1 = qs[kk][tx + 16];
-            acc[0][0] = fmaf(x0, q0, acc[0][0]);
-            acc[0][1] = fmaf(x0, q1, acc[0][1]);
-            acc[1][0] = fmaf(x1, q0, acc[1][0]);
-            acc[1][1] = fmaf(x1, q1, acc[1][1]);
         }
-        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < EG_PF; ++t) {
+            if (kg + t * EG_T >= ke) break;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = ty + 16 * (e >> 1), j = tx + 16 * (e & 1);
+                xs[i][j] = xr[t][e];
+                // qs[kk][cc] = Qop[k0 + kk][c0 + cc]
+                if (TRANS) qs[j][i] = qr[t][e];
+                else qs[i][j] = qr[t][e];
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < EG_T; ++kk) {
+                const float x0 = xs[ty][kk], x1 = xs[ty + 16][kk];
+                const float q0 = qs[kk][tx], q1 = qs[kk][tx + 16];
+                acc[0][0] = fmaf(x0, q0, acc[0][0]);
+                acc[0][1] = fmaf(x0, q1, acc[0][1]);
+                acc[1][0] = fmaf(x1, q0, acc[1][0]);
+                acc[1][1] = fmaf(x1, q1, acc[1][1]);
+            }
+            __syncthreads();
+        }
     }
     float *pz = part + (size_t)blockIdx.z * V * B;
 #pragma unroll
