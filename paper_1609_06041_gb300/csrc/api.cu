@@ -884,7 +884,12 @@ ct_status ctpd::pdtv_solve(const ct_geometry *g, const float *b, const float *w,
                 }
                 backproject(mubar, out, 0, nullptr);
             };
-            lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, S_LZ, S_LN0, partials, ticket, S_NADA, st);
+            {
+                // its projector and backprojector launches, like the loop's, may start as their
+                // predecessors finish (each waits for it before any memory access)
+                PdlScope pdl(true);
+                lanczos_norm(op_ada, z, uimg, w3img, J, nlz, scal, S_LZ, S_LN0, partials, ticket, S_NADA, st);
+            }
             if (fk) fork_end(fk, st);
         }
         launch_scalars(scal, SC_SIGMA, prm->sigma, rho, 0, mode, st);
