@@ -53,6 +53,7 @@ struct Geometry {
     int tune_orb_si;      // the same for the slice-image form (solves side by side, the persistent kernel)
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     int tune_qbal;        // projector form: 1 band pair per block, 2 work-balanced ranges (0: the rule)
+    int qbal_occ[2][17];  // blocks per SM of the work-balanced projector by (4 steps per pass, items); 0: not queried
     double *h_angles;     // host copy
     void *eps_cache;      // eigenbases of D for the error-tolerant form (eps.cu)
     void *graph_cache;    // instantiated CUDA graphs of repeated solves (api.cu)

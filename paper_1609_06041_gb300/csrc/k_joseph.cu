@@ -378,9 +378,14 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
             const long long total = U.u_z * batch;
             const size_t smem2 = quad_smem(N) + 16;
             auto kern = rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
-            int occ = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem2) != cudaSuccess || occ < 1)
-                occ = 1;
+            // blocks per SM, queried once per (steps per pass, items) for the geometry
+            int &occ_slot = const_cast<Geometry *>(g)->qbal_occ[rows4][pgb];
+            int occ = occ_slot;
+            if (occ < 1) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem2) != cudaSuccess || occ < 1)
+                    occ = 1;
+                occ_slot = occ;
+            }
             const long long by_work = (total + 4 * pgb - 1) / (4 * pgb);   // two units per warp
             const int blocks = (int)std::max(1LL, std::min((long long)g->n_sm * occ, by_work));
             launch_kernel(kern, dim3(blocks), dim3(threads), smem2, st, x, g->d_views, g->d_row_items,
