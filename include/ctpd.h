@@ -342,6 +342,12 @@ size_t ct_pdtv_workspace_bytes(const ct_geometry *geom, const ct_pdtv_params *pa
  * b: V x B line integrals.  w: V x B statistical weights W = diag(w), w > 0
  * (CT_LOWDOSE; NULL for CT_FEWVIEW).  x_out: N x N, receives x^K (with
  * params->resume it must hold the x of the resumed state).
+ * b, w and x_out are device memory or page-locked host memory (pageable
+ * host memory: CT_ERR_ARG).  Host buffers are copied stream-ordered
+ * through a staging area of the workspace: b and w (and x_out with resume)
+ * before the solve, x^K into a host x_out after it, which then holds it
+ * once the stream has reached that copy (before the call returns when a
+ * report is asked for).
  * Input checks: b and w live on the device, so a device pass checks them
  * (w > 0 and finite, b finite) and the result (x^K and mu^K finite) and records what
  * it finds in the workspace.  The result comes back at the next

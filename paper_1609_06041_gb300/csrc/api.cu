@@ -127,7 +127,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace layout of one solve (offsets in bytes, 256-aligned).
 struct Layout {
     size_t scal, partials, taps, hhat, taps2, hhat2, sv, winv, mu, mubar, r, z, u, w3, p0, p1, band, orb, aux, eps,
-        total;
+        stage, total;
 };
 
 Layout layout(const Geometry *g, const ct_pdtv_params *prm)
@@ -155,6 +155,8 @@ Layout layout(const Geometry *g, const ct_pdtv_params *prm)
     L.band = o;     o += align256(sizeof(float) * (size_t)proj_bands(g->n) * I);
     L.orb = o;      o += align256(sizeof(float) * (orbit_ok(g) ? orbit_partial_floats(g, 1) : 1));
     L.aux = o;      o += align256(sizeof(float) * 2 * I);   // the sinogram-side Lanczos, run beside the image side
+    // device copies of page-locked host b, w and x (ct_pdtv_solve with host buffers)
+    L.stage = o;    o += align256(sizeof(float) * (2 * I + J));
     // error-tolerant form: s, w2 and the split-K partial sums of its maps
     L.eps = o;
     if (prm && prm->eps > 0.0) o += align256(sizeof(float) * (2 * (size_t)g->n_bins + eps_partial_floats(g)));
@@ -702,9 +704,22 @@ size_t ct_pdtv_workspace_bytes(const ct_geometry *g, const ct_pdtv_params *p)
     return layout(g, p).total;
 }
 
-ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
-                        const ct_pdtv_params *prm, float *x_out, void *workspace,
-                        ct_pdtv_report *report, void *stream)
+// Where a buffer lives: 0 device (or managed) memory, 1 page-locked host
+// memory, -1 memory the device cannot copy from asynchronously (pageable).
+static int buffer_kind(const void *p)
+{
+    if (!p) return 0;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
+    return a.type == cudaMemoryTypeHost ? 1 : -1;
+}
+
+static ct_status solve_device(const ct_geometry *g, const float *b, const float *w, const ct_pdtv_params *prm,
+                              float *x_out, void *workspace, ct_pdtv_report *report, void *stream)
 {
     // a repeat of an earlier call replays that call's CUDA graph (the
     // error-tolerant form once D's eigenbasis is cached: its first solve
@@ -713,6 +728,58 @@ ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
         (!(prm->eps > 0.0) || eps_basis_ready(g, prm->precond, prm->tau)))
         return solve_graph(g, b, w, prm, x_out, workspace, stream);
     return ctpd::pdtv_solve(g, b, w, prm, x_out, workspace, report, stream, true);
+}
+
+ct_status ct_pdtv_solve(const ct_geometry *g, const float *b, const float *w,
+                        const ct_pdtv_params *prm, float *x_out, void *workspace,
+                        ct_pdtv_report *report, void *stream)
+{
+    const int kb = buffer_kind(b), kw = buffer_kind(w), kx = buffer_kind(x_out);
+    if (kb < 0 || kw < 0 || kx < 0)
+        return fail(CT_ERR_ARG, "ct_pdtv_solve: host buffers must be page-locked (cudaHostAlloc, cudaHostRegister)");
+    if (!(kb || kw || kx) || !g || !prm || !b || !x_out) return solve_device(g, b, w, prm, x_out, workspace, report, stream);
+    // page-locked host buffers: stream-ordered copies to and from the
+    // workspace's staging area around the device solve
+    g_err[0] = 0;
+    const Layout L = layout(g, prm);
+    const size_t I = (size_t)g->n_views * g->n_bins, J = (size_t)g->n * g->n;
+    cudaStream_t st = S(stream);
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    if (!ws) {
+        if (prm->resume) return fail(CT_ERR_ARG, "ct_pdtv_solve: resume needs the workspace");
+        if (cudaMallocAsync((void **)&ws, L.total, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CT_ERR_OOM, "ct_pdtv_solve: workspace allocation failed");
+        }
+        owned = true;
+    }
+    float *bd = (float *)(ws + L.stage), *wd = bd + I, *xd = wd + I;
+    const float *b_use = b, *w_use = w;
+    float *x_use = x_out;
+    cudaError_t e = cudaSuccess;
+    if (kb) {
+        e = cudaMemcpyAsync(bd, b, sizeof(float) * I, cudaMemcpyHostToDevice, st);
+        b_use = bd;
+    }
+    if (kw && e == cudaSuccess) {
+        e = cudaMemcpyAsync(wd, w, sizeof(float) * I, cudaMemcpyHostToDevice, st);
+        w_use = wd;
+    }
+    if (kx) {
+        if (prm->resume && e == cudaSuccess) e = cudaMemcpyAsync(xd, x_out, sizeof(float) * J, cudaMemcpyHostToDevice, st);
+        x_use = xd;
+    }
+    ct_status cs = e == cudaSuccess ? solve_device(g, b_use, w_use, prm, x_use, ws, report, stream)
+                                    : fail(CT_ERR_CUDA, "ct_pdtv_solve: host copy: %s", cudaGetErrorString(e));
+    if (kx && cs == CT_OK) {
+        e = cudaMemcpyAsync(x_out, xd, sizeof(float) * J, cudaMemcpyDeviceToHost, st);
+        // the report path synchronises: x_out is then ready when the call returns
+        if (e == cudaSuccess && report) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) cs = fail(CT_ERR_CUDA, "ct_pdtv_solve: host copy: %s", cudaGetErrorString(e));
+    }
+    if (owned) cudaFreeAsync(ws, st);
+    return cs;
 }
 
 }  // extern "C"

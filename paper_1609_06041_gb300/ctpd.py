@@ -1,7 +1,8 @@
 """Thin Python binding of libctpd.so (include/ctpd.h), one function per C
-entry point with the same name.  Arguments are torch CUDA tensors; this
-module only checks shapes and passes raw device pointers and the current
-CUDA stream.  All arithmetic runs in the library's CUDA kernels; there is no
+entry point with the same name.  Arguments are torch CUDA tensors (and, for
+ct_pdtv_solve's b, w and x_out, page-locked CPU tensors, which the library
+copies through the solve's workspace); this module only checks shapes and
+passes raw pointers and the current CUDA stream.  All arithmetic runs in the library's CUDA kernels; there is no
 CPU or PyTorch fallback: a missing library raises at import time.
 """
 from __future__ import annotations
@@ -111,6 +112,19 @@ def _dev(t, name, shape_tail=None):
     if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected (..., {shape_tail})")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _buf(t, name, shape_tail=None):
+    """A CUDA tensor, or a page-locked CPU tensor (the solve copies it through its workspace)."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError(f"{name}: a CPU tensor must be page-locked (pin_memory())")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous float32")
+        if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected (..., {shape_tail})")
+        return ctypes.c_void_p(t.data_ptr())
+    return _dev(t, name, shape_tail)
 
 
 def _batch(t, ndim_tail):
@@ -349,15 +363,17 @@ def ct_pdtv_solve(g: Geometry, b: torch.Tensor, w: torch.Tensor | None, params: 
                   x_out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
                   report: bool = True, trace: bool = False):
     """Algorithm 1 / 1' / 2.  Returns (x, report dict or None).
+    b, w, x_out: CUDA tensors or page-locked CPU tensors (a CPU x is ready
+    once the stream has finished the call; at return when report is True).
     `workspace` (uint8 CUDA tensor of ct_pdtv_workspace_bytes) holds the
     iteration state for params.resume.  trace (needs report): the report's
     "trace" lists the cost of Eq. 1 (low-dose) or ||Ax - b|| (few-view)
     after each iteration."""
-    pb = _dev(b, "b", (g.n_views, g.n_bins))
-    pw = None if w is None else _dev(w, "w", (g.n_views, g.n_bins))
+    pb = _buf(b, "b", (g.n_views, g.n_bins))
+    pw = None if w is None else _buf(w, "w", (g.n_views, g.n_bins))
     if x_out is None:
-        x_out = torch.empty(g.n, g.n, device=b.device, dtype=torch.float32)
-    px = _dev(x_out, "x_out", (g.n, g.n))
+        x_out = torch.empty(g.n, g.n, device=b.device, dtype=torch.float32, pin_memory=not b.is_cuda)
+    px = _buf(x_out, "x_out", (g.n, g.n))
     pws = None
     if workspace is not None:
         if not workspace.is_cuda or workspace.numel() * workspace.element_size() < ct_pdtv_workspace_bytes(g, params):
