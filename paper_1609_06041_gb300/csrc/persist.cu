@@ -3,7 +3,7 @@
 // Each slice's iteration (Steps 1-3 of Algorithm 1 / Algorithm 2, Secs. 2.3
 // and 3) is a chain of phases: A^T with the primal step (orbit tiles, plus
 // the slice reduction when the base views are split), the TV prox (tiles),
-// A (band pair x view group blocks) and the dual update with the next
+// A (ranges of band pair x view pair x ray units) and the dual update with the next
 // Step 1 (view pairs).  A phase of one slice may start only when the
 // slice's previous phase is complete; different slices are independent.
 //
@@ -24,7 +24,7 @@
 // make the slice's finished writes visible to the block's loads.
 //
 // The item bodies are those of the single-slice kernels (body_*.cuh), run
-// by the whole 1024-thread block (the projector with 16 view-pair items) or
+// by the whole 1024-thread block (the work-balanced projector's unit ranges) or
 // by groups with their own named barriers (eight 128-thread orbit tiles,
 // four 256-thread view pairs of the dual update, two 512-thread TV tiles),
 // so A, A^T and the dual update keep the 32 warps per SM of their own
@@ -60,7 +60,7 @@ static_assert(ORB_GROUPS * ORB_TH == PS_THREADS && DUAL_GROUPS * FFT_T == PS_THR
 
 struct PSlice {
     int N, V, B, P, nb, lowdose, al;
-    int n_row_items, n_col_items, qgroups, qrows4;
+    int n_row_items, n_col_items, qseg;   // qseg: one projector item per staged band pair (segment)
     int nsl, q16, orb_smem, dual_smem;
     int tv_tc, tv_tr, tv_ncb, tv_nrb, ntv, fgp;
     int n_items[PH_N], pre[PH_N], per_iter;
@@ -144,10 +144,28 @@ __device__ __forceinline__ void run_item(const PSlice &S, int p, int k, int i, u
                                       S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
         }
     } else if (p == PH_QUAD) {
-        // band partial sums of A x^{k+1}
-        const int nbp = S.N / (2 * MR), bx = i % nbp, by = i / nbp;
-        quad_body<2, false>(BlockCtx{}, bx, by, 0, nbp, psm, S.x, S.views, S.row_items, S.n_row_items, S.col_items,
-                            S.n_col_items, S.N, S.V, S.B, QUAD_PG, 1, S.band);
+        // band partial sums of A x^{k+1}: item i takes the i-th of the
+        // phase's equal ranges of (band pair, view pair, 64-ray) units, as a
+        // block of the work-balanced projector does
+        const int npair = (S.B + 1) / 2;
+        QuadUnits U;
+        U.nch = (npair + 63) / 64;
+        U.u_rows = S.n_row_items * U.nch;
+        U.u_cols = S.n_col_items * U.nch;
+        U.u_z = (long long)(S.N / (2 * MR)) * (U.u_rows + U.u_cols);
+        const long long nq = S.n_items[PH_QUAD];
+        long long u0 = U.u_z * i / nq, u1 = U.u_z * (i + 1) / nq;
+        if (S.qseg) {
+            // small slices: item i is segment i (row-class band pairs, then column-class)
+            const int nbp = S.N / (2 * MR);
+            const bool rows = i < nbp;
+            const int bp = rows ? i : i - nbp;
+            u0 = rows ? (long long)bp * U.u_rows : (long long)nbp * U.u_rows + (long long)bp * U.u_cols;
+            u1 = u0 + (rows ? U.u_rows : U.u_cols);
+        }
+        quad_balanced_body<2, true>(BlockCtx{}, u0, u1, U, psm,
+                                    reinterpret_cast<int *>(psm + quad_smem(S.N)), S.x, S.views, S.row_items,
+                                    S.col_items, S.N, S.V, S.B, S.band);
     } else if (p == PH_DUAL) {
         // residual, Step 3 and the next Step 1 for one view pair per group
         const int g = tid / FFT_T, vp = i * DUAL_GROUPS + g;
@@ -285,8 +303,6 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.al = g->n_bins % 4 == 0;   // workspace buffers are 256-byte aligned
             S.n_row_items = g->n_row_items;
             S.n_col_items = g->n_col_items;
-            S.qgroups = (g->n_row_items + QUAD_PG - 1) / QUAD_PG + (g->n_col_items + QUAD_PG - 1) / QUAD_PG;
-            S.qrows4 = 0;   // 1024 threads: two steps per pass
             S.nsl = orbit_slices(g, false);
             S.q16 = (g->n / 2 + ORB_T - 1) / ORB_T;
             S.orb_smem = (int)a16(orbit_smem_bytes());
@@ -300,7 +316,17 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.n_items[PH_ORBIT] = (S.q16 * S.q16 * S.nsl + ORB_GROUPS - 1) / ORB_GROUPS;
             S.n_items[PH_OREDUCE] = S.nsl > 1 ? (int)(((size_t)g->n * g->n + RED_PIX - 1) / RED_PIX) : 0;
             S.n_items[PH_TV] = (S.tv_ncb * S.tv_nrb + TV_GROUPS - 1) / TV_GROUPS;
-            S.n_items[PH_QUAD] = (g->n / (2 * MR)) * S.qgroups;
+            {
+                // projector items: ranges of about 228 units (the share of one block of the
+                // work-balanced projector at 512^2 / 720 views), at most one per SM; slices
+                // with fewer such ranges than staged band pairs take one item per band pair
+                const int nbp = g->n / (2 * MR);
+                const long long nch = ((g->n_bins + 1) / 2 + 63) / 64;
+                const long long u_z = (long long)nbp * (g->n_row_items + g->n_col_items) * nch;
+                const long long nr = (u_z + 227) / 228;
+                S.qseg = nr <= 2 * nbp;
+                S.n_items[PH_QUAD] = S.qseg ? 2 * nbp : (int)std::min((long long)g->n_sm, nr);
+            }
             S.n_items[PH_DUAL] = ((g->n_views + 1) / 2 + DUAL_GROUPS - 1) / DUAL_GROUPS;
             S.per_iter = 0;
             for (int q = 0; q < PH_N; ++q) {
@@ -325,7 +351,7 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.orb = sb.orb;
             S.scal = sb.scal;
             const size_t tv_smem = sizeof(float2) * 2 * (TV_ROWS + 2) * 32 * TV_GROUPS;
-            smem = std::max({smem, (size_t)ORB_GROUPS * S.orb_smem, tv_smem, quad_smem(g->n),
+            smem = std::max({smem, (size_t)ORB_GROUPS * S.orb_smem, tv_smem, quad_smem(g->n) + 16,
                              (size_t)DUAL_GROUPS * S.dual_smem});
             n_sm = std::max(n_sm, g->n_sm);
         }
