@@ -30,10 +30,11 @@ __host__ __device__ __forceinline__ int tv_halo(int steps, bool even) { return e
 // (momentum restarted at every call).  Each cell keeps p_prev as well, and
 // the field published for the divergence is r_y (p_y after the last step).
 // Body of tile (bx, by) of image bz of a batch of gz images, on the
-// TV_THREADS threads of context cb; pub_x and pub_y: (TV_ROWS + 2) * 32
+// TV_THREADS threads of context cb; J rows per warp (the region holds
+// TV_WARPS J rows, TV_ROWS by default); pub_x and pub_y: (TV_WARPS J + 2) * 32
 // float2 of shared memory each (row li of the region at index
 // (li + 1) * 32 + lane; rows -1 and beyond the region read zeros).
-template <bool FGP, bool TRAJ, class Ctx>
+template <bool FGP, bool TRAJ, class Ctx, int J = TV_J>
 __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, int gz, float2 *pub_x, float2 *pub_y,
                                         const float *z, const float *p_in, float *p_out, float *x, int N,
                                         int steps, int final_, int tc, int tr, const double *scal, float *traj)
@@ -55,15 +56,15 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
     const bool cx0 = (unsigned)c0 < (unsigned)(N - 1), cx1 = (unsigned)(c0 + 1) < (unsigned)(N - 1);
     const bool cy0 = (unsigned)c0 < (unsigned)N, cy1 = (unsigned)(c0 + 1) < (unsigned)N;
 
-    for (int i = cb.tid(); i < (TV_ROWS + 2) * 32; i += TV_THREADS) {
+    for (int i = cb.tid(); i < (TV_WARPS * J + 2) * 32; i += TV_THREADS) {
         pub_x[i] = make_float2(0.0f, 0.0f);
         pub_y[i] = make_float2(0.0f, 0.0f);
     }
-    float zr[TV_J][2], pxr[TV_J][2], pyr[TV_J][2], xr[TV_J][2];
-    float pxo[TV_J][2], pyo[TV_J][2];   // FGP: p of the previous step
+    float zr[J][2], pxr[J][2], pyr[J][2], xr[J][2];
+    float pxo[J][2], pyo[J][2];   // FGP: p of the previous step
     unsigned rowx = 0, rowy = 0;   // bit j: row in the image / row with a y difference
 #pragma unroll
-    for (int j = 0; j < TV_J; ++j) {
+    for (int j = 0; j < J; ++j) {
         const int li = w + TV_WARPS * j, rr = R0 + li;
         const bool rin = li < Sr && (unsigned)rr < (unsigned)N;
         const bool ryd = li < Sr && (unsigned)rr < (unsigned)(N - 1);
@@ -82,7 +83,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
         }
     }
 #pragma unroll
-    for (int j = 0; j < TV_J; ++j) {
+    for (int j = 0; j < J; ++j) {
         pxo[j][0] = pxr[j][0];
         pxo[j][1] = pxr[j][1];
         pyo[j][0] = pyr[j][0];
@@ -90,7 +91,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
     }
     cb.sync();
 #pragma unroll
-    for (int j = 0; j < TV_J; ++j) {
+    for (int j = 0; j < J; ++j) {
         const int li = w + TV_WARPS * j;
         if (li < Sr) pub_y[(li + 1) * 32 + lane] = make_float2(pyr[j][0], pyr[j][1]);
     }
@@ -101,7 +102,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
         for (int it = 0; it < steps; ++it) {
             // x = max(0, z + lam div r), r = p (GP) or p + theta (p - p_prev) (FGP)
 #pragma unroll
-            for (int j = 0; j < TV_J; ++j) {
+            for (int j = 0; j < J; ++j) {
                 const int li = w + TV_WARPS * j;
                 if (li < Sr) {
                     const float2 pa = pub_y[li * 32 + lane];   // r_y of row li - 1
@@ -125,7 +126,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
             const bool last = it + 1 == steps;
             // p = Pi(p + grad x / (8 lam)), Pi(q) = q / max(1, |q|)
 #pragma unroll
-            for (int j = 0; j < TV_J; ++j) {
+            for (int j = 0; j < J; ++j) {
                 const int li = w + TV_WARPS * j;
                 if (li < Sr) {
                     const float2 xb = pub_x[(li + 2) * 32 + lane];   // x of row li + 1
@@ -164,7 +165,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
             if (TRAJ && !last) {   // the tile interior's p after this step
                 float *tp = traj + ((size_t)it * gz + img) * 2 * NN;
 #pragma unroll
-                for (int j = 0; j < TV_J; ++j) {
+                for (int j = 0; j < J; ++j) {
                     const int li = w + TV_WARPS * j, rr = R0 + li;
                     if (li >= H && li < H + tr && rr < N) {
                         if (vec2) {   // H, tc even: both columns of the pair are interior, or neither
@@ -196,7 +197,7 @@ __device__ __forceinline__ void tv_body(const Ctx &cb, int bx, int by, int bz, i
 
     // the tile interior: p, and x = max(0, z + lam div p) on the last chunk
 #pragma unroll
-    for (int j = 0; j < TV_J; ++j) {
+    for (int j = 0; j < J; ++j) {
         const int li = w + TV_WARPS * j, rr = R0 + li;
         if (li >= H && li < H + tr && rr < N) {
             const float2 pa = pub_y[li * 32 + lane];

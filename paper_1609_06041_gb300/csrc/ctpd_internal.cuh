@@ -330,7 +330,7 @@ int orbit_slices(const Geometry *g, bool cluster = true);
 size_t orbit_smem_bytes();                      // shared memory of one orbit block
 bool quad_ok(const Geometry *g);                // the view-pair projector serves this geometry
 // TV prox tiles of one image spread over n_sm blocks (k_tv.cu's rule)
-void tv_tile_shape(int n, int steps, int n_sm, int min_rows, int *tc, int *tr, int *ncb, int *nrb);
+void tv_tile_shape(int n, int steps, int n_sm, int min_rows, int *tc, int *tr, int *ncb, int *nrb, int rows = 0);
 size_t dual_fft_smem(const Geometry *g);
 // Device pointers into a solve workspace (api.cu's layout).
 struct SolveBuffers {

@@ -36,13 +36,13 @@ struct TvTiles {
 // Column tiles are as wide as the region allows; rows are split so that the
 // tiles of one image about fill the GPU once (one block per SM), but no
 // narrower than TV_MIN_TR rows and no taller than the region.
-static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr, bool even = false)
+static TvTiles tv_tiles(int N, int steps, int n_sm, int min_tr, bool even = false, int rows = TV_ROWS)
 {
     const int H = tv_halo(steps, even);
     TvTiles t;
     t.tc = 64 - 2 * H;
     t.ncb = (N + t.tc - 1) / t.tc;
-    const int tr_max = TV_ROWS - 2 * H;
+    const int tr_max = rows - 2 * H;
     int nrb = std::max(1, n_sm / t.ncb);
     nrb = std::min(nrb, (N + min_tr - 1) / min_tr);
     nrb = std::max(nrb, (N + tr_max - 1) / tr_max);
@@ -64,9 +64,10 @@ k_tv(const float *__restrict__ z, const float *__restrict__ p_in, float *__restr
                        N, steps, final_, tc, tr, scal, traj);
 }
 
-void tv_tile_shape(int n, int steps, int n_sm, int min_rows, int *tc, int *tr, int *ncb, int *nrb)
+void tv_tile_shape(int n, int steps, int n_sm, int min_rows, int *tc, int *tr, int *ncb, int *nrb, int rows)
 {
-    const TvTiles t = tv_tiles(n, steps, std::max(1, n_sm), min_rows > 0 ? min_rows : TV_MIN_TR);
+    const TvTiles t = tv_tiles(n, steps, std::max(1, n_sm), min_rows > 0 ? min_rows : TV_MIN_TR, false,
+                               rows > 0 ? rows : TV_ROWS);
     *tc = t.tc;
     *tr = t.tr;
     *ncb = t.ncb;

@@ -29,7 +29,7 @@
 // four 256-thread view pairs of the dual update, two 512-thread TV tiles),
 // so A, A^T and the dual update keep the 32 warps per SM of their own
 // kernels; the block's 64 registers per thread are fewer than the TV
-// prox's own kernel uses.  All counters live in the slices' scalar blocks,
+// prox's own kernel uses, so the prox here holds regions of 48 rows.  All counters live in the slices' scalar blocks,
 // which each slice's setup clears.
 #include <stdio.h>
 
@@ -54,6 +54,11 @@ constexpr int DUAL_GROUPS = PS_THREADS / FFT_T;    // view pairs per item
 constexpr int RED_PIX = PS_THREADS * 8;            // pixels per slice-reduction item
 constexpr int QUAD_PG = PS_THREADS / 64;           // projector view-pair items per block
 constexpr int TV_GROUPS = PS_THREADS / TV_THREADS; // TV tiles per item
+// rows per warp of the prox's region here: three (48 rows) rather than the
+// prox kernel's five, so that its cells fit the 64 registers a thread of a
+// 1024-thread block has (with five they spill), at more halo work
+constexpr int PS_TV_J = 3;
+constexpr int PS_TV_PUB = (TV_WARPS * PS_TV_J + 2) * 32;   // float2 per published field
 static_assert(TV_GROUPS * TV_THREADS == PS_THREADS && QUAD_PG == PG, "whole groups");
 static_assert(1 + ORB_GROUPS + DUAL_GROUPS + TV_GROUPS <= 16, "named barriers 1..15");
 static_assert(ORB_GROUPS * ORB_TH == PS_THREADS && DUAL_GROUPS * FFT_T == PS_THREADS, "whole groups");
@@ -132,16 +137,18 @@ __device__ __forceinline__ void run_item(const PSlice &S, int p, int k, int i, u
         // p[k & 1] and written to p[(k + 1) & 1]
         const int g = tid / TV_THREADS, j = i * TV_GROUPS + g;
         if (j < S.tv_ncb * S.tv_nrb) {
-            float2 *pub_x = reinterpret_cast<float2 *>(psm) + (size_t)g * 2 * (TV_ROWS + 2) * 32;
-            float2 *pub_y = pub_x + (TV_ROWS + 2) * 32;
+            float2 *pub_x = reinterpret_cast<float2 *>(psm) + (size_t)g * 2 * PS_TV_PUB;
+            float2 *pub_y = pub_x + PS_TV_PUB;
             const int bx = j % S.tv_ncb, by = j / S.tv_ncb;
             const GroupCtx c{tid % TV_THREADS, TV_THREADS, 1 + ORB_GROUPS + DUAL_GROUPS + g};
             if (S.fgp)
-                tv_body<true, false>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x, S.N,
-                                     S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
+                tv_body<true, false, GroupCtx, PS_TV_J>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1],
+                                                        S.p[(k + 1) & 1], S.x, S.N, S.ntv, 1, S.tv_tc, S.tv_tr,
+                                                        S.scal, nullptr);
             else
-                tv_body<false, false>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1], S.p[(k + 1) & 1], S.x, S.N,
-                                      S.ntv, 1, S.tv_tc, S.tv_tr, S.scal, nullptr);
+                tv_body<false, false, GroupCtx, PS_TV_J>(c, bx, by, 0, 1, pub_x, pub_y, S.z, S.p[k & 1],
+                                                         S.p[(k + 1) & 1], S.x, S.N, S.ntv, 1, S.tv_tc, S.tv_tr,
+                                                         S.scal, nullptr);
         }
     } else if (p == PH_QUAD) {
         // band partial sums of A x^{k+1}: item i takes the i-th of the
@@ -312,7 +319,7 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             // TV tiles: the batch's tiles together fill the GPU about twice
             // (tiling does not change the prox's values)
             tv_tile_shape(g->n, S.ntv, std::max(1, 2 * g->n_sm / m), g->tune_tv, &S.tv_tc, &S.tv_tr, &S.tv_ncb,
-                          &S.tv_nrb);
+                          &S.tv_nrb, TV_WARPS * PS_TV_J);
             S.n_items[PH_ORBIT] = (S.q16 * S.q16 * S.nsl + ORB_GROUPS - 1) / ORB_GROUPS;
             S.n_items[PH_OREDUCE] = S.nsl > 1 ? (int)(((size_t)g->n * g->n + RED_PIX - 1) / RED_PIX) : 0;
             S.n_items[PH_TV] = (S.tv_ncb * S.tv_nrb + TV_GROUPS - 1) / TV_GROUPS;
@@ -350,7 +357,7 @@ ct_status launch_persistent(int n, const ct_geometry *const *geoms, const float 
             S.band = sb.band;
             S.orb = sb.orb;
             S.scal = sb.scal;
-            const size_t tv_smem = sizeof(float2) * 2 * (TV_ROWS + 2) * 32 * TV_GROUPS;
+            const size_t tv_smem = sizeof(float2) * 2 * PS_TV_PUB * TV_GROUPS;
             smem = std::max({smem, (size_t)ORB_GROUPS * S.orb_smem, tv_smem, quad_smem(g->n) + 16,
                              (size_t)DUAL_GROUPS * S.dual_smem});
             n_sm = std::max(n_sm, g->n_sm);
