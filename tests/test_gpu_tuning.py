@@ -31,7 +31,7 @@ def test_operator_shapes_parity(N, V, B, items, rows, slices, form):
 
 
 @pytest.mark.parametrize("N,V,B,batch", [(64, 90, 95, 1), (96, 12, 140, 3), (64, 33, 93, 2), (128, 360, 185, 2),
-                                         (512, 720, 736, 1), (256, 180, 368, 5)])
+                                         (512, 720, 736, 1), (256, 180, 368, 5), (64, 1, 96, 2), (32, 3, 47, 1)])
 def test_projector_forms_agree_bit_for_bit(N, V, B, batch):
     # the work-balanced projector forms every band sum exactly as the
     # band-pair-per-block form does, whatever the items per block or the
