@@ -185,6 +185,7 @@ bool toeplitz_eig(const double *t, int n, double *q, double *lambda)
 constexpr int EG_T = 32;    // output tile (views x columns) and K tile
 constexpr int EG_KS = 8;    // most K chunks of the split GEMM
 constexpr int EG_PF = 4;    // K tiles whose global loads are in flight together
+constexpr int EPS_ROOT_T = 512;   // threads of the multiplier's solve
 
 // K chunks: enough blocks for about two per SM (few views give few tiles)
 int eps_ksplit(const Geometry *g)
@@ -339,7 +340,7 @@ __global__ void k_eps_w2(const float *__restrict__ W, int V, int B, float *__res
     w2[j] = a;
 }
 
-// One block; warp 0 solves.  se = sigma eps.  With u = 1 / c the condition
+// One block; each evaluation of f and g is spread over its threads.  se = sigma eps.  With u = 1 / c the condition
 // c |nu(c)| = se reads f(u) = sum_j W2_j / (u + l_j)^2 = se^2 (l_j =
 // max(lambda_j, 0); lambda = NULL: 1), the secular equation of a
 // trust-region step: f falls from f(0) (infinite when some l_j = 0 carries
@@ -349,22 +350,26 @@ __global__ void k_eps_w2(const float *__restrict__ W, int V, int B, float *__res
 // overshooting (Hebden; More and Sorensen).  The start is the last step's
 // u when psi < 0 there, else u = 0 (or the smallest l_j > 0 / 1e6 when
 // f(0) is infinite, halved until psi < 0).  Stops at |sqrt(f) - se| <=
-// 2e-6 se, the FP32 map's own accuracy.  All FP32 (lane sums by a fixed
-// butterfly).  Writes s_j = u / (u + l_j) = 1 / (1 + c l_j), or 0; u is
+// 2e-6 se, the FP32 map's own accuracy.  All FP32, the sums in a fixed
+// order (a butterfly per warp, then the warps in order).  Writes s_j = u / (u + l_j) = 1 / (1 + c l_j), or 0; u is
 // kept as a float in the double slot scal[S_EPSC].
-__global__ void k_eps_root(const float *__restrict__ w2g, const float *__restrict__ lambda, int B, double *scal,
-                           float eps, float *__restrict__ s)
+__global__ void __launch_bounds__(EPS_ROOT_T)
+k_eps_root(const float *__restrict__ w2g, const float *__restrict__ lambda, int B, double *scal,
+           float eps, float *__restrict__ s)
 {
-    // W2 and l staged once by the whole block (n_bins <= 4096), then warp 0
-    // alone solves, every evaluation reading shared memory
+    // W2 and l staged once (n_bins <= 4096); every evaluation is spread over
+    // the whole block: each thread sums its terms, the warps' sums meet in
+    // shared memory, and every thread adds the EPS_ROOT_T / 32 warp sums in
+    // the same order, so all threads hold the same f, g and take the same
+    // Newton steps
     __shared__ float w2[4096], ls[4096];
-    for (int j = threadIdx.x; j < B; j += blockDim.x) {
+    __shared__ float red[2][EPS_ROOT_T / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < B; j += EPS_ROOT_T) {
         w2[j] = w2g[j];
         ls[j] = lambda ? fmaxf(lambda[j], 0.0f) : 1.0f;
     }
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const int l = threadIdx.x;
     float *uslot = reinterpret_cast<float *>(scal + S_EPSC);
     const float se = fscal(scal, F_SIGMA) * eps, se2 = se * se;
     auto wsum = [](float v) {
@@ -372,32 +377,55 @@ __global__ void k_eps_root(const float *__restrict__ w2g, const float *__restric
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
+    // block sums of two per-thread values, the same in every thread
+    auto bsum2 = [&](float a, float b, float &sa, float &sb) {
+        a = wsum(a);
+        b = wsum(b);
+        if (lane == 0) {
+            red[0][warp] = a;
+            red[1][warp] = b;
+        }
+        __syncthreads();
+        sa = 0.0f;
+        sb = 0.0f;
+#pragma unroll
+        for (int q = 0; q < EPS_ROOT_T / 32; ++q) {
+            sa += red[0][q];
+            sb += red[1][q];
+        }
+        __syncthreads();   // red is reused by the next sum
+    };
     // f(u) and g(u) = sum_j W2_j / (u + l_j)^3
     auto eval = [&](float u, float &f, float &g) {
         float a = 0.0f, b = 0.0f;
-        for (int j = l; j < B; j += 32) {
+        for (int j = tid; j < B; j += EPS_ROOT_T) {
             const float inv = __fdividef(1.0f, u + ls[j]), t = w2[j] * inv * inv;
             a += t;
             b = fmaf(t, inv, b);
         }
-        f = wsum(a);
-        g = wsum(b);
+        bsum2(a, b, f, g);
     };
-    float f0 = 0.0f, lmin = 3.0e38f;
-    int unb = 0;
-    for (int j = l; j < B; j += 32) {
+    float f0 = 0.0f, lmin = 3.0e38f, unbf = 0.0f;
+    for (int j = tid; j < B; j += EPS_ROOT_T) {
         const float lj = ls[j], wj = w2[j];
         if (lj > 0.0f) {
             f0 += wj / (lj * lj);
             lmin = fminf(lmin, lj);
         } else if (wj > 0.0f) {
-            unb = 1;
+            unbf = 1.0f;
         }
     }
-    f0 = wsum(f0);
-    unb = __any_sync(0xffffffffu, unb);
+    float unbs;
+    bsum2(f0, unbf, f0, unbs);
+    const bool unb = unbs > 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    if (lane == 0) red[0][warp] = lmin;
+    __syncthreads();
+    lmin = 3.0e38f;
+#pragma unroll
+    for (int q = 0; q < EPS_ROOT_T / 32; ++q) lmin = fminf(lmin, red[0][q]);
+    __syncthreads();
     float u = 0.0f;
     bool zero = false, all = false;
     if (!(se > 0.0f)) {
@@ -427,8 +455,9 @@ __global__ void k_eps_root(const float *__restrict__ w2g, const float *__restric
             u = un > 0.0f ? un : 0.5f * u;
         }
     }
-    for (int j = l; j < B; j += 32) s[j] = all ? 1.0f : zero ? 0.0f : __fdividef(u, u + ls[j]);
-    if (l == 0) *uslot = (zero || all) ? 0.0f : u;
+    for (int j = tid; j < B; j += EPS_ROOT_T) s[j] = all ? 1.0f : zero ? 0.0f : __fdividef(u, u + ls[j]);
+    __syncthreads();   // every thread has read the previous u
+    if (tid == 0) *uslot = (zero || all) ? 0.0f : u;
 }
 
 void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2, const float *mu0, const float *Q,
@@ -444,13 +473,13 @@ void launch_eps_step(const Geometry *g, const float *q, float *out, float *out2,
         counted(5);
         k_eps_gemm<false><<<grid, tb, 0, st>>>(q, Q, nullptr, part, V, B, kchunk);
         k_eps_sum_w2<<<(B + 31) / 32, dim3(32, 8), 0, st>>>(part, ks, V, B, wbuf, w2);
-        k_eps_root<<<1, 512, 0, st>>>(w2, lambda, B, scal, (float)eps, s);
+        k_eps_root<<<1, EPS_ROOT_T, 0, st>>>(w2, lambda, B, scal, (float)eps, s);
         k_eps_gemm<true><<<grid, tb, 0, st>>>(wbuf, Q, s, part, V, B, kchunk);
         k_eps_sum_out<<<eblocks, 256, 0, st>>>(part, ks, n, out, out2, mu0);
     } else {
         counted(3);
         k_eps_w2<<<(B + 127) / 128, 128, 0, st>>>(q, V, B, w2);
-        k_eps_root<<<1, 512, 0, st>>>(w2, nullptr, B, scal, (float)eps, s);
+        k_eps_root<<<1, EPS_ROOT_T, 0, st>>>(w2, nullptr, B, scal, (float)eps, s);
         k_eps_scale<<<eblocks, 256, 0, st>>>(q, s, out, out2, mu0, V, B);
     }
 }
