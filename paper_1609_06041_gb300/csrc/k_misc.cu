@@ -2,6 +2,8 @@
 // scalar program of the step-size setup (Alg. 1 / Alg. 2 boxes).
 #include <math.h>
 
+#include <algorithm>
+
 #include "ctpd_internal.cuh"
 
 namespace ctpd {
@@ -388,8 +390,13 @@ k_lanczos_step(float *__restrict__ w, const float *__restrict__ tp, const float 
 void launch_lanczos_step(float *w, const float *tp, const float *tc, size_t n, double *scal, int base, int n0slot,
                          int j, int phase, double *partials, unsigned *ticket, cudaStream_t st)
 {
+    // one four-element group per thread: no block without elements, so the
+    // ticket sees only as many arrivals as the vector needs (256 blocks for
+    // a 512^2 image instead of the full reduction grid)
+    const size_t groups = (n + 4 * (size_t)DOT_THREADS - 1) / (4 * (size_t)DOT_THREADS);
+    const int blocks = (int)std::min<size_t>(std::max<size_t>(groups, 1), DOT_BLOCKS);
     counted();
-    k_lanczos_step<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(w, tp, tc, n, scal, base, n0slot, j, phase, partials, ticket);
+    k_lanczos_step<<<blocks, DOT_THREADS, 0, st>>>(w, tp, tc, n, scal, base, n0slot, j, phase, partials, ticket);
 }
 
 __global__ void k_axpy_neg(float *w, const float *q, size_t n, const double *scal, int slot)
