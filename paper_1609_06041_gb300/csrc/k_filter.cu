@@ -211,7 +211,7 @@ __global__ void k_taps(int mode, int m, int P, int B, const double *__restrict__
         const float Hj = (mode == 0) ? w / den
                        : (mode == 1) ? w / two_m_tau
                        : (mode == 2) ? two_m_tau * w / (den * den) : kappa * w * w / (den * den);
-        const int ph = (int)(((long long)j * k) % P);
+        const int ph = (int)(((unsigned)j * (unsigned)k) & (unsigned)(P - 1));   // j k mod P, P a power of two
         const float term = Hj * cospif(2.0f * (float)ph / (float)P);
         const float y = term - comp;
         const float t = sum + y;
