@@ -61,46 +61,69 @@ __host__ __device__ __forceinline__ size_t quad_smem(int N) { return sizeof(floa
 // serves both bands and the two bands' samples are one packed two-wide
 // FMA, mid + g delta, into a pair accumulator (the reflected pair with -g).
 // The coordinates of two steps are evaluated as one packed pair as well.
+// A pass of ROWS = 4 is two passes of ROWS = 2 whose loads are issued
+// together: the same coordinates (u' = (s - h) m + q for even steps,
+// (s - 1 - h) m + (q + m) for odd ones), the same two accumulators (even
+// and odd steps) updated in the same order and the same tail, so both
+// give the same sums to the bit.
 template <bool PAIR, int ROWS>
 __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP, float q, float m, int lo, int hi,
                                             int s0, float h, unsigned top)
 {
-    static_assert(ROWS % 2 == 0, "steps are evaluated in pairs");
-    float2 qk[ROWS / 2];   // q + k m for the steps k, k + 1 of a pass
-#pragma unroll
-    for (int k = 0; k < ROWS / 2; ++k) qk[k] = pk(__fmaf_rn((float)(2 * k), m, q), __fmaf_rn((float)(2 * k + 1), m, q));
+    static_assert(ROWS == 2 || ROWS == 4, "steps are evaluated in pairs, one or two pairs per pass");
+    const float2 qk = pk(q, __fmaf_rn(1.0f, m, q));   // q + k m for the steps k = 0, 1 of a pair
     const float2 mm = pk(m, m), bias = pk(JOSEPH_BIAS, JOSEPH_BIAS);
     float spk = (float)lo - h;
     int ridx = (lo - s0) * SP;
-    float2 ab[ROWS], ce[ROWS];   // (band A, band B) sums at i0 and at the reflected pair
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) ab[k] = ce[k] = pk(0.0f, 0.0f);
+    float2 ab[2], ce[2];   // (band A, band B) sums of the even and odd steps, at i0 and at the reflected pair
+    ab[0] = ab[1] = ce[0] = ce[1] = pk(0.0f, 0.0f);
+    // the samples of the steps s and s + 1, at (s - h) = sp
+    auto pair_samples = [&](float sp, int rr, float4 &p0, float4 &p1, float4 &r0, float4 &r1, float2 &g) {
+        const float2 up = pfma(pk(sp, sp), mm, qk);
+        const float2 t = padd(up, bias);
+        const float2 tb = psub(t, bias);
+        g = psub(up, tb);
+        const unsigned i0 = min((unsigned)(__float_as_int(t.x) - (JOSEPH_BIAS_BITS - 2)), top);
+        const unsigned i1 = min((unsigned)(__float_as_int(t.y) - (JOSEPH_BIAS_BITS - 2)), top);
+        p0 = Q[rr + (int)i0];
+        p1 = Q[rr + SP + (int)i1];
+        if (PAIR) {
+            r0 = Q[rr + (int)(top - i0)];
+            r1 = Q[rr + SP + (int)(top - i1)];
+        }
+    };
+    auto pair_add = [&](const float4 &p0, const float4 &p1, const float4 &r0, const float4 &r1, float2 g) {
+        ab[0] = pfma(pk(g.x, g.x), pk(p0.z, p0.w), padd(ab[0], pk(p0.x, p0.y)));
+        ab[1] = pfma(pk(g.y, g.y), pk(p1.z, p1.w), padd(ab[1], pk(p1.x, p1.y)));
+        if (PAIR) {
+            ce[0] = pfma(pk(-g.x, -g.x), pk(r0.z, r0.w), padd(ce[0], pk(r0.x, r0.y)));
+            ce[1] = pfma(pk(-g.y, -g.y), pk(r1.z, r1.w), padd(ce[1], pk(r1.x, r1.y)));
+        }
+    };
     int s = lo;
     for (; s + ROWS - 1 <= hi; s += ROWS) {
+        float4 p[ROWS], r[ROWS];
+        float2 g[ROWS / 2];
 #pragma unroll
-        for (int k = 0; k < ROWS / 2; ++k) {
-            const float2 up = pfma(pk(spk, spk), mm, qk[k]);
-            const float2 t = padd(up, bias);
-            const float2 tb = psub(t, bias);
-            const float2 g = psub(up, tb), gn = psub(tb, up);
-            const unsigned i0 = min((unsigned)(__float_as_int(t.x) - (JOSEPH_BIAS_BITS - 2)), top);
-            const unsigned i1 = min((unsigned)(__float_as_int(t.y) - (JOSEPH_BIAS_BITS - 2)), top);
-            const float4 p0 = Q[ridx + (2 * k) * SP + (int)i0];
-            const float4 p1 = Q[ridx + (2 * k + 1) * SP + (int)i1];
-            ab[2 * k] = pfma(pk(g.x, g.x), pk(p0.z, p0.w), padd(ab[2 * k], pk(p0.x, p0.y)));
-            ab[2 * k + 1] = pfma(pk(g.y, g.y), pk(p1.z, p1.w), padd(ab[2 * k + 1], pk(p1.x, p1.y)));
-            if (PAIR) {
-                const float4 r0 = Q[ridx + (2 * k) * SP + (int)(top - i0)];
-                const float4 r1 = Q[ridx + (2 * k + 1) * SP + (int)(top - i1)];
-                ce[2 * k] = pfma(pk(gn.x, gn.x), pk(r0.z, r0.w), padd(ce[2 * k], pk(r0.x, r0.y)));
-                ce[2 * k + 1] = pfma(pk(gn.y, gn.y), pk(r1.z, r1.w), padd(ce[2 * k + 1], pk(r1.x, r1.y)));
-            }
-        }
+        for (int k = 0; k < ROWS / 2; ++k)
+            pair_samples(k == 0 ? spk : __fadd_rn(spk, (float)(2 * k)), ridx + 2 * k * SP, p[2 * k], p[2 * k + 1],
+                         r[2 * k], r[2 * k + 1], g[k]);
+#pragma unroll
+        for (int k = 0; k < ROWS / 2; ++k) pair_add(p[2 * k], p[2 * k + 1], r[2 * k], r[2 * k + 1], g[k]);
         spk = __fadd_rn(spk, (float)ROWS);
         ridx += ROWS * SP;
     }
-    for (; s <= hi; ++s) {
-        const float up = joseph_u(spk, m, qk[0].x);
+    if (ROWS == 4 && s + 1 <= hi) {   // the pair ROWS = 2 would still take
+        float4 p0, p1, r0, r1;
+        float2 g;
+        pair_samples(spk, ridx, p0, p1, r0, r1, g);
+        pair_add(p0, p1, r0, r1, g);
+        spk = __fadd_rn(spk, 2.0f);
+        ridx += 2 * SP;
+        s += 2;
+    }
+    if (s <= hi) {   // one step left
+        const float up = joseph_u(spk, m, qk.x);
         const float t = __fadd_rn(up, JOSEPH_BIAS);
         const unsigned i = min((unsigned)(__float_as_int(t) - (JOSEPH_BIAS_BITS - 2)), top);
         const float g = __fsub_rn(up, __fsub_rn(t, JOSEPH_BIAS));
@@ -110,14 +133,9 @@ __device__ __forceinline__ float4 quad_walk(const float4 *__restrict__ Q, int SP
             const float4 rv = Q[ridx + (int)(top - i)];
             ce[0] = pfma(pk(-g, -g), pk(rv.z, rv.w), padd(ce[0], pk(rv.x, rv.y)));
         }
-        spk = __fadd_rn(spk, 1.0f);
-        ridx += SP;
     }
-#pragma unroll
-    for (int k = 1; k < ROWS; ++k) {
-        ab[0] = padd(ab[0], ab[k]);
-        ce[0] = padd(ce[0], ce[k]);
-    }
+    ab[0] = padd(ab[0], ab[1]);
+    ce[0] = padd(ce[0], ce[1]);
     return make_float4(ab[0].x, ab[0].y, ce[0].x, ce[0].y);
 }
 

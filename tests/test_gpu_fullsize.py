@@ -83,3 +83,51 @@ def test_fewview_512_v32_100_iterations(record_property):
     record_property("fewview_512_tuning", str(tun))
     assert r <= TOL
     assert mx <= 10 * TOL
+
+
+def test_batched_64_mixed_slices_sampled(record_property):
+    # the batched workload as the benchmark builds it: 64 slices of mixed
+    # N (256, 384, 512), views (32, 90, 360, 720), bins ceil(1.44 N) and
+    # mode, 30 iterations each, launch shapes tuned per geometry, one
+    # ct_pdtv_solve_batched call in the persistent form and in the
+    # stream-pool form.  Every slice agrees bit for bit between the two
+    # forms; four sampled slices (few-view 256^2/32 and 384^2/90, low-dose
+    # 384^2/720 and 512^2/720), whose tau and sigma are set from the
+    # oracle, match the oracle's 30 iterations.
+    P = need_gpu()
+    import torch
+    shapes = synth.mixed_slices(64, 0)
+    sampled = [2, 1, 5, 27]
+    slices, geoms, cases = [], {}, {}
+    for i, (n, v, nb, mode, sd) in enumerate(shapes):
+        g = geoms.setdefault((n, v, nb), P.Geometry(n, v, nb))
+        x = synth.ellipse_phantom(n, 10, sd) * ((2.0 / n) if mode == 0 else 1.0)
+        p = O.project(x, v, nb)
+        if mode == 0:
+            b, w = synth.poisson_data(p, 1e4, sd)
+            b, w = f32(b), f32(w)
+        else:
+            b, w = f32(p), None
+        prm = P.PDTVParams(mode=mode, iters=30, tv_iters=10, beta=0.005)
+        if i in sampled:
+            kappa = float(np.mean(1.0 / w)) if mode == 0 else 0.0
+            prm.tau = O.default_tau(mode, v, kappa)
+            taps = O.ramp_taps(mode, v, nb, prm.tau, kappa)
+            prm.sigma, _, _ = O.step_sizes(mode, n, v, nb, taps, w, prm.tau, iters=20)
+            cases[i] = (b, w, taps, mode, prm.tau, prm.sigma, n)
+        slices.append((g, to_gpu(b), None if w is None else to_gpu(w), prm))
+    bs = P.BatchedSolve(slices, autotune=True)
+    bs.form = P.CT_BATCH_AUTO            # the persistent launch (every slice qualifies)
+    xs, _ = bs.run()
+    torch.cuda.synchronize()
+    persistent = [to_np(x).copy() for x in xs]
+    bs.form = P.CT_BATCH_POOL
+    xs, _ = bs.run()
+    torch.cuda.synchronize()
+    for i, x in enumerate(xs):
+        assert np.array_equal(to_np(x), persistent[i]), i
+    for i, (b, w, taps, mode, tau, sigma, n) in cases.items():
+        st, _ = O.pdtv(b, w, taps, mode, 0.005 if mode == 0 else 0.0, tau, sigma, 10, 30, n)
+        r, mx = report(record_property, f"batched_slice_{i}", persistent[i], st.x)
+        assert r <= TOL, i
+        assert mx <= 10 * TOL, i

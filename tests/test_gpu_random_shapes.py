@@ -47,7 +47,7 @@ def draw(seed):
     return N, V, B, angles, batch
 
 
-SEEDS = list(range(24))
+SEEDS = list(range(48))
 
 
 @pytest.mark.parametrize("seed", SEEDS)

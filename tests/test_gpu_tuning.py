@@ -34,25 +34,26 @@ def test_operator_shapes_parity(N, V, B, items, rows, slices, form):
                                          (512, 720, 736, 1), (256, 180, 368, 5), (64, 1, 96, 2), (32, 3, 47, 1)])
 def test_projector_forms_agree_bit_for_bit(N, V, B, batch):
     # the work-balanced projector forms every band sum exactly as the
-    # band-pair-per-block form does, whatever the items per block or the
-    # batch: for one number of steps per pass (which sets how a ray's samples
-    # are grouped into partial sums) the projections are equal bit for bit
+    # band-pair-per-block form does, whatever the items per block, the steps
+    # per pass of a ray walk (a pass of four steps is two passes of two with
+    # their loads issued together) or the batch: the projections are equal
+    # bit for bit
     P = need_gpu()
     import torch
     g = P.Geometry(N, V, B)
     xs = np.stack([f32(synth.ellipse_phantom(N, 6, 3 + i)) for i in range(batch)])
     xg = to_gpu(xs)
+    outs = []
     for rows, shapes in [(2, [(8, 1), (16, 2), (8, 2), (13, 1), (12, 2)]), (4, [(10, 1), (12, 2), (8, 2)])]:
-        outs = []
         for items, form in shapes:
             g.set_tuning(items_per_block=items, proj_rows=rows, proj_form=form)
             outs.append(P.ct_project(g, xg).clone())
-        for o in outs[1:]:
-            assert torch.equal(o, outs[0])
-        # each slice of the batch equals its own single projection
-        for i in range(batch):
-            assert torch.equal(P.ct_project(g, xg[i].contiguous()), outs[0][i])
-        assert rel_l2(to_np(outs[0][0]), O.project(xs[0], V, B)) <= TOL
+            # each slice of the batch equals its own single projection
+            for i in range(batch):
+                assert torch.equal(P.ct_project(g, xg[i].contiguous()), outs[-1][i])
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    assert rel_l2(to_np(outs[0][0]), O.project(xs[0], V, B)) <= TOL
 
 
 @pytest.mark.parametrize("rows", [4, 16, 64])
