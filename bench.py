@@ -48,7 +48,7 @@ SMEM_PEAK_TBPS = 152 * 128 * 2.070e9 / 1e12         # SMs x 128 shared-memory by
 # capture of the current kernel exists.  A: k_project_qbal<4> (the
 # work-balanced projector, 12 items' threads per block, 4 steps per pass);
 # AT: k_backproject_orbit_cl<true> (mu_bar and x read once).
-TRAFFIC_BYTES = {"A": 1.137152e6, "AT": 3.080704e6}
+TRAFFIC_BYTES = {"A": 1.132544e6, "AT": 3.080704e6}
 
 
 def dist_info():
