@@ -2,9 +2,10 @@
 // geometry, data, mode and parameters) solved in one call.
 //
 // The call forks the caller's stream onto a pool of streams (one pool per
-// device, created on first use and kept until exit) with events, enqueues
-// slice i on pool stream i mod S, and joins every pool stream back into
-// the caller's stream.  The fork and join are stream-ordered event waits,
+// device, created on first use and kept until exit) with events, hands the
+// slices to the pool streams largest first, each to the stream with the
+// least work so far (work ~ N^2 V (iterations + Lanczos steps)), and joins
+// every pool stream back into the caller's stream.  The fork and join are stream-ordered event waits,
 // so the whole call can be captured into one CUDA graph.  When every slice
 // qualifies for the persistent form, the pool runs only the slices' setups
 // and one persistent launch after the join runs all their iterations
@@ -12,6 +13,7 @@
 // solve, so small slices that cannot fill the GPU alone run side by side.
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -104,10 +106,28 @@ extern "C" ct_status ct_pdtv_solve_batched(int n, const ct_geometry *const *geom
     std::unique_lock<std::mutex> lock(pool->mu);
     cudaEventRecord(pool->fork, st);
     for (int i = 0; i < used; ++i) cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
+    // largest first onto the least-loaded stream: the streams end close
+    // together instead of the last large slices running alone
+    std::vector<int> order(n), stream_of(n);
+    std::vector<double> work(n), load(used, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const ct_geometry *g = geoms[i];
+        const int its = persistent ? 0 : params[i].iters;
+        const int nlz = params[i].sigma > 0.0 ? 0 : (params[i].norm_iters > 0 ? params[i].norm_iters : 12);
+        order[i] = i;
+        work[i] = (double)g->n * g->n * g->n_views * (double)(its + nlz + 1);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    for (int i : order) {
+        const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        stream_of[i] = j;
+        load[j] += work[i];
+    }
     ct_status result = CT_OK;
-    for (int i = 0; i < n && result == CT_OK; ++i) {
+    for (int k = 0; k < n && result == CT_OK; ++k) {
+        const int i = order[k];
         result = ctpd::pdtv_solve(geoms[i], b[i], w ? w[i] : nullptr, persistent ? &setup[i] : &params[i], x_out[i],
-                                  workspaces[i], nullptr, pool->s[i % POOL_STREAMS], false);
+                                  workspaces[i], nullptr, pool->s[stream_of[i]], false);
         if (result != CT_OK) {
             char msg[400];
             snprintf(msg, sizeof(msg), "%s", ct_last_error());
