@@ -105,7 +105,8 @@ void ct_geometry_destroy(ct_geometry *geom);
  *                    projector, 64 threads each (4..16; 4..12 when
  *                    proj_rows is 4);
  *   proj_rows        steps a projector thread evaluates per pass of a ray
- *                    walk (2 or 4: more loads in flight, more registers);
+ *                    walk (2 or 4: more loads in flight, more registers;
+ *                    the same sums either way);
  *   orbit_slices     base-view slices of the rotation-orbit backprojector
  *                    (1..8, at most 1024 base views per slice), added in a
  *                    thread-block cluster of the slices' blocks, or (solves
@@ -125,9 +126,12 @@ void ct_geometry_destroy(ct_geometry *geom);
  *                    from a shared counter.  Both give the same sums.
  * 0 selects the built-in rule (a wave-count model for items_per_block, 2
  * steps per pass, 4 slices, 16 rows; form 2 with 16 items' threads when
- * form 1 would need two waves of blocks or more, else form 1).  A shape changes the order in which independent
- * partial sums are added, so results can differ in the last float bits
- * between shapes; for one shape they are deterministic.
+ * form 1 would need two waves of blocks or more, else form 1).  The
+ * projector's shapes (items_per_block, proj_rows, proj_form) and tv_rows
+ * leave every result bit unchanged; orbit_slices changes the order in
+ * which the backprojector's slice sums are added, so results can differ in
+ * the last float bits between slice counts; for one shape they are
+ * deterministic.
  *
  * ct_geometry_autotune times every candidate of each shape on synthetic data
  * of the geometry's size (batch images for A and A^T) on `stream`, with
