@@ -56,6 +56,27 @@ def test_projector_forms_agree_bit_for_bit(N, V, B, batch):
     assert rel_l2(to_np(outs[0][0]), O.project(xs[0], V, B)) <= TOL
 
 
+def test_projector_and_prox_shapes_leave_the_solve_unchanged():
+    # every projector shape (form, items per block, steps per pass) and every
+    # prox tile height gives the same solve bit for bit: the tiles and unit
+    # ranges only decide which thread forms which sum, not how
+    P = need_gpu()
+    import torch
+    N, V, B = 96, 60, 137
+    x_true = synth.ellipse_phantom(N, 8, 4) * (2.0 / N)
+    b, w = synth.poisson_data(O.project(x_true, V, B), 1e4, 104)
+    g = P.Geometry(N, V, B)
+    prm = P.PDTVParams(mode=P.CT_LOWDOSE, iters=8, tv_iters=10, beta=0.01, sigma=0.5)
+    ref = None
+    for items, rows, form, tv in [(0, 0, 0, 0), (6, 2, 1, 4), (12, 4, 1, 64), (8, 2, 2, 8), (12, 4, 2, 16)]:
+        g.set_tuning(items_per_block=items, proj_rows=rows, proj_form=form, tv_rows=tv)
+        xg, _ = P.ct_pdtv_solve(g, to_gpu(f32(b)), to_gpu(f32(w)), prm)
+        if ref is None:
+            ref = xg.clone()
+        else:
+            assert torch.equal(xg, ref), (items, rows, form, tv)
+
+
 @pytest.mark.parametrize("rows", [4, 16, 64])
 def test_tv_rows_solve_parity(rows):
     # the low-dose 64^2 / 90 / 95 solve (20 iterations, n_tv = 10) under
