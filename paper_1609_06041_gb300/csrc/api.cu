@@ -574,6 +574,7 @@ void ct_geometry_destroy(ct_geometry *g)
     if (g->d_tw) cudaFree(g->d_tw);
     if (g->d_row_items) cudaFree(g->d_row_items);
     if (g->d_col_items) cudaFree(g->d_col_items);
+    if (g->d_qbounds) cudaFree(g->d_qbounds);
     eps_cache_free(g);
     graph_cache_free(g);
     delete[] g->h_angles;

@@ -15,7 +15,9 @@
 //     (one partial image per slice and k_orbit_reduce, taken by solves run
 //     side by side and by the persistent batched kernel);
 //   - the TV prox's fewest interior rows per tile (k_tv), 4 .. 64, which
-//     sets how many tiles one image is cut into.
+//     sets how many tiles one image is cut into;
+// and, with the work-balanced projector form, its unit ranges for one image
+// balanced from measured block times (qbal_balance).
 // Each choice changes only the launch shape and the order in which
 // independent partial sums are formed, never the arithmetic of a sample.
 #include <stdio.h>
@@ -180,6 +182,8 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
         g->tune_pg = best_pg;
         g->tune_qrows = best_rows;
         g->tune_qbal = best_form;
+        // the balanced form's unit ranges for one image, from measured block times
+        if (result == CT_OK) result = qbal_balance(g, x, band, st);
     }
     // the orbit backprojector's slices, for each of its two forms: slices
     // added in a thread-block cluster (single solves) and slice images with

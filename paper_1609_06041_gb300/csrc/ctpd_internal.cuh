@@ -54,10 +54,21 @@ struct Geometry {
     int tune_tv;          // fewest interior rows of a TV tile (4..64)
     int tune_qbal;        // projector form: 1 band pair per block, 2 work-balanced ranges (0: the rule)
     int qbal_occ[2][17];  // blocks per SM of the work-balanced projector by (4 steps per pass, items); 0: not queried
+    long long *d_qbounds; // device, qbounds_nb + 1 entries: the work-balanced projector's unit ranges for one
+                          // image, balanced by the tuner from measured block times (NULL: equal unit counts)
+    int qbounds_nb;       // the launch they fit: blocks ...
+    int qbounds_key;      // ... and 64 (4 steps per pass) + items per block
+    unsigned long long *d_qtimes;   // device: the tuner's per-block start and end times while it measures
     double *h_angles;     // host copy
     void *eps_cache;      // eigenbases of D for the error-tolerant form (eps.cu)
     void *graph_cache;    // instantiated CUDA graphs of repeated solves (api.cu)
 };
+
+// Balances the work-balanced projector's unit ranges for one image by
+// measuring its blocks (k_joseph.cu; the tuner calls it once it has chosen
+// the launch shape): keeps g->d_qbounds when it makes the launch faster.
+// x and band: an image and band partials of the geometry's size.
+ct_status qbal_balance(Geometry *g, const float *x, float *band, cudaStream_t st);
 
 // Records a printf-style message as the calling thread's last error.
 void set_error(const char *fmt, ...);

@@ -2,6 +2,8 @@
 // A^T (pixel-driven gather), the A and A^T of Eqs. 18-20 / 29-31.  Both are
 // deterministic (fixed summation orders, no atomics).
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -310,18 +312,46 @@ k_project_quad(const float *__restrict__ x, const ViewP *__restrict__ views,
 
 // The work-balanced form: block b takes units [total b / nb, total (b+1) / nb)
 // (see quad_balanced_body); its unit counter sits after the staged pairs.
+__device__ __forceinline__ unsigned long long global_time()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounds (optional): block b takes units [bounds[b], bounds[b+1]), a table
+// of the geometry's written before any launch that reads it (so it is read
+// before the wait for the previous kernel); else equal unit counts.
+// times (optional): block b writes its start and end times (ns) to
+// times[2b], times[2b+1].
 template <int ROWS, bool DEEP>
 __global__ void __launch_bounds__(ROWS == 2 ? 1024 : 768)
 k_project_qbal(const float *__restrict__ x, const ViewP *__restrict__ views, const int2 *__restrict__ row_items,
                const int2 *__restrict__ col_items, int N, int V, int B, QuadUnits U, long long total,
+               const long long *__restrict__ bounds, unsigned long long *__restrict__ times,
                float *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    pdl_wait();
     const long long nb = gridDim.x;
-    const long long u0 = total * blockIdx.x / nb, u1 = total * (blockIdx.x + 1) / nb;
+    long long u0, u1;
+    if (bounds) {
+        u0 = bounds[blockIdx.x];
+        u1 = bounds[blockIdx.x + 1];
+    } else {
+        u0 = total * blockIdx.x / nb;
+        u1 = total * (blockIdx.x + 1) / nb;
+    }
+    pdl_wait();
+    const unsigned long long t0 = times ? global_time() : 0ull;
     quad_balanced_body<ROWS, DEEP>(whole_block(), u0, u1, U, smraw, reinterpret_cast<int *>(smraw + quad_smem(N)),
                                    x, views, row_items, col_items, N, V, B, partial);
+    if (times) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            times[2 * blockIdx.x] = t0;
+            times[2 * blockIdx.x + 1] = global_time();
+        }
+    }
 }
 
 // Launch shape of k_project_quad: items per group (pg, 64 threads each) and
@@ -347,6 +377,44 @@ static void quad_shape(const Geometry *g, int batch, int max_pg, int pg_fixed, i
     }
 }
 
+// Launch shape of the work-balanced form: as many blocks as fit on the
+// device at once (fewer when the work would leave a warp under two units).
+struct QbalShape {
+    QuadUnits U;
+    long long total;
+    int rows4, pgb, threads, blocks, key;
+    size_t smem;
+};
+static QbalShape qbal_shape(const Geometry *g, int batch)
+{
+    QbalShape q;
+    const int N = g->n;
+    q.rows4 = g->tune_qrows == 4;
+    const int max_pg = q.rows4 ? 12 : PG;
+    q.pgb = g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : max_pg;
+    q.threads = q.pgb * 64;
+    q.key = 64 * q.rows4 + q.pgb;
+    const int npair = (g->n_bins + 1) / 2, nch = (npair + 63) / 64;
+    q.U.nch = nch;
+    q.U.u_rows = g->n_row_items * nch;
+    q.U.u_cols = g->n_col_items * nch;
+    q.U.u_z = (long long)(N / (2 * MR)) * (q.U.u_rows + q.U.u_cols);
+    q.total = q.U.u_z * batch;
+    q.smem = quad_smem(N) + 16;
+    auto kern = q.rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
+    // blocks per SM, queried once per (steps per pass, items) for the geometry
+    int &occ_slot = const_cast<Geometry *>(g)->qbal_occ[q.rows4][q.pgb];
+    int occ = occ_slot;
+    if (occ < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, q.threads, q.smem) != cudaSuccess || occ < 1)
+            occ = 1;
+        occ_slot = occ;
+    }
+    const long long by_work = (q.total + 4 * q.pgb - 1) / (4 * q.pgb);   // two units per warp
+    q.blocks = (int)std::max(1LL, std::min((long long)g->n_sm * occ, by_work));
+    return q;
+}
+
 void launch_project_bands(const Geometry *g, const float *x, float *partial, int batch, cudaStream_t st)
 {
     const int N = g->n;
@@ -366,30 +434,14 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
         // the built-in rule takes the work-balanced form when one band pair
         // per block would need two waves of blocks or more
         if (g->tune_qbal == 2 || (g->tune_qbal == 0 && static_blocks >= 2L * g->n_sm)) {
-            // work-balanced: as many blocks as fit on the device at once
-            // (fewer when the work would leave a warp under two units)
-            const int pgb = g->tune_pg > 0 ? std::min(g->tune_pg, max_pg) : max_pg, threads = pgb * 64;
-            const int npair = (g->n_bins + 1) / 2, nch = (npair + 63) / 64;
-            QuadUnits U;
-            U.nch = nch;
-            U.u_rows = g->n_row_items * nch;
-            U.u_cols = g->n_col_items * nch;
-            U.u_z = (long long)(N / (2 * MR)) * (U.u_rows + U.u_cols);
-            const long long total = U.u_z * batch;
-            const size_t smem2 = quad_smem(N) + 16;
-            auto kern = rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
-            // blocks per SM, queried once per (steps per pass, items) for the geometry
-            int &occ_slot = const_cast<Geometry *>(g)->qbal_occ[rows4][pgb];
-            int occ = occ_slot;
-            if (occ < 1) {
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem2) != cudaSuccess || occ < 1)
-                    occ = 1;
-                occ_slot = occ;
-            }
-            const long long by_work = (total + 4 * pgb - 1) / (4 * pgb);   // two units per warp
-            const int blocks = (int)std::max(1LL, std::min((long long)g->n_sm * occ, by_work));
-            launch_kernel(kern, dim3(blocks), dim3(threads), smem2, st, x, g->d_views, g->d_row_items,
-                          g->d_col_items, N, g->n_views, g->n_bins, U, total, partial);
+            const QbalShape q = qbal_shape(g, batch);
+            auto kern = q.rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
+            // the tuner's measured-balance ranges, for the launch they were made for
+            const long long *bounds = batch == 1 && g->d_qbounds && g->qbounds_nb == q.blocks && g->qbounds_key == q.key
+                                          ? g->d_qbounds
+                                          : nullptr;
+            launch_kernel(kern, dim3(q.blocks), dim3(q.threads), q.smem, st, x, g->d_views, g->d_row_items,
+                          g->d_col_items, N, g->n_views, g->n_bins, q.U, q.total, bounds, g->d_qtimes, partial);
             return;
         }
         const size_t smem2 = quad_smem(N);
@@ -666,6 +718,117 @@ int orbit_slices(const Geometry *g, bool cluster)
 }
 size_t orbit_smem_bytes() { return orbit_smem(); }
 bool quad_ok(const Geometry *g) { return g->vpair && g->n % (2 * MR) == 0 && g->n + 3 <= PROJ_CW; }
+
+// Measured balance of the work-balanced projector for one image.  Equal
+// unit counts per block leave the blocks' times about 20 % apart at
+// 512^2 / 720 views (views whose rays cross fewer staged steps, bank
+// conflicts that differ by view, the two line classes), and the launch
+// lasts as long as its slowest block.  The tuner keeps a cost per unit,
+// uniform at first.  Each round times every block of a few launches
+// (%globaltimer at its start and end), scales the costs of each block's
+// units by (measured / modelled time)^0.7, and cuts the units again at
+// equal shares of the modelled cost; as the ranges move between rounds the
+// model resolves finer than one block.  The ranges of the round whose
+// launch time (CUDA events) is least are kept, if they beat equal counts.
+// A range only decides which block forms which units' sums, so results do
+// not change.
+ct_status qbal_balance(Geometry *g, const float *x, float *band, cudaStream_t st)
+{
+    if (g->d_qbounds) {
+        cudaFree(g->d_qbounds);
+        g->d_qbounds = nullptr;
+    }
+    if (!quad_ok(g) || g->tune_qbal != 2) return CT_OK;
+    const QbalShape q = qbal_shape(g, 1);
+    const int nb = q.blocks;
+    if (nb < 2) return CT_OK;
+    const long long uz = q.U.u_z;
+    unsigned long long *times = nullptr;
+    long long *bounds = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&times, sizeof(unsigned long long) * 2 * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&bounds, sizeof(long long) * (nb + 1));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<long long> b(nb + 1), best;
+    for (int i = 0; i <= nb; ++i) b[i] = uz * i / nb;
+    std::vector<unsigned long long> h(2 * nb);
+    std::vector<double> dur(nb), cost((size_t)uz, 1.0), cum((size_t)uz + 1);
+    float best_ms = -1.0f;
+    // the mean time of 8 launches with the current table (none: equal counts)
+    auto time_it = [&](float &ms) {
+        launch_project_bands(g, x, band, 1, st);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 8; ++r) launch_project_bands(g, x, band, 1, st);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 8.0f;
+    };
+    if (e == cudaSuccess) time_it(best_ms);
+    g->qbounds_nb = nb;
+    g->qbounds_key = q.key;
+    for (int round = 0; round < 12 && e == cudaSuccess; ++round) {
+        // block times of four launches with the current ranges
+        e = cudaMemcpy(bounds, b.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
+        g->d_qbounds = bounds;
+        g->d_qtimes = times;
+        std::fill(dur.begin(), dur.end(), 0.0);
+        for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+            launch_project_bands(g, x, band, 1, st);
+            e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = cudaMemcpy(h.data(), times, sizeof(unsigned long long) * 2 * nb,
+                                                 cudaMemcpyDeviceToHost);
+            for (int i = 0; i < nb && e == cudaSuccess; ++i) dur[i] += (double)(h[2 * i + 1] - h[2 * i]);
+        }
+        g->d_qtimes = nullptr;
+        if (e != cudaSuccess) break;
+        // scale each block's unit costs towards its measured time, then cut
+        // the units at equal shares of the modelled cost
+        for (int i = 0; i < nb; ++i) {
+            double model = 0.0;
+            for (long long u = b[i]; u < b[i + 1]; ++u) model += cost[(size_t)u];
+            if (model <= 0.0 || b[i + 1] == b[i]) continue;
+            const double f = std::pow(std::max(dur[i], 1.0) / model, 0.7);
+            for (long long u = b[i]; u < b[i + 1]; ++u) cost[(size_t)u] *= f;
+        }
+        cum[0] = 0.0;
+        for (long long u = 0; u < uz; ++u) cum[(size_t)u + 1] = cum[(size_t)u] + cost[(size_t)u];
+        b[0] = 0;
+        b[nb] = uz;
+        for (int k = 1; k < nb; ++k) {
+            const double t = cum[(size_t)uz] * k / nb;
+            const long long u = (long long)(std::lower_bound(cum.begin(), cum.end(), t) - cum.begin());
+            b[k] = std::min(uz, std::max(b[k - 1], u));
+        }
+        e = cudaMemcpy(bounds, b.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
+        float ms = -1.0f;
+        if (e == cudaSuccess) time_it(ms);
+        if (e == cudaSuccess && ms > 0.0f && ms < best_ms) {
+            best_ms = ms;
+            best = b;
+        }
+    }
+    g->d_qtimes = nullptr;
+    g->d_qbounds = nullptr;
+    if (e == cudaSuccess && !best.empty()) {
+        e = cudaMemcpy(bounds, best.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            g->d_qbounds = bounds;
+            bounds = nullptr;
+        }
+    }
+    if (bounds) cudaFree(bounds);
+    if (times) cudaFree(times);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("ct_geometry_autotune: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
+    }
+    return CT_OK;
+}
 
 void launch_backproject_orbit(const Geometry *g, const float *y, float *out, int mode, const float *xin,
                               const double *scal, int batch, float *partial, cudaStream_t st, bool cluster)
