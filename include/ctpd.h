@@ -135,7 +135,10 @@ void ct_geometry_destroy(ct_geometry *geom);
  *
  * ct_geometry_autotune times every candidate of each shape on synthetic data
  * of the geometry's size (batch images for A and A^T) on `stream`, with
- * CUDA events, and stores the fastest.  It allocates and frees device
+ * CUDA events, and stores the fastest; when it picks proj_form 2 it also
+ * balances that form's unit ranges for single-image launches from measured
+ * block times (a table the geometry keeps for that launch shape; it moves
+ * work between blocks and leaves every result bit unchanged).  It allocates and frees device
  * memory and synchronises the stream: call it before capturing a graph and
  * not while other calls use the geometry.  On error the previous shapes
  * are kept.  Errors: CT_ERR_ARG (NULL geometry, batch outside [1, 64]),
