@@ -9,7 +9,7 @@
 //     with its steps per pass of a ray walk (2, or 4 with pg <= 12) and its
 //     form (one band pair per block, or the work-balanced k_project_qbal
 //     with 8, 12 or 16 items' threads per block);
-//   - the backprojector's base-view slices (grid.z), 1, 2, 4 or 8, for its
+//   - the backprojector's base-view slices (grid.z), 1 .. 8, for its
 //     cluster form (k_backproject_orbit_cl: the slices' blocks add their
 //     sums through distributed shared memory) and for its slice-image form
 //     (one partial image per slice and k_orbit_reduce, taken by solves run
@@ -193,7 +193,7 @@ extern "C" ct_status ct_geometry_autotune(ct_geometry *g, int batch, void *strea
         int &slot = cl ? g->tune_orb : g->tune_orb_si;
         float best = -1.0f;
         int best_sl = 0;
-        for (int nsl = 1; nsl <= 8 && result == CT_OK; nsl *= 2) {
+        for (int nsl = 1; nsl <= 8 && result == CT_OK; ++nsl) {
             if (!orbit_slices_ok(g, nsl)) continue;
             slot = nsl;
             t = time_launches([&] { launch_backproject_orbit(g, sino, img, 0, nullptr, scal, batch, orb, st, cl); },
