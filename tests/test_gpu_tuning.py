@@ -104,7 +104,7 @@ def test_autotune_picks_valid_shapes_and_keeps_parity():
     t = g.autotune(batch=2)
     assert 4 <= t["items_per_block"] <= (12 if t["proj_rows"] == 4 else 16)
     assert t["proj_rows"] in (2, 4)
-    assert t["orbit_slices"] in (1, 2, 4, 8)
+    assert 1 <= t["orbit_slices"] <= 8
     assert t["tv_rows"] in (4, 8, 16, 32, 64)
     assert t["proj_form"] in (1, 2)
     x = f32(synth.ellipse_phantom(N, 8, 5))
