@@ -177,3 +177,28 @@ def test_single_orbit_slice_writes_the_result():
     # so no reduction pass runs either
     assert P.ct_kernel_launches() - n1 == n1 - n0
     assert rel_l2(to_np(x2), st.x) <= 1e-3
+
+
+def test_measured_balance_ranges_give_the_same_projection():
+    # at 512^2 / 720 views the tuner picks the work-balanced projector and
+    # balances its unit ranges from measured block times; every unit must
+    # still be formed exactly once, so the projection with the tuned table
+    # equals, bit for bit, the one with equal unit counts (another shape,
+    # for which the table does not apply) and matches the oracle
+    P = need_gpu()
+    import torch
+    N, V, B = 512, 720, 736
+    g = P.Geometry(N, V, B)
+    t = g.autotune()
+    if t["proj_form"] != 2:
+        pytest.skip("the tuner picked the band-pair form on this device")
+    x = f32(synth.ellipse_phantom(N, 20, 7) * (2.0 / N))
+    xg = to_gpu(x)
+    tuned = P.ct_project_bands(g, xg).clone()
+    g.set_tuning(items_per_block=8, proj_rows=2, proj_form=2, orbit_slices=t["orbit_slices"], tv_rows=t["tv_rows"])
+    equal = P.ct_project_bands(g, xg)
+    assert torch.equal(tuned, equal)
+    g.set_tuning(items_per_block=t["items_per_block"], proj_rows=t["proj_rows"], proj_form=2,
+                 orbit_slices=t["orbit_slices"], tv_rows=t["tv_rows"])
+    again = P.ct_project(g, xg)
+    assert rel_l2(to_np(again), O.project(x, V, B)) <= TOL
