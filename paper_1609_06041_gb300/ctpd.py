@@ -187,7 +187,9 @@ class Geometry:
             self._h = ctypes.c_void_p()
 
     def autotune(self, batch: int = 1) -> dict:
-        """ct_geometry_autotune on the current stream; returns the chosen shapes."""
+        """ct_geometry_autotune on the current stream; returns the chosen shapes.  With the
+        work-balanced projector form it also balances that form's unit ranges for one image from
+        measured block times (a table the geometry keeps; results are unchanged)."""
         _check(_lib.ct_geometry_autotune(self.handle, int(batch), _stream()))
         return self.tuning
 
