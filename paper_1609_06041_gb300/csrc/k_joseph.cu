@@ -334,9 +334,9 @@ k_project_qbal(const float *__restrict__ x, const ViewP *__restrict__ views, con
     extern __shared__ __align__(16) unsigned char smraw[];
     const long long nb = gridDim.x;
     long long u0, u1;
-    if (bounds) {
-        u0 = bounds[blockIdx.x];
-        u1 = bounds[blockIdx.x + 1];
+    if (bounds) {   // clamped: a table is never read outside [0, total)
+        u0 = min(max(bounds[blockIdx.x], 0LL), total);
+        u1 = min(max(bounds[blockIdx.x + 1], u0), total);
     } else {
         u0 = total * blockIdx.x / nb;
         u1 = total * (blockIdx.x + 1) / nb;
@@ -437,9 +437,10 @@ void launch_project_bands(const Geometry *g, const float *x, float *partial, int
             const QbalShape q = qbal_shape(g, batch);
             auto kern = q.rows4 ? k_project_qbal<4, true> : k_project_qbal<2, true>;
             // the tuner's measured-balance ranges, for the launch they were made for
-            const long long *bounds = batch == 1 && g->d_qbounds && g->qbounds_nb == q.blocks && g->qbounds_key == q.key
-                                          ? g->d_qbounds
-                                          : nullptr;
+            const long long *bounds =
+                batch == 1 && g->d_qbounds && g->qbounds_nb > 0 && g->qbounds_nb == q.blocks && g->qbounds_key == q.key
+                    ? g->d_qbounds
+                    : nullptr;
             launch_kernel(kern, dim3(q.blocks), dim3(q.threads), q.smem, st, x, g->d_views, g->d_row_items,
                           g->d_col_items, N, g->n_views, g->n_bins, q.U, q.total, bounds, g->d_qtimes, partial);
             return;
@@ -731,22 +732,28 @@ bool quad_ok(const Geometry *g) { return g->vpair && g->n % (2 * MR) == 0 && g->
 // model resolves finer than one block.  The ranges of the round whose
 // launch time (CUDA events) is least are kept, if they beat equal counts.
 // A range only decides which block forms which units' sums, so results do
-// not change.
+// not change.  The geometry's table (QB_CAP entries) is allocated once and
+// kept until the geometry is destroyed, so that a graph captured before a
+// later tuning never reads freed memory (and the kernel clamps what it
+// reads); the rounds run on a scratch table.
+constexpr int QB_CAP = 4096;
 ct_status qbal_balance(Geometry *g, const float *x, float *band, cudaStream_t st)
 {
-    if (g->d_qbounds) {
-        cudaFree(g->d_qbounds);
-        g->d_qbounds = nullptr;
-    }
+    g->qbounds_nb = 0;   // no table until a better one is written
     if (!quad_ok(g) || g->tune_qbal != 2) return CT_OK;
     const QbalShape q = qbal_shape(g, 1);
     const int nb = q.blocks;
-    if (nb < 2) return CT_OK;
+    if (nb < 2 || nb + 1 > QB_CAP) return CT_OK;
     const long long uz = q.U.u_z;
     unsigned long long *times = nullptr;
-    long long *bounds = nullptr;
+    long long *bounds = nullptr, *keep = g->d_qbounds;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&times, sizeof(unsigned long long) * 2 * nb);
+    cudaError_t e = cudaSuccess;
+    if (!keep) {
+        e = cudaMalloc(&keep, sizeof(long long) * QB_CAP);
+        if (e == cudaSuccess) g->d_qbounds = keep;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&times, sizeof(unsigned long long) * 2 * nb);
     if (e == cudaSuccess) e = cudaMalloc(&bounds, sizeof(long long) * (nb + 1));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -766,12 +773,12 @@ ct_status qbal_balance(Geometry *g, const float *x, float *band, cudaStream_t st
         ms /= 8.0f;
     };
     if (e == cudaSuccess) time_it(best_ms);
-    g->qbounds_nb = nb;
     g->qbounds_key = q.key;
     for (int round = 0; round < 12 && e == cudaSuccess; ++round) {
         // block times of four launches with the current ranges
         e = cudaMemcpy(bounds, b.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
-        g->d_qbounds = bounds;
+        g->d_qbounds = bounds;   // the scratch table for the rounds' launches
+        g->qbounds_nb = nb;
         g->d_qtimes = times;
         std::fill(dur.begin(), dur.end(), 0.0);
         for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
@@ -810,13 +817,11 @@ ct_status qbal_balance(Geometry *g, const float *x, float *band, cudaStream_t st
         }
     }
     g->d_qtimes = nullptr;
-    g->d_qbounds = nullptr;
-    if (e == cudaSuccess && !best.empty()) {
-        e = cudaMemcpy(bounds, best.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) {
-            g->d_qbounds = bounds;
-            bounds = nullptr;
-        }
+    g->d_qbounds = keep;
+    g->qbounds_nb = 0;
+    if (e == cudaSuccess && !best.empty() && keep) {
+        e = cudaMemcpy(keep, best.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) g->qbounds_nb = nb;
     }
     if (bounds) cudaFree(bounds);
     if (times) cudaFree(times);
